@@ -1,0 +1,165 @@
+/*
+ * lls.h -- C ABI of the B300 (sm_103a) randUTV least-squares library.
+ *
+ * The library computes the least-squares solution of A x = b that
+ * (1) minimizes ||A x - b||_2 and (2) among the minimizers has the smallest
+ * ||x||_2 (Chillaron, Quintana-Orti, Vidal, Martinsson, arXiv 2408.05238,
+ * Sec. 2, conditions (1)-(2)).  It factors A V = U T with randUTV (Fig. 2),
+ * decides the numerical rank r against a tolerance (Compute_rank, Fig. 4),
+ * annihilates T(0:r, r:n) (Nullify, Fig. 3) and returns
+ * x = V T(0:r,0:r)^{-1} U(:,0:r)^T b (Fig. 4; Eq. (4) when r = n).
+ *
+ * Conventions shared by every call:
+ *  - Matrices are column-major FP64.  A is m x n with leading dimension
+ *    lda >= max(1, m); B is m x nrhs (ldb >= max(1, m)); X is n x nrhs
+ *    (ldx >= max(1, n)).  Sizes are int64.
+ *  - Pointers passed to lls_solve / lls_factor / lls_solve_factored /
+ *    lls_solve_batched / lls_submit are DEVICE pointers on the handle's
+ *    device; lls_solve_host takes HOST pointers.  The caller owns every
+ *    buffer it passes and must keep it alive until the call returns (or, for
+ *    lls_submit, until lls_poll reports completion).  The library never
+ *    frees or retains caller memory; A and B are only read.
+ *  - The handle owns its stream (or borrows the one given to lls_create),
+ *    its workspace and every resident factorization.  A handle is not
+ *    thread-safe: one host thread at a time.
+ *  - Return value: LLS_OK (0), a positive warning (the result is valid) or
+ *    a negative error.  After LLS_ERR_ARG, lls_last_error() reports the
+ *    1-based index of the offending argument (LAPACK's info = -i).
+ *  - m = 0, n = 0 or nrhs = 0 are valid and do nothing (rank 0, X = 0).
+ *  - Non-finite entries in A or B give LLS_ERR_NONFINITE (no result).
+ */
+#ifndef LLS_H
+#define LLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+  LLS_OK = 0,
+  LLS_PENDING = 1,              /* lls_poll: request not finished yet */
+  LLS_WARN_RANK_NONPREFIX = 2,  /* some |T_jj| > tol after the first |T_jj| <= tol */
+  LLS_ERR_ARG = -1,             /* invalid argument (see lls_last_error) */
+  LLS_ERR_NOMEM = -2,           /* device or host allocation failed */
+  LLS_ERR_CUDA = -3,            /* a CUDA runtime call failed */
+  LLS_ERR_NONFINITE = -4,       /* NaN or Inf in A or B */
+  LLS_ERR_SVD_NOCONV = -5,      /* block SVD hit its sweep limit */
+  LLS_ERR_TIMEOUT = -6,         /* a device-side wait hit its iteration limit */
+  LLS_ERR_NOT_FOUND = -7,       /* unknown factor id or ticket */
+  LLS_ERR_CAPACITY = -8         /* request larger than the serving memory cap */
+};
+
+/* ---- precision modes --------------------------------------------------- */
+enum {
+  LLS_FP64 = 0,        /* every step in FP64 */
+  LLS_MIXED_BF16 = 1   /* sampling products (step a2) in BF16 on tcgen05 tensor
+                          cores with FP32 accumulation; everything that forms
+                          T, U, V and x stays FP64 */
+};
+
+typedef struct lls_handle_s* lls_handle;
+
+/* Options (lls_default_options fills the defaults in brackets). */
+typedef struct {
+  int32_t nb;          /* block size n_b of Fig. 2, 1..128 [64] */
+  int32_t q;           /* power iterations of Y = (A^T A)^q A^T G, 0..4 [1] */
+  int32_t precision;   /* LLS_FP64 | LLS_MIXED_BF16 [LLS_FP64] */
+  int32_t nullify;     /* 1: run Nullify (minimum-norm x, Fig. 3) [1];
+                          0: fast option (Remark after Fig. 4, Eq. (7)) */
+  uint64_t seed;       /* key of the Gaussian sketch generator [2001] */
+  int32_t reserved[4]; /* must be zero */
+} lls_options;
+
+/* One problem of lls_solve_batched / one request of lls_submit (device
+ * pointers).  rank_out, if not NULL, is a HOST pointer written when the
+ * problem is done. */
+typedef struct {
+  const double* A; int64_t m, n, lda;
+  const double* B; int64_t nrhs, ldb;
+  double tol;
+  double* X; int64_t ldx;
+  int64_t* rank_out;
+  int64_t factor_id;   /* lls_submit only: >= 0 reuses a resident factor
+                          (A ignored; m, n must match), -1 factors A; with
+                          keep_factor = 1 the new factor stays resident */
+  int32_t keep_factor;
+  int32_t status;      /* written by lls_solve_batched: per-problem status */
+} lls_problem;
+
+/* Fill *opt with the defaults.  Returns LLS_OK or LLS_ERR_ARG (opt NULL). */
+int lls_default_options(lls_options* opt);
+
+/* Create a handle on the current CUDA device.  opt NULL = defaults.
+ * cuda_stream: a cudaStream_t to borrow, or NULL for a handle-owned stream.
+ * Errors: LLS_ERR_ARG (bad option; index 2), LLS_ERR_CUDA, LLS_ERR_NOMEM. */
+int lls_create(lls_handle* h, const lls_options* opt, void* cuda_stream);
+
+/* Free the handle, its workspace and all resident factors. */
+int lls_destroy(lls_handle h);
+
+/* Change nb / q / precision / nullify / seed for later calls. */
+int lls_set_options(lls_handle h, const lls_options* opt);
+
+/* Solve min ||A X - B|| with minimum ||X|| (per column), tol absolute:
+ * diagonal entries of T with |T_jj| <= tol count as zero (tol < 0 selects
+ * max(m,n) * eps * |T_00|).  Synchronous: returns when X is written.
+ * rank (host pointer, may be NULL) receives r.  A is not modified. */
+int lls_solve(lls_handle h, const double* A, int64_t m, int64_t n, int64_t lda,
+              const double* B, int64_t nrhs, int64_t ldb, double tol,
+              double* X, int64_t ldx, int64_t* rank);
+
+/* As lls_solve with HOST pointers: A and B are copied to the device, X is
+ * copied back, all inside the call (pinned host memory is fastest). */
+int lls_solve_host(lls_handle h, const double* A, int64_t m, int64_t n, int64_t lda,
+                   const double* B, int64_t nrhs, int64_t ldb, double tol,
+                   double* X, int64_t ldx, int64_t* rank);
+
+/* Factor A and keep the factorization resident (the paper's stored U
+ * variant, Sec. 3.4).  *factor_id receives a handle-local id (>= 0). */
+int lls_factor(lls_handle h, const double* A, int64_t m, int64_t n, int64_t lda,
+               double tol, int64_t* factor_id, int64_t* rank);
+
+/* Solve with a resident factorization and new right-hand sides. */
+int lls_solve_factored(lls_handle h, int64_t factor_id, const double* B, int64_t nrhs,
+                       int64_t ldb, double* X, int64_t ldx);
+
+/* Release a resident factorization. */
+int lls_factor_release(lls_handle h, int64_t factor_id);
+
+/* Copy |diag(T)| (min(m,n) values) of a resident factor to a HOST buffer;
+ * rank_count (host, may be NULL) receives the number of entries > tol. */
+int lls_factor_diag(lls_handle h, int64_t factor_id, double* diag, int64_t len,
+                    int64_t* rank_count);
+
+/* Solve count independent problems (device pointers in each entry).
+ * Problems run concurrently on the device.  Returns the first error, and
+ * each entry's status field holds its own result. */
+int lls_solve_batched(lls_handle h, int64_t count, lls_problem* problems);
+
+/* Serving: enqueue one request (copied; buffers must stay alive until it
+ * completes).  *ticket receives its id.  LLS_ERR_CAPACITY if the request
+ * alone exceeds the handle's memory cap (lls_set_memory_cap). */
+int lls_submit(lls_handle h, const lls_problem* request, int64_t* ticket);
+
+/* Serving: advance the scheduler and report a ticket's state in *status:
+ * LLS_PENDING, or the request's final status.  A finished ticket is
+ * forgotten after it has been reported once. */
+int lls_poll(lls_handle h, int64_t ticket, int* status);
+
+/* Serving: device-memory cap in bytes for admitted work (0 = no cap). */
+int lls_set_memory_cap(lls_handle h, int64_t bytes);
+
+/* Static text for a status code. */
+const char* lls_status_string(int status);
+
+/* Details of the last error on h: 1-based argument index (0 if none) and a
+ * message copied into msg (NUL-terminated, up to len bytes). */
+int lls_last_error(lls_handle h, int* arg_index, char* msg, int64_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LLS_H */

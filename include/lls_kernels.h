@@ -1,0 +1,76 @@
+/*
+ * lls_kernels.h -- step-level entry points of the randUTV library.
+ *
+ * Each call runs one step of the method on caller-owned DEVICE buffers, on
+ * the given cudaStream_t (NULL = legacy default stream), and returns after
+ * enqueueing (no synchronization unless stated).  They exist so that every
+ * kernel of the solver can be checked on its own; lls_solve chains the same
+ * launchers.  Matrices are column-major FP64.  Return values follow lls.h:
+ * LLS_OK, LLS_ERR_ARG (bad size / leading dimension / NULL pointer, nothing
+ * launched), LLS_ERR_CUDA (launch failed) or LLS_ERR_NOMEM (scratch).
+ */
+#ifndef LLS_KERNELS_H
+#define LLS_KERNELS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Raw Philox4x64-10 blocks (Salmon et al., SC'11) used by the sketch of
+ * Fig. 2: block (g, j) has counter (g, j, step, 0) and key (seed, 0); its
+ * four words go to out[4 * (g + groups * j) + w], w = 0..3. */
+int lls_k_philox(uint64_t seed, int64_t step, int64_t groups, int64_t cols,
+                 uint64_t* out, void* stream);
+
+/* Gaussian sketch G (rows x cols, leading dimension ldg) of step `step`
+ * (Fig. 2, generate_iid_stdnorm_matrix): entry (p, j) is normal number
+ * p % 4 of the Box-Muller pairs of block (p / 4, j):
+ *   u = ((w >> 11) + 1) 2^-53, t = (w >> 11) 2^-53,
+ *   (G(4g, j), G(4g+1, j)) = sqrt(-2 ln u0) (cos 2 pi t1, sin 2 pi t1),
+ *   (G(4g+2, j), G(4g+3, j)) = sqrt(-2 ln u2) (cos 2 pi t3, sin 2 pi t3). */
+int lls_k_sketch(uint64_t seed, int64_t step, int64_t rows, int64_t cols,
+                 double* G, int64_t ldg, void* stream);
+
+/* C = alpha op(A) op(B) + beta C in FP64 (op(X) = X or X^T for trans = 0/1).
+ * op(A) is m x k, op(B) is k x n.  unit_lower_a / unit_lower_b = 1 reads
+ * the stored matrix as unit lower trapezoidal (entries above the diagonal
+ * read as 0, the diagonal as 1), the layout of Householder vectors kept
+ * below a QR's R (the "W" of Fig. 2).  beta = 0 ignores the old C. */
+int lls_k_gemm(int transa, int transb, int unit_lower_a, int unit_lower_b,
+               int64_t m, int64_t n, int64_t k, double alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, void* stream);
+
+/* Householder QR of the m x n panel A in place (unpivoted_QR of Fig. 2):
+ * on return R is in the upper trapezoid and the Householder vectors W (unit
+ * diagonal implied) below the diagonal, tau[min(m,n)] holds the scalars and
+ * T (min(m,n) x min(m,n), ldt) the upper triangular compact-WY factor with
+ * H_0 H_1 ... H_{k-1} = I - W T W^T.  LAPACK xLARFG sign convention. */
+int lls_k_geqrf(int64_t m, int64_t n, double* A, int64_t lda, double* tau,
+                double* T, int64_t ldt, void* stream);
+
+/* SVD of the b x b block R (b <= 128) by one-sided Jacobi in one CTA
+ * (Fig. 2, SVD(A_11)): R = Us diag(sigma) Vs^T, sigma descending >= 0.
+ * status (device int, may be NULL) receives 0, or LLS_ERR_SVD_NOCONV when
+ * the sweep limit was hit. */
+int lls_k_jacobi_svd(int64_t b, const double* R, int64_t ldr, double* sigma,
+                     double* Us, int64_t ldu, double* Vs, int64_t ldv,
+                     int* status, void* stream);
+
+/* B <- R^{-1} B for the upper triangular r x r matrix R (only its upper
+ * triangle is read), B r x nrhs: the T_tl^{-1} of Fig. 4. */
+int lls_k_trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
+                     double* B, int64_t ldb, void* stream);
+
+/* Compute_rank (Fig. 4) of diag(T) (len entries, T with leading dimension
+ * ldt): out[0] = length of the leading run of |T_jj| > tol, out[1] = number
+ * of |T_jj| > tol, out[2] = 1 if a diagonal entry is NaN (device int64[3]). */
+int lls_k_rank(int64_t len, const double* T, int64_t ldt, double tol,
+               int64_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LLS_KERNELS_H */

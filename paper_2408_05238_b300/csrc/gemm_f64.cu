@@ -1,0 +1,254 @@
+// FP64 GEMM for the dense contractions of randUTV (steps a2, a4, a6 and the
+// small products of the SVD, Nullify and solve steps).
+//
+// sm_103a has no FP64 tensor-core kind (tcgen05 has none, and mma.sync f64
+// measured slower than DFMA on B300), so this is a register-blocked DFMA
+// kernel: 64 x 64 output tile per CTA, 16-deep K slices staged in shared
+// memory, 4 x 4 outputs per thread, the next slice prefetched into
+// registers while the current one is consumed.  At ~2 DFMA/clk/SM the FP64
+// pipe, not memory, bounds every shape the solver issues (arithmetic
+// intensity >= 2 b / 8 flop/byte with b = nb), so the design goal is simply
+// to keep that pipe busy: enough CTAs (split-K with a deterministic
+// reduction when the output has few tiles) and no stalls on loads.
+#include <algorithm>
+
+#include "internal.h"
+#include "lls_kernels.h"
+
+namespace lls {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ double load_op(const double* X, int64_t ld, int64_t p, int64_t c,
+                                          int mode) {
+  // (p, c) index the STORED matrix.
+  if (mode == kUnitLower) {
+    if (p < c) return 0.0;
+    if (p == c) return 1.0;
+  }
+  return X[p + c * ld];
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(NT) dgemm_kernel(int64_t M, int64_t N, int64_t K, double alpha,
+                                                   const double* __restrict__ A, int64_t lda,
+                                                   int ma, const double* __restrict__ B,
+                                                   int64_t ldb, int mb, double beta,
+                                                   double* __restrict__ C, int64_t ldc,
+                                                   int64_t kchunk, double* __restrict__ partial) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int t = threadIdx.x;
+  const int tx = t % 16, ty = t / 16;
+  const int64_t i0 = (int64_t)blockIdx.x * BM;
+  const int64_t j0 = (int64_t)blockIdx.y * BN;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = min(K, kbeg + kchunk);
+
+  double ra[4], rb[4];
+  auto load_tile = [&](int64_t k0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int i, k;
+      if (!TA) {
+        i = t % 64;
+        k = t / 64 + 4 * e;
+      } else {
+        k = t % 16;
+        i = t / 16 + 16 * e;
+      }
+      int64_t gi = i0 + i, gk = k0 + k;
+      double v = 0.0;
+      if (gi < M && gk < kend) v = TA ? load_op(A, lda, gk, gi, ma) : load_op(A, lda, gi, gk, ma);
+      ra[e] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int j, k;
+      if (!TB) {
+        k = t % 16;
+        j = t / 16 + 16 * e;
+      } else {
+        j = t % 64;
+        k = t / 64 + 4 * e;
+      }
+      int64_t gj = j0 + j, gk = k0 + k;
+      double v = 0.0;
+      if (gj < N && gk < kend) v = TB ? load_op(B, ldb, gj, gk, mb) : load_op(B, ldb, gk, gj, mb);
+      rb[e] = v;
+    }
+  };
+  auto store_tile = [&]() {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (!TA) As[t / 64 + 4 * e][t % 64] = ra[e];
+      else As[t % 16][t / 16 + 16 * e] = ra[e];
+      if (!TB) Bs[t % 16][t / 16 + 16 * e] = rb[e];
+      else Bs[t / 64 + 4 * e][t % 64] = rb[e];
+    }
+  };
+
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+  if (kbeg < kend) {
+    load_tile(kbeg);
+    store_tile();
+    __syncthreads();
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+      const bool more = k0 + BK < kend;
+      if (more) load_tile(k0 + BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+      __syncthreads();
+      if (more) {
+        store_tile();
+        __syncthreads();
+      }
+    }
+  }
+
+  if (partial) {
+    double* P = partial + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int64_t gj = j0 + ty + 16 * b;
+      if (gj >= N) continue;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        int64_t gi = i0 + tx + 16 * a;
+        if (gi < M) P[gi + gj * M] = acc[a][b];
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    int64_t gj = j0 + ty + 16 * b;
+    if (gj >= N) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int64_t gi = i0 + tx + 16 * a;
+      if (gi >= M) continue;
+      double* c = C + gi + gj * ldc;
+      *c = (beta == 0.0) ? alpha * acc[a][b] : fma(alpha, acc[a][b], beta * *c);
+    }
+  }
+}
+
+__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, double alpha,
+                                     const double* __restrict__ partial, double beta,
+                                     double* __restrict__ C, int64_t ldc) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  int64_t i = idx % M, j = idx / M;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * M * N + idx];
+  double* c = C + i + j * ldc;
+  *c = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *c);
+}
+
+__global__ void scale_kernel(int64_t M, int64_t N, double beta, double* C, int64_t ldc) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  double* c = C + (idx % M) + (idx / M) * ldc;
+  *c = (beta == 0.0) ? 0.0 : beta * *c;
+}
+
+// Enough CTAs to fill 148 SMs several times over: ~3 resident per SM.
+constexpr int64_t kTargetCtas = 148 * 12;
+constexpr int64_t kMinSplitDepth = 512;
+
+int choose_splits(int64_t m, int64_t n, int64_t k) {
+  if (m <= 0 || n <= 0 || k <= 0) return 1;
+  int64_t tiles = ceil_div(m, BM) * ceil_div(n, BN);
+  if (tiles >= kTargetCtas || k < 2 * kMinSplitDepth) return 1;
+  int64_t s = ceil_div(kTargetCtas, tiles);
+  s = std::min<int64_t>(s, k / kMinSplitDepth);
+  s = std::min<int64_t>(s, 64);
+  return (int)std::max<int64_t>(s, 1);
+}
+
+}  // namespace
+
+size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k) {
+  int s = choose_splits(m, n, k);
+  return s > 1 ? (size_t)s * (size_t)m * (size_t)n * sizeof(double) : 0;
+}
+
+Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t n, int64_t k,
+            double alpha, const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+            double* C, int64_t ldc, Scratch scratch, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return ok_status();
+  if (k <= 0 || alpha == 0.0) {
+    if (beta == 1.0) return ok_status();
+    scale_kernel<<<(unsigned)ceil_div(m * n, 256), 256, 0, st>>>(m, n, beta, C, ldc);
+    LLS_LAUNCHED("scale_kernel");
+    return ok_status();
+  }
+  int splits = choose_splits(m, n, k);
+  size_t need = splits > 1 ? (size_t)splits * m * n * sizeof(double) : 0;
+  if (need > scratch.bytes) {
+    // Not enough scratch: fall back to fewer splits that fit (or none).
+    while (splits > 1 && (size_t)splits * m * n * sizeof(double) > scratch.bytes) --splits;
+  }
+  int64_t kchunk = splits > 1 ? ceil_div(ceil_div(k, splits), BK) * BK : k;
+  splits = (int)ceil_div(k, kchunk);
+  double* partial = splits > 1 ? static_cast<double*>(scratch.ptr) : nullptr;
+  dim3 grid((unsigned)ceil_div(m, BM), (unsigned)ceil_div(n, BN), (unsigned)splits);
+  if (grid.y > 65535u) return make_error(LLS_ERR_ARG, "gemm: n too large for grid");
+#define LLS_GEMM_CASE(TA_, TB_)                                                              \
+  dgemm_kernel<TA_, TB_><<<grid, NT, 0, st>>>(m, n, k, alpha, A, lda, (int)ma, B, ldb,        \
+                                              (int)mb, beta, C, ldc, kchunk, partial)
+  if (!ta && !tb) LLS_GEMM_CASE(false, false);
+  else if (!ta && tb) LLS_GEMM_CASE(false, true);
+  else if (ta && !tb) LLS_GEMM_CASE(true, false);
+  else LLS_GEMM_CASE(true, true);
+#undef LLS_GEMM_CASE
+  LLS_LAUNCHED("dgemm_kernel");
+  if (partial) {
+    splitk_reduce_kernel<<<(unsigned)ceil_div(m * n, 256), 256, 0, st>>>(m, n, splits, alpha,
+                                                                        partial, beta, C, ldc);
+    LLS_LAUNCHED("splitk_reduce_kernel");
+  }
+  return ok_status();
+}
+
+}  // namespace lls
+
+extern "C" int lls_k_gemm(int transa, int transb, int unit_lower_a, int unit_lower_b, int64_t m,
+                          int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                          const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                          void* stream) {
+  if (m < 0 || n < 0 || k < 0) return LLS_ERR_ARG;
+  int64_t arows = transa ? k : m, brows = transb ? n : k;
+  if (lda < (arows > 1 ? arows : 1) || ldb < (brows > 1 ? brows : 1) || ldc < (m > 1 ? m : 1))
+    return LLS_ERR_ARG;
+  if (m * n > 0 && (!C || (k > 0 && (!A || !B)))) return LLS_ERR_ARG;
+  lls::Scratch s;
+  size_t need = lls::gemm_scratch_bytes(m, n, k);
+  if (need) {
+    if (cudaMallocAsync(&s.ptr, need, (cudaStream_t)stream) != cudaSuccess) return LLS_ERR_NOMEM;
+    s.bytes = need;
+  }
+  lls::Status st = lls::gemm(transa != 0, transb != 0,
+                             unit_lower_a ? lls::kUnitLower : lls::kDense,
+                             unit_lower_b ? lls::kUnitLower : lls::kDense, m, n, k, alpha, A, lda,
+                             B, ldb, beta, C, ldc, s, (cudaStream_t)stream);
+  if (s.ptr) cudaFreeAsync(s.ptr, (cudaStream_t)stream);
+  return st.code;
+}

@@ -1,0 +1,97 @@
+// Launchers shared between the library's translation units.  All matrices
+// are column-major FP64; all pointers are device pointers; every launcher
+// only enqueues work on `st`.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lls {
+
+// Operand layout flag for the GEMM loader: the stored matrix is read as
+// unit lower trapezoidal (0 above the diagonal, 1 on it).
+enum OperandMode { kDense = 0, kUnitLower = 1 };
+
+// Reusable device scratch owned by the caller of a launcher.
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// sketch.cu -----------------------------------------------------------------
+Status launch_philox_raw(uint64_t seed, int64_t step, int64_t groups, int64_t cols,
+                         uint64_t* out, cudaStream_t st);
+Status launch_sketch(uint64_t seed, int64_t step, int64_t rows, int64_t cols,
+                     double* G, int64_t ldg, cudaStream_t st);
+// Same sketch written as bf16 (mixed-precision sampling).
+Status launch_sketch_bf16(uint64_t seed, int64_t step, int64_t rows, int64_t cols,
+                          void* G, int64_t ldg, cudaStream_t st);
+
+// gemm_f64.cu ----------------------------------------------------------------
+// Scratch bytes the GEMM may use for split-K partial sums (0 = no split).
+size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k);
+Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t n,
+            int64_t k, double alpha, const double* A, int64_t lda, const double* B,
+            int64_t ldb, double beta, double* C, int64_t ldc, Scratch scratch,
+            cudaStream_t st);
+
+// panel_qr.cu ----------------------------------------------------------------
+size_t panel_qr_scratch_bytes(int64_t m, int64_t n);
+// Householder QR of the m x n panel in place; tau[min(m,n)]; err (device
+// int) is raised if a grid barrier timed out.
+Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
+                int* err, cudaStream_t st);
+// T factor (k x k, ldt) of H_0 ... H_{k-1} = I - W T W^T from the Gram
+// matrix S = W^T W (k x k, lds) and tau.
+Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, double* T,
+                  int64_t ldt, cudaStream_t st);
+
+// jacobi_svd.cu --------------------------------------------------------------
+// SVD of b x b R (b <= 128).  status: device int (0 / LLS_ERR_SVD_NOCONV).
+Status jacobi_svd(int64_t b, const double* R, int64_t ldr, double* sigma, double* Us,
+                  int64_t ldu, double* Vs, int64_t ldv, int* status, cudaStream_t st);
+
+// small_kernels.cu -----------------------------------------------------------
+// Copy src (m x n) to dst and raise *flag if any entry is not finite.
+Status copy_check(int64_t m, int64_t n, const double* src, int64_t lds, double* dst,
+                  int64_t ldd, int* flag, cudaStream_t st);
+Status copy_matrix(int64_t m, int64_t n, const double* src, int64_t lds, double* dst,
+                   int64_t ldd, cudaStream_t st);
+Status fill_zero(int64_t m, int64_t n, double* dst, int64_t ldd, cudaStream_t st);
+// dst (k x k) = upper triangle of src, zeros below.
+Status copy_upper(int64_t k, const double* src, int64_t lds, double* dst, int64_t ldd,
+                  cudaStream_t st);
+// Block (k x k) at D: diagonal = sigma, strictly upper part = 0, strictly
+// lower part untouched (it holds Householder vectors).
+Status set_diag_block(int64_t k, const double* sigma, double* D, int64_t ldd, cudaStream_t st);
+// Compute_rank on diag(T).  out: device int64[3] = {prefix, count, nan}.
+Status rank_scan(int64_t len, const double* T, int64_t ldt, double tol, int64_t* out,
+                 cudaStream_t st);
+// Default tolerance max(m,n) * eps * |T_00| written to *tol_dev if tol < 0.
+Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, cudaStream_t st);
+// Rank scan with a device tolerance.
+Status rank_scan_dev(int64_t len, const double* T, int64_t ldt, const double* tol_dev,
+                     int64_t* out, cudaStream_t st);
+// Reversed-index gather / scatter used by Nullify (see nullify in solver.cu).
+Status rz_gather(int64_t bsz, int64_t L, const double* T, int64_t ldt, int64_t j0,
+                 int64_t r, double* M, int64_t ldm, cudaStream_t st);
+Status rz_scatter(int64_t bsz, const double* M, int64_t ldm, double* T, int64_t ldt,
+                  int64_t j0, int64_t r, int64_t L, cudaStream_t st);
+// Y <- Y + alpha X (m x n blocks).
+Status axpy_matrix(int64_t m, int64_t n, double alpha, const double* X, int64_t ldx, double* Y,
+                   int64_t ldy, cudaStream_t st);
+// dst(i, :) = src(rows - 1 - i, :) for a rows x cols block.
+Status copy_rows_reversed(int64_t rows, int64_t cols, const double* src, int64_t lds,
+                          double* dst, int64_t ldd, cudaStream_t st);
+// dst(:, j) = src(:, cols - 1 - j).
+Status copy_cols_reversed(int64_t rows, int64_t cols, const double* src, int64_t lds,
+                          double* dst, int64_t ldd, cudaStream_t st);
+// Back substitution for one diagonal block: B (k x nrhs) <- R^{-1} B.
+Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double* B,
+                  int64_t ldb, cudaStream_t st);
+Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
+                  int64_t ldb, Scratch scratch, cudaStream_t st);
+
+}  // namespace lls

@@ -1,0 +1,399 @@
+// Host driver: randUTV (Fig. 2), Compute_rank and Nullify (Fig. 3), and the
+// solve x = V (T_tl^{-1} (U^T b)) of Fig. 4, chained from the launchers of
+// the other translation units on the handle's stream.
+//
+// Differences from the paper's formulation (same mathematics):
+//  * U and V are never formed.  Each step keeps its reflectors (W_U below the
+//    diagonal of T, W_V in a side buffer), their compact-WY factors and the
+//    diagonal block's singular vectors; U^T b and V y are applied from them
+//    (the paper's v23t variant applies U to B on the fly, Sec. 3.4).
+//  * The right update of step i runs over all m rows of columns k..n-1
+//    (Fig. 2 prints only the A_BR block; the rows above must change too for
+//    A V = U T to hold).
+//  * The diagonal-block SVD and its two updates A_01 <- A_01 V_SVD and
+//    A_12 <- U_SVD^T A_12 are taken off the step loop.  Later steps never
+//    read those blocks (the next sample only reads A_22), and the row update
+//    commutes with the later right updates of the same rows, so all SVDs run
+//    as one batched launch after the loop, then all column updates, then all
+//    row updates.
+#include <algorithm>
+#include <cstring>
+
+#include "lls_kernels.h"
+#include "solver.h"
+
+namespace lls {
+
+Handle::~Handle() {
+  if (hstat) cudaFreeHost(hstat);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+namespace {
+
+Scratch scratch_of(DevBuf& b) { return Scratch{b.p, b.bytes}; }
+
+// Largest split-K scratch any GEMM of the step loop asks for.
+size_t loop_gemm_scratch(int64_t m, int64_t n, int nb, int64_t max_nrhs) {
+  size_t need = 0;
+  for (int64_t k = 0; k < std::min(m, n); k += nb) {
+    int64_t b = std::min<int64_t>(nb, std::min(m - k, n - k));
+    int64_t mp = m - k, np = n - k;
+    need = std::max(need, gemm_scratch_bytes(np, b, mp));      // A^T G, A^T W
+    need = std::max(need, gemm_scratch_bytes(mp, b, np));      // A Y
+    need = std::max(need, gemm_scratch_bytes(b, b, std::max(mp, np)));  // Gram
+    need = std::max(need, gemm_scratch_bytes(m, b, np));       // T W_V
+    need = std::max(need, gemm_scratch_bytes(b, np - b, mp));  // W_U^T T
+    need = std::max(need, gemm_scratch_bytes(b, max_nrhs, mp));
+    need = std::max(need, gemm_scratch_bytes(b, max_nrhs, np));
+    need = std::max(need, gemm_scratch_bytes(b, b + n, n));
+    need = std::max(need, gemm_scratch_bytes(n, b, n));
+  }
+  return need;
+}
+
+}  // namespace
+
+size_t factor_bytes(int64_t m, int64_t n, int nb) {
+  int64_t steps = ceil_div(std::min(m, n), nb);
+  size_t blk = (size_t)nb * nb * sizeof(double);
+  size_t b = (size_t)m * n * sizeof(double) + (size_t)n * n * sizeof(double);
+  b += 5 * steps * blk + 3 * steps * nb * sizeof(double);
+  // Nullify panels at worst (r ~ n/2): n/2 x (nb + n/2)
+  b += (size_t)(n / 2 + nb) * (size_t)(n / 2 + nb) * sizeof(double);
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// randUTV + rank (+ Nullify when opt.nullify)
+// ---------------------------------------------------------------------------
+Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, int64_t lda,
+                 double tol) {
+  cudaStream_t st = h.stream;
+  const int nb = h.opt.nb;
+  const int q = h.opt.q;
+  f.m = m;
+  f.n = n;
+  f.ldt = std::max<int64_t>(m, 1);
+  f.nb = nb;
+  f.q = q;
+  f.precision = h.opt.precision;
+  f.nullified = false;
+  f.ks.clear();
+  f.bs.clear();
+  f.rz.clear();
+  f.rank = f.rank_count = 0;
+  const int64_t mn = std::min(m, n);
+  for (int64_t k = 0; k < mn; k += nb) {
+    f.ks.push_back(k);
+    f.bs.push_back(std::min<int64_t>(nb, std::min(m - k, n - k)));
+  }
+  const int64_t steps = (int64_t)f.ks.size();
+  const size_t blk = (size_t)nb * nb;
+  const int64_t ldt = f.ldt, ldw = std::max<int64_t>(n, 1);
+
+  LLS_TRY(f.T.reserve(sizeof(double) * (size_t)ldt * n));
+  LLS_TRY(f.WV.reserve(sizeof(double) * (size_t)ldw * n));
+  LLS_TRY(f.TV.reserve(sizeof(double) * blk * std::max<int64_t>(steps, 1)));
+  LLS_TRY(f.TU.reserve(sizeof(double) * blk * std::max<int64_t>(steps, 1)));
+  LLS_TRY(f.US.reserve(sizeof(double) * blk * std::max<int64_t>(steps, 1)));
+  LLS_TRY(f.VS.reserve(sizeof(double) * blk * std::max<int64_t>(steps, 1)));
+  LLS_TRY(f.Rblk.reserve(sizeof(double) * blk * std::max<int64_t>(steps, 1)));
+  LLS_TRY(f.tauV.reserve(sizeof(double) * nb * std::max<int64_t>(steps, 1)));
+  LLS_TRY(f.tauU.reserve(sizeof(double) * nb * std::max<int64_t>(steps, 1)));
+  LLS_TRY(f.sigma.reserve(sizeof(double) * nb * std::max<int64_t>(steps, 1)));
+
+  // workspace
+  const int64_t mx = std::max(m, n);
+  LLS_TRY(h.G.reserve(sizeof(double) * (size_t)std::max<int64_t>(m, 1) * nb));
+  LLS_TRY(h.Wt.reserve(sizeof(double) * (size_t)std::max<int64_t>(mx, 1) * nb));
+  LLS_TRY(h.P.reserve(sizeof(double) * (size_t)std::max<int64_t>(mx, 1) * nb));
+  LLS_TRY(h.P2.reserve(sizeof(double) * (size_t)std::max<int64_t>(mx, 1) * nb));
+  LLS_TRY(h.Q.reserve(sizeof(double) * (size_t)nb * std::max<int64_t>(n, 1)));
+  LLS_TRY(h.Q2.reserve(sizeof(double) * (size_t)nb * std::max<int64_t>(n, 1)));
+  LLS_TRY(h.S.reserve(sizeof(double) * blk));
+  LLS_TRY(h.gemm_ws.reserve(loop_gemm_scratch(m, n, nb, 64)));
+  LLS_TRY(h.panel_ws.reserve(panel_qr_scratch_bytes(std::max<int64_t>(mx + nb, 1), nb) + 64));
+  LLS_TRY(h.dstat.reserve(sizeof(DevStatus)));
+  DevStatus* ds = h.dstat.as<DevStatus>();
+  LLS_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevStatus), st));
+  Scratch gws = scratch_of(h.gemm_ws), pws = scratch_of(h.panel_ws);
+
+  // T <- A, with the finiteness check.
+  LLS_TRY(copy_check(m, n, A, lda, f.T.d(), ldt, &ds->nonfinite, st));
+
+  double* T = f.T.d();
+  double* WV = f.WV.d();
+  for (int64_t i = 0; i < steps; ++i) {
+    const int64_t k = f.ks[i], b = f.bs[i];
+    const int64_t mp = m - k, np = n - k;
+    double* ABR = T + k + k * ldt;
+    double* Y = WV + k + k * ldw;
+    double* TVi = f.TV.d() + i * blk;
+    double* TUi = f.TU.d() + i * blk;
+    double* tauVi = f.tauV.d() + i * nb;
+    double* tauUi = f.tauU.d() + i * nb;
+
+    // ---- a1/a2: sketch and sample Y = (A_BR^T A_BR)^q A_BR^T G
+    if (h.opt.precision == LLS_MIXED_BF16) {
+      LLS_TRY(sample_bf16(h, ABR, ldt, mp, np, b, q, h.opt.seed, i, Y, ldw));
+    } else {
+      LLS_TRY(launch_sketch(h.opt.seed, i, mp, b, h.G.d(), std::max<int64_t>(m, 1), st));
+      LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.G.d(),
+                   std::max<int64_t>(m, 1), 0.0, Y, ldw, gws, st));
+      for (int it = 0; it < q; ++it) {
+        LLS_TRY(gemm(false, false, kDense, kDense, mp, b, np, 1.0, ABR, ldt, Y, ldw, 0.0, h.Wt.d(),
+                     std::max<int64_t>(mp, 1), gws, st));
+        LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.Wt.d(),
+                     std::max<int64_t>(mp, 1), 0.0, Y, ldw, gws, st));
+      }
+    }
+    // ---- a3: [Y, T_V, W_V] = unpivoted_QR(Y)
+    LLS_TRY(panel_qr(np, b, Y, ldw, tauVi, pws, &ds->barrier_err, st));
+    LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, b, b, np, 1.0, Y, ldw, Y, ldw, 0.0, h.S.d(),
+                 nb, gws, st));
+    LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauVi, TVi, nb, st));
+    // ---- a4: T(:, k:n) <- T(:, k:n) - (T(:, k:n) W_V) T_V W_V^T, all m rows
+    double* Tk = T + k * ldt;
+    LLS_TRY(gemm(false, false, kDense, kUnitLower, m, b, np, 1.0, Tk, ldt, Y, ldw, 0.0, h.P.d(), m,
+                 gws, st));
+    LLS_TRY(gemm(false, false, kDense, kDense, m, b, b, 1.0, h.P.d(), m, TVi, nb, 0.0, h.P2.d(), m,
+                 gws, st));
+    LLS_TRY(gemm(false, true, kDense, kUnitLower, m, np, b, -1.0, h.P2.d(), m, Y, ldw, 1.0, Tk, ldt,
+                 gws, st));
+    // ---- a5: [[A11; A21], T_U, W_U] = unpivoted_QR([A11; A21])
+    LLS_TRY(panel_qr(mp, b, ABR, ldt, tauUi, pws, &ds->barrier_err, st));
+    LLS_TRY(copy_upper(b, ABR, ldt, f.Rblk.d() + i * blk, nb, st));
+    LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, b, b, mp, 1.0, ABR, ldt, ABR, ldt, 0.0,
+                 h.S.d(), nb, gws, st));
+    LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauUi, TUi, nb, st));
+    // ---- a6: [A12; A22] <- (I - W_U T_U W_U^T)^T [A12; A22]
+    if (np > b) {
+      double* A12 = ABR + b * ldt;
+      LLS_TRY(gemm(true, false, kUnitLower, kDense, b, np - b, mp, 1.0, ABR, ldt, A12, ldt, 0.0,
+                   h.Q.d(), nb, gws, st));
+      LLS_TRY(gemm(true, false, kDense, kDense, b, np - b, b, 1.0, TUi, nb, h.Q.d(), nb, 0.0,
+                   h.Q2.d(), nb, gws, st));
+      LLS_TRY(gemm(false, false, kUnitLower, kDense, mp, np - b, b, -1.0, ABR, ldt, h.Q2.d(), nb,
+                   1.0, A12, ldt, gws, st));
+    }
+  }
+
+  // ---- a7: all diagonal-block SVDs in one launch, then their updates
+  if (steps > 0) {
+    LLS_TRY(jacobi_svd_batched((int)steps, nb, (int)f.bs.back(), f.Rblk.d(), nb, (int64_t)blk,
+                               f.sigma.d(), nb, f.US.d(), nb, (int64_t)blk, f.VS.d(), nb,
+                               (int64_t)blk, &ds->svd_status, st));
+  }
+  for (int64_t i = 0; i < steps; ++i) {
+    const int64_t k = f.ks[i], b = f.bs[i];
+    LLS_TRY(set_diag_block(b, f.sigma.d() + i * nb, T + k + k * ldt, ldt, st));
+    if (k > 0) {  // A01 <- A01 V_SVD
+      LLS_TRY(gemm(false, false, kDense, kDense, k, b, b, 1.0, T + k * ldt, ldt,
+                   f.VS.d() + i * blk, nb, 0.0, h.P.d(), k, gws, st));
+      LLS_TRY(copy_matrix(k, b, h.P.d(), k, T + k * ldt, ldt, st));
+    }
+  }
+  for (int64_t i = 0; i < steps; ++i) {
+    const int64_t k = f.ks[i], b = f.bs[i], np = n - k;
+    if (np > b) {  // A12 <- U_SVD^T A12
+      double* A12 = T + k + (k + b) * ldt;
+      LLS_TRY(gemm(true, false, kDense, kDense, b, np - b, b, 1.0, f.US.d() + i * blk, nb, A12, ldt,
+                   0.0, h.Q.d(), nb, gws, st));
+      LLS_TRY(copy_matrix(b, np - b, h.Q.d(), nb, A12, ldt, st));
+    }
+  }
+
+  // ---- a8: Compute_rank
+  if (mn > 0) {
+    LLS_TRY(resolve_tol(tol, std::max(m, n), T, &ds->tol, st));
+    LLS_TRY(rank_scan_dev(mn, T, ldt, &ds->tol, ds->rank, st));
+  }
+  if (!h.hstat) LLS_CUDA(cudaMallocHost((void**)&h.hstat, sizeof(DevStatus)));
+  LLS_CUDA(cudaMemcpyAsync(h.hstat, ds, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  LLS_CUDA(cudaStreamSynchronize(st));
+  DevStatus hs = *h.hstat;
+  if (hs.nonfinite) return make_error(LLS_ERR_NONFINITE, "A has a NaN or Inf entry", 2);
+  if (hs.barrier_err) return make_error(LLS_ERR_TIMEOUT, "panel QR grid barrier timed out");
+  if (hs.rank[2]) return make_error(LLS_ERR_NONFINITE, "NaN on the diagonal of T");
+  if (hs.svd_status) return make_error(LLS_ERR_SVD_NOCONV, "block SVD did not converge");
+  f.tol = mn > 0 ? hs.tol : tol;
+  f.rank = mn > 0 ? hs.rank[0] : 0;
+  f.rank_count = mn > 0 ? hs.rank[1] : 0;
+
+  // ---- a9: Nullify_top_right_part_of_T (Fig. 3)
+  //
+  // Row block [C11 D1] (rows j0..j1-1 of T, C11 = T(j0:j1, j0:j1), D1 =
+  // T(j0:j1, r:n)) is annihilated by one reflector per row, bottom row first,
+  // each acting on column i and columns r..n-1.  Written as a QR: with rows
+  // and columns of the block reversed and transposed,
+  //   M = [ C11 reversed^T ; D1 reversed^T ]   ((bsz + L) x bsz, L = n - r),
+  // M(p', j) = T(j1-1-j, j1-1-p') for p' < bsz, M(bsz+p, j) = T(j1-1-j, r+p);
+  // the top block of M is upper triangular, so the Householder QR M = Q R
+  // produces exactly the RZ reflectors (their top part is the identity).
+  // [C11 D1] Q = R^T gives the new C11 (reversed back) and D1 = 0; the rows
+  // above (C01 | D0 in the same coordinates) are multiplied by
+  // Q = I - W T W^T from the right, and x gets Q from the left.
+  const int64_t r = f.rank;
+  if (h.opt.nullify && r > 0 && r < n) {
+    const int64_t L = n - r;
+    int64_t j1 = r;
+    size_t off_m = 0, off_t = 0, off_tau = 0;
+    while (j1 > 0) {
+      int64_t j0 = std::max<int64_t>(0, j1 - nb);
+      Factor::RzBlock bl{j0, j1 - j0, off_m, off_t, off_tau};
+      off_m += (size_t)(bl.bsz + L) * bl.bsz;
+      off_t += (size_t)bl.bsz * bl.bsz;
+      off_tau += (size_t)bl.bsz;
+      f.rz.push_back(bl);
+      j1 = j0;
+    }
+    LLS_TRY(f.RzM.reserve(sizeof(double) * off_m));
+    LLS_TRY(f.RzT.reserve(sizeof(double) * off_t));
+    LLS_TRY(f.RzTau.reserve(sizeof(double) * off_tau));
+    LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)std::max<int64_t>(r, 1) * nb));
+    LLS_TRY(h.gemm_ws.reserve(std::max(h.gemm_ws.bytes,
+                                       std::max(gemm_scratch_bytes(nb, nb, L + nb),
+                                                gemm_scratch_bytes(r, nb, L)))));
+    gws = scratch_of(h.gemm_ws);
+    LLS_TRY(h.panel_ws.reserve(panel_qr_scratch_bytes(L + nb, nb) + 64));
+    pws = scratch_of(h.panel_ws);
+    LLS_TRY(h.P.reserve(sizeof(double) * (size_t)std::max<int64_t>(r, 1) * nb));
+    LLS_TRY(h.P2.reserve(sizeof(double) * (size_t)std::max<int64_t>(r, 1) * nb));
+    for (const auto& bl : f.rz) {
+      const int64_t j0 = bl.j0, bsz = bl.bsz, ldm = bsz + L;
+      double* M = f.RzM.d() + bl.off_m;
+      double* Tz = f.RzT.d() + bl.off_t;
+      double* tz = f.RzTau.d() + bl.off_tau;
+      LLS_TRY(rz_gather(bsz, L, T, ldt, j0, r, M, ldm, st));
+      LLS_TRY(panel_qr(ldm, bsz, M, ldm, tz, pws, &ds->barrier_err, st));
+      LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, bsz, bsz, ldm, 1.0, M, ldm, M, ldm, 0.0,
+                   h.S.d(), nb, gws, st));
+      LLS_TRY(wy_tfactor(bsz, h.S.d(), nb, tz, Tz, bsz, st));
+      LLS_TRY(rz_scatter(bsz, M, ldm, T, ldt, j0, r, L, st));
+      if (j0 > 0) {
+        // X~ = [C01 reversed | D0]; X~ <- X~ - (X~ W) T W^T with W = [I; W_bot]
+        double* Xc = h.xc.d();
+        double* D0 = T + r * ldt;
+        const double* Wbot = M + bsz;
+        LLS_TRY(copy_cols_reversed(j0, bsz, T + j0 * ldt, ldt, Xc, j0, st));
+        LLS_TRY(copy_matrix(j0, bsz, Xc, j0, h.P.d(), j0, st));
+        LLS_TRY(gemm(false, false, kDense, kDense, j0, bsz, L, 1.0, D0, ldt, Wbot, ldm, 1.0,
+                     h.P.d(), j0, gws, st));
+        LLS_TRY(gemm(false, false, kDense, kDense, j0, bsz, bsz, 1.0, h.P.d(), j0, Tz, bsz, 0.0,
+                     h.P2.d(), j0, gws, st));
+        LLS_TRY(gemm(false, true, kDense, kDense, j0, L, bsz, -1.0, h.P2.d(), j0, Wbot, ldm, 1.0,
+                     D0, ldt, gws, st));
+        // C01 (reversed) -= P2 W_top^T with W_top = I, then reversed back into T
+        LLS_TRY(axpy_matrix(j0, bsz, -1.0, h.P2.d(), j0, Xc, j0, st));
+        LLS_TRY(copy_cols_reversed(j0, bsz, Xc, j0, T + j0 * ldt, ldt, st));
+      }
+    }
+    f.nullified = true;
+    LLS_CUDA(cudaMemcpyAsync(&h.hstat->barrier_err, &ds->barrier_err, sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+    LLS_CUDA(cudaStreamSynchronize(st));
+    if (h.hstat->barrier_err) return make_error(LLS_ERR_TIMEOUT, "Nullify grid barrier timed out");
+  }
+  if (f.rank != f.rank_count) return make_error(LLS_WARN_RANK_NONPREFIX, "rank is not a prefix");
+  return ok_status();
+}
+
+// ---------------------------------------------------------------------------
+// a10: x = V (T_tl^{-1} (U^T b))
+// ---------------------------------------------------------------------------
+Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64_t ldb, double* X,
+                      int64_t ldx) {
+  cudaStream_t st = h.stream;
+  const int64_t m = f.m, n = f.n, ldt = f.ldt, ldw = std::max<int64_t>(n, 1);
+  const int nb = f.nb;
+  const size_t blk = (size_t)nb * nb;
+  const int64_t r = f.rank;
+  if (n == 0 || nrhs == 0) return ok_status();
+  if (r == 0 || m == 0) return fill_zero(n, nrhs, X, ldx, st);
+  LLS_TRY(h.bw.reserve(sizeof(double) * (size_t)m * nrhs));
+  LLS_TRY(h.z.reserve(sizeof(double) * (size_t)n * nrhs));
+  LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)nb * nrhs));
+  LLS_TRY(h.sp2.reserve(sizeof(double) * (size_t)nb * nrhs));
+  LLS_TRY(h.dstat.reserve(sizeof(DevStatus)));
+  size_t gneed = 0;
+  for (size_t i = 0; i < f.ks.size(); ++i) {
+    gneed = std::max(gneed, gemm_scratch_bytes(f.bs[i], nrhs, m - f.ks[i]));
+    gneed = std::max(gneed, gemm_scratch_bytes(f.bs[i], nrhs, n - f.ks[i]));
+  }
+  gneed = std::max(gneed, gemm_scratch_bytes(nb, nrhs, n));
+  gneed = std::max(gneed, gemm_scratch_bytes(r, nrhs, nb));
+  LLS_TRY(h.gemm_ws.reserve(gneed));
+  Scratch gws = scratch_of(h.gemm_ws);
+  DevStatus* ds = h.dstat.as<DevStatus>();
+  double* Bw = h.bw.d();
+  double* Z = h.z.d();
+  double* p = h.sp.d();
+  double* p2 = h.sp2.d();
+  const double* T = f.T.d();
+  LLS_CUDA(cudaMemsetAsync(&ds->nonfinite, 0, sizeof(int), st));
+  LLS_TRY(copy_check(m, nrhs, B, ldb, Bw, m, &ds->nonfinite, st));
+
+  // c = U^T b, one step at a time
+  for (size_t i = 0; i < f.ks.size(); ++i) {
+    const int64_t k = f.ks[i], b = f.bs[i], mp = m - k;
+    const double* WU = T + k + k * ldt;
+    LLS_TRY(gemm(true, false, kUnitLower, kDense, b, nrhs, mp, 1.0, WU, ldt, Bw + k, m, 0.0, p, nb,
+                 gws, st));
+    LLS_TRY(gemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TU.d() + i * blk, nb, p, nb, 0.0,
+                 p2, nb, gws, st));
+    LLS_TRY(gemm(false, false, kUnitLower, kDense, mp, nrhs, b, -1.0, WU, ldt, p2, nb, 1.0, Bw + k,
+                 m, gws, st));
+    LLS_TRY(gemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.US.d() + i * blk, nb, Bw + k, m,
+                 0.0, p, nb, gws, st));
+    LLS_TRY(copy_matrix(b, nrhs, p, nb, Bw + k, m, st));
+  }
+  // y = T_tl^{-1} c
+  LLS_TRY(trsm_upper(r, nrhs, T, ldt, Bw, m, gws, st));
+  // z = [y; 0]
+  LLS_TRY(copy_matrix(r, nrhs, Bw, m, Z, ldw, st));
+  if (r < n) LLS_TRY(fill_zero(n - r, nrhs, Z + r, ldw, st));
+  // Nullify reflectors, last processed block first
+  if (f.nullified) {
+    const int64_t L = n - r;
+    LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)nb * nrhs));
+    double* zc = h.xc.d();
+    for (auto it = f.rz.rbegin(); it != f.rz.rend(); ++it) {
+      const int64_t j0 = it->j0, bsz = it->bsz, ldm = bsz + L;
+      const double* M = f.RzM.d() + it->off_m;
+      const double* Tz = f.RzT.d() + it->off_t;
+      LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldw, zc, bsz, st));
+      LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
+      LLS_TRY(gemm(true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldw, 1.0, p,
+                   bsz, gws, st));
+      LLS_TRY(gemm(false, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2, bsz,
+                   gws, st));
+      LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p2, bsz, zc, bsz, st));  // W_top = I
+      LLS_TRY(gemm(false, false, kDense, kDense, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0,
+                   Z + r, ldw, gws, st));
+      LLS_TRY(copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldw, st));
+    }
+  }
+  // x = V z, last step first
+  for (size_t ii = f.ks.size(); ii-- > 0;) {
+    const int64_t k = f.ks[ii], b = f.bs[ii], np = n - k;
+    const double* WVi = f.WV.d() + k + k * ldw;
+    LLS_TRY(gemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.VS.d() + ii * blk, nb, Z + k, ldw,
+                 0.0, p, nb, gws, st));
+    LLS_TRY(copy_matrix(b, nrhs, p, nb, Z + k, ldw, st));
+    LLS_TRY(gemm(true, false, kUnitLower, kDense, b, nrhs, np, 1.0, WVi, ldw, Z + k, ldw, 0.0, p,
+                 nb, gws, st));
+    LLS_TRY(gemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.TV.d() + ii * blk, nb, p, nb, 0.0,
+                 p2, nb, gws, st));
+    LLS_TRY(gemm(false, false, kUnitLower, kDense, np, nrhs, b, -1.0, WVi, ldw, p2, nb, 1.0, Z + k,
+                 ldw, gws, st));
+  }
+  LLS_TRY(copy_matrix(n, nrhs, Z, ldw, X, ldx, st));
+  int flag = 0;
+  LLS_CUDA(cudaMemcpyAsync(&flag, &ds->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LLS_CUDA(cudaStreamSynchronize(st));
+  if (flag) return make_error(LLS_ERR_NONFINITE, "B has a NaN or Inf entry", 6);
+  return ok_status();
+}
+
+}  // namespace lls

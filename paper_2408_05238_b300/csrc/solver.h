@@ -1,0 +1,136 @@
+// Host driver of the solver: handle, resident factors and the step loop.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "lls.h"
+
+namespace lls {
+
+// Owning device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    // Work queued on any stream may still use the old buffer.
+    if (p) {
+      cudaDeviceSynchronize();
+      cudaFree(p);
+    }
+    p = nullptr;
+    bytes = 0;
+  }
+  // Grow to at least `need` bytes (contents are not kept).
+  Status reserve(size_t need) {
+    if (need <= bytes) return ok_status();
+    release();
+    if (need == 0) return ok_status();
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return make_error(LLS_ERR_NOMEM, "device allocation of " + std::to_string(need) + " bytes failed");
+    }
+    bytes = need;
+    return ok_status();
+  }
+  double* d() const { return static_cast<double*>(p); }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// Small device-side status block read back once per factorization.
+struct DevStatus {
+  int nonfinite;    // copy_check flag
+  int barrier_err;  // grid-barrier timeout in a cooperative kernel
+  int svd_status;   // LLS_ERR_SVD_NOCONV or 0
+  int pad;
+  int64_t rank[3];  // prefix, count, nan
+  double tol;
+};
+
+// A randUTV factorization A V = U T kept on the device.
+//  T       m x n (ld = m): T's upper trapezoid; below the diagonal of each
+//          step's block column the Householder vectors W_U (unit diagonal
+//          implied).
+//  WV      n x n (ld = n): step i's W_V in rows k..n-1, columns k..k+b-1.
+//  TV, TU  per step nb x nb compact-WY factors (ld nb).
+//  US, VS  per step nb x nb singular vectors of the diagonal block (ld nb).
+//  Rz*     Nullify: per row block, the (bsz + n - r) x bsz reflector panel
+//          M (Householder vectors below its diagonal) and its T factor.
+struct Factor {
+  int64_t m = 0, n = 0, ldt = 0;
+  int nb = 0, q = 0, precision = 0;
+  bool nullified = false;
+  std::vector<int64_t> ks, bs;
+  DevBuf T, WV, TV, TU, US, VS, tauV, tauU, Rblk, sigma;
+  int64_t rank = 0, rank_count = 0;
+  double tol = 0.0;
+  struct RzBlock {
+    int64_t j0, bsz;
+    size_t off_m, off_t, off_tau;
+  };
+  std::vector<RzBlock> rz;
+  DevBuf RzM, RzT, RzTau;
+  size_t bytes() const {
+    return T.bytes + WV.bytes + TV.bytes + TU.bytes + US.bytes + VS.bytes + tauV.bytes +
+           tauU.bytes + Rblk.bytes + sigma.bytes + RzM.bytes + RzT.bytes + RzTau.bytes;
+  }
+};
+
+struct Handle {
+  lls_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // workspace
+  DevBuf G, Wt, P, P2, Q, Q2, S, gemm_ws, panel_ws, bw, z, sp, sp2, xc;
+  DevBuf dstat;           // DevStatus
+  DevBuf G16, A16;        // bf16 sketch / shadow of A_BR (mixed precision)
+  DevStatus* hstat = nullptr;  // pinned host mirror
+  // lls_solve reuses one factor object between calls of the same shape
+  std::unique_ptr<Factor> scratch_factor;
+  std::map<int64_t, std::unique_ptr<Factor>> factors;
+  int64_t next_factor = 0;
+  // errors
+  int last_arg = 0;
+  std::string last_msg;
+  // serving
+  int64_t mem_cap = 0;
+  struct Ticket;
+  std::map<int64_t, std::shared_ptr<Ticket>> tickets;
+  int64_t next_ticket = 0;
+  ~Handle();
+};
+
+Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, int64_t lda,
+                 double tol);
+Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64_t ldb, double* X,
+                      int64_t ldx);
+// Device bytes a factorization of m x n (and a solve with nrhs) will hold.
+size_t factor_bytes(int64_t m, int64_t n, int nb);
+
+Status jacobi_svd_batched(int count, int b, int b_last, const double* R, int64_t ldr,
+                          int64_t strideR, double* sigma, int64_t strideS, double* U, int64_t ldu,
+                          int64_t strideU, double* V, int64_t ldv, int64_t strideV, int* status,
+                          cudaStream_t st);
+
+// Mixed precision sampling (sampling_bf16.cu): Y (n' x b, ld ldy) =
+// (A^T A)^q A^T G with A = the m' x n' block at A (ld lda), products in
+// BF16 on tensor cores with FP32 accumulation, results stored as FP64.
+Status sample_bf16(Handle& h, const double* A, int64_t lda, int64_t mp, int64_t np, int64_t b,
+                   int q, uint64_t seed, int64_t step, double* Y, int64_t ldy);
+
+}  // namespace lls

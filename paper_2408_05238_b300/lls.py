@@ -1,0 +1,343 @@
+"""ctypes binding of ``liblls.so`` (include/lls.h, include/lls_kernels.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library.
+Device matrices are torch float64 CUDA tensors in column-major layout, i.e.
+an (m, n) tensor with stride (1, ld) -- ``colmajor`` makes one.  If the
+library has not been built, importing this module raises: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblls.so")
+
+LLS_OK = 0
+LLS_PENDING = 1
+LLS_WARN_RANK_NONPREFIX = 2
+LLS_ERR_ARG = -1
+LLS_ERR_NOMEM = -2
+LLS_ERR_CUDA = -3
+LLS_ERR_NONFINITE = -4
+LLS_ERR_SVD_NOCONV = -5
+LLS_ERR_TIMEOUT = -6
+LLS_ERR_NOT_FOUND = -7
+LLS_ERR_CAPACITY = -8
+LLS_FP64 = 0
+LLS_MIXED_BF16 = 1
+
+
+class lls_options(C.Structure):
+    _fields_ = [("nb", C.c_int32), ("q", C.c_int32), ("precision", C.c_int32),
+                ("nullify", C.c_int32), ("seed", C.c_uint64), ("reserved", C.c_int32 * 4)]
+
+
+class lls_problem(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("m", C.c_int64), ("n", C.c_int64), ("lda", C.c_int64),
+                ("B", C.c_void_p), ("nrhs", C.c_int64), ("ldb", C.c_int64),
+                ("tol", C.c_double), ("X", C.c_void_p), ("ldx", C.c_int64),
+                ("rank_out", C.POINTER(C.c_int64)), ("factor_id", C.c_int64),
+                ("keep_factor", C.c_int32), ("status", C.c_int32)]
+
+
+class LLSError(RuntimeError):
+    def __init__(self, status: int, arg: int = 0, msg: str = ""):
+        self.status, self.arg, self.msg = status, arg, msg
+        super().__init__(f"lls status {status} ({status_string(status)}), arg {arg}: {msg}")
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_2408_05238_b300.build` (no CPU fallback exists)")
+_lib = C.CDLL(LIB_PATH)
+
+_H = C.c_void_p
+_P = C.c_void_p
+_I = C.c_int64
+_D = C.c_double
+
+
+def _sig(name, args, res=C.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("lls_default_options", [C.POINTER(lls_options)])
+_sig("lls_create", [C.POINTER(_H), C.POINTER(lls_options), _P])
+_sig("lls_destroy", [_H])
+_sig("lls_set_options", [_H, C.POINTER(lls_options)])
+_sig("lls_solve", [_H, _P, _I, _I, _I, _P, _I, _I, _D, _P, _I, C.POINTER(_I)])
+_sig("lls_solve_host", [_H, _P, _I, _I, _I, _P, _I, _I, _D, _P, _I, C.POINTER(_I)])
+_sig("lls_factor", [_H, _P, _I, _I, _I, _D, C.POINTER(_I), C.POINTER(_I)])
+_sig("lls_solve_factored", [_H, _I, _P, _I, _I, _P, _I])
+_sig("lls_factor_release", [_H, _I])
+_sig("lls_factor_diag", [_H, _I, _P, _I, C.POINTER(_I)])
+_sig("lls_solve_batched", [_H, _I, C.POINTER(lls_problem)])
+_sig("lls_submit", [_H, C.POINTER(lls_problem), C.POINTER(_I)])
+_sig("lls_poll", [_H, _I, C.POINTER(C.c_int)])
+_sig("lls_set_memory_cap", [_H, _I])
+_sig("lls_status_string", [C.c_int], C.c_char_p)
+_sig("lls_last_error", [_H, C.POINTER(C.c_int), C.c_char_p, _I])
+_sig("lls_k_philox", [C.c_uint64, _I, _I, _I, _P, _P])
+_sig("lls_k_sketch", [C.c_uint64, _I, _I, _I, _P, _I, _P])
+_sig("lls_k_gemm", [C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P,
+                    _I, _P])
+_sig("lls_k_geqrf", [_I, _I, _P, _I, _P, _P, _I, _P])
+_sig("lls_k_jacobi_svd", [_I, _P, _I, _P, _P, _I, _P, _I, _P, _P])
+_sig("lls_k_trsm_upper", [_I, _I, _P, _I, _P, _I, _P])
+_sig("lls_k_rank", [_I, _P, _I, _D, _P, _P])
+
+EXPORTED = [n for n in dir(_lib) if n.startswith("lls_")]
+
+
+def status_string(status: int) -> str:
+    return _lib.lls_status_string(int(status)).decode()
+
+
+# --------------------------------------------------------------------------- helpers
+def colmajor(t: torch.Tensor) -> torch.Tensor:
+    """Column-major (m, n) copy/view of a 2-D tensor (stride (1, m))."""
+    if t.dim() == 1:
+        t = t[:, None]
+    if t.stride(0) == 1 and (t.shape[1] <= 1 or t.stride(1) >= max(1, t.shape[0])):
+        return t
+    return t.t().contiguous().t()
+
+
+def empty_colmajor(m: int, n: int, device="cuda", dtype=torch.float64) -> torch.Tensor:
+    return torch.empty((n, max(m, 1)), device=device, dtype=dtype).t()[:m]
+
+
+def _ld(t: torch.Tensor) -> int:
+    return max(1, t.stride(1) if t.shape[1] > 1 else t.shape[0])
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(h, code: int):
+    if code < 0:
+        arg = C.c_int(0)
+        buf = C.create_string_buffer(512)
+        if h is not None:
+            _lib.lls_last_error(h, C.byref(arg), buf, 512)
+        raise LLSError(code, arg.value, buf.value.decode(errors="replace"))
+    return code
+
+
+# --------------------------------------------------------------------------- handle API
+def lls_default_options(**kw) -> lls_options:
+    o = lls_options()
+    _lib.lls_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def lls_create(options: lls_options | None = None, stream=None, **kw):
+    """Handle on torch's current device, borrowing ``stream`` (default: the
+    current torch stream)."""
+    o = options if options is not None else lls_default_options(**kw)
+    h = _H()
+    _check(None, _lib.lls_create(C.byref(h), C.byref(o), _stream(stream)))
+    return h
+
+
+def lls_destroy(h):
+    _check(None, _lib.lls_destroy(h))
+
+
+def lls_set_options(h, options: lls_options | None = None, **kw):
+    o = options if options is not None else lls_default_options(**kw)
+    _check(h, _lib.lls_set_options(h, C.byref(o)))
+
+
+def lls_solve(h, A: torch.Tensor, B: torch.Tensor, tol: float, X: torch.Tensor | None = None):
+    """X = argmin ||A X - B|| with minimum norm; returns (X, rank, status)."""
+    m, n = A.shape
+    Bm = B if B.dim() == 2 else B[:, None]
+    nrhs = Bm.shape[1]
+    if X is None:
+        X = empty_colmajor(n, nrhs, device=A.device)
+    rank = _I(0)
+    code = _check(h, _lib.lls_solve(h, _ptr(A), m, n, _ld(A), _ptr(Bm), nrhs, _ld(Bm), float(tol),
+                                    _ptr(X), _ld(X), C.byref(rank)))
+    return X, rank.value, code
+
+
+def lls_solve_host(h, A, B, tol: float, X=None):
+    """Host-memory variant (numpy or CPU torch, column-major float64)."""
+    import numpy as np
+
+    A = np.asfortranarray(A, dtype=np.float64)
+    B2 = np.asfortranarray(B if np.ndim(B) == 2 else np.reshape(B, (-1, 1)), dtype=np.float64)
+    m, n = A.shape
+    nrhs = B2.shape[1]
+    if X is None:
+        X = np.zeros((n, nrhs), order="F")
+    rank = _I(0)
+    code = _check(h, _lib.lls_solve_host(h, A.ctypes.data, m, n, max(1, m), B2.ctypes.data, nrhs,
+                                         max(1, m), float(tol), X.ctypes.data, max(1, n),
+                                         C.byref(rank)))
+    return X, rank.value, code
+
+
+def lls_solve_host_ptr(h, A_ptr: int, m: int, n: int, B_ptr: int, nrhs: int, tol: float,
+                       X_ptr: int):
+    """Host-pointer variant for pinned buffers (column-major, ld = rows)."""
+    rank = _I(0)
+    code = _check(h, _lib.lls_solve_host(h, C.c_void_p(A_ptr), m, n, max(1, m), C.c_void_p(B_ptr),
+                                         nrhs, max(1, m), float(tol), C.c_void_p(X_ptr), max(1, n),
+                                         C.byref(rank)))
+    return rank.value, code
+
+
+def lls_factor(h, A: torch.Tensor, tol: float):
+    m, n = A.shape
+    fid, rank = _I(0), _I(0)
+    code = _check(h, _lib.lls_factor(h, _ptr(A), m, n, _ld(A), float(tol), C.byref(fid),
+                                     C.byref(rank)))
+    return fid.value, rank.value, code
+
+
+def lls_solve_factored(h, factor_id: int, B: torch.Tensor, n: int, X=None):
+    Bm = B if B.dim() == 2 else B[:, None]
+    nrhs = Bm.shape[1]
+    if X is None:
+        X = empty_colmajor(n, nrhs, device=B.device)
+    _check(h, _lib.lls_solve_factored(h, factor_id, _ptr(Bm), nrhs, _ld(Bm), _ptr(X), _ld(X)))
+    return X
+
+
+def lls_factor_release(h, factor_id: int):
+    _check(h, _lib.lls_factor_release(h, factor_id))
+
+
+def lls_factor_diag(h, factor_id: int, length: int):
+    import numpy as np
+
+    d = np.zeros(max(length, 1))
+    cnt = _I(0)
+    _check(h, _lib.lls_factor_diag(h, factor_id, d.ctypes.data, length, C.byref(cnt)))
+    return d[:length], cnt.value
+
+
+def make_problem(A, B, tol, X, factor_id=-1, keep_factor=0, rank_out=None) -> lls_problem:
+    p = lls_problem()
+    m, n = (A.shape if A is not None else (B.shape[0], X.shape[0]))
+    Bm = B if B.dim() == 2 else B[:, None]
+    p.A = A.data_ptr() if A is not None else None
+    p.m, p.n = m, n
+    p.lda = _ld(A) if A is not None else max(1, m)
+    p.B, p.nrhs, p.ldb = Bm.data_ptr(), Bm.shape[1], _ld(Bm)
+    p.tol = float(tol)
+    p.X, p.ldx = X.data_ptr(), _ld(X)
+    p.rank_out = rank_out if rank_out is not None else C.POINTER(_I)()
+    p.factor_id, p.keep_factor, p.status = factor_id, keep_factor, 0
+    return p
+
+
+def lls_solve_batched(h, problems: list[lls_problem]) -> int:
+    arr = (lls_problem * len(problems))(*problems)
+    code = _lib.lls_solve_batched(h, len(problems), arr)
+    for i, p in enumerate(problems):
+        p.status = arr[i].status
+        p.factor_id = arr[i].factor_id
+    if code < 0:
+        _check(h, code)
+    return code
+
+
+def lls_submit(h, problem: lls_problem) -> int:
+    t = _I(0)
+    _check(h, _lib.lls_submit(h, C.byref(problem), C.byref(t)))
+    return t.value
+
+
+def lls_poll(h, ticket: int) -> int:
+    s = C.c_int(0)
+    _check(h, _lib.lls_poll(h, ticket, C.byref(s)))
+    return s.value
+
+
+def lls_set_memory_cap(h, nbytes: int):
+    _check(h, _lib.lls_set_memory_cap(h, int(nbytes)))
+
+
+# --------------------------------------------------------------------------- step-level API
+def _kcheck(code):
+    if code != LLS_OK:
+        raise LLSError(code)
+
+
+def lls_k_philox(seed: int, step: int, groups: int, cols: int) -> torch.Tensor:
+    out = torch.zeros(groups * cols * 4, dtype=torch.int64, device="cuda")
+    _kcheck(_lib.lls_k_philox(seed, step, groups, cols, _ptr(out), _stream()))
+    return out
+
+
+def lls_k_sketch(seed: int, step: int, rows: int, cols: int) -> torch.Tensor:
+    G = empty_colmajor(rows, cols)
+    _kcheck(_lib.lls_k_sketch(seed, step, rows, cols, _ptr(G), max(1, rows), _stream()))
+    return G
+
+
+def lls_k_gemm(transa, transb, A, B, C_=None, alpha=1.0, beta=0.0, unit_lower_a=False,
+               unit_lower_b=False):
+    m = A.shape[1] if transa else A.shape[0]
+    k = A.shape[0] if transa else A.shape[1]
+    n = B.shape[0] if transb else B.shape[1]
+    if C_ is None:
+        C_ = torch.zeros((n, max(m, 1)), dtype=torch.float64, device=A.device).t()[:m]
+    _kcheck(_lib.lls_k_gemm(int(transa), int(transb), int(unit_lower_a), int(unit_lower_b), m, n,
+                            k, float(alpha), _ptr(A), _ld(A), _ptr(B), _ld(B), float(beta),
+                            _ptr(C_), _ld(C_), _stream()))
+    return C_
+
+
+def lls_k_geqrf(A: torch.Tensor):
+    """In-place Householder QR; returns (A, tau, T)."""
+    m, n = A.shape
+    k = min(m, n)
+    tau = torch.zeros(max(k, 1), dtype=torch.float64, device=A.device)
+    T = empty_colmajor(max(k, 1), max(k, 1))
+    _kcheck(_lib.lls_k_geqrf(m, n, _ptr(A), _ld(A), _ptr(tau), _ptr(T), max(1, k), _stream()))
+    return A, tau[:k], T[:k, :k]
+
+
+def lls_k_jacobi_svd(R: torch.Tensor):
+    b = R.shape[0]
+    sigma = torch.zeros(max(b, 1), dtype=torch.float64, device=R.device)
+    Us = empty_colmajor(b, b)
+    Vs = empty_colmajor(b, b)
+    st = torch.zeros(1, dtype=torch.int32, device=R.device)
+    _kcheck(_lib.lls_k_jacobi_svd(b, _ptr(R), _ld(R), _ptr(sigma), _ptr(Us), max(1, b), _ptr(Vs),
+                                  max(1, b), _ptr(st), _stream()))
+    return sigma[:b], Us, Vs, int(st.item())
+
+
+def lls_k_trsm_upper(R: torch.Tensor, B: torch.Tensor):
+    r = R.shape[0]
+    _kcheck(_lib.lls_k_trsm_upper(r, B.shape[1], _ptr(R), _ld(R), _ptr(B), _ld(B), _stream()))
+    return B
+
+
+def lls_k_rank(T: torch.Tensor, tol: float):
+    out = torch.zeros(3, dtype=torch.int64, device=T.device)
+    length = min(T.shape)
+    _kcheck(_lib.lls_k_rank(length, _ptr(T), _ld(T), float(tol), _ptr(out), _stream()))
+    return tuple(int(v) for v in out.cpu())

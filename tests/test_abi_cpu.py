@@ -1,0 +1,81 @@
+"""The C-ABI library loads and exports every entry point its headers declare;
+host-side argument checks that run before any CUDA call (CPU only)."""
+
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_05238_b300 import build
+
+    build.build()
+    from paper_2408_05238_b300 import lls
+
+    return lls
+
+
+def declared_functions():
+    names = set()
+    for hdr in ("lls.h", "lls_kernels.h"):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(lls_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(lls_\w+)", out))
+    missing = names - exported
+    assert not missing, missing
+    for n in names:
+        assert getattr(lib._lib, n) is not None
+
+
+def test_status_strings(lib):
+    for code in (0, 1, 2, -1, -2, -3, -4, -5, -6, -7, -8):
+        s = lib.status_string(code)
+        assert s and s != "unknown status"
+    assert lib.status_string(12345) == "unknown status"
+
+
+def test_default_options(lib):
+    o = lib.lls_default_options()
+    assert (o.nb, o.q, o.precision, o.nullify, o.seed) == (64, 1, 0, 1, 2001)
+    assert lib._lib.lls_default_options(None) == lib.LLS_ERR_ARG
+
+
+def test_null_handle_and_bad_create(lib):
+    assert lib._lib.lls_create(None, None, None) == lib.LLS_ERR_ARG
+    assert lib._lib.lls_destroy(None) == lib.LLS_ERR_ARG
+    assert lib._lib.lls_solve(None, None, 0, 0, 1, None, 0, 1, 0.0, None, 1, None) == lib.LLS_ERR_ARG
+    h = C.c_void_p()
+    bad = lib.lls_default_options(nb=0)
+    assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
+    bad = lib.lls_default_options(q=9)
+    assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
+
+
+def test_kernel_entry_points_reject_bad_sizes(lib):
+    L = lib._lib
+    assert L.lls_k_gemm(0, 0, 0, 0, -1, 1, 1, 1.0, None, 1, None, 1, 0.0, None, 1, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_gemm(0, 0, 0, 0, 4, 4, 4, 1.0, None, 3, None, 4, 0.0, None, 4, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_sketch(1, 0, 10, 2, None, 5, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_philox(1, -1, 2, 2, None, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_geqrf(10, 3, None, 5, None, None, 3, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_jacobi_svd(129, None, 129, None, None, 129, None, 129, None, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_trsm_upper(5, 1, None, 4, None, 5, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_rank(-1, None, 1, 0.0, None, None) == lib.LLS_ERR_ARG
+    # zero-size problems are valid no-ops
+    assert L.lls_k_geqrf(0, 3, None, 1, None, None, 1, None) == lib.LLS_OK
+    assert L.lls_k_jacobi_svd(0, None, 1, None, None, 1, None, 1, None, None) == lib.LLS_OK
