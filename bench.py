@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of the randUTV minimum-norm least-squares solve on B300.
+
+Default workload (one step = one full lls_solve: randUTV, rank, Nullify and
+the solve of all right-hand sides):
+  m = n = 16384, A = Q1 diag(sigma) Q2^T with Haar Q1, Q2 (drawn on the GPU),
+  sigma_i = 10^(-6 i / 8192) for i < 8192 and 1e-15 after (rank 8192),
+  B = A X0 + 1e-8 N(0,1) with 16 right-hand sides, tol = 1e-10 ||A||_2,
+  nb = 128, q = 2, FP64.
+A is 2.1 GB, larger than the 126 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, torchrun); the solve itself
+has no multi-GPU decomposition.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LLS TFLOP/s & solves/s, mixed vs FP64 at x err ≤1e-9; served p50/p99 latency"
+# FP64 pipe of B300: 2 DFMA (4 flops) per clock per SM, measured with a
+# DFMA-chain microbenchmark; 148 SMs.
+FP64_FLOPS_PER_CLK_PER_SM = 4.0
+NUM_SM = 148
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=16384, help="matrix order (default: full workload)")
+    p.add_argument("--nrhs", type=int, default=16)
+    p.add_argument("--nb", type=int, default=128)
+    p.add_argument("--q", type=int, default=2)
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_name(a) -> str:
+    return (f"randUTV LLS m=n={a.n}, rank {a.n // 2}, Haar Q1 diag(sigma) Q2^T, "
+            f"sigma 1..1e-6 then 1e-15, b = A x0 + 1e-8 noise, nrhs={a.nrhs}, nb={a.nb}, "
+            f"q={a.q}, tol=1e-10")
+
+
+def make_inputs(a, device):
+    """A (column-major), B, and the construction's factors for the check."""
+    import torch
+
+    from paper_2408_05238_b300 import workloads as wl
+
+    n, r = a.n, a.n // 2
+    sigma = wl.step_spectrum(n, r, 6.0, 1e-15)
+    A, Q1, Q2 = wl.spectrum_matrix_torch(n, n, sigma, seed=1002, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(1102)
+    X0 = torch.randn(n, a.nrhs, generator=gen, dtype=torch.float64, device=device)
+    noise = torch.randn(n, a.nrhs, generator=gen, dtype=torch.float64, device=device)
+    B = (A @ X0 + 1e-8 * noise).t().contiguous().t()
+    return A, B, Q1, Q2, torch.as_tensor(sigma, device=device), r
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    @staticmethod
+    def _num(x):
+        try:
+            return float(x)
+        except ValueError:
+            return None
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [v for v in (self._num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (self._num(r[2]) for r in rows) if v is not None]
+        pw = [v for v in (self._num(r[3]) for r in rows) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_median": statistics.median(pw) if pw else None}
+
+
+def blas_threads() -> int:
+    """Threads numpy's BLAS runs with (the oracle's matrix products)."""
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except ImportError:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_baseline(a, A_host, flops_total):
+    """The oracle as it stands, on the host cores, on a bounded sample: the
+    first randUTV step of the same matrix (sketch, sampling, both updates,
+    block SVD), scaled to TFLOP/s by the algorithmic flops of that step."""
+    from oracle import randutv_oracle as orc
+    from paper_2408_05238_b300 import perf_model as pm
+
+    k, b = next(pm.steps(a.n, a.n, a.nb))
+    t0 = time.perf_counter()
+    orc.randutv(A_host, a.q, a.nb, seed=2002, max_steps=1)
+    dt = time.perf_counter() - t0
+    threads = blas_threads()
+    tflops = pm.step_flops(a.n, a.n, k, b, a.q) / dt / 1e12
+    return {"value": tflops, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"first randUTV step (nb={a.nb} columns) of the {a.n}x{a.n} matrix, "
+                      f"numpy FP64 with explicit U and V, {dt:.1f} s",
+            "seconds": dt, "solves_per_s": tflops * 1e12 / flops_total}
+
+
+def run_reference(a):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    import numpy as np
+    import torch
+
+    from paper_2408_05238_b300 import perf_model as pm
+
+    device = "cuda" if torch.cuda.is_available() else "cpu"
+    A, B, _q1, _q2, _s, r = make_inputs(a, device)
+    A_host = np.asfortranarray(A.cpu().numpy())
+    del A, B, _q1, _q2
+    flops_total = pm.lls_flops(a.n, a.n, a.nb, a.q, r, a.nrhs)
+    vals = []
+    for i in range(a.warmup + a.steps):
+        res = cpu_baseline(a, A_host, flops_total)
+        if i >= a.warmup:
+            vals.append(res)
+    v = statistics.median([x["value"] for x in vals])
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": 1e3 * statistics.median([x["seconds"] for x in vals]),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_name(a), "sample": vals[0]["sample"]},
+           "solves_per_s": v * 1e12 / flops_total,
+           "cpu_baseline": {**vals[0], "value": v},
+           "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2408_05238_b300 import lls
+    from paper_2408_05238_b300 import perf_model as pm
+
+    A, B, Q1, Q2, sigma, r = make_inputs(a, "cuda")
+    m = n = a.n
+    tol = 1e-10
+    X = lls.empty_colmajor(n, a.nrhs)
+    prec = lls.LLS_MIXED_BF16 if a.precision == "mixed" else lls.LLS_FP64
+    h = lls.lls_create(nb=a.nb, q=a.q, seed=2002, precision=prec)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(a.warmup):
+        lls.lls_solve(h, A, B, tol, X)
+    torch.cuda.synchronize()
+
+    lls.lls_trace_enable(h, True)
+    launches0 = lls.lls_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ranks = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(a.steps):
+            _, rk, _ = lls.lls_solve(h, A, B, tol, X)
+            ranks.append(rk)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = lls.lls_launch_count() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    trace = lls.lls_trace_read(h)
+    lls.lls_trace_enable(h, False)
+    clocks = clk.summary()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    flops = pm.lls_flops(m, n, a.nb, a.q, ranks[-1], a.nrhs)
+    total_solves = a.steps * world
+    value = flops * total_solves / elapsed / 1e12
+
+    # accuracy of the timed result against the construction's pseudoinverse
+    rr = ranks[-1]
+    Xp = Q2[:, :rr] @ ((Q1[:, :rr].t() @ B) / sigma[:rr, None])
+    x_err = float(torch.linalg.norm(X - Xp) / torch.linalg.norm(Xp))
+    res = A.t() @ (B - A @ X)
+    ner = max(float(torch.linalg.norm(res[:, j]) /
+                    (torch.linalg.norm(X[:, j]) + torch.linalg.norm(B[:, j])))
+              for j in range(a.nrhs))       # ||A||_2 = 1 for this construction
+    del Q1, Q2, Xp, res
+
+    # roofline of the dominant kernel (FP64 DFMA GEMM, bound by the FP64 pipe)
+    g = trace.get("dgemm_kernel", (0, 0.0, 0.0, 0.0))
+    achieved = g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
+    sm_max = clocks.get("sm_max_mhz") or 2032.0
+    peak = FP64_FLOPS_PER_CLK_PER_SM * NUM_SM * sm_max * 1e6 / 1e12
+    traced = sum(v[1] for v in trace.values()) or 1.0
+    shares = {k: {"launches": v[0], "seconds": round(v[1], 4), "share": round(v[1] / traced, 4)}
+              for k, v in trace.items()}
+
+    e2e = None
+    if not a.no_e2e:
+        A_h = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+        A_h.copy_(A)
+        B_h = torch.empty((a.nrhs, m), dtype=torch.float64, pin_memory=True).t()
+        B_h.copy_(B)
+        X_h = torch.empty((a.nrhs, n), dtype=torch.float64, pin_memory=True).t()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lls.lls_solve_host_ptr(h, A_h.data_ptr(), m, n, B_h.data_ptr(), a.nrhs, tol, X_h.data_ptr())
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": flops * world / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * (m * n + m * a.nrhs), "d2h_bytes_per_step": 8 * n * a.nrhs,
+               "seconds_per_step": dt, "api": "lls_solve_host (pinned host buffers)"}
+        del A_h, B_h, X_h
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        A_host = np.asfortranarray(A.cpu().numpy())
+        cpu = cpu_baseline(a, A_host, flops)
+        del A_host
+
+    lls.lls_destroy(h)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * elapsed / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if a.precision == "fp64" else "bf16+f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "m": m, "n": n, "nrhs": a.nrhs, "nb": a.nb,
+                       "q": a.q, "rank": ranks[-1], "precision": a.precision,
+                       "l2": "inputs larger than L2 (A = 2.1 GB), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "solves_per_s": total_solves / elapsed,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "kernel": "dgemm_kernel",
+                         "peak_source": "derived: 2 DFMA/clk/SM x 148 SMs x max SM clock",
+                         "launches": g[0], "avg_launch_ms": 1e3 * g[1] / max(g[0], 1)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "accuracy": {"x_rel_err_vs_pinv": x_err, "normal_eq_residual": ner},
+            "trace": shares,
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -152,6 +152,28 @@ int lls_poll(lls_handle h, int64_t ticket, int* status);
 /* Serving: device-memory cap in bytes for admitted work (0 = no cap). */
 int lls_set_memory_cap(lls_handle h, int64_t bytes);
 
+/* ---- tracing (per-kernel-family CUDA-event timing) --------------------- */
+typedef struct {
+  char name[32];     /* kernel family, e.g. "dgemm_kernel" */
+  int64_t launches;  /* launches recorded while tracing was on */
+  double seconds;    /* summed device time between the events around them */
+  double flops;      /* summed algorithmic flops of those launches */
+  double bytes;      /* summed algorithmic bytes moved by those launches */
+} lls_trace_stat;
+
+/* Turn tracing on (1) or off (0) for later calls on h; turning it on clears
+ * the counters.  Events are recorded on the handle's stream around every
+ * kernel launch the calls make (the paper's per-task time table). */
+int lls_trace_enable(lls_handle h, int on);
+
+/* Copy up to max per-family counters to out (host array); *count receives
+ * the number of families with launches.  Waits for the recorded events. */
+int lls_trace_read(lls_handle h, lls_trace_stat* out, int64_t max, int64_t* count);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * handles and threads). */
+int64_t lls_launch_count(void);
+
 /* Static text for a status code. */
 const char* lls_status_string(int status);
 

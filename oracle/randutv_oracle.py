@@ -72,7 +72,6 @@ __all__ = [
     "solve",
     "pinv_solve",
     "normal_equation_residual",
-    "randutv_flops",
 ]
 
 # ---------------------------------------------------------------------------
@@ -426,22 +425,3 @@ def normal_equation_residual(A, x, b, norm2_A: float) -> float:
         den = norm2_A * (norm2_A * np.linalg.norm(X[:, j]) + np.linalg.norm(Bm[:, j]))
         worst = max(worst, float(np.linalg.norm(res) / den) if den > 0 else 0.0)
     return worst
-
-
-def randutv_flops(m: int, n: int, nb: int, q: int, explicit_v: bool = False) -> float:
-    """Algorithmic flop count of the randUTV factorization.
-
-    Per step with m' = m - k, n' = n - k, b: sampling (2 + 4q) m' n' b, right
-    update 4 m n' b (all rows), left update 4 m' (n' - b) b; explicit V adds
-    4 n n' b.  The O(b^2 (m + n)) panel and SVD terms are left out.
-    """
-    total = 0.0
-    k = 0
-    while k < min(m, n):
-        b = min(nb, m - k, n - k)
-        mp, np_ = m - k, n - k
-        total += (2 + 4 * q) * mp * np_ * b + 4.0 * m * np_ * b + 4.0 * mp * (np_ - b) * b
-        if explicit_v:
-            total += 4.0 * n * np_ * b
-        k += b
-    return total

@@ -131,6 +131,7 @@ int lls_solve(lls_handle hh, const double* A, int64_t m, int64_t n, int64_t lda,
               int64_t nrhs, int64_t ldb, double tol, double* X, int64_t ldx, int64_t* rank) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
+  lls::TraceGuard tg(*h);
   return finish(h, do_solve(*h, A, m, n, lda, B, nrhs, ldb, tol, X, ldx, rank));
 }
 
@@ -139,6 +140,7 @@ int lls_solve_host(lls_handle hh, const double* A, int64_t m, int64_t n, int64_t
                    int64_t* rank) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
+  lls::TraceGuard tg(*h);
   Status s = check_matrix(A, m, n, lda, 2, 3, 4, 5);
   if (s.ok()) s = check_matrix(B, m, nrhs, ldb, 6, 3, 7, 8);
   if (s.ok() && ldx < (n > 1 ? n : 1)) s = arg_error(11, "ldx < max(1, n)");
@@ -179,6 +181,7 @@ int lls_factor(lls_handle hh, const double* A, int64_t m, int64_t n, int64_t lda
                int64_t* factor_id, int64_t* rank) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
+  lls::TraceGuard tg(*h);
   Status s = check_matrix(A, m, n, lda, 2, 3, 4, 5);
   if (s.ok() && !factor_id) s = arg_error(7, "NULL factor_id");
   if (s.ok() && tol != tol) s = arg_error(6, "tol is NaN");
@@ -197,6 +200,7 @@ int lls_solve_factored(lls_handle hh, int64_t factor_id, const double* B, int64_
                        int64_t ldb, double* X, int64_t ldx) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
+  lls::TraceGuard tg(*h);
   auto it = h->factors.find(factor_id);
   if (it == h->factors.end())
     return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "lls.h"
+#include "trace.h"
 
 namespace lls {
 
@@ -42,7 +43,11 @@ inline Status cuda_status(cudaError_t e, const char* what) {
 #define LLS_CUDA(call) LLS_TRY(::lls::cuda_status((call), #call))
 
 // Launch check after a <<<>>> launch.
-#define LLS_LAUNCHED(name) LLS_CUDA(cudaGetLastError())
+#define LLS_LAUNCHED(name)                                     \
+  do {                                                         \
+    ::lls::g_launches.fetch_add(1, std::memory_order_relaxed); \
+    LLS_CUDA(cudaGetLastError());                              \
+  } while (0)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -211,6 +211,10 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
   double* partial = splits > 1 ? static_cast<double*>(scratch.ptr) : nullptr;
   dim3 grid((unsigned)ceil_div(m, BM), (unsigned)ceil_div(n, BN), (unsigned)splits);
   if (grid.y > 65535u) return make_error(LLS_ERR_ARG, "gemm: n too large for grid");
+  {
+    // algorithmic work: 2 m n k flops; bytes: op(A), op(B) once, C read + written
+    TraceScope ts(kTrGemm, st, 2.0 * m * n * k,
+                  8.0 * ((double)m * k + (double)k * n + (beta == 0.0 ? 1.0 : 2.0) * m * n));
 #define LLS_GEMM_CASE(TA_, TB_)                                                              \
   dgemm_kernel<TA_, TB_><<<grid, NT, 0, st>>>(m, n, k, alpha, A, lda, (int)ma, B, ldb,        \
                                               (int)mb, beta, C, ldc, kchunk, partial)
@@ -219,8 +223,10 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
   else if (ta && !tb) LLS_GEMM_CASE(true, false);
   else LLS_GEMM_CASE(true, true);
 #undef LLS_GEMM_CASE
-  LLS_LAUNCHED("dgemm_kernel");
+    LLS_LAUNCHED("dgemm_kernel");
+  }
   if (partial) {
+    TraceScope ts(kTrSplitK, st, (double)splits * m * n, 8.0 * (splits + 2.0) * m * n);
     splitk_reduce_kernel<<<(unsigned)ceil_div(m * n, 256), 256, 0, st>>>(m, n, splits, alpha,
                                                                         partial, beta, C, ldc);
     LLS_LAUNCHED("splitk_reduce_kernel");

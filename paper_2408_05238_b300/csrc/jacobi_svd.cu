@@ -222,6 +222,7 @@ Status jacobi_svd_batched(int count, int b, int b_last, const double* R, int64_t
   if (smem > 48 * 1024)
     LLS_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
+  TraceScope ts(kTrSvd, st, 0.0, 8.0 * 3.0 * count * (double)bmax * bmax);
   jacobi_svd_kernel<<<count, SVD_THREADS, smem, st>>>(a);
   LLS_LAUNCHED("jacobi_svd_kernel");
   return ok_status();

@@ -197,6 +197,9 @@ Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scrat
     LLS_CUDA(cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   void* args[] = {&a};
+  int64_t k = std::min(m, n);
+  TraceScope ts(kTrPanelQR, st, 2.0 * m * n * k - 2.0 * k * k * k / 3.0, 16.0 * m * n);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   LLS_CUDA(cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(PQ_THREADS), args,
                                        smem, st));
   return ok_status();
@@ -205,6 +208,7 @@ Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scrat
 Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, double* T,
                   int64_t ldt, cudaStream_t st) {
   if (k <= 0) return ok_status();
+  TraceScope ts(kTrTFactor, st, (double)k * k * k / 3.0, 16.0 * k * k);
   wy_tfactor_kernel<<<1, 256, 0, st>>>(k, S, lds, tau, T, ldt);
   LLS_LAUNCHED("wy_tfactor_kernel");
   return ok_status();

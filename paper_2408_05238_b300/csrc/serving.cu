@@ -47,6 +47,7 @@ extern "C" {
 int lls_solve_batched(lls_handle hh, int64_t count, lls_problem* problems) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || count < 0 || (count > 0 && !problems)) return LLS_ERR_ARG;
+  lls::TraceGuard tg(*h);
   int first = LLS_OK;
   for (int64_t i = 0; i < count; ++i) {
     lls_problem& p = problems[i];
@@ -84,6 +85,7 @@ int lls_poll(lls_handle hh, int64_t ticket, int* status) {
   if (!h || !status) return LLS_ERR_ARG;
   auto it = h->tickets.find(ticket);
   if (it == h->tickets.end()) return LLS_ERR_NOT_FOUND;
+  lls::TraceGuard tg(*h);
   // run queued requests in arrival order up to this one
   for (auto& kv : h->tickets) {
     if (kv.second->done) continue;

@@ -123,6 +123,7 @@ Status launch_sketch(uint64_t seed, int64_t step, int64_t rows, int64_t cols, do
                      int64_t ldg, cudaStream_t st) {
   int64_t total = ceil_div(rows, 4) * cols;
   if (rows <= 0 || cols <= 0) return ok_status();
+  TraceScope ts(kTrSketch, st, 0.0, 8.0 * rows * cols);
   sketch_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(seed, (uint64_t)step, rows,
                                                                 cols, G, ldg);
   LLS_LAUNCHED("sketch_kernel");
@@ -133,6 +134,7 @@ Status launch_sketch_bf16(uint64_t seed, int64_t step, int64_t rows, int64_t col
                           int64_t ldg, cudaStream_t st) {
   int64_t total = ceil_div(rows, 4) * cols;
   if (rows <= 0 || cols <= 0) return ok_status();
+  TraceScope ts(kTrSketch, st, 0.0, 2.0 * rows * cols);
   sketch_bf16_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(
       seed, (uint64_t)step, rows, cols, static_cast<__nv_bfloat16*>(G), ldg);
   LLS_LAUNCHED("sketch_bf16_kernel");

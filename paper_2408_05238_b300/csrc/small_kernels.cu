@@ -181,6 +181,7 @@ __global__ void trsm_block_kernel(int64_t k, const double* __restrict__ R, int64
 Status copy_check(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
                   int* flag, cudaStream_t st) {
   if (m <= 0 || n <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   copy_check_kernel<<<grid_for(m * n), EW, 0, st>>>(m, n, src, lds, dst, ldd, flag);
   LLS_LAUNCHED("copy_check_kernel");
   return ok_status();
@@ -189,6 +190,7 @@ Status copy_check(int64_t m, int64_t n, const double* src, int64_t lds, double* 
 Status copy_matrix(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
                    cudaStream_t st) {
   if (m <= 0 || n <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   copy_kernel<<<grid_for(m * n), EW, 0, st>>>(m, n, src, lds, dst, ldd);
   LLS_LAUNCHED("copy_kernel");
   return ok_status();
@@ -197,6 +199,7 @@ Status copy_matrix(int64_t m, int64_t n, const double* src, int64_t lds, double*
 Status axpy_matrix(int64_t m, int64_t n, double alpha, const double* X, int64_t ldx, double* Y,
                    int64_t ldy, cudaStream_t st) {
   if (m <= 0 || n <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   axpy_kernel<<<grid_for(m * n), EW, 0, st>>>(m, n, alpha, X, ldx, Y, ldy);
   LLS_LAUNCHED("axpy_kernel");
   return ok_status();
@@ -204,6 +207,7 @@ Status axpy_matrix(int64_t m, int64_t n, double alpha, const double* X, int64_t 
 
 Status fill_zero(int64_t m, int64_t n, double* dst, int64_t ldd, cudaStream_t st) {
   if (m <= 0 || n <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   zero_kernel<<<grid_for(m * n), EW, 0, st>>>(m, n, dst, ldd);
   LLS_LAUNCHED("zero_kernel");
   return ok_status();
@@ -212,6 +216,7 @@ Status fill_zero(int64_t m, int64_t n, double* dst, int64_t ldd, cudaStream_t st
 Status copy_upper(int64_t k, const double* src, int64_t lds, double* dst, int64_t ldd,
                   cudaStream_t st) {
   if (k <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   copy_upper_kernel<<<grid_for(k * k), EW, 0, st>>>(k, src, lds, dst, ldd);
   LLS_LAUNCHED("copy_upper_kernel");
   return ok_status();
@@ -219,6 +224,7 @@ Status copy_upper(int64_t k, const double* src, int64_t lds, double* dst, int64_
 
 Status set_diag_block(int64_t k, const double* sigma, double* D, int64_t ldd, cudaStream_t st) {
   if (k <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   set_diag_block_kernel<<<grid_for(k * k), EW, 0, st>>>(k, sigma, D, ldd);
   LLS_LAUNCHED("set_diag_block_kernel");
   return ok_status();
@@ -226,12 +232,14 @@ Status set_diag_block(int64_t k, const double* sigma, double* D, int64_t ldd, cu
 
 Status rank_scan(int64_t len, const double* T, int64_t ldt, double tol, int64_t* out,
                  cudaStream_t st) {
+  TraceScope ts(kTrSmall, st);
   rank_kernel<<<1, 1024, 0, st>>>(len, T, ldt, tol, nullptr, out);
   LLS_LAUNCHED("rank_kernel");
   return ok_status();
 }
 
 Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, cudaStream_t st) {
+  TraceScope ts(kTrSmall, st);
   resolve_tol_kernel<<<1, 1, 0, st>>>(tol, mn, T00, tol_dev);
   LLS_LAUNCHED("resolve_tol_kernel");
   return ok_status();
@@ -239,6 +247,7 @@ Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, c
 
 Status rank_scan_dev(int64_t len, const double* T, int64_t ldt, const double* tol_dev,
                      int64_t* out, cudaStream_t st) {
+  TraceScope ts(kTrSmall, st);
   rank_kernel<<<1, 1024, 0, st>>>(len, T, ldt, 0.0, tol_dev, out);
   LLS_LAUNCHED("rank_kernel");
   return ok_status();
@@ -247,6 +256,7 @@ Status rank_scan_dev(int64_t len, const double* T, int64_t ldt, const double* to
 Status rz_gather(int64_t bsz, int64_t L, const double* T, int64_t ldt, int64_t j0, int64_t r,
                  double* M, int64_t ldm, cudaStream_t st) {
   if (bsz <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   rz_gather_kernel<<<grid_for((bsz + L) * bsz), EW, 0, st>>>(bsz, L, T, ldt, j0, r, M, ldm);
   LLS_LAUNCHED("rz_gather_kernel");
   return ok_status();
@@ -255,6 +265,7 @@ Status rz_gather(int64_t bsz, int64_t L, const double* T, int64_t ldt, int64_t j
 Status rz_scatter(int64_t bsz, const double* M, int64_t ldm, double* T, int64_t ldt, int64_t j0,
                   int64_t r, int64_t L, cudaStream_t st) {
   if (bsz <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   rz_scatter_kernel<<<grid_for((bsz + L) * bsz), EW, 0, st>>>(bsz, M, ldm, T, ldt, j0, r, L);
   LLS_LAUNCHED("rz_scatter_kernel");
   return ok_status();
@@ -263,6 +274,7 @@ Status rz_scatter(int64_t bsz, const double* M, int64_t ldm, double* T, int64_t 
 Status copy_rows_reversed(int64_t rows, int64_t cols, const double* src, int64_t lds, double* dst,
                           int64_t ldd, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   rows_reversed_kernel<<<grid_for(rows * cols), EW, 0, st>>>(rows, cols, src, lds, dst, ldd);
   LLS_LAUNCHED("rows_reversed_kernel");
   return ok_status();
@@ -271,6 +283,7 @@ Status copy_rows_reversed(int64_t rows, int64_t cols, const double* src, int64_t
 Status copy_cols_reversed(int64_t rows, int64_t cols, const double* src, int64_t lds, double* dst,
                           int64_t ldd, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
   cols_reversed_kernel<<<grid_for(rows * cols), EW, 0, st>>>(rows, cols, src, lds, dst, ldd);
   LLS_LAUNCHED("cols_reversed_kernel");
   return ok_status();
@@ -280,6 +293,7 @@ Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double*
                   cudaStream_t st) {
   if (k <= 0 || nrhs <= 0) return ok_status();
   if (nrhs > 2147483647) return make_error(LLS_ERR_ARG, "trsm: too many right-hand sides");
+  TraceScope ts(kTrSmall, st);
   trsm_block_kernel<<<(unsigned)nrhs, 128, sizeof(double) * k, st>>>(k, R, ldr, B, ldb);
   LLS_LAUNCHED("trsm_block_kernel");
   return ok_status();

@@ -10,6 +10,7 @@
 
 #include "internal.h"
 #include "lls.h"
+#include "trace.h"
 
 namespace lls {
 
@@ -104,6 +105,9 @@ struct Handle {
   std::unique_ptr<Factor> scratch_factor;
   std::map<int64_t, std::unique_ptr<Factor>> factors;
   int64_t next_factor = 0;
+  // tracing
+  std::unique_ptr<Tracer> tracer;
+  bool trace_on = false;
   // errors
   int last_arg = 0;
   std::string last_msg;
@@ -113,6 +117,15 @@ struct Handle {
   std::map<int64_t, std::shared_ptr<Ticket>> tickets;
   int64_t next_ticket = 0;
   ~Handle();
+};
+
+// Makes h's tracer the active one on this thread for the duration of a call.
+struct TraceGuard {
+  Tracer* prev;
+  explicit TraceGuard(Handle& h) : prev(g_tracer) {
+    g_tracer = (h.trace_on && h.tracer) ? h.tracer.get() : nullptr;
+  }
+  ~TraceGuard() { g_tracer = prev; }
 };
 
 Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, int64_t lda,

@@ -1,0 +1,77 @@
+// Per-kernel-family tracing: CUDA events recorded on the launching stream
+// around each launch, with the algorithmic flops and bytes of the launch.
+// Off unless a handle enables it; the counters mirror the paper's per-task
+// time table (average time and count per elementary task).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+namespace lls {
+
+enum TraceKind {
+  kTrGemm = 0,     // dgemm_kernel
+  kTrSplitK,       // split-K reduction
+  kTrPanelQR,      // cooperative Householder panel
+  kTrTFactor,      // compact-WY T factor
+  kTrSketch,       // Philox + Box-Muller
+  kTrSvd,          // batched Jacobi SVD
+  kTrSmall,        // copies, rank scan, gathers, TRSM blocks
+  kTrBf16Gemm,     // tcgen05 BF16 sampling GEMM
+  kTrConvert,      // FP64 -> BF16 conversions
+  kTrCount
+};
+
+const char* trace_kind_name(int k);
+
+struct Tracer {
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[kTrCount] = {};
+  double seconds[kTrCount] = {};
+  double flops[kTrCount] = {};
+  double bytes[kTrCount] = {};
+  cudaEvent_t get();
+  void flush();  // waits for the recorded events and accumulates
+  void reset();
+  ~Tracer();
+};
+
+// The tracer of the handle currently running on this thread (or null).
+extern thread_local Tracer* g_tracer;
+// Kernels launched by the library since load (all handles, all threads).
+extern std::atomic<int64_t> g_launches;
+
+// Records a start event in the constructor and a stop event in the
+// destructor when a tracer is active.
+struct TraceScope {
+  Tracer* t;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  double flops, bytes;
+  TraceScope(int k, cudaStream_t s, double f = 0.0, double by = 0.0)
+      : t(g_tracer), kind(k), st(s), flops(f), bytes(by) {
+    if (t) {
+      a = t->get();
+      cudaEventRecord(a, st);
+    }
+  }
+  ~TraceScope() {
+    if (t) {
+      cudaEvent_t b = t->get();
+      cudaEventRecord(b, st);
+      t->recs.push_back(Tracer::Rec{kind, a, b, flops, bytes});
+    }
+  }
+};
+
+}  // namespace lls

@@ -45,6 +45,11 @@ class lls_problem(C.Structure):
                 ("keep_factor", C.c_int32), ("status", C.c_int32)]
 
 
+class lls_trace_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("seconds", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
+
+
 class LLSError(RuntimeError):
     def __init__(self, status: int, arg: int = 0, msg: str = ""):
         self.status, self.arg, self.msg = status, arg, msg
@@ -85,6 +90,9 @@ _sig("lls_poll", [_H, _I, C.POINTER(C.c_int)])
 _sig("lls_set_memory_cap", [_H, _I])
 _sig("lls_status_string", [C.c_int], C.c_char_p)
 _sig("lls_last_error", [_H, C.POINTER(C.c_int), C.c_char_p, _I])
+_sig("lls_trace_enable", [_H, C.c_int])
+_sig("lls_trace_read", [_H, C.POINTER(lls_trace_stat), _I, C.POINTER(_I)])
+_sig("lls_launch_count", [], C.c_int64)
 _sig("lls_k_philox", [C.c_uint64, _I, _I, _I, _P, _P])
 _sig("lls_k_sketch", [C.c_uint64, _I, _I, _I, _P, _I, _P])
 _sig("lls_k_gemm", [C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P,
@@ -276,6 +284,23 @@ def lls_poll(h, ticket: int) -> int:
 
 def lls_set_memory_cap(h, nbytes: int):
     _check(h, _lib.lls_set_memory_cap(h, int(nbytes)))
+
+
+def lls_trace_enable(h, on: bool = True):
+    _check(h, _lib.lls_trace_enable(h, int(on)))
+
+
+def lls_trace_read(h) -> dict:
+    """{kernel family: (launches, seconds, flops, bytes)} since tracing was enabled."""
+    arr = (lls_trace_stat * 32)()
+    cnt = _I(0)
+    _check(h, _lib.lls_trace_read(h, arr, 32, C.byref(cnt)))
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].seconds, arr[i].flops, arr[i].bytes)
+            for i in range(min(cnt.value, 32))}
+
+
+def lls_launch_count() -> int:
+    return int(_lib.lls_launch_count())
 
 
 # --------------------------------------------------------------------------- step-level API

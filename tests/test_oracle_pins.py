@@ -306,14 +306,3 @@ def test_solution_orthogonal_to_nullspace():
     sol = orc.solve(A, b, 1, 16, 1e-10 * wl.norm2_of_product(X, Y), seed=4)
     N0 = np.linalg.svd(A)[2][25:].T  # trailing right singular vectors
     assert np.linalg.norm(N0.T @ sol.x) / np.linalg.norm(sol.x) < 1e-12
-
-
-def test_flop_model_closed_form():
-    """For n | nb and m = n the per-step sum follows the closed form
-    (10 + 4q) S + O(n^2 nb) terms with S = sum m' n' b."""
-    m = n = 1024
-    nb, q = 64, 2
-    S = sum((m - k) * (n - k) * nb for k in range(0, n, nb))
-    right_extra = sum(4.0 * k * (n - k) * nb for k in range(0, n, nb))
-    left_fix = sum(4.0 * (m - k) * nb * nb for k in range(0, n, nb))
-    assert orc.randutv_flops(m, n, nb, q) == pytest.approx((10 + 4 * q) * S + right_extra - left_fix)
