@@ -70,6 +70,29 @@ int lls_k_trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
 int lls_k_rank(int64_t len, const double* T, int64_t ldt, double tol,
                int64_t* out, void* stream);
 
+/* The Householder panel QR of lls_k_geqrf (R, W and tau in place; no T
+ * factor) for callers that cannot allocate device memory: code whose device
+ * memory is owned by another allocator (a framework's pool, a fixed budget
+ * set at start-up), or loops that must not block, since cudaMalloc/cudaFree
+ * can synchronize the device.  The paper has no counterpart; this is a
+ * library convenience.
+ *
+ * The kernel's scratch (grid-barrier words and per-CTA partial sums) lives
+ * in one fixed array of the library (under 270 KB, held by every GPU that
+ * loads the library until the process exits), so this call allocates
+ * nothing.  n may be at most 128; larger n returns LLS_ERR_CAPACITY and
+ * launches nothing.  status is a caller-owned device int: it is set to 0 and
+ * becomes nonzero if a grid barrier of the kernel timed out (then A and tau
+ * are not valid).  The call only enqueues work on `stream`; it does not
+ * synchronize.  The first call on each device looks up the array's device
+ * address (once, with that device current), so make that first call before
+ * any stream capture.  All calls share the one array, which keeps the last
+ * call's contents (the barrier words are cleared by each call): calls that
+ * overlap on the GPU -- on different streams, or from several threads --
+ * race on it, so issue them one after another. */
+int lls_k_panel_qr_noalloc(int64_t m, int64_t n, double* A, int64_t lda, double* tau,
+                           int* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,7 @@ _sig("lls_k_geqrf", [_I, _I, _P, _I, _P, _P, _I, _P])
 _sig("lls_k_jacobi_svd", [_I, _P, _I, _P, _P, _I, _P, _I, _P, _P])
 _sig("lls_k_trsm_upper", [_I, _I, _P, _I, _P, _I, _P])
 _sig("lls_k_rank", [_I, _P, _I, _D, _P, _P])
+_sig("lls_k_panel_qr_noalloc", [_I, _I, _P, _I, _P, _P, _P])
 
 EXPORTED = [n for n in dir(_lib) if n.startswith("lls_")]
 
@@ -366,3 +367,11 @@ def lls_k_rank(T: torch.Tensor, tol: float):
     length = min(T.shape)
     _kcheck(_lib.lls_k_rank(length, _ptr(T), _ld(T), float(tol), _ptr(out), _stream()))
     return tuple(int(v) for v in out.cpu())
+
+
+def lls_k_panel_qr_noalloc(A: torch.Tensor, tau: torch.Tensor, status: torch.Tensor) -> int:
+    """Panel QR of A in place using the library's fixed scratch (no device
+    allocation inside the call); returns the status code of the call."""
+    m, n = A.shape
+    return int(_lib.lls_k_panel_qr_noalloc(m, n, _ptr(A), _ld(A), _ptr(tau), _ptr(status),
+                                           _stream()))
