@@ -70,6 +70,17 @@ int lls_k_trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
 int lls_k_rank(int64_t len, const double* T, int64_t ldt, double tol,
                int64_t* out, void* stream);
 
+/* D = X^T Z on the tcgen05 tensor cores: X is K x M and Z is K x N, both
+ * column-major BF16 (ldx, ldz multiples of 8, 16-byte aligned base), D is
+ * M x N column-major FP32 (ldd >= M), N <= 128.  BF16 products, FP32
+ * accumulation.  This is the sampling product Y = A^T G (and A^T (A Y)) of
+ * Fig. 2 in mixed precision.  status (device int) becomes nonzero if a
+ * device-side wait timed out.  Scratch for split-K partial sums is
+ * allocated and freed on the stream inside the call. */
+int lls_k_gemm_bf16_tn(int64_t M, int64_t N, int64_t K, const void* X, int64_t ldx,
+                       const void* Z, int64_t ldz, float* D, int64_t ldd, int* status,
+                       void* stream);
+
 /* The Householder panel QR of lls_k_geqrf (R, W and tau in place; no T
  * factor) for callers that cannot allocate device memory: code whose device
  * memory is owned by another allocator (a framework's pool, a fixed budget

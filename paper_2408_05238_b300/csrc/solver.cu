@@ -214,7 +214,7 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   LLS_CUDA(cudaStreamSynchronize(st));
   DevStatus hs = *h.hstat;
   if (hs.nonfinite) return make_error(LLS_ERR_NONFINITE, "A has a NaN or Inf entry", 2);
-  if (hs.barrier_err) return make_error(LLS_ERR_TIMEOUT, "panel QR grid barrier timed out");
+  if (hs.barrier_err) return make_error(LLS_ERR_TIMEOUT, "a device-side wait timed out");
   if (hs.rank[2]) return make_error(LLS_ERR_NONFINITE, "NaN on the diagonal of T");
   if (hs.svd_status) return make_error(LLS_ERR_SVD_NOCONV, "block SVD did not converge");
   f.tol = mn > 0 ? hs.tol : tol;

@@ -99,7 +99,9 @@ struct Handle {
   // workspace
   DevBuf G, Wt, P, P2, Q, Q2, S, gemm_ws, panel_ws, bw, z, sp, sp2, xc;
   DevBuf dstat;           // DevStatus
-  DevBuf G16, A16;        // bf16 sketch / shadow of A_BR (mixed precision)
+  // mixed precision sampling: bf16 copies of A_BR and A_BR^T, bf16 sketch /
+  // product, fp32 product, tensor-core split-K partials, scalars
+  DevBuf G16, A16, A16t, Z16, F32, tc_ws, mixed_misc;
   DevStatus* hstat = nullptr;  // pinned host mirror
   // lls_solve reuses one factor object between calls of the same shape
   std::unique_ptr<Factor> scratch_factor;

@@ -101,6 +101,7 @@ _sig("lls_k_geqrf", [_I, _I, _P, _I, _P, _P, _I, _P])
 _sig("lls_k_jacobi_svd", [_I, _P, _I, _P, _P, _I, _P, _I, _P, _P])
 _sig("lls_k_trsm_upper", [_I, _I, _P, _I, _P, _I, _P])
 _sig("lls_k_rank", [_I, _P, _I, _D, _P, _P])
+_sig("lls_k_gemm_bf16_tn", [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P])
 _sig("lls_k_panel_qr_noalloc", [_I, _I, _P, _I, _P, _P, _P])
 
 EXPORTED = [n for n in dir(_lib) if n.startswith("lls_")]
@@ -367,6 +368,17 @@ def lls_k_rank(T: torch.Tensor, tol: float):
     length = min(T.shape)
     _kcheck(_lib.lls_k_rank(length, _ptr(T), _ld(T), float(tol), _ptr(out), _stream()))
     return tuple(int(v) for v in out.cpu())
+
+
+def lls_k_gemm_bf16_tn(X: torch.Tensor, Z: torch.Tensor):
+    """D = X^T Z (FP32) with X (K x M) and Z (K x N) column-major bf16."""
+    K, M = X.shape
+    N = Z.shape[1]
+    D = torch.zeros((N, max(M, 1)), dtype=torch.float32, device=X.device).t()[:M]
+    status = torch.zeros(1, dtype=torch.int32, device=X.device)
+    _kcheck(_lib.lls_k_gemm_bf16_tn(M, N, K, _ptr(X), _ld(X), _ptr(Z), _ld(Z), _ptr(D), max(1, M),
+                                    _ptr(status), _stream()))
+    return D, int(status.item())
 
 
 def lls_k_panel_qr_noalloc(A: torch.Tensor, tau: torch.Tensor, status: torch.Tensor) -> int:
