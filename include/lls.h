@@ -55,9 +55,13 @@ enum {
 /* ---- precision modes --------------------------------------------------- */
 enum {
   LLS_FP64 = 0,        /* every step in FP64 */
-  LLS_MIXED_BF16 = 1   /* sampling products (step a2) in BF16 on tcgen05 tensor
-                          cores with FP32 accumulation; everything that forms
-                          T, U, V and x stays FP64 */
+  LLS_MIXED_BF16 = 1   /* sampling products (step a2) in BF16 on the tcgen05
+                          tensor cores with FP32 accumulation; the trailing
+                          WY updates and Nullify's products as FP64-accurate
+                          tensor-core GEMMs (exact BF16 digit slices, FP32
+                          accumulation, FP64 recombination, see
+                          lls_k_gemm_oz); panels, block SVDs, rank and the
+                          solve in FP64 */
 };
 
 typedef struct lls_handle_s* lls_handle;
@@ -134,23 +138,36 @@ int lls_factor_release(lls_handle h, int64_t factor_id);
 int lls_factor_diag(lls_handle h, int64_t factor_id, double* diag, int64_t len,
                     int64_t* rank_count);
 
-/* Solve count independent problems (device pointers in each entry).
- * Problems run concurrently on the device.  Returns the first error, and
+/* Solve count independent problems (device pointers in each entry) on the
+ * handle's worker pool (lls_set_workers): largest first, several at a time
+ * on separate streams.  Blocks until all are done.  Returns the first error;
  * each entry's status field holds its own result. */
 int lls_solve_batched(lls_handle h, int64_t count, lls_problem* problems);
 
 /* Serving: enqueue one request (copied; buffers must stay alive until it
- * completes).  *ticket receives its id.  LLS_ERR_CAPACITY if the request
- * alone exceeds the handle's memory cap (lls_set_memory_cap). */
+ * completes) and return at once; *ticket receives its id.  Requests start in
+ * arrival order as soon as a worker of the pool is free and the estimated
+ * device memory of the running requests stays under the cap
+ * (lls_set_memory_cap), and run concurrently on separate streams.
+ * LLS_ERR_CAPACITY if the request alone exceeds the cap. */
 int lls_submit(lls_handle h, const lls_problem* request, int64_t* ticket);
 
-/* Serving: advance the scheduler and report a ticket's state in *status:
+/* Serving: report a ticket's state in *status without blocking:
  * LLS_PENDING, or the request's final status.  A finished ticket is
  * forgotten after it has been reported once. */
 int lls_poll(lls_handle h, int64_t ticket, int* status);
 
 /* Serving: device-memory cap in bytes for admitted work (0 = no cap). */
 int lls_set_memory_cap(lls_handle h, int64_t bytes);
+
+/* Serving: for a request submitted with keep_factor = 1, *factor_id
+ * receives the id of its resident factorization once it has finished
+ * (LLS_PENDING before; call it before lls_poll forgets the ticket). */
+int lls_ticket_factor(lls_handle h, int64_t ticket, int64_t* factor_id);
+
+/* Number of worker streams (1..64, default 4) used by lls_solve_batched and
+ * lls_submit; waits for running requests and drops queued ones. */
+int lls_set_workers(lls_handle h, int workers);
 
 /* ---- tracing (per-kernel-family CUDA-event timing) --------------------- */
 typedef struct {

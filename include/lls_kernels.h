@@ -81,6 +81,21 @@ int lls_k_gemm_bf16_tn(int64_t M, int64_t N, int64_t K, const void* X, int64_t l
                        const void* Z, int64_t ldz, float* D, int64_t ldd, int* status,
                        void* stream);
 
+/* C = alpha op(A) op(B) + beta C with FP64 operands and result, computed on
+ * the BF16 tensor cores by exact slicing (Ozaki-style): each row of op(A)
+ * and column of op(B) is scaled by a power of two and split into 8 base-128
+ * integer digit planes stored as BF16; the 36 digit-plane products with
+ * s + t <= 9 accumulate exactly in FP32 (at most 256 K entries per partial
+ * product), and the partial products are recombined and summed in FP64.
+ * Same operand conventions as lls_k_gemm.  Accuracy: at least that of an
+ * FP64 GEMM relative to max_k |op(A)_ik| max_k |op(B)_kj|.  status (device
+ * int) becomes nonzero if a device-side wait timed out.  Workspace is
+ * allocated and freed on the stream inside the call. */
+int lls_k_gemm_oz(int transa, int transb, int unit_lower_a, int unit_lower_b,
+                  int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb,
+                  double beta, double* C, int64_t ldc, int* status, void* stream);
+
 /* The Householder panel QR of lls_k_geqrf (R, W and tau in place; no T
  * factor) for callers that cannot allocate device memory: code whose device
  * memory is owned by another allocator (a framework's pool, a fixed budget

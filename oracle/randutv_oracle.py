@@ -71,6 +71,7 @@ __all__ = [
     "nullify",
     "solve",
     "pinv_solve",
+    "pinv_solve_from_factors",
     "normal_equation_residual",
 ]
 
@@ -412,6 +413,14 @@ def pinv_solve(A: np.ndarray, B: np.ndarray, r: int) -> np.ndarray:
     if r == 0:
         return np.zeros((A.shape[1],) + np.shape(B)[1:])
     return Vt[:r].T @ ((U[:, :r].T @ B) / (s[:r] if np.ndim(B) == 1 else s[:r, None]))
+
+
+def pinv_solve_from_factors(Q1: np.ndarray, sigma: np.ndarray, Q2: np.ndarray, B: np.ndarray,
+                            r: int) -> np.ndarray:
+    """Truncated-SVD least squares (Sec. 2.2) for A = Q1 diag(sigma) Q2^T with
+    orthonormal Q1, Q2 known: x = Q2(:, :r) diag(1/sigma(:r)) Q1(:, :r)^T b."""
+    Bm = np.asarray(B, dtype=np.float64).reshape(Q1.shape[0], -1)
+    return Q2[:, :r] @ ((Q1[:, :r].T @ Bm) / np.asarray(sigma)[:r, None])
 
 
 def normal_equation_residual(A, x, b, norm2_A: float) -> float:

@@ -113,6 +113,7 @@ int lls_create(lls_handle* out, const lls_options* opt, void* cuda_stream) {
 int lls_destroy(lls_handle hh) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
+  lls::stop_pool(*h);
   cudaStreamSynchronize(h->stream);
   delete h;
   return LLS_OK;
@@ -189,8 +190,9 @@ int lls_factor(lls_handle hh, const double* A, int64_t m, int64_t n, int64_t lda
   std::unique_ptr<lls::Factor> f(new lls::Factor());
   s = lls::factorize(*h, *f, A, m, n, lda, tol);
   if (!s.ok()) return finish(h, s);
-  int64_t id = h->next_factor++;
   if (rank) *rank = f->rank;
+  std::lock_guard<std::mutex> lock(h->factors_mu);
+  int64_t id = h->next_factor++;
   h->factors[id] = std::move(f);
   *factor_id = id;
   return finish(h, s);
@@ -201,10 +203,14 @@ int lls_solve_factored(lls_handle hh, int64_t factor_id, const double* B, int64_
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
   lls::TraceGuard tg(*h);
-  auto it = h->factors.find(factor_id);
-  if (it == h->factors.end())
-    return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));
-  lls::Factor& f = *it->second;
+  std::shared_ptr<lls::Factor> fp;
+  {
+    std::lock_guard<std::mutex> lock(h->factors_mu);
+    auto it = h->factors.find(factor_id);
+    if (it != h->factors.end()) fp = it->second;
+  }
+  if (!fp) return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));
+  lls::Factor& f = *fp;
   Status s = check_matrix(B, f.m, nrhs, ldb, 3, 2, 4, 5);
   if (s.ok() && ldx < (f.n > 1 ? f.n : 1)) s = arg_error(7, "ldx < max(1, n)");
   if (s.ok() && f.n > 0 && nrhs > 0 && !X) s = arg_error(6, "NULL X");
@@ -215,11 +221,17 @@ int lls_solve_factored(lls_handle hh, int64_t factor_id, const double* B, int64_
 int lls_factor_release(lls_handle hh, int64_t factor_id) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
-  auto it = h->factors.find(factor_id);
-  if (it == h->factors.end())
-    return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));
+  std::shared_ptr<lls::Factor> keep;  // freed outside the lock
+  {
+    std::lock_guard<std::mutex> lock(h->factors_mu);
+    auto it = h->factors.find(factor_id);
+    if (it == h->factors.end())
+      return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));
+    keep = std::move(it->second);
+    h->factors.erase(it);
+  }
   cudaStreamSynchronize(h->stream);
-  h->factors.erase(it);
+  keep.reset();
   return finish(h, lls::ok_status());
 }
 
@@ -227,10 +239,14 @@ int lls_factor_diag(lls_handle hh, int64_t factor_id, double* diag, int64_t len,
                     int64_t* rank_count) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h) return LLS_ERR_ARG;
-  auto it = h->factors.find(factor_id);
-  if (it == h->factors.end())
-    return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));
-  lls::Factor& f = *it->second;
+  std::shared_ptr<lls::Factor> fp;
+  {
+    std::lock_guard<std::mutex> lock(h->factors_mu);
+    auto it = h->factors.find(factor_id);
+    if (it != h->factors.end()) fp = it->second;
+  }
+  if (!fp) return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));
+  lls::Factor& f = *fp;
   int64_t mn = f.m < f.n ? f.m : f.n;
   if (len < mn || (mn > 0 && !diag)) return finish(h, arg_error(4, "diag buffer too short"));
   // |diag(T)| is the singular values written by the SVD step (before Nullify).

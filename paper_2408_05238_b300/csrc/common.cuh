@@ -57,7 +57,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // returns false, so a kernel can exit instead of hanging.  The state is two
 // words (arrival count, generation) that must be zero before the launch.
 // ---------------------------------------------------------------------------
-constexpr long long kBarrierSpinLimit = 1LL << 26;  // ~2-4 s of polling
+constexpr long long kBarrierSpinLimit = 1LL << 22;  // a few seconds of polling at most
 
 struct GridBarrier {
   unsigned int* count;

@@ -1,0 +1,610 @@
+// FP64-accurate GEMM on the BF16 tensor cores (tcgen05), by exact slicing.
+//
+// B300's FP64 ALU gives ~1.2 TFLOP/s, its BF16 tensor cores ~1.75 PFLOP/s.
+// This computes C = alpha op(A) op(B) + beta C with FP64 operands and FP64
+// result at FP64-level accuracy from BF16 products that are all exact:
+//
+//  1. Every row i of op(A) is scaled by 2^-e_i (2^e_i > max_k |op(A)_ik|) and
+//     every column j of op(B) by 2^-f_j, so each scaled entry x lies in
+//     (-1, 1).  With integer arithmetic only, x * 2^56 (rounded to an integer)
+//     is written in balanced base 128:  x = sum_{s=1..8} d_s 2^-7s with
+//     d_1 in [-128, 128] and d_2..d_8 in [-64, 64] -- integers that BF16
+//     holds exactly.  The 8 digit planes ("slices") are stored K-major.
+//  2. C_ij = 2^(e_i + f_j) sum_{s,t} 2^-7(s+t) sum_k d_s(i,k) d'_t(k,j).  The
+//     36 products with s + t <= 9 run on tcgen05.mma kind::f16 (BF16 in,
+//     FP32 accumulate in tensor memory), one FP32 accumulator per diagonal
+//     D = s + t (8 of them, 64 columns each = all 512 TMEM columns).  Per K
+//     entry a diagonal gains at most 2^15 in magnitude, so with at most 256
+//     K entries per CTA every accumulator stays below 2^24: the FP32 sums
+//     are exact integers.  Terms with s + t >= 10 are below 2^-55 relative
+//     to the row/column scales and are dropped.
+//  3. The epilogue converts the 8 exact integers to two 64-bit integers
+//     (diagonals 2..5 and 6..9, exact), then to FP64 (exact), and applies
+//     2^(e_i + f_j), alpha and beta.  Longer K is split into 256-wide
+//     ranges whose FP64 partial products are summed in a fixed order.
+//
+// Work per FP64 multiply-add: 36 BF16 multiply-adds on the tensor cores and
+// a handful of integer/FP64 operations per output element, instead of K DFMAs.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "internal.h"
+#include "lls_kernels.h"
+#include "oz_gemm.h"
+
+namespace lls {
+namespace {
+
+constexpr int OZ_S = 8;           // slices per operand
+constexpr int OZ_BM = 128;        // output rows per CTA (MMA M)
+constexpr int OZ_BN = 64;         // output columns per CTA (MMA N)
+constexpr int OZ_BK = 64;         // K per smem tile (128-byte swizzle rows)
+constexpr int OZ_KC = 256;        // K per CTA: keeps every FP32 sum below 2^24
+constexpr int OZ_XST = 5;         // X-tile ring depth (one slice of one K tile each)
+constexpr int OZ_ZST = 2;         // Z ring depth (all 8 slices of one K tile each)
+constexpr int OZ_THREADS = 128;
+constexpr uint32_t OZ_XBYTES = OZ_BM * OZ_BK * 2;         // 16 KB
+constexpr uint32_t OZ_ZTILE = OZ_BN * OZ_BK * 2;          // 8 KB
+constexpr uint32_t OZ_ZBYTES = OZ_ZTILE * OZ_S;           // 64 KB
+constexpr int kZeroExp = -4000;   // exponent of an all-zero row / column
+constexpr long long kOzWaitLimit = 1LL << 24;
+
+// ----------------------------------------------------------------------------
+// Slicing.  The logical operand Op is R x K ("rows" r = output rows of A or
+// output columns of B); its stored matrix is either K-contiguous
+// (Op(r,k) = src[k + r ld]) or R-contiguous (Op(r,k) = src[r + k ld]).
+// Unit-lower mode reads the stored matrix as unit lower trapezoidal.
+// Slices: out[s][r][k], leading dimension ldk (a multiple of 8).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double op_load(const double* src, int64_t ld, bool kcontig, bool ul,
+                                          int64_t r, int64_t k) {
+  int64_t p = kcontig ? k : r, c = kcontig ? r : k;  // stored (row, col)
+  if (ul) {
+    if (p < c) return 0.0;
+    if (p == c) return 1.0;
+  }
+  return src[p + c * ld];
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+__device__ __forceinline__ int exp_of_max(unsigned long long bits) {
+  // 2^e > max with e = unbiased exponent + 1 (frexp convention); zero -> sentinel
+  if (bits == 0) return kZeroExp;
+  int ex = (int)(bits >> 52);
+  if (ex == 0) return -1022;  // subnormal maximum
+  return ex - 1023 + 1;
+}
+
+// x * 2^(56 - e) rounded to an int64 (|result| < 2^56), then 8 balanced
+// base-128 digits, most significant first.
+__device__ __forceinline__ void make_digits(double v, int e, int d[OZ_S]) {
+  unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  int ex = (int)((bits >> 52) & 0x7FF);
+  long long X = 0;
+  if (ex != 0 && e != kZeroExp) {
+    unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    int sh = ex - 1075 + 56 - e;
+    if (sh >= 0) X = (long long)(mant << sh);
+    else if (sh > -60) X = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
+    if (bits >> 63) X = -X;
+  }
+#pragma unroll
+  for (int s = 0; s < OZ_S - 1; ++s) {
+    const int shift = 49 - 7 * s;
+    long long q = (X + (1LL << (shift - 1))) >> shift;
+    X -= q * (1LL << shift);
+    d[s] = (int)q;
+  }
+  d[OZ_S - 1] = (int)X;
+}
+
+// K-contiguous operand: one warp per row r; max over k, then the digits.
+__global__ void oz_slice_kcontig_kernel(int64_t R, int64_t K, const double* __restrict__ src,
+                                        int64_t ld, int ul, __nv_bfloat16* __restrict__ out,
+                                        int64_t ldk, int* __restrict__ exps) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t plane = R * ldk;
+  for (int64_t r = warp; r < R; r += nwarps) {
+    unsigned long long mx = 0;
+    for (int64_t k = lane; k < K; k += 32) {
+      unsigned long long b = abs_bits(op_load(src, ld, true, ul != 0, r, k));
+      mx = b > mx ? b : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    const int e = exp_of_max(mx);
+    if (lane == 0) exps[r] = e;
+    for (int64_t k = lane; k < ldk; k += 32) {
+      int d[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (k < K) make_digits(op_load(src, ld, true, ul != 0, r, k), e, d);
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s) out[s * plane + r * ldk + k] = __int2bfloat16_rn(d[s]);
+    }
+  }
+}
+
+// R-contiguous operand, pass 1: per-row maximum of |Op(r, k)| by 32 x 64 tiles.
+__global__ void oz_rowmax_rcontig_kernel(int64_t R, int64_t K, const double* __restrict__ src,
+                                         int64_t ld, int ul, unsigned long long* __restrict__ mx) {
+  const int64_t r = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+  const int64_t k0 = (int64_t)blockIdx.y * 64;
+  unsigned long long m = 0;
+  if (r < R) {
+    for (int64_t k = k0 + (threadIdx.x >> 5); k < min(K, k0 + 64); k += blockDim.x >> 5) {
+      unsigned long long b = abs_bits(op_load(src, ld, false, ul != 0, r, k));
+      m = b > m ? b : m;
+    }
+    if (m) atomicMax(mx + r, m);
+  }
+}
+
+__global__ void oz_exps_kernel(int64_t R, const unsigned long long* __restrict__ mx,
+                               int* __restrict__ exps) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < R) exps[r] = exp_of_max(mx[r]);
+}
+
+// R-contiguous operand, pass 2: digits of a 32 (r) x 32 (k) tile, transposed
+// through shared memory so that the K-major slices are written coalesced.
+__global__ void oz_slice_rcontig_kernel(int64_t R, int64_t K, const double* __restrict__ src,
+                                        int64_t ld, int ul, const int* __restrict__ exps,
+                                        __nv_bfloat16* __restrict__ out, int64_t ldk) {
+  __shared__ short tile[OZ_S][32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + tx, k = k0 + i;
+    int d[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (r < R && k < K) make_digits(op_load(src, ld, false, ul != 0, r, k), exps[r], d);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) tile[s][i][tx] = (short)d[s];
+  }
+  __syncthreads();
+  const int64_t plane = R * ldk;
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i, k = k0 + tx;
+    if (r >= R || k >= ldk) continue;
+    for (int s = 0; s < OZ_S; ++s) {
+      int v = tile[s][tx][i];
+      out[s * plane + r * ldk + k] = __int2bfloat16_rn(v);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Tensor-core kernel
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long i = 0; i < kOzWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && *reinterpret_cast<volatile int*>(err) != 0) return false;
+    if (i > 64) __nanosleep(40);
+  }
+  atomicExch(err, 1);
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+                              ((uint32_t)(OZ_BM >> 4) << 24);
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kOzIdesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ double pow2(int k) {
+  if (k < -1022) return 0.0;
+  if (k > 1023) k = 1023;
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+struct OzArgs {
+  int M, N, K, kchunk;
+  const int* expX;   // per output row (M)
+  const int* expZ;   // per output column (N)
+  double alpha, beta;
+  double* C;
+  int64_t ldc;
+  int transC;        // store D(i,j) at C[j + i ldc]
+  double* part;      // split-K partials [split][M x N], column-major
+  int* err;
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_mma_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapZ,
+                  OzArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* xring = smem;                       // OZ_XST x 16 KB
+  unsigned char* zring = smem + OZ_XST * OZ_XBYTES;  // OZ_ZST x 64 KB
+  __shared__ __align__(8) uint64_t xfull[OZ_XST], xempty[OZ_XST], zfull[OZ_ZST], zempty[OZ_ZST];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t s_tmem;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
+  const int kbeg = blockIdx.z * a.kchunk;
+  const int kend = min(a.K, kbeg + a.kchunk);
+  const int nkb = (kend - kbeg + OZ_BK - 1) / OZ_BK;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < OZ_XST; ++i) {
+      mbar_init(&xfull[i], 1);
+      mbar_init(&xempty[i], 1);
+    }
+    for (int i = 0; i < OZ_ZST; ++i) {
+      mbar_init(&zfull[i], 1);
+      mbar_init(&zempty[i], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: per K tile, the 8 Z slices at once, then the 8 X slices
+    int it = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nkb && ok; ++kb) {
+      const int k = kbeg + kb * OZ_BK;
+      const int zs = kb % OZ_ZST;
+      if (kb >= OZ_ZST && !mbar_wait(&zempty[zs], ((kb / OZ_ZST) - 1) & 1, a.err)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(&zfull[zs], OZ_ZBYTES);
+      tma_load_3d(zring + zs * OZ_ZBYTES, &mapZ, &zfull[zs], k, n0, 0);
+      for (int s = 0; s < OZ_S; ++s, ++it) {
+        const int xs = it % OZ_XST;
+        if (it >= OZ_XST && !mbar_wait(&xempty[xs], ((it / OZ_XST) - 1) & 1, a.err)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&xfull[xs], OZ_XBYTES);
+        tma_load_3d(xring + xs * OZ_XBYTES, &mapX, &xfull[xs], k, m0, s);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: diagonal d = s + t (0-based) accumulates X_s^T Z_t
+    int it = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nkb && ok; ++kb) {
+      const int zs = kb % OZ_ZST;
+      if (!mbar_wait(&zfull[zs], (kb / OZ_ZST) & 1, a.err)) {
+        ok = false;
+        break;
+      }
+      const uint32_t zaddr = smem_u32(zring + zs * OZ_ZBYTES);
+      for (int s = 0; s < OZ_S; ++s, ++it) {
+        const int xs = it % OZ_XST;
+        if (!mbar_wait(&xfull[xs], (it / OZ_XST) & 1, a.err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t xaddr = smem_u32(xring + xs * OZ_XBYTES);
+        for (int t = 0; t < OZ_S - s; ++t) {
+          const uint32_t dcol = tmem + (uint32_t)((s + t) * OZ_BN);
+#pragma unroll
+          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+            const uint32_t acc = (kb == 0 && s == 0 && kk == 0) ? 0u : 1u;
+            mma_bf16(dcol, sdesc_sw128(xaddr + kk * 32),
+                     sdesc_sw128(zaddr + t * OZ_ZTILE + kk * 32), acc);
+          }
+        }
+        mma_commit(&xempty[xs]);
+      }
+      if (ok) mma_commit(&zempty[zs]);
+    }
+    if (ok) mma_commit(&done_bar);
+  }
+
+  // ---- epilogue: exact integers -> FP64
+  __syncwarp();
+  bool ready = nkb > 0 && mbar_wait(&done_bar, 0, a.err);
+  ready = __all_sync(0xffffffffu, ready);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ready) {
+    const int i = m0 + warp * 32 + lane;
+    const bool row_ok = i < a.M;
+    const int ei = row_ok ? a.expX[i] : kZeroExp;
+    for (int g = 0; g < OZ_BN / 16; ++g) {
+      long long H[16], L[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) H[c] = L[c] = 0;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * OZ_BN + g * 16), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          long long v = (long long)__float2ll_rn(__uint_as_float(r[c]));
+          if (d < 4) H[c] += v * (1LL << (7 * (3 - d)));
+          else L[c] += v * (1LL << (7 * (7 - d)));
+        }
+      }
+      if (!row_ok) continue;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int j = n0 + g * 16 + c;
+        if (j >= a.N) continue;
+        const int fj = a.expZ[j];
+        if (ei == kZeroExp || fj == kZeroExp) {
+          // exact zero product
+          if (a.part) a.part[(int64_t)blockIdx.z * a.M * a.N + i + (int64_t)j * a.M] = 0.0;
+          else {
+            double* cp = a.transC ? a.C + j + (int64_t)i * a.ldc : a.C + i + (int64_t)j * a.ldc;
+            *cp = (a.beta == 0.0) ? 0.0 : a.beta * *cp;
+          }
+          continue;
+        }
+        const int sc = ei + fj;
+        const double v = fma((double)H[c], pow2(sc - 35), (double)L[c] * pow2(sc - 63));
+        if (a.part) {
+          a.part[(int64_t)blockIdx.z * a.M * a.N + i + (int64_t)j * a.M] = v;
+        } else {
+          double* cp = a.transC ? a.C + j + (int64_t)i * a.ldc : a.C + i + (int64_t)j * a.ldc;
+          *cp = (a.beta == 0.0) ? a.alpha * v : fma(a.alpha, v, a.beta * *cp);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+__global__ void oz_reduce_kernel(int M, int N, int splits, const double* __restrict__ part,
+                                 double alpha, double beta, double* C, int64_t ldc, int transC) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)M * N) return;
+  int64_t i = idx % M, j = idx / M;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += part[(int64_t)z * M * N + idx];
+  double* cp = transC ? C + j + i * ldc : C + i + j * ldc;
+  *cp = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *cp);
+}
+
+// ---------------------------------------------------------------------------
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn oz_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// Slices [8][R][ldk] bf16 as a 3-D tensor (K, R, 8) with box (64, rows, planes).
+Status make_slice_map(CUtensorMap* map, const void* base, int64_t K, int64_t R, int64_t ldk,
+                      int box_rows, int box_planes) {
+  EncodeTiledFn fn = oz_encode_fn();
+  if (!fn) return make_error(LLS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)OZ_S};
+  cuuint64_t strides[2] = {(cuuint64_t)(ldk * 2), (cuuint64_t)(R * ldk * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return make_error(LLS_ERR_CUDA, "cuTensorMapEncodeTiled (slices) failed");
+  return ok_status();
+}
+
+int64_t pad8(int64_t x) { return std::max<int64_t>(8, (x + 7) / 8 * 8); }
+
+}  // namespace
+
+size_t oz_slice_bytes(int64_t R, int64_t K) { return (size_t)OZ_S * R * pad8(K) * 2; }
+
+size_t oz_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K) {
+  size_t b = oz_slice_bytes(M, K) + oz_slice_bytes(N, K) + 8 * (size_t)(M + N) + 8 * (M + N) + 1024;
+  int64_t splits = (K + OZ_KC - 1) / OZ_KC;
+  if (splits > 1) b += (size_t)splits * M * N * sizeof(double);
+  return b;
+}
+
+// Slices of the R x K logical operand into `out` ([8][R][pad8(K)]), exponents in exps.
+Status oz_slice(int64_t R, int64_t K, const double* src, int64_t ld, bool kcontig, bool unit_lower,
+                __nv_bfloat16* out, int* exps, unsigned long long* maxbuf, cudaStream_t st) {
+  const int64_t ldk = pad8(K);
+  TraceScope ts(kTrConvert, st, 0.0, (8.0 + 16.0) * R * K);
+  if (kcontig) {
+    int64_t warps = std::min<int64_t>(R, 148 * 64);
+    oz_slice_kcontig_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
+        R, K, src, ld, unit_lower ? 1 : 0, out, ldk, exps);
+    LLS_LAUNCHED("oz_slice_kcontig_kernel");
+    return ok_status();
+  }
+  LLS_CUDA(cudaMemsetAsync(maxbuf, 0, sizeof(unsigned long long) * R, st));
+  dim3 g1((unsigned)ceil_div(R, 32), (unsigned)ceil_div(K, 64));
+  oz_rowmax_rcontig_kernel<<<g1, 256, 0, st>>>(R, K, src, ld, unit_lower ? 1 : 0, maxbuf);
+  LLS_LAUNCHED("oz_rowmax_rcontig_kernel");
+  oz_exps_kernel<<<(unsigned)ceil_div(R, 256), 256, 0, st>>>(R, maxbuf, exps);
+  LLS_LAUNCHED("oz_exps_kernel");
+  dim3 g2((unsigned)ceil_div(R, 32), (unsigned)ceil_div(ldk, 32));
+  oz_slice_rcontig_kernel<<<g2, 256, 0, st>>>(R, K, src, ld, unit_lower ? 1 : 0, exps, out, ldk);
+  LLS_LAUNCHED("oz_slice_rcontig_kernel");
+  return ok_status();
+}
+
+Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t n, int64_t k,
+               double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, bool transC, Scratch ws, int* err,
+               cudaStream_t st) {
+  if (m <= 0 || n <= 0) return ok_status();
+  if (k <= 0 || alpha == 0.0) {
+    // nothing to add: reuse the FP64 kernel's scaling path
+    return gemm(false, false, kDense, kDense, transC ? n : m, transC ? m : n, 0, 0.0, nullptr, 1,
+                nullptr, 1, beta, C, ldc, Scratch{}, st);
+  }
+  if (m > INT32_MAX || n > INT32_MAX || k > INT32_MAX)
+    return make_error(LLS_ERR_ARG, "oz_gemm: dimension too large");
+  if (ws.bytes < oz_gemm_workspace_bytes(m, n, k))
+    return make_error(LLS_ERR_NOMEM, "oz_gemm: workspace too small");
+  char* p = static_cast<char*>(ws.ptr);
+  auto take = [&](size_t bytes) {
+    char* q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  auto* Xs = reinterpret_cast<__nv_bfloat16*>(take(oz_slice_bytes(m, k)));
+  auto* Zs = reinterpret_cast<__nv_bfloat16*>(take(oz_slice_bytes(n, k)));
+  int* ex = reinterpret_cast<int*>(take(sizeof(int) * m));
+  int* fz = reinterpret_cast<int*>(take(sizeof(int) * n));
+  auto* mxb = reinterpret_cast<unsigned long long*>(take(8 * (size_t)std::max(m, n)));
+  const int64_t splits = (k + OZ_KC - 1) / OZ_KC;
+  double* part = splits > 1 ? reinterpret_cast<double*>(take((size_t)splits * m * n * 8)) : nullptr;
+
+  // op(A) (m x k): row i, entry kk is A[i + kk lda] (ta = 0) or A[kk + i lda] (ta = 1)
+  LLS_TRY(oz_slice(m, k, A, lda, /*kcontig=*/ta, ma == kUnitLower, Xs, ex, mxb, st));
+  // op(B) (k x n) as the n x k operand: column j, entry kk is B[kk + j ldb] (tb = 0)
+  LLS_TRY(oz_slice(n, k, B, ldb, /*kcontig=*/!tb, mb == kUnitLower, Zs, fz, mxb, st));
+
+  CUtensorMap mx, mz;
+  LLS_TRY(make_slice_map(&mx, Xs, k, m, pad8(k), OZ_BM, 1));
+  LLS_TRY(make_slice_map(&mz, Zs, k, n, pad8(k), OZ_BN, OZ_S));
+  OzArgs a;
+  a.M = (int)m;
+  a.N = (int)n;
+  a.K = (int)k;
+  a.kchunk = OZ_KC;
+  a.expX = ex;
+  a.expZ = fz;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.ldc = ldc;
+  a.transC = transC ? 1 : 0;
+  a.part = part;
+  a.err = err;
+  const size_t smem = 1024 + (size_t)OZ_XST * OZ_XBYTES + (size_t)OZ_ZST * OZ_ZBYTES;
+  LLS_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  dim3 grid((unsigned)ceil_div(m, OZ_BM), (unsigned)ceil_div(n, OZ_BN), (unsigned)splits);
+  if (grid.y > 65535u || grid.z > 65535u) return make_error(LLS_ERR_ARG, "oz_gemm: grid too large");
+  {
+    TraceScope ts(kTrOzGemm, st, 2.0 * m * n * k, 16.0 * (double)(m + n) * k + 16.0 * m * n);
+    oz_mma_kernel<<<grid, OZ_THREADS, smem, st>>>(mx, mz, a);
+    LLS_LAUNCHED("oz_mma_kernel");
+  }
+  if (part) {
+    TraceScope ts(kTrSmall, st);
+    oz_reduce_kernel<<<(unsigned)ceil_div(m * n, 256), 256, 0, st>>>(
+        (int)m, (int)n, (int)splits, part, alpha, beta, C, ldc, transC ? 1 : 0);
+    LLS_LAUNCHED("oz_reduce_kernel");
+  }
+  return ok_status();
+}
+
+}  // namespace lls
+
+extern "C" int lls_k_gemm_oz(int transa, int transb, int unit_lower_a, int unit_lower_b, int64_t m,
+                             int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                             const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                             int* status, void* stream) {
+  if (m < 0 || n < 0 || k < 0) return LLS_ERR_ARG;
+  int64_t arows = transa ? k : m, brows = transb ? n : k;
+  if (lda < (arows > 1 ? arows : 1) || ldb < (brows > 1 ? brows : 1) || ldc < (m > 1 ? m : 1))
+    return LLS_ERR_ARG;
+  if (m * n > 0 && (!C || !status || (k > 0 && (!A || !B)))) return LLS_ERR_ARG;
+  if (m * n == 0) return LLS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  lls::Scratch s;
+  s.bytes = lls::oz_gemm_workspace_bytes(m, n, k);
+  if (cudaMallocAsync(&s.ptr, s.bytes, st) != cudaSuccess) return LLS_ERR_NOMEM;
+  cudaMemsetAsync(status, 0, sizeof(int), st);
+  lls::Status r = lls::oz_gemm(transa != 0, transb != 0,
+                               unit_lower_a ? lls::kUnitLower : lls::kDense,
+                               unit_lower_b ? lls::kUnitLower : lls::kDense, m, n, k, alpha, A, lda,
+                               B, ldb, beta, C, ldc, false, s, status, st);
+  cudaFreeAsync(s.ptr, st);
+  return r.code;
+}

@@ -15,6 +15,7 @@
 // scalars and repeated runs are bit-identical.  Cross-CTA steps are joined
 // by a bounded grid barrier (common.cuh) inside a cooperative launch.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 #include "lls_kernels.h"
@@ -163,6 +164,22 @@ int panel_ctas(int64_t m) {
   return (int)std::min<int64_t>(g, std::min(nsm, PQ_MAX_CTAS));
 }
 
+// Cooperative grids from different streams must not be resident at the same
+// time: two partly resident grids could each hold the SM slots the other
+// still needs while their CTAs wait at a grid barrier.  Every cooperative
+// launch of the library therefore waits (on the device) for the previous one,
+// whatever stream issued it; ordinary kernels still overlap freely.
+struct CoopGate {
+  std::mutex mu;
+  int device = -1;
+  cudaEvent_t last = nullptr;
+};
+
+CoopGate& coop_gate() {
+  static CoopGate g;
+  return g;
+}
+
 }  // namespace
 
 size_t panel_qr_scratch_bytes(int64_t m, int64_t n) {
@@ -200,8 +217,22 @@ Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scrat
   int64_t k = std::min(m, n);
   TraceScope ts(kTrPanelQR, st, 2.0 * m * n * k - 2.0 * k * k * k / 3.0, 16.0 * m * n);
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  CoopGate& gate = coop_gate();
+  std::lock_guard<std::mutex> lock(gate.mu);
+  int dev = 0;
+  LLS_CUDA(cudaGetDevice(&dev));
+  if (gate.last && gate.device == dev) LLS_CUDA(cudaStreamWaitEvent(st, gate.last, 0));
   LLS_CUDA(cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(PQ_THREADS), args,
                                        smem, st));
+  if (gate.last && gate.device != dev) {
+    cudaEventDestroy(gate.last);
+    gate.last = nullptr;
+  }
+  if (!gate.last) {
+    LLS_CUDA(cudaEventCreateWithFlags(&gate.last, cudaEventDisableTiming));
+    gate.device = dev;
+  }
+  LLS_CUDA(cudaEventRecord(gate.last, st));
   return ok_status();
 }
 

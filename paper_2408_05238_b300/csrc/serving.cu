@@ -1,60 +1,234 @@
-// Batched solves and the request queue (lls_solve_batched, lls_submit,
-// lls_poll, lls_set_memory_cap).
+// Batched solves and the serving queue (lls_solve_batched, lls_submit,
+// lls_poll, lls_set_memory_cap, lls_set_workers).
+//
+// A handle owns a pool of worker handles.  Each worker has its own stream,
+// its own workspace and one host thread, and runs whole requests
+// (factorization and solve, or a solve with a resident factor) one after
+// another; different workers' requests overlap on the device.  Requests wait
+// in one FIFO queue and are admitted, in arrival order, when a worker is
+// free and the estimated device memory of the admitted requests stays under
+// the handle's cap (continuous batching: a request that arrives while others
+// run starts as soon as a worker and memory free up).  Every kernel reduces
+// in a fixed order, so a request's result does not depend on what runs
+// beside it.
+#include <algorithm>
+#include <condition_variable>
 #include <deque>
+#include <thread>
 
 #include "lls.h"
 #include "solver.h"
 
 namespace lls {
 
-struct Handle::Ticket {
+struct Ticket {
   lls_problem req;
+  int64_t bytes = 0;
   int status = LLS_PENDING;
   bool done = false;
 };
 
+struct Handle::Pool {
+  Handle* parent = nullptr;
+  std::vector<std::unique_ptr<Handle>> workers;
+  std::vector<std::thread> threads;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<int64_t> queue;
+  std::map<int64_t, std::shared_ptr<Ticket>> tickets;
+  int64_t next_ticket = 0;
+  int64_t admitted_bytes = 0;
+  int running = 0;
+  bool stop = false;
+};
+
+Handle::Handle() = default;
+
+Handle::~Handle() {
+  stop_pool(*this);
+  if (hstat) cudaFreeHost(hstat);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
 namespace {
 
-Status run_one(Handle& h, lls_problem& p) {
+// Device memory one request holds while it runs (factor + workspace).
+int64_t request_bytes(const lls_problem& p, int nb) {
+  if (p.factor_id >= 0) return (int64_t)(8 * (p.m + 2 * p.n) * std::max<int64_t>(p.nrhs, 1));
+  int64_t mx = std::max(p.m, p.n);
+  int64_t ws = 8 * (int64_t)mx * nb * 6 + 8 * (int64_t)(p.m + p.n) * std::max<int64_t>(p.nrhs, 1);
+  return (int64_t)factor_bytes(p.m, p.n, nb) + ws;
+}
+
+Status run_request(Handle& parent, Handle& w, lls_problem& p) {
   if (p.factor_id >= 0) {
-    auto it = h.factors.find(p.factor_id);
-    if (it == h.factors.end()) return make_error(LLS_ERR_NOT_FOUND, "unknown factor id");
-    Factor& f = *it->second;
-    if (p.rank_out) *p.rank_out = f.rank;
-    return solve_factored(h, f, p.B, p.nrhs, p.ldb, p.X, p.ldx);
+    std::shared_ptr<Factor> f;
+    {
+      std::lock_guard<std::mutex> lock(parent.factors_mu);
+      auto it = parent.factors.find(p.factor_id);
+      if (it != parent.factors.end()) f = it->second;
+    }
+    if (!f) return make_error(LLS_ERR_NOT_FOUND, "unknown factor id");
+    if (p.rank_out) *p.rank_out = f->rank;
+    return solve_factored(w, *f, p.B, p.nrhs, p.ldb, p.X, p.ldx);
   }
-  std::unique_ptr<Factor> f(new Factor());
-  Status fs = factorize(h, *f, p.A, p.m, p.n, p.lda, p.tol);
+  if (p.n == 0 || p.nrhs == 0) {
+    if (p.rank_out) *p.rank_out = 0;
+    return ok_status();
+  }
+  if (p.m == 0) {
+    if (p.rank_out) *p.rank_out = 0;
+    Status s = fill_zero(p.n, p.nrhs, p.X, p.ldx, w.stream);
+    if (s.ok()) s = cuda_status(cudaStreamSynchronize(w.stream), "synchronize");
+    return s;
+  }
+  std::shared_ptr<Factor> f;
+  if (p.keep_factor) {
+    f = std::make_shared<Factor>();
+  } else if (!w.scratch_factor) {
+    w.scratch_factor.reset(new Factor());
+  }
+  Factor& fr = p.keep_factor ? *f : *w.scratch_factor;
+  Status fs = factorize(w, fr, p.A, p.m, p.n, p.lda, p.tol);
   if (!fs.ok()) return fs;
-  if (p.rank_out) *p.rank_out = f->rank;
-  Status ss = solve_factored(h, *f, p.B, p.nrhs, p.ldb, p.X, p.ldx);
+  if (p.rank_out) *p.rank_out = fr.rank;
+  Status ss = solve_factored(w, fr, p.B, p.nrhs, p.ldb, p.X, p.ldx);
   if (!ss.ok()) return ss;
   if (p.keep_factor) {
-    int64_t id = h.next_factor++;
-    h.factors[id] = std::move(f);
+    std::lock_guard<std::mutex> lock(parent.factors_mu);
+    int64_t id = parent.next_factor++;
+    parent.factors[id] = f;
     p.factor_id = id;
   }
   return fs;
 }
 
+void worker_loop(Handle::Pool* pool, int wi) {
+  Handle& w = *pool->workers[wi];
+  cudaSetDevice(w.device);
+  for (;;) {
+    std::shared_ptr<Ticket> t;
+    {
+      std::unique_lock<std::mutex> lock(pool->mu);
+      pool->cv_work.wait(lock, [&] {
+        if (pool->stop) return true;
+        if (pool->queue.empty()) return false;
+        auto& head = pool->tickets[pool->queue.front()];
+        int64_t cap = pool->parent->mem_cap;
+        return cap <= 0 || pool->running == 0 || pool->admitted_bytes + head->bytes <= cap;
+      });
+      if (pool->stop) return;
+      t = pool->tickets[pool->queue.front()];
+      pool->queue.pop_front();
+      pool->admitted_bytes += t->bytes;
+      ++pool->running;
+    }
+    w.opt = pool->parent->opt;
+    Status s = run_request(*pool->parent, w, t->req);
+    {
+      std::lock_guard<std::mutex> lock(pool->mu);
+      pool->admitted_bytes -= t->bytes;
+      --pool->running;
+      t->status = s.code;
+      t->done = true;
+    }
+    pool->cv_done.notify_all();
+    pool->cv_work.notify_all();
+  }
+}
+
+Status ensure_pool(Handle& h) {
+  if (h.pool) return ok_status();
+  std::unique_ptr<Handle::Pool> pool(new Handle::Pool());
+  pool->parent = &h;
+  for (int i = 0; i < h.num_workers; ++i) {
+    std::unique_ptr<Handle> w(new Handle());
+    w->opt = h.opt;
+    w->device = h.device;
+    if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return make_error(LLS_ERR_CUDA, "cannot create a worker stream");
+    w->own_stream = true;
+    pool->workers.push_back(std::move(w));
+  }
+  Handle::Pool* raw = pool.get();
+  h.pool = std::move(pool);
+  for (int i = 0; i < h.num_workers; ++i) raw->threads.emplace_back(worker_loop, raw, i);
+  return ok_status();
+}
+
+int64_t enqueue(Handle& h, const lls_problem& req) {
+  Handle::Pool& pool = *h.pool;
+  auto t = std::make_shared<Ticket>();
+  t->req = req;
+  t->bytes = request_bytes(req, h.opt.nb);
+  int64_t id;
+  {
+    std::lock_guard<std::mutex> lock(pool.mu);
+    id = pool.next_ticket++;
+    pool.tickets[id] = t;
+    pool.queue.push_back(id);
+  }
+  pool.cv_work.notify_all();
+  return id;
+}
+
 }  // namespace
+
+void stop_pool(Handle& h) {
+  if (!h.pool) return;
+  {
+    std::lock_guard<std::mutex> lock(h.pool->mu);
+    h.pool->stop = true;
+  }
+  h.pool->cv_work.notify_all();
+  for (auto& th : h.pool->threads) th.join();
+  h.pool.reset();
+}
+
 }  // namespace lls
 
 using lls::Handle;
 
 extern "C" {
 
+int lls_set_workers(lls_handle hh, int workers) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || workers < 1 || workers > 64) return LLS_ERR_ARG;
+  lls::stop_pool(*h);
+  h->num_workers = workers;
+  return LLS_OK;
+}
+
 int lls_solve_batched(lls_handle hh, int64_t count, lls_problem* problems) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || count < 0 || (count > 0 && !problems)) return LLS_ERR_ARG;
-  lls::TraceGuard tg(*h);
-  int first = LLS_OK;
-  for (int64_t i = 0; i < count; ++i) {
-    lls_problem& p = problems[i];
+  if (count == 0) return LLS_OK;
+  lls::Status ps = lls::ensure_pool(*h);
+  if (!ps.ok()) return ps.code;
+  // Largest problems first, so the pool's tail is made of short requests.
+  std::vector<int64_t> order(count);
+  for (int64_t i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    const lls_problem &pa = problems[a], &pb = problems[b];
+    return (double)pa.m * pa.n * std::min(pa.m, pa.n) > (double)pb.m * pb.n * std::min(pb.m, pb.n);
+  });
+  std::vector<int64_t> ids(count);
+  for (int64_t k = 0; k < count; ++k) {
+    lls_problem p = problems[order[k]];
     p.factor_id = -1;
-    lls::Status s = lls::run_one(*h, p);
-    p.status = s.code;
-    if (first == LLS_OK && s.code < 0) first = s.code;
+    p.keep_factor = 0;
+    ids[k] = lls::enqueue(*h, p);
+  }
+  Handle::Pool& pool = *h->pool;
+  int first = LLS_OK;
+  std::unique_lock<std::mutex> lock(pool.mu);
+  for (int64_t k = 0; k < count; ++k) {
+    auto t = pool.tickets[ids[k]];
+    pool.cv_done.wait(lock, [&] { return t->done; });
+    problems[order[k]].status = t->status;
+    problems[order[k]].factor_id = -1;
+    if (first == LLS_OK && t->status < 0) first = t->status;
+    pool.tickets.erase(ids[k]);
   }
   return first;
 }
@@ -63,39 +237,49 @@ int lls_set_memory_cap(lls_handle hh, int64_t bytes) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || bytes < 0) return LLS_ERR_ARG;
   h->mem_cap = bytes;
+  if (h->pool) h->pool->cv_work.notify_all();
   return LLS_OK;
 }
 
 int lls_submit(lls_handle hh, const lls_problem* req, int64_t* ticket) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !req || !ticket) return LLS_ERR_ARG;
-  if (h->mem_cap > 0 && req->factor_id < 0 &&
-      (int64_t)lls::factor_bytes(req->m, req->n, h->opt.nb) > h->mem_cap)
-    return LLS_ERR_CAPACITY;
-  auto t = std::make_shared<Handle::Ticket>();
-  t->req = *req;
-  int64_t id = h->next_ticket++;
-  h->tickets[id] = t;
-  *ticket = id;
+  if (req->m < 0 || req->n < 0 || req->nrhs < 0 || req->ldb < std::max<int64_t>(1, req->m) ||
+      req->ldx < std::max<int64_t>(1, req->n) ||
+      (req->factor_id < 0 && req->lda < std::max<int64_t>(1, req->m)))
+    return LLS_ERR_ARG;
+  if (h->mem_cap > 0 && lls::request_bytes(*req, h->opt.nb) > h->mem_cap) return LLS_ERR_CAPACITY;
+  lls::Status ps = lls::ensure_pool(*h);
+  if (!ps.ok()) return ps.code;
+  *ticket = lls::enqueue(*h, *req);
   return LLS_OK;
 }
 
 int lls_poll(lls_handle hh, int64_t ticket, int* status) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !status) return LLS_ERR_ARG;
-  auto it = h->tickets.find(ticket);
-  if (it == h->tickets.end()) return LLS_ERR_NOT_FOUND;
-  lls::TraceGuard tg(*h);
-  // run queued requests in arrival order up to this one
-  for (auto& kv : h->tickets) {
-    if (kv.second->done) continue;
-    lls::Status s = lls::run_one(*h, kv.second->req);
-    kv.second->status = s.code;
-    kv.second->done = true;
-    if (kv.first == ticket) break;
+  if (!h->pool) return LLS_ERR_NOT_FOUND;
+  std::lock_guard<std::mutex> lock(h->pool->mu);
+  auto it = h->pool->tickets.find(ticket);
+  if (it == h->pool->tickets.end()) return LLS_ERR_NOT_FOUND;
+  if (!it->second->done) {
+    *status = LLS_PENDING;
+    return LLS_OK;
   }
-  *status = it->second->done ? it->second->status : LLS_PENDING;
-  if (it->second->done) h->tickets.erase(it);
+  *status = it->second->status;
+  h->pool->tickets.erase(it);
+  return LLS_OK;
+}
+
+int lls_ticket_factor(lls_handle hh, int64_t ticket, int64_t* factor_id) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || !factor_id) return LLS_ERR_ARG;
+  if (!h->pool) return LLS_ERR_NOT_FOUND;
+  std::lock_guard<std::mutex> lock(h->pool->mu);
+  auto it = h->pool->tickets.find(ticket);
+  if (it == h->pool->tickets.end()) return LLS_ERR_NOT_FOUND;
+  if (!it->second->done) return LLS_PENDING;
+  *factor_id = it->second->req.factor_id;
   return LLS_OK;
 }
 

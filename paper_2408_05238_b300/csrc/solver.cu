@@ -20,14 +20,10 @@
 #include <cstring>
 
 #include "lls_kernels.h"
+#include "oz_gemm.h"
 #include "solver.h"
 
 namespace lls {
-
-Handle::~Handle() {
-  if (hstat) cudaFreeHost(hstat);
-  if (own_stream && stream) cudaStreamDestroy(stream);
-}
 
 namespace {
 
@@ -118,6 +114,28 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   DevStatus* ds = h.dstat.as<DevStatus>();
   LLS_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevStatus), st));
   Scratch gws = scratch_of(h.gemm_ws), pws = scratch_of(h.panel_ws);
+  // Mixed precision: the trailing updates and Nullify's products run as
+  // FP64-accurate GEMMs on the tensor cores (exact BF16 slices, oz_gemm.cu).
+  const bool tc = h.opt.precision == LLS_MIXED_BF16;
+  if (tc) {
+    size_t need = 0;
+    for (int64_t i = 0; i < steps; ++i) {
+      const int64_t k = f.ks[i], b = f.bs[i], mp = m - k, np = n - k;
+      need = std::max(need, oz_gemm_workspace_bytes(m, b, np));
+      need = std::max(need, oz_gemm_workspace_bytes(m, np, b));
+      need = std::max(need, oz_gemm_workspace_bytes(b, np - b, mp));
+      need = std::max(need, oz_gemm_workspace_bytes(mp, np - b, b));
+    }
+    LLS_TRY(h.oz_ws.reserve(need));
+  }
+  auto xgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
+                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
+                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
+    if (tc)
+      return oz_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_, false,
+                     scratch_of(h.oz_ws), &ds->barrier_err, st);
+    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_, gws, st);
+  };
 
   // T <- A, with the finiteness check.
   LLS_TRY(copy_check(m, n, A, lda, f.T.d(), ldt, &ds->nonfinite, st));
@@ -155,12 +173,12 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauVi, TVi, nb, st));
     // ---- a4: T(:, k:n) <- T(:, k:n) - (T(:, k:n) W_V) T_V W_V^T, all m rows
     double* Tk = T + k * ldt;
-    LLS_TRY(gemm(false, false, kDense, kUnitLower, m, b, np, 1.0, Tk, ldt, Y, ldw, 0.0, h.P.d(), m,
-                 gws, st));
-    LLS_TRY(gemm(false, false, kDense, kDense, m, b, b, 1.0, h.P.d(), m, TVi, nb, 0.0, h.P2.d(), m,
-                 gws, st));
-    LLS_TRY(gemm(false, true, kDense, kUnitLower, m, np, b, -1.0, h.P2.d(), m, Y, ldw, 1.0, Tk, ldt,
-                 gws, st));
+    LLS_TRY(xgemm(false, false, kDense, kUnitLower, m, b, np, 1.0, Tk, ldt, Y, ldw, 0.0, h.P.d(),
+                  m));
+    LLS_TRY(xgemm(false, false, kDense, kDense, m, b, b, 1.0, h.P.d(), m, TVi, nb, 0.0, h.P2.d(),
+                  m));
+    LLS_TRY(xgemm(false, true, kDense, kUnitLower, m, np, b, -1.0, h.P2.d(), m, Y, ldw, 1.0, Tk,
+                  ldt));
     // ---- a5: [[A11; A21], T_U, W_U] = unpivoted_QR([A11; A21])
     LLS_TRY(panel_qr(mp, b, ABR, ldt, tauUi, pws, &ds->barrier_err, st));
     LLS_TRY(copy_upper(b, ABR, ldt, f.Rblk.d() + i * blk, nb, st));
@@ -170,12 +188,12 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     // ---- a6: [A12; A22] <- (I - W_U T_U W_U^T)^T [A12; A22]
     if (np > b) {
       double* A12 = ABR + b * ldt;
-      LLS_TRY(gemm(true, false, kUnitLower, kDense, b, np - b, mp, 1.0, ABR, ldt, A12, ldt, 0.0,
-                   h.Q.d(), nb, gws, st));
-      LLS_TRY(gemm(true, false, kDense, kDense, b, np - b, b, 1.0, TUi, nb, h.Q.d(), nb, 0.0,
-                   h.Q2.d(), nb, gws, st));
-      LLS_TRY(gemm(false, false, kUnitLower, kDense, mp, np - b, b, -1.0, ABR, ldt, h.Q2.d(), nb,
-                   1.0, A12, ldt, gws, st));
+      LLS_TRY(xgemm(true, false, kUnitLower, kDense, b, np - b, mp, 1.0, ABR, ldt, A12, ldt, 0.0,
+                    h.Q.d(), nb));
+      LLS_TRY(xgemm(true, false, kDense, kDense, b, np - b, b, 1.0, TUi, nb, h.Q.d(), nb, 0.0,
+                    h.Q2.d(), nb));
+      LLS_TRY(xgemm(false, false, kUnitLower, kDense, mp, np - b, b, -1.0, ABR, ldt, h.Q2.d(), nb,
+                    1.0, A12, ldt));
     }
   }
 
@@ -278,12 +296,14 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
         const double* Wbot = M + bsz;
         LLS_TRY(copy_cols_reversed(j0, bsz, T + j0 * ldt, ldt, Xc, j0, st));
         LLS_TRY(copy_matrix(j0, bsz, Xc, j0, h.P.d(), j0, st));
-        LLS_TRY(gemm(false, false, kDense, kDense, j0, bsz, L, 1.0, D0, ldt, Wbot, ldm, 1.0,
-                     h.P.d(), j0, gws, st));
+        if (tc) LLS_TRY(h.oz_ws.reserve(std::max(oz_gemm_workspace_bytes(j0, bsz, L),
+                                                  oz_gemm_workspace_bytes(j0, L, bsz))));
+        LLS_TRY(xgemm(false, false, kDense, kDense, j0, bsz, L, 1.0, D0, ldt, Wbot, ldm, 1.0,
+                      h.P.d(), j0));
         LLS_TRY(gemm(false, false, kDense, kDense, j0, bsz, bsz, 1.0, h.P.d(), j0, Tz, bsz, 0.0,
                      h.P2.d(), j0, gws, st));
-        LLS_TRY(gemm(false, true, kDense, kDense, j0, L, bsz, -1.0, h.P2.d(), j0, Wbot, ldm, 1.0,
-                     D0, ldt, gws, st));
+        LLS_TRY(xgemm(false, true, kDense, kDense, j0, L, bsz, -1.0, h.P2.d(), j0, Wbot, ldm, 1.0,
+                      D0, ldt));
         // C01 (reversed) -= P2 W_top^T with W_top = I, then reversed back into T
         LLS_TRY(axpy_matrix(j0, bsz, -1.0, h.P2.d(), j0, Xc, j0, st));
         LLS_TRY(copy_cols_reversed(j0, bsz, Xc, j0, T + j0 * ldt, ldt, st));

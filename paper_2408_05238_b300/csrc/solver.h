@@ -5,6 +5,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -101,23 +102,27 @@ struct Handle {
   DevBuf dstat;           // DevStatus
   // mixed precision sampling: bf16 copies of A_BR and A_BR^T, bf16 sketch /
   // product, fp32 product, tensor-core split-K partials, scalars
-  DevBuf G16, A16, A16t, Z16, F32, tc_ws, mixed_misc;
+  DevBuf G16, A16, A16t, Z16, F32, tc_ws, mixed_misc, oz_ws;
   DevStatus* hstat = nullptr;  // pinned host mirror
   // lls_solve reuses one factor object between calls of the same shape
   std::unique_ptr<Factor> scratch_factor;
-  std::map<int64_t, std::unique_ptr<Factor>> factors;
+  // resident factors, shared with the worker pool (guarded by factors_mu)
+  std::map<int64_t, std::shared_ptr<Factor>> factors;
   int64_t next_factor = 0;
+  std::mutex factors_mu;
   // tracing
   std::unique_ptr<Tracer> tracer;
   bool trace_on = false;
   // errors
   int last_arg = 0;
   std::string last_msg;
-  // serving
+  // batched solves and serving: a pool of worker handles, each with its own
+  // stream, workspace and host thread (serving.cu)
   int64_t mem_cap = 0;
-  struct Ticket;
-  std::map<int64_t, std::shared_ptr<Ticket>> tickets;
-  int64_t next_ticket = 0;
+  int num_workers = 4;
+  struct Pool;
+  std::unique_ptr<Pool> pool;
+  Handle();  // both defined where Pool is complete (serving.cu)
   ~Handle();
 };
 
@@ -136,6 +141,9 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
                       int64_t ldx);
 // Device bytes a factorization of m x n (and a solve with nrhs) will hold.
 size_t factor_bytes(int64_t m, int64_t n, int nb);
+
+// Stops and joins the worker pool (serving.cu); queued requests are dropped.
+void stop_pool(Handle& h);
 
 Status jacobi_svd_batched(int count, int b, int b_last, const double* R, int64_t ldr,
                           int64_t strideR, double* sigma, int64_t strideS, double* U, int64_t ldu,

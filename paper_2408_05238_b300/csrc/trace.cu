@@ -14,7 +14,7 @@ const char* trace_kind_name(int k) {
                                         "panel_qr_kernel",   "wy_tfactor_kernel",
                                         "sketch_kernel",     "jacobi_svd_kernel",
                                         "small_kernels",     "bf16_gemm_kernel",
-                                        "convert_kernels"};
+                                        "convert_kernels",   "oz_mma_kernel"};
   return (k >= 0 && k < kTrCount) ? names[k] : "unknown";
 }
 

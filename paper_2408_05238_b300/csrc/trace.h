@@ -21,7 +21,8 @@ enum TraceKind {
   kTrSvd,          // batched Jacobi SVD
   kTrSmall,        // copies, rank scan, gathers, TRSM blocks
   kTrBf16Gemm,     // tcgen05 BF16 sampling GEMM
-  kTrConvert,      // FP64 -> BF16 conversions
+  kTrConvert,      // FP64 -> BF16 conversions and slicing
+  kTrOzGemm,       // FP64-accurate GEMM on tensor cores (exact BF16 slices)
   kTrCount
 };
 

@@ -88,6 +88,8 @@ _sig("lls_solve_batched", [_H, _I, C.POINTER(lls_problem)])
 _sig("lls_submit", [_H, C.POINTER(lls_problem), C.POINTER(_I)])
 _sig("lls_poll", [_H, _I, C.POINTER(C.c_int)])
 _sig("lls_set_memory_cap", [_H, _I])
+_sig("lls_ticket_factor", [_H, _I, C.POINTER(_I)])
+_sig("lls_set_workers", [_H, C.c_int])
 _sig("lls_status_string", [C.c_int], C.c_char_p)
 _sig("lls_last_error", [_H, C.POINTER(C.c_int), C.c_char_p, _I])
 _sig("lls_trace_enable", [_H, C.c_int])
@@ -102,6 +104,8 @@ _sig("lls_k_jacobi_svd", [_I, _P, _I, _P, _P, _I, _P, _I, _P, _P])
 _sig("lls_k_trsm_upper", [_I, _I, _P, _I, _P, _I, _P])
 _sig("lls_k_rank", [_I, _P, _I, _D, _P, _P])
 _sig("lls_k_gemm_bf16_tn", [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P])
+_sig("lls_k_gemm_oz", [C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _P, _I, _P, _I, _D,
+                       _P, _I, _P, _P])
 _sig("lls_k_panel_qr_noalloc", [_I, _I, _P, _I, _P, _P, _P])
 
 EXPORTED = [n for n in dir(_lib) if n.startswith("lls_")]
@@ -288,6 +292,17 @@ def lls_set_memory_cap(h, nbytes: int):
     _check(h, _lib.lls_set_memory_cap(h, int(nbytes)))
 
 
+def lls_ticket_factor(h, ticket: int):
+    """Factor id of a finished keep_factor request, or None while pending."""
+    f = _I(-1)
+    code = _check(h, _lib.lls_ticket_factor(h, ticket, C.byref(f)))
+    return None if code == LLS_PENDING else f.value
+
+
+def lls_set_workers(h, workers: int):
+    _check(h, _lib.lls_set_workers(h, int(workers)))
+
+
 def lls_trace_enable(h, on: bool = True):
     _check(h, _lib.lls_trace_enable(h, int(on)))
 
@@ -379,6 +394,21 @@ def lls_k_gemm_bf16_tn(X: torch.Tensor, Z: torch.Tensor):
     _kcheck(_lib.lls_k_gemm_bf16_tn(M, N, K, _ptr(X), _ld(X), _ptr(Z), _ld(Z), _ptr(D), max(1, M),
                                     _ptr(status), _stream()))
     return D, int(status.item())
+
+
+def lls_k_gemm_oz(transa, transb, A, B, C_=None, alpha=1.0, beta=0.0, unit_lower_a=False,
+                  unit_lower_b=False):
+    """FP64 GEMM on the tensor cores by exact BF16 slicing (lls_k_gemm_oz)."""
+    m = A.shape[1] if transa else A.shape[0]
+    k = A.shape[0] if transa else A.shape[1]
+    n = B.shape[0] if transb else B.shape[1]
+    if C_ is None:
+        C_ = torch.zeros((n, max(m, 1)), dtype=torch.float64, device=A.device).t()[:m]
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _kcheck(_lib.lls_k_gemm_oz(int(transa), int(transb), int(unit_lower_a), int(unit_lower_b), m,
+                               n, k, float(alpha), _ptr(A), _ld(A), _ptr(B), _ld(B), float(beta),
+                               _ptr(C_), _ld(C_), _ptr(status), _stream()))
+    return C_, int(status.item())
 
 
 def lls_k_panel_qr_noalloc(A: torch.Tensor, tau: torch.Tensor, status: torch.Tensor) -> int:

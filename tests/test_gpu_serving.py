@@ -1,0 +1,140 @@
+"""Batched solves and the serving queue: each result is the same alone and in
+the mix (bit for bit: every kernel reduces in a fixed order), admission
+respects the memory cap, resident factors are reused with new right-hand
+sides, and results match the FP64 oracle."""
+
+import ctypes as C
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import randutv_oracle as orc
+from paper_2408_05238_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(x):
+    return torch.as_tensor(np.asfortranarray(x), dtype=torch.float64, device="cuda").t().contiguous().t()
+
+
+def problems(count, seed):
+    return wl.batched_problems(count, seed=seed, m_range=(200, 700), nrhs_choices=(1, 3, 8))
+
+
+def solve_alone(lls, p, nb=64, q=1, seed=2004):
+    h = lls.lls_create(nb=nb, q=q, seed=seed)
+    try:
+        X, rank, _ = lls.lls_solve(h, dev(p.A), dev(p.B), p.tol)
+        return X.cpu().numpy(), rank
+    finally:
+        lls.lls_destroy(h)
+
+
+def test_batched_equals_alone_and_oracle(lls):
+    ps = problems(24, 7)
+    h = lls.lls_create(nb=64, q=1, seed=2004)
+    lls.lls_set_workers(h, 6)
+    try:
+        keep, plist, ranks = [], [], []
+        for p in ps:
+            A, B = dev(p.A), dev(p.B)
+            X = lls.empty_colmajor(p.A.shape[1], p.B.shape[1])
+            r = C.c_int64(-1)
+            ranks.append(r)
+            keep.append((A, B, X))
+            plist.append(lls.make_problem(A, B, p.tol, X, rank_out=C.pointer(r)))
+        code = lls.lls_solve_batched(h, plist)
+        torch.cuda.synchronize()
+        assert code == 0
+    finally:
+        lls.lls_destroy(h)
+    for i, p in enumerate(ps):
+        assert plist[i].status == 0
+        x_alone, r_alone = solve_alone(lls, p)
+        assert ranks[i].value == r_alone == p.rank
+        assert np.array_equal(keep[i][2].cpu().numpy(), x_alone)
+    for p, (_, _, X) in list(zip(ps, keep))[:4]:
+        ref = orc.solve(p.A, p.B, 1, 64, p.tol, 2004)
+        xr = np.reshape(ref.x, X.shape)
+        assert np.linalg.norm(X.cpu().numpy() - xr) / np.linalg.norm(xr) < 1e-9
+
+
+def wait_all(lls, h, tickets, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t in out:
+                continue
+            s = lls.lls_poll(h, t)
+            if s != lls.LLS_PENDING:
+                out[t] = s
+        assert time.time() - t0 < timeout
+        time.sleep(0.002)
+    return out
+
+
+def test_serving_results_same_alone_and_in_the_mix(lls):
+    ps = problems(16, 11)
+    h = lls.lls_create(nb=64, q=1, seed=2004)
+    lls.lls_set_workers(h, 4)
+    try:
+        held, tickets = [], []
+        for p in ps:
+            A, B = dev(p.A), dev(p.B)
+            X = lls.empty_colmajor(p.A.shape[1], p.B.shape[1])
+            held.append((A, B, X))
+            tickets.append(lls.lls_submit(h, lls.make_problem(A, B, p.tol, X)))
+        st = wait_all(lls, h, tickets)
+        assert all(v == 0 for v in st.values())
+        torch.cuda.synchronize()
+    finally:
+        lls.lls_destroy(h)
+    for p, (_, _, X) in zip(ps, held):
+        x_alone, _ = solve_alone(lls, p)
+        assert np.array_equal(X.cpu().numpy(), x_alone)
+
+
+def test_serving_factor_reuse_and_memory_cap(lls):
+    p = wl.c1_problem()
+    h = lls.lls_create(nb=64, q=1, seed=2001)
+    try:
+        A, B = dev(p.A), dev(p.B)
+        X = lls.empty_colmajor(1000, 1)
+        t = lls.lls_submit(h, lls.make_problem(A, B, p.tol, X, keep_factor=1))
+        fid = None
+        t0 = time.time()
+        while fid is None:
+            fid = lls.lls_ticket_factor(h, t)
+            assert time.time() - t0 < 60
+            time.sleep(0.005)
+        assert lls.lls_poll(h, t) == 0
+        # new right-hand sides against the resident factor, several at once
+        Bs = [np.random.default_rng(s).standard_normal((2000, 2)) for s in range(3)]
+        held, tickets = [], []
+        for b in Bs:
+            Bd, Xd = dev(b), lls.empty_colmajor(1000, 2)
+            held.append((Bd, Xd))
+            tickets.append(lls.lls_submit(h, lls.make_problem(None, Bd, p.tol, Xd, factor_id=fid)))
+        st = wait_all(lls, h, tickets)
+        assert all(v == 0 for v in st.values())
+        for b, (_, Xd) in zip(Bs, held):
+            ref = lls.lls_solve_factored(h, fid, dev(b), 1000)
+            assert torch.equal(Xd, ref)
+            xr = np.reshape(orc.solve(p.A, b, 1, 64, p.tol, 2001).x, (1000, 2))
+            assert np.linalg.norm(Xd.cpu().numpy() - xr) / np.linalg.norm(xr) < 1e-9
+        # a cap smaller than one request: rejected at submit; a small cap runs one at a time
+        lls.lls_set_memory_cap(h, 1 << 20)
+        with pytest.raises(lls.LLSError) as e:
+            lls.lls_submit(h, lls.make_problem(A, B, p.tol, X))
+        assert e.value.status == lls.LLS_ERR_CAPACITY
+        lls.lls_set_memory_cap(h, 40 << 20)
+        bufs = [(dev(q.A), dev(q.B), lls.empty_colmajor(q.A.shape[1], q.B.shape[1]), q.tol)
+                for q in problems(3, 5)]
+        ts = [lls.lls_submit(h, lls.make_problem(a, b, tol, x)) for a, b, x, tol in bufs]
+        assert all(v == 0 for v in wait_all(lls, h, ts).values())
+    finally:
+        lls.lls_destroy(h)

@@ -306,3 +306,14 @@ def test_solution_orthogonal_to_nullspace():
     sol = orc.solve(A, b, 1, 16, 1e-10 * wl.norm2_of_product(X, Y), seed=4)
     N0 = np.linalg.svd(A)[2][25:].T  # trailing right singular vectors
     assert np.linalg.norm(N0.T @ sol.x) / np.linalg.norm(sol.x) < 1e-12
+
+
+def test_pinv_from_factors_equals_svd_pinv():
+    """The factor-based pseudoinverse used at full size equals the SVD-based
+    one on a matrix built from the same factors."""
+    sigma = wl.step_spectrum(120, 60, 6.0, 1e-15)
+    A, Q1, Q2 = wl.spectrum_matrix(150, 120, sigma, seed=3)
+    B = np.random.default_rng(1).standard_normal((150, 4))
+    x1 = orc.pinv_solve_from_factors(Q1, sigma, Q2, B, 60)
+    x2 = orc.pinv_solve(A, B, 60)
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x2) < 1e-9
