@@ -255,6 +255,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+// v * 2^p as an FP64 for an int64 |v| < 2^53, assembled from bits (exact;
+// returns false when the result would leave the normal range).
+__device__ __forceinline__ bool i64_scaled(long long v, int p, double& out) {
+  if (v == 0) {
+    out = 0.0;
+    return true;
+  }
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int e = 63 - __clzll((long long)a);  // a in [2^e, 2^(e+1)), e <= 52
+  const int be = e + p + 1023;
+  if (be <= 0 || be >= 2047) return false;
+  const unsigned long long mant = (a << (52 - e)) & ((1ull << 52) - 1);
+  out = __longlong_as_double((long long)(((unsigned long long)be << 52) | mant |
+                                         (v < 0 ? (1ull << 63) : 0ull)));
+  return true;
+}
+
 __device__ __forceinline__ double pow2(int k) {
   if (k < -1022) return 0.0;
   if (k > 1023) k = 1023;
@@ -382,6 +399,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const bool row_ok = i < a.M;
     const int ei = row_ok ? a.expX[i] : kZeroExp;
     for (int g = 0; g < OZ_BN / 16; ++g) {
+      // H = ((a0 128 + a1) 128 + a2) 128 + a3 and the same for a4..a7: the
+      // diagonals are read from the highest weight down (Horner in int64)
       long long H[16], L[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) H[c] = L[c] = 0;
@@ -392,9 +411,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          long long v = (long long)__float2ll_rn(__uint_as_float(r[c]));
-          if (d < 4) H[c] += v * (1LL << (7 * (3 - d)));
-          else L[c] += v * (1LL << (7 * (7 - d)));
+          const long long v = (long long)__float2int_rn(__uint_as_float(r[c]));
+          if (d < 4) H[c] = H[c] * 128 + v;
+          else L[c] = L[c] * 128 + v;
         }
       }
       if (!row_ok) continue;
@@ -413,12 +432,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           continue;
         }
         const int sc = ei + fj;
-        const double v = fma((double)H[c], pow2(sc - 35), (double)L[c] * pow2(sc - 63));
+        double hs, ls;
+        double v;
+        if (i64_scaled(H[c], sc - 35, hs) && i64_scaled(L[c], sc - 63, ls)) v = hs + ls;
+        else v = fma((double)H[c], pow2(sc - 35), (double)L[c] * pow2(sc - 63));
         if (a.part) {
           a.part[(int64_t)blockIdx.z * a.M * a.N + i + (int64_t)j * a.M] = v;
         } else {
           double* cp = a.transC ? a.C + j + (int64_t)i * a.ldc : a.C + i + (int64_t)j * a.ldc;
-          *cp = (a.beta == 0.0) ? a.alpha * v : fma(a.alpha, v, a.beta * *cp);
+          if (a.beta == 0.0) *cp = a.alpha * v;
+          else if (a.beta == 1.0) *cp = fma(a.alpha, v, *cp);
+          else *cp = fma(a.alpha, v, a.beta * *cp);
         }
       }
     }
