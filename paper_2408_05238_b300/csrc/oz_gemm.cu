@@ -18,9 +18,14 @@
 //     K entries per CTA every accumulator stays below 2^24: the FP32 sums
 //     are exact integers.  Terms with s + t >= 10 are below 2^-55 relative
 //     to the row/column scales and are dropped.
-//  3. The epilogue converts the 8 exact integers to two 64-bit integers
-//     (diagonals 2..5 and 6..9, exact), then to FP64 (exact), and applies
-//     2^(e_i + f_j), alpha and beta.  Longer K is split into 256-wide
+//  3. The epilogue combines the 8 exact integers into two 64-bit integers,
+//     H (diagonals 2..5, unit 2^-35 of the row/column scale 2^(e_i + f_j))
+//     and L (diagonals 6..9, unit 2^-63), and folds them into one,
+//     v = H 2^19 + round(L 2^-9) (unit 2^-54; |H| <= K 2^35 (1 + tiny) with
+//     K <= 256, so |v| < 2^63).  The only roundings are that fold (half a
+//     unit, 2^-55 of the scale) and v -> FP64 (53 bits, to nearest), both at
+//     FP64 GEMM accuracy.  The FP64 value is assembled from bits, then alpha
+//     and beta are applied.  Longer K is split into 256-wide
 //     ranges whose FP64 partial products are summed in a fixed order.
 //
 // Work per FP64 multiply-add: 36 BF16 multiply-adds on the tensor cores and
@@ -45,7 +50,7 @@ constexpr int OZ_BK = 64;         // K per smem tile (128-byte swizzle rows)
 constexpr int OZ_KC = 256;        // K per CTA: keeps every FP32 sum below 2^24
 constexpr int OZ_XST = 5;         // X-tile ring depth (one slice of one K tile each)
 constexpr int OZ_ZST = 2;         // Z ring depth (all 8 slices of one K tile each)
-constexpr int OZ_THREADS = 128;
+constexpr int OZ_THREADS = 256;  // 8 warps: all run the epilogue
 constexpr uint32_t OZ_XBYTES = OZ_BM * OZ_BK * 2;         // 16 KB
 constexpr uint32_t OZ_ZTILE = OZ_BN * OZ_BK * 2;          // 8 KB
 constexpr uint32_t OZ_ZBYTES = OZ_ZTILE * OZ_S;           // 64 KB
@@ -255,19 +260,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-// v * 2^p as an FP64 for an int64 |v| < 2^53, assembled from bits (exact;
-// returns false when the result would leave the normal range).
+// v * 2^p as an FP64, assembled from bits: v rounded to 53 significant bits
+// (to nearest, ties to even), then the exponent set directly.  Returns false
+// when the result would leave the normal range.
 __device__ __forceinline__ bool i64_scaled(long long v, int p, double& out) {
   if (v == 0) {
     out = 0.0;
     return true;
   }
-  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-  const int e = 63 - __clzll((long long)a);  // a in [2^e, 2^(e+1)), e <= 52
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  int e = 63 - __clzll((long long)a);  // a in [2^e, 2^(e+1))
+  unsigned long long mant;
+  if (e <= 52) {
+    mant = a << (52 - e);
+  } else {
+    const int sh = e - 52;
+    mant = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++e;
+      }
+    }
+  }
   const int be = e + p + 1023;
   if (be <= 0 || be >= 2047) return false;
-  const unsigned long long mant = (a << (52 - e)) & ((1ull << 52) - 1);
-  out = __longlong_as_double((long long)(((unsigned long long)be << 52) | mant |
+  out = __longlong_as_double((long long)(((unsigned long long)be << 52) |
+                                         (mant & ((1ull << 52) - 1)) |
                                          (v < 0 ? (1ull << 63) : 0ull)));
   return true;
 }
@@ -301,6 +322,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __shared__ __align__(8) uint64_t xfull[OZ_XST], xempty[OZ_XST], zfull[OZ_ZST], zempty[OZ_ZST];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t s_tmem;
+
+  __shared__ int s_ex[OZ_BM], s_fz[OZ_BN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
@@ -387,62 +410,77 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (ok) mma_commit(&zempty[zs]);
     }
     if (ok) mma_commit(&done_bar);
+  } else if (warp >= 2) {
+    // exponents of this tile's rows and columns, staged while the MMAs run
+    for (int t = threadIdx.x - 64; t < OZ_BM + OZ_BN; t += OZ_THREADS - 64) {
+      if (t < OZ_BM) s_ex[t] = (m0 + t < a.M) ? a.expX[m0 + t] : kZeroExp;
+      else s_fz[t - OZ_BM] = (n0 + t - OZ_BM < a.N) ? a.expZ[n0 + t - OZ_BM] : kZeroExp;
+    }
   }
 
-  // ---- epilogue: exact integers -> FP64
+  // ---- epilogue: exact integers -> FP64.  Warp w reads TMEM lanes
+  // 32 (w mod 4) .. +31 (its rows) and column groups 2 (w / 4), +1.
   __syncwarp();
   bool ready = nkb > 0 && mbar_wait(&done_bar, 0, a.err);
   ready = __all_sync(0xffffffffu, ready);
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ready) {
-    const int i = m0 + warp * 32 + lane;
+    const int q = warp & 3;
+    const int il = q * 32 + lane;
+    const int i = m0 + il;
     const bool row_ok = i < a.M;
-    const int ei = row_ok ? a.expX[i] : kZeroExp;
-    for (int g = 0; g < OZ_BN / 16; ++g) {
-      // H = ((a0 128 + a1) 128 + a2) 128 + a3 and the same for a4..a7: the
-      // diagonals are read from the highest weight down (Horner in int64)
-      long long H[16], L[16];
+    const int ei = s_ex[il];
+    const bool use_c = a.part == nullptr && a.beta != 0.0;
+    for (int g = (warp >> 2) * 2; g < (warp >> 2) * 2 + 2; ++g) {
+      const int jb = n0 + g * 16;
+      // C of the 16 columns first: independent loads in flight during the TMEM reads
+      double cv[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) H[c] = L[c] = 0;
+      for (int c = 0; c < 16; ++c) {
+        cv[c] = 0.0;
+        if (use_c && row_ok && jb + c < a.N)
+          cv[c] = a.transC ? a.C[jb + c + (int64_t)i * a.ldc] : a.C[i + (int64_t)(jb + c) * a.ldc];
+      }
+      long long V[16];
 #pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * OZ_BN + g * 16), r);
+      for (int half = 0; half < 2; ++half) {
+        uint32_t r[4][16];
+#pragma unroll
+        for (int dd = 0; dd < 4; ++dd)
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((half * 4 + dd) * OZ_BN + g * 16),
+                    r[dd]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const long long v = (long long)__float2int_rn(__uint_as_float(r[c]));
-          if (d < 4) H[c] = H[c] * 128 + v;
-          else L[c] = L[c] * 128 + v;
+          // |acc| <= 10.5e6 < 2^24: each pair a 128 + b fits in int32
+          const int a0 = __float2int_rn(__uint_as_float(r[0][c]));
+          const int a1 = __float2int_rn(__uint_as_float(r[1][c]));
+          const int a2 = __float2int_rn(__uint_as_float(r[2][c]));
+          const int a3 = __float2int_rn(__uint_as_float(r[3][c]));
+          const long long w = (long long)(a0 * 128 + a1) * 16384 + (a2 * 128 + a3);
+          if (half == 0) V[c] = w * (1LL << 19);
+          else V[c] += (w + (1LL << 8)) >> 9;
         }
       }
       if (!row_ok) continue;
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        const int j = n0 + g * 16 + c;
+        const int j = jb + c;
         if (j >= a.N) continue;
-        const int fj = a.expZ[j];
-        if (ei == kZeroExp || fj == kZeroExp) {
-          // exact zero product
-          if (a.part) a.part[(int64_t)blockIdx.z * a.M * a.N + i + (int64_t)j * a.M] = 0.0;
-          else {
-            double* cp = a.transC ? a.C + j + (int64_t)i * a.ldc : a.C + i + (int64_t)j * a.ldc;
-            *cp = (a.beta == 0.0) ? 0.0 : a.beta * *cp;
-          }
-          continue;
+        const int fj = s_fz[g * 16 + c];
+        double v = 0.0;
+        if (ei != kZeroExp && fj != kZeroExp) {
+          const int p = ei + fj - 54;
+          if (!i64_scaled(V[c], p, v)) v = (double)V[c] * pow2(p / 2) * pow2(p - p / 2);
         }
-        const int sc = ei + fj;
-        double hs, ls;
-        double v;
-        if (i64_scaled(H[c], sc - 35, hs) && i64_scaled(L[c], sc - 63, ls)) v = hs + ls;
-        else v = fma((double)H[c], pow2(sc - 35), (double)L[c] * pow2(sc - 63));
         if (a.part) {
           a.part[(int64_t)blockIdx.z * a.M * a.N + i + (int64_t)j * a.M] = v;
         } else {
           double* cp = a.transC ? a.C + j + (int64_t)i * a.ldc : a.C + i + (int64_t)j * a.ldc;
           if (a.beta == 0.0) *cp = a.alpha * v;
-          else if (a.beta == 1.0) *cp = fma(a.alpha, v, *cp);
-          else *cp = fma(a.alpha, v, a.beta * *cp);
+          else if (a.beta == 1.0) *cp = fma(a.alpha, v, cv[c]);
+          else *cp = fma(a.alpha, v, a.beta * cv[c]);
         }
       }
     }
