@@ -104,7 +104,7 @@ int lls_k_gemm_oz(int transa, int transb, int unit_lower_a, int unit_lower_b,
  * library convenience.
  *
  * The kernel's scratch (grid-barrier words and per-CTA partial sums) lives
- * in one fixed array of the library (under 270 KB, held by every GPU that
+ * in one fixed array of the library (under 520 KB, held by every GPU that
  * loads the library until the process exits), so this call allocates
  * nothing.  n may be at most 128; larger n returns LLS_ERR_CAPACITY and
  * launches nothing.  status is a caller-owned device int: it is set to 0 and

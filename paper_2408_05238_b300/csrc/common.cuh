@@ -54,14 +54,13 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // ---------------------------------------------------------------------------
 // Device-side grid barrier for cooperative launches.  Every waiting CTA
 // spins with a bounded number of polls; on running out it raises *err and
-// returns false, so a kernel can exit instead of hanging.  The state is two
-// words (arrival count, generation) that must be zero before the launch.
+// returns false, so a kernel can exit instead of hanging.  The state is one
+// arrival-count word that must be zero before the launch.
 // ---------------------------------------------------------------------------
 constexpr long long kBarrierSpinLimit = 1LL << 22;  // a few seconds of polling at most
 
 struct GridBarrier {
   unsigned int* count;
-  unsigned int* gen;
   int* err;
 };
 
@@ -72,28 +71,33 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
+// Grid-wide barrier on a monotonically increasing arrival counter (reset to
+// 0 before each launch; a launch passes at most 2^31 / CTAs barriers): CTA
+// thread 0 adds 1 with release semantics and waits, with acquire loads,
+// until the counter reaches the next multiple of the CTA count.  The wait is
+// bounded (kBarrierSpinLimit polls); on expiry, or when another CTA has
+// already failed, it sets *err and every thread of the CTA gets false.
 __device__ inline bool grid_sync(const GridBarrier& bar) {
   __syncthreads();
   __shared__ int s_fail;
   if (threadIdx.x == 0) {
     s_fail = 0;
-    unsigned int g = ld_volatile_u32(bar.gen);
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
     __threadfence();
-    unsigned int arrived = atomicAdd(bar.count, 1u);
-    if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
-      atomicExch(bar.count, 0u);
-      __threadfence();
-      atomicAdd(bar.gen, 1u);
-    } else {
-      long long it = 0;
-      while (ld_volatile_u32(bar.gen) == g) {
-        if (++it > kBarrierSpinLimit || ld_volatile_i32(bar.err) != 0) {
-          atomicExch(bar.err, 1);
-          s_fail = 1;
-          break;
-        }
-        __nanosleep(20);
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar.count) : "memory");
+    const unsigned int target = (old / nb + 1) * nb;
+    long long it = 0;
+    for (;;) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar.count) : "memory");
+      if ((int)(cur - target) >= 0) break;
+      if (++it > kBarrierSpinLimit || ((it & 255) == 0 && ld_volatile_i32(bar.err) != 0)) {
+        atomicExch(bar.err, 1);
+        s_fail = 1;
+        break;
       }
+      if (it > 4096) __nanosleep(64);
     }
     __threadfence();
   }

@@ -3,17 +3,24 @@
 //
 // The panel (m x n, n <= nb) is factored one column at a time, as in
 // Golub & Van Loan Alg. 5.2.1, by G cooperating CTAs, each owning a
-// contiguous slab of rows.  Per column j:
-//   1. the squared norm of A(j+1:m, j) is summed per CTA and across CTAs;
-//   2. every CTA derives beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta
-//      and the scaled vector v for its rows (LAPACK xLARFG convention,
-//      tau = 0 when the column below the diagonal is zero), then forms its
-//      part of the dot products v^T A(:, c) for the columns c > j;
-//   3. the dot products are reduced across CTAs (CTA c mod G owns column c)
-//      and every CTA updates its rows: A(:, c) -= tau (v^T A(:, c)) v.
-// Reductions run in a fixed order, so every CTA derives bit-identical
-// scalars and repeated runs are bit-identical.  Cross-CTA steps are joined
-// by a bounded grid barrier (common.cuh) inside a cooperative launch.
+// contiguous slab of rows, with reflectors in the LAPACK xLARFG convention
+// (beta = -sign(alpha) ||(alpha, x)||, tau = (beta - alpha) / beta,
+// v = (1, x / (alpha - beta)); tau = 0 when x = 0).
+//
+// Main kernel (panel_qr_slab_kernel): each CTA keeps its slab in shared
+// memory for the whole panel.  Per column j, before a first grid barrier
+// every CTA sums, over its rows below j, x_p^2 and x_p A(p, c) for the
+// columns c > j (x = the column below the diagonal, before scaling), and the
+// owner of row j publishes that row.  Between the first and a second
+// barrier, CTA c mod G adds up column j + c over all CTAs in a fixed order
+// (FP64 instructions are scarce on this part, so no CTA repeats another's
+// sums) and CTA 0 derives beta, tau and the scale of v.  After it every CTA
+// forms w_c = A(j, c) + (x^T A(:, c)) / (alpha - beta) = v^T A(:, c) and
+// updates its rows, A(p, c) -= tau w_c v_p.  Partial sums and rows are
+// double-buffered by column parity, which the barriers make safe.
+//
+// Panels whose slabs do not fit in shared memory use panel_qr_kernel, which
+// works on the panel in global memory with three barriers per column.
 #include <algorithm>
 #include <mutex>
 
@@ -132,6 +139,164 @@ __global__ void __launch_bounds__(PQ_THREADS) panel_qr_kernel(PanelArgs a) {
   }
 }
 
+constexpr int PS_TPC = 4;                  // threads per column
+constexpr int PS_THREADS = 128 * PS_TPC;   // columns per panel <= 128
+
+struct SlabArgs {
+  int64_t m, lda;
+  int n, rows_per, ldsl;
+  double* A;
+  double* tau;
+  GridBarrier bar;
+  double* part;  // [2][n][G]: partial sums, column-major over CTAs
+  double* rowj;  // [2][n]: row j of the panel when column j is eliminated
+  double* totg;  // [2][n + 4]: reduced sums of column j, then tau, beta, scale
+};
+
+// Sum of the PS_TPC threads of one column, in a fixed pairing; commutative
+// adds make the result bit-identical in all of them.
+__device__ __forceinline__ double column_group_sum(double s) {
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  return s;
+}
+
+// Range [b, e) of part q of [lo, hi) split in PS_TPC contiguous pieces.
+__device__ __forceinline__ void quarter(int lo, int hi, int q, int& b, int& e) {
+  const int len = hi > lo ? hi - lo : 0;
+  const int step = (len + PS_TPC - 1) / PS_TPC;
+  b = min(hi, lo + q * step);
+  e = min(hi, b + step);
+  if (b > e) b = e;
+}
+
+__global__ void __launch_bounds__(PS_THREADS) panel_qr_slab_kernel(SlabArgs a) {
+  extern __shared__ double sm[];
+  const int n = a.n, ldsl = a.ldsl;
+  double* slab = sm;                          // ldsl x n, column-major
+  double* tot = slab + (size_t)ldsl * n;      // [n] reduced sums of this column
+  double* roww = tot + n;                     // [n] row j, then tau w_c
+  __shared__ double sc[3];                    // tau, beta, scale of the current column
+  const int G = gridDim.x, cta = blockIdx.x, t = threadIdx.x;
+  const int ci = t / PS_TPC, q = t % PS_TPC;  // column offset and quarter of this thread
+  const int64_t m = a.m;
+  const int64_t r0 = (int64_t)cta * a.rows_per;
+  const int64_t r1 = m < r0 + a.rows_per ? m : r0 + a.rows_per;
+  const int nr = r1 > r0 ? (int)(r1 - r0) : 0;
+  const int kmax = m < (int64_t)n ? (int)m : n;
+
+  for (int idx = t; idx < nr * n; idx += PS_THREADS) {
+    const int p = idx % nr, c = idx / nr;
+    slab[p + c * ldsl] = a.A[r0 + p + (int64_t)c * a.lda];
+  }
+  __syncthreads();
+
+  // Partial sums for column j over this CTA's rows p > j: x^T A(:, j + ci).
+  auto publish = [&](int j) {
+    const int plo = (int)(j + 1 - r0 <= 0 ? 0 : (j + 1 - r0 >= nr ? nr : j + 1 - r0));
+    const int ncol = n - j;
+    double s0 = 0.0, s1 = 0.0;
+    if (ci < ncol) {
+      const double* xc = slab + (size_t)j * ldsl;
+      const double* ac = slab + (size_t)(j + ci) * ldsl;
+      int pb, pe;
+      quarter(plo, nr, q, pb, pe);
+      int p = pb;
+      for (; p + 1 < pe; p += 2) {
+        s0 = fma(xc[p], ac[p], s0);
+        s1 = fma(xc[p + 1], ac[p + 1], s1);
+      }
+      if (p < pe) s0 = fma(xc[p], ac[p], s0);
+    }
+    const double s = column_group_sum(s0 + s1);
+    double* P = a.part + (size_t)(j & 1) * n * G;
+    if (ci < ncol && q == 0) P[(size_t)(j + ci) * G + cta] = s;
+    if (r0 <= j && j < r0 + nr && t < ncol)
+      a.rowj[(size_t)(j & 1) * n + j + t] = slab[(j - r0) + (size_t)(j + t) * ldsl];
+  };
+
+  if (kmax > 0) publish(0);
+  const int warp = t >> 5, lane = t & 31;
+  for (int j = 0; j < kmax; ++j) {
+    if (!grid_sync(a.bar)) return;  // partial sums of column j are in
+    const int ncol = n - j;
+    // ---- column j + c is reduced by CTA c mod G, one warp per column, over
+    // the CTAs in a fixed order; CTA 0 also derives the reflector.
+    {
+      const double* P = a.part + (size_t)(j & 1) * n * G;
+      double* TG = a.totg + (size_t)(j & 1) * (n + 4);
+      for (int c = cta + warp * G; c < ncol; c += G * (PS_THREADS / 32)) {
+        const double* src = P + (size_t)(j + c) * G;
+        double v[5];
+#pragma unroll
+        for (int u = 0; u < 5; ++u) v[u] = (lane + 32 * u < G) ? __ldcg(src + lane + 32 * u) : 0.0;
+        double s = v[0];
+#pragma unroll
+        for (int u = 1; u < 5; ++u)
+          if (lane + 32 * u < G) s += v[u];
+        for (int g = lane + 160; g < G; g += 32) s += __ldcg(src + g);
+        s = warp_sum(s);
+        if (lane == 0) {
+          TG[j + c] = s;
+          if (c == 0) {
+            const double alpha = __ldcg(a.rowj + (size_t)(j & 1) * n + j);
+            double tau = 0.0, beta = alpha, scale = 0.0;
+            if (s != 0.0) {
+              beta = -copysign(hypot(alpha, sqrt(s)), alpha);
+              tau = (beta - alpha) / beta;
+              scale = 1.0 / (alpha - beta);
+            }
+            TG[n] = tau;
+            TG[n + 1] = beta;
+            TG[n + 2] = scale;
+          }
+        }
+      }
+    }
+    if (!grid_sync(a.bar)) return;  // totals and the reflector are in
+    {
+      const double* TG = a.totg + (size_t)(j & 1) * (n + 4);
+      if (t < ncol) {
+        tot[j + t] = __ldcg(TG + j + t);
+        roww[j + t] = __ldcg(a.rowj + (size_t)(j & 1) * n + j + t);
+      }
+      if (t < 3) sc[t] = __ldcg(TG + n + t);
+    }
+    __syncthreads();
+    const double tau = sc[0], beta = sc[1], scale = sc[2];
+    for (int c = j + 1 + t; c < n; c += PS_THREADS) roww[c] = tau * fma(scale, tot[c], roww[c]);
+    const int lo = (int)(j - r0 <= 0 ? 0 : (j - r0 >= nr ? nr : j - r0));  // first own row >= j
+    const bool own_j = r0 <= j && j < r0 + nr;
+    for (int p = lo + (own_j ? 1 : 0) + t; p < nr; p += PS_THREADS) slab[p + (size_t)j * ldsl] *= scale;
+    __syncthreads();
+
+    // ---- update of this CTA's rows: A(p, c) -= tau w_c v_p (v_j = 1)
+    if (tau != 0.0 && ci + 1 < ncol) {
+      const int c = j + 1 + ci;
+      const double tw = roww[c];
+      double* ac = slab + (size_t)c * ldsl;
+      const double* vc = slab + (size_t)j * ldsl;
+      int pb, pe;
+      quarter(lo, nr, q, pb, pe);
+      if (own_j && pb == lo && pb < pe) {
+        ac[pb] -= tw;  // row j: v_j = 1
+        ++pb;
+      }
+      for (int p = pb; p < pe; ++p) ac[p] = fma(-tw, vc[p], ac[p]);
+    }
+    __syncthreads();
+    if (own_j && t == 0) slab[lo + (size_t)j * ldsl] = beta;
+    if (cta == 0 && t == 0) a.tau[j] = tau;
+    __syncthreads();
+    if (j + 1 < kmax) publish(j + 1);
+  }
+
+  for (int idx = t; idx < nr * n; idx += PS_THREADS) {
+    const int p = idx % nr, c = idx / nr;
+    a.A[r0 + p + (int64_t)c * a.lda] = slab[p + c * ldsl];
+  }
+}
+
 // T factor of the compact WY form: T(j, j) = tau_j and
 // T(0:j, j) = -tau_j T(0:j, 0:j) S(0:j, j), S = W^T W (Schreiber-Van Loan).
 __global__ void wy_tfactor_kernel(int64_t k, const double* __restrict__ S, int64_t lds,
@@ -150,6 +315,40 @@ __global__ void wy_tfactor_kernel(int64_t k, const double* __restrict__ S, int64
     }
     if (threadIdx.x == 0) T[j + j * ldt] = tj;
     __syncthreads();
+  }
+}
+
+// The same recurrence with T in shared memory (k <= 128): per column j, two
+// threads per row i < j split the sum over l in [i, j) and combine in a
+// fixed order.
+constexpr int TF_MAX = 128;
+
+__global__ void __launch_bounds__(2 * TF_MAX) wy_tfactor_smem_kernel(int k, const double* __restrict__ S,
+                                                                      int64_t lds,
+                                                                      const double* __restrict__ tau,
+                                                                      double* T, int64_t ldt) {
+  extern __shared__ double tsm[];
+  double* Ts = tsm;                   // k x k, leading dimension k
+  double* z = tsm + (size_t)k * k;    // S(0:j, j)
+  const int t = threadIdx.x, i = t >> 1, h = t & 1;
+  for (int j = 0; j < k; ++j) {
+    for (int l = t; l < j; l += blockDim.x) z[l] = S[l + (int64_t)j * lds];
+    __syncthreads();
+    const double tj = tau[j];
+    double s = 0.0;
+    if (i < j) {
+      const int mid = i + (j - i + 1) / 2;
+      const int lb = h ? mid : i, le = h ? j : mid;
+      for (int l = lb; l < le; ++l) s = fma(Ts[i + l * k], z[l], s);
+    }
+    const double other = __shfl_xor_sync(0xffffffffu, s, 1);
+    if (i < j && h == 0) Ts[i + j * k] = -tj * (s + other);
+    if (t == 0) Ts[j + j * k] = tj;
+    __syncthreads();
+  }
+  for (int idx = t; idx < k * k; idx += blockDim.x) {
+    const int r = idx % k, c = idx / k;
+    T[r + (int64_t)c * ldt] = r <= c ? Ts[r + c * k] : 0.0;
   }
 }
 
@@ -180,50 +379,46 @@ CoopGate& coop_gate() {
   return g;
 }
 
-}  // namespace
-
-size_t panel_qr_scratch_bytes(int64_t m, int64_t n) {
-  int G = panel_ctas(m);
-  return 64 + sizeof(double) * ((size_t)G + (size_t)G * n + (size_t)n);
+int max_dyn_smem() {
+  static int bytes = -1;
+  if (bytes < 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      v = 48 * 1024;
+    bytes = v - 1024;  // room for the kernels' static shared memory
+  }
+  return bytes;
 }
 
-Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
-                int* err, cudaStream_t st) {
-  if (m <= 0 || n <= 0) return ok_status();
-  if (scratch.bytes < panel_qr_scratch_bytes(m, n))
-    return make_error(LLS_ERR_NOMEM, "panel_qr: scratch too small");
-  int G = panel_ctas(m);
-  PanelArgs a;
-  a.m = m;
-  a.n = n;
-  a.lda = lda;
-  a.rows_per = ceil_div(m, G);
-  a.A = A;
-  a.tau = tau;
-  char* base = static_cast<char*>(scratch.ptr);
-  a.bar.count = reinterpret_cast<unsigned int*>(base);
-  a.bar.gen = reinterpret_cast<unsigned int*>(base + 4);
-  a.bar.err = err;
-  a.part_ss = reinterpret_cast<double*>(base + 64);
-  a.part_dot = a.part_ss + G;
-  a.dot_final = a.part_dot + (size_t)G * n;
-  size_t smem = sizeof(double) * (size_t)(a.rows_per + n);
-  if (smem > 200 * 1024) return make_error(LLS_ERR_ARG, "panel_qr: panel too tall");
-  LLS_CUDA(cudaMemsetAsync(base, 0, 8, st));
-  if (smem > 48 * 1024)
-    LLS_CUDA(cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-  void* args[] = {&a};
-  int64_t k = std::min(m, n);
-  TraceScope ts(kTrPanelQR, st, 2.0 * m * n * k - 2.0 * k * k * k / 3.0, 16.0 * m * n);
+// Slab layout for the shared-memory kernel: rows per CTA, leading dimension
+// (odd, to spread columns over banks) and dynamic shared memory.
+struct SlabPlan {
+  int G, rows_per, ldsl;
+  size_t smem;
+  bool fits;
+};
+
+SlabPlan slab_plan(int64_t m, int64_t n) {
+  SlabPlan p;
+  p.G = panel_ctas(m);
+  p.rows_per = (int)ceil_div(m, p.G);
+  p.ldsl = p.rows_per | 1;
+  p.smem = sizeof(double) * ((size_t)p.ldsl * n + 2 * (size_t)n);
+  p.fits = n <= PS_THREADS / PS_TPC && p.smem <= (size_t)max_dyn_smem();
+  return p;
+}
+
+// Launches a cooperative kernel behind the library-wide gate.
+Status coop_launch(const void* fn, int G, int threads, void** args, size_t smem,
+                   cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   CoopGate& gate = coop_gate();
   std::lock_guard<std::mutex> lock(gate.mu);
   int dev = 0;
   LLS_CUDA(cudaGetDevice(&dev));
   if (gate.last && gate.device == dev) LLS_CUDA(cudaStreamWaitEvent(st, gate.last, 0));
-  LLS_CUDA(cudaLaunchCooperativeKernel((void*)panel_qr_kernel, dim3(G), dim3(PQ_THREADS), args,
-                                       smem, st));
+  LLS_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(threads), args, smem, st));
   if (gate.last && gate.device != dev) {
     cudaEventDestroy(gate.last);
     gate.last = nullptr;
@@ -236,10 +431,84 @@ Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scrat
   return ok_status();
 }
 
+}  // namespace
+
+size_t panel_qr_scratch_bytes(int64_t m, int64_t n) {
+  int G = panel_ctas(m);
+  size_t global_kernel = (size_t)G + (size_t)G * n + (size_t)n;
+  size_t slab_kernel = 2 * (size_t)G * n + 2 * (size_t)n + 2 * ((size_t)n + 4);
+  return 64 + sizeof(double) * std::max(global_kernel, slab_kernel);
+}
+
+Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
+                int* err, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return ok_status();
+  if (scratch.bytes < panel_qr_scratch_bytes(m, n))
+    return make_error(LLS_ERR_NOMEM, "panel_qr: scratch too small");
+  char* base = static_cast<char*>(scratch.ptr);
+  GridBarrier bar;
+  bar.count = reinterpret_cast<unsigned int*>(base);
+  bar.err = err;
+  double* work = reinterpret_cast<double*>(base + 64);
+  const int64_t k = std::min(m, n);
+  TraceScope ts(kTrPanelQR, st, 2.0 * m * n * k - 2.0 * k * k * k / 3.0, 16.0 * m * n);
+  LLS_CUDA(cudaMemsetAsync(base, 0, 8, st));
+
+  const SlabPlan sp = slab_plan(m, n);
+  if (sp.fits) {
+    SlabArgs a;
+    a.m = m;
+    a.lda = lda;
+    a.n = (int)n;
+    a.rows_per = sp.rows_per;
+    a.ldsl = sp.ldsl;
+    a.A = A;
+    a.tau = tau;
+    a.bar = bar;
+    a.part = work;
+    a.rowj = work + 2 * (size_t)sp.G * n;
+    a.totg = a.rowj + 2 * (size_t)n;
+    if (sp.smem > 48 * 1024)
+      LLS_CUDA(cudaFuncSetAttribute(panel_qr_slab_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem));
+    void* args[] = {&a};
+    return coop_launch((const void*)panel_qr_slab_kernel, sp.G, PS_THREADS, args, sp.smem, st);
+  }
+
+  const int G = panel_ctas(m);
+  PanelArgs a;
+  a.m = m;
+  a.n = n;
+  a.lda = lda;
+  a.rows_per = ceil_div(m, G);
+  a.A = A;
+  a.tau = tau;
+  a.bar = bar;
+  a.part_ss = work;
+  a.part_dot = a.part_ss + G;
+  a.dot_final = a.part_dot + (size_t)G * n;
+  size_t smem = sizeof(double) * (size_t)(a.rows_per + n);
+  if (smem > 200 * 1024) return make_error(LLS_ERR_ARG, "panel_qr: panel too tall");
+  if (smem > 48 * 1024)
+    LLS_CUDA(cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  void* args[] = {&a};
+  return coop_launch((const void*)panel_qr_kernel, G, PQ_THREADS, args, smem, st);
+}
+
 Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, double* T,
                   int64_t ldt, cudaStream_t st) {
   if (k <= 0) return ok_status();
   TraceScope ts(kTrTFactor, st, (double)k * k * k / 3.0, 16.0 * k * k);
+  if (k <= TF_MAX) {
+    const size_t smem = sizeof(double) * ((size_t)k * k + k);
+    if (smem > 48 * 1024)
+      LLS_CUDA(cudaFuncSetAttribute(wy_tfactor_smem_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    wy_tfactor_smem_kernel<<<1, 2 * TF_MAX, smem, st>>>((int)k, S, lds, tau, T, ldt);
+    LLS_LAUNCHED("wy_tfactor_kernel");
+    return ok_status();
+  }
   wy_tfactor_kernel<<<1, 256, 0, st>>>(k, S, lds, tau, T, ldt);
   LLS_LAUNCHED("wy_tfactor_kernel");
   return ok_status();

@@ -2,10 +2,12 @@
 // fixed device array owned by the library, for callers that must not
 // allocate device memory (see include/lls_kernels.h).
 //
-// Scratch use of the panel kernel: two grid-barrier words, one barrier-error
-// word, and per-CTA partial sums (one norm per CTA, one dot product per CTA
-// and column, one reduced dot per column).  With at most 256 CTAs and 128
-// columns that is under 270 KB; the array below holds it.
+// Scratch use of the panel kernels: one grid-barrier word, one barrier-error
+// word, and partial sums -- for the shared-memory kernel two buffers of one
+// value per CTA and column, two copies of one row and two of the column
+// totals; for the global-memory kernel one norm per CTA, one dot product per
+// CTA and column and one reduced dot per column.  With at most 256 CTAs and
+// 128 columns that is under 520 KB; the array below holds it.
 #include <mutex>
 
 #include "internal.h"
@@ -14,7 +16,7 @@
 namespace {
 
 constexpr int64_t kNoAllocMaxCols = 128;
-constexpr size_t kNoAllocBytes = 64 + sizeof(double) * (256 + 256 * 128 + 128);
+constexpr size_t kNoAllocBytes = 64 + sizeof(double) * (2 * 256 * 128 + 4 * 128 + 8);
 
 // Every device that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_panel_scratch[kNoAllocBytes];
