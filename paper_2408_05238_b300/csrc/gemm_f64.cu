@@ -150,16 +150,124 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(int64_t M, int64_t N, int64_t
   }
 }
 
-__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, double alpha,
-                                     const double* __restrict__ partial, double beta,
-                                     double* __restrict__ C, int64_t ldc) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= M * N) return;
-  int64_t i = idx % M, j = idx / M;
+// Narrow outputs (N <= 16: the right-hand sides of the solve, one block
+// column of a factor): a 64 x 64 tile would leave 3/4 of every FMA idle, so
+// these use a 128 x 16 tile, 8 outputs per thread (rows r + 32 a, columns
+// c + 8 b), and split-K deep enough to put every SM to work.
+constexpr int BM2 = 128, BN2 = 16, BK2 = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(NT) dgemm_narrow_kernel(
+    int64_t M, int64_t N, int64_t K, double alpha, const double* __restrict__ A, int64_t lda,
+    int ma, const double* __restrict__ B, int64_t ldb, int mb, double beta,
+    double* __restrict__ C, int64_t ldc, int64_t kchunk, double* __restrict__ partial) {
+  __shared__ double As[BK2][BM2 + 1];
+  __shared__ double Bs[BK2][BN2 + 1];
+  const int t = threadIdx.x;
+  const int r = t & 31, c = t >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * BM2;
+  const int64_t j0 = (int64_t)blockIdx.y * BN2;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = min(K, kbeg + kchunk);
+
+  double ra[8], rb;
+  auto load_tile = [&](int64_t k0) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = TA ? t / 16 + 16 * e : t % 128;
+      const int k = TA ? t % 16 : t / 128 + 2 * e;
+      const int64_t gi = i0 + i, gk = k0 + k;
+      double v = 0.0;
+      if (gi < M && gk < kend) v = TA ? load_op(A, lda, gk, gi, ma) : load_op(A, lda, gi, gk, ma);
+      ra[e] = v;
+    }
+    const int j = TB ? t % 16 : t / 16;
+    const int k = TB ? t / 16 : t % 16;
+    const int64_t gj = j0 + j, gk = k0 + k;
+    rb = 0.0;
+    if (gj < N && gk < kend) rb = TB ? load_op(B, ldb, gj, gk, mb) : load_op(B, ldb, gk, gj, mb);
+  };
+  auto store_tile = [&]() {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (TA) As[t % 16][t / 16 + 16 * e] = ra[e];
+      else As[t / 128 + 2 * e][t % 128] = ra[e];
+    }
+    if (TB) Bs[t / 16][t % 16] = rb;
+    else Bs[t % 16][t / 16] = rb;
+  };
+
+  double acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.0;
+
+  if (kbeg < kend) {
+    load_tile(kbeg);
+    store_tile();
+    __syncthreads();
+    for (int64_t k0 = kbeg; k0 < kend; k0 += BK2) {
+      const bool more = k0 + BK2 < kend;
+      if (more) load_tile(k0 + BK2);
+#pragma unroll
+      for (int kk = 0; kk < BK2; ++kk) {
+        const double b0 = Bs[kk][c], b1 = Bs[kk][c + 8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const double av = As[kk][r + 32 * a];
+          acc[a][0] = fma(av, b0, acc[a][0]);
+          acc[a][1] = fma(av, b1, acc[a][1]);
+        }
+      }
+      __syncthreads();
+      if (more) {
+        store_tile();
+        __syncthreads();
+      }
+    }
+  }
+
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int64_t gj = j0 + c + 8 * b;
+    if (gj >= N) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int64_t gi = i0 + r + 32 * a;
+      if (gi >= M) continue;
+      if (partial) {
+        partial[(int64_t)blockIdx.z * M * N + gi + gj * M] = acc[a][b];
+      } else {
+        double* cp = C + gi + gj * ldc;
+        *cp = (beta == 0.0) ? alpha * acc[a][b] : fma(alpha, acc[a][b], beta * *cp);
+      }
+    }
+  }
+}
+
+// Split-K reduction: 32 outputs per CTA (one per lane), warp w summing
+// splits w, w + 8, ... in order, then the 8 warp sums in order.  The order is
+// fixed, so results do not depend on the launch.
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(int64_t M, int64_t N, int splits,
+                                                            double alpha,
+                                                            const double* __restrict__ partial,
+                                                            double beta, double* __restrict__ C,
+                                                            int64_t ldc) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t MN = M * N;
   double s = 0.0;
-  for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * M * N + idx];
-  double* c = C + i + j * ldc;
-  *c = (beta == 0.0) ? alpha * s : fma(alpha, s, beta * *c);
+  if (idx < MN)
+    for (int z = w; z < splits; z += 8) s += partial[(int64_t)z * MN + idx];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && idx < MN) {
+    double tsum = red[0][lane];
+#pragma unroll
+    for (int u = 1; u < 8; ++u) tsum += red[u][lane];
+    double* cp = C + (idx % M) + (idx / M) * ldc;
+    *cp = (beta == 0.0) ? alpha * tsum : fma(alpha, tsum, beta * *cp);
+  }
 }
 
 __global__ void scale_kernel(int64_t M, int64_t N, double beta, double* C, int64_t ldc) {
@@ -172,21 +280,35 @@ __global__ void scale_kernel(int64_t M, int64_t N, double beta, double* C, int64
 // Enough CTAs to fill 148 SMs several times over: ~3 resident per SM.
 constexpr int64_t kTargetCtas = 148 * 12;
 constexpr int64_t kMinSplitDepth = 512;
+// Narrow tiles: the FP64 pipe is the bound, so ~4 CTAs per SM suffice.
+constexpr int64_t kNarrowTargetCtas = 148 * 4;
+constexpr int64_t kNarrowMinSplitDepth = 2 * BK2;
 
-int choose_splits(int64_t m, int64_t n, int64_t k) {
-  if (m <= 0 || n <= 0 || k <= 0) return 1;
-  int64_t tiles = ceil_div(m, BM) * ceil_div(n, BN);
-  if (tiles >= kTargetCtas || k < 2 * kMinSplitDepth) return 1;
-  int64_t s = ceil_div(kTargetCtas, tiles);
-  s = std::min<int64_t>(s, k / kMinSplitDepth);
-  s = std::min<int64_t>(s, 64);
-  return (int)std::max<int64_t>(s, 1);
+struct GemmPlan {
+  bool narrow;
+  int splits;
+};
+
+GemmPlan plan_gemm(int64_t m, int64_t n, int64_t k) {
+  GemmPlan p{n <= BN2, 1};
+  if (m <= 0 || n <= 0 || k <= 0) return p;
+  const int64_t bm = p.narrow ? BM2 : BM, bn = p.narrow ? BN2 : BN;
+  const int64_t target = p.narrow ? kNarrowTargetCtas : kTargetCtas;
+  const int64_t depth = p.narrow ? kNarrowMinSplitDepth : kMinSplitDepth;
+  const int64_t cap = p.narrow ? 512 : 64;
+  const int64_t tiles = ceil_div(m, bm) * ceil_div(n, bn);
+  if (tiles >= (p.narrow ? 148 : target) || k < 2 * depth) return p;
+  int64_t s = ceil_div(target, tiles);
+  s = std::min<int64_t>(s, k / depth);
+  s = std::min<int64_t>(s, cap);
+  p.splits = (int)std::max<int64_t>(s, 1);
+  return p;
 }
 
 }  // namespace
 
 size_t gemm_scratch_bytes(int64_t m, int64_t n, int64_t k) {
-  int s = choose_splits(m, n, k);
+  int s = plan_gemm(m, n, k).splits;
   return s > 1 ? (size_t)s * (size_t)m * (size_t)n * sizeof(double) : 0;
 }
 
@@ -200,7 +322,8 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
     LLS_LAUNCHED("scale_kernel");
     return ok_status();
   }
-  int splits = choose_splits(m, n, k);
+  const GemmPlan plan = plan_gemm(m, n, k);
+  int splits = plan.splits;
   size_t need = splits > 1 ? (size_t)splits * m * n * sizeof(double) : 0;
   if (need > scratch.bytes) {
     // Not enough scratch: fall back to fewer splits that fit (or none).
@@ -209,15 +332,21 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
   int64_t kchunk = splits > 1 ? ceil_div(ceil_div(k, splits), BK) * BK : k;
   splits = (int)ceil_div(k, kchunk);
   double* partial = splits > 1 ? static_cast<double*>(scratch.ptr) : nullptr;
-  dim3 grid((unsigned)ceil_div(m, BM), (unsigned)ceil_div(n, BN), (unsigned)splits);
+  dim3 grid((unsigned)ceil_div(m, plan.narrow ? BM2 : BM), (unsigned)ceil_div(n, plan.narrow ? BN2 : BN),
+            (unsigned)splits);
   if (grid.y > 65535u) return make_error(LLS_ERR_ARG, "gemm: n too large for grid");
   {
     // algorithmic work: 2 m n k flops; bytes: op(A), op(B) once, C read + written
     TraceScope ts(kTrGemm, st, 2.0 * m * n * k,
                   8.0 * ((double)m * k + (double)k * n + (beta == 0.0 ? 1.0 : 2.0) * m * n));
 #define LLS_GEMM_CASE(TA_, TB_)                                                              \
-  dgemm_kernel<TA_, TB_><<<grid, NT, 0, st>>>(m, n, k, alpha, A, lda, (int)ma, B, ldb,        \
-                                              (int)mb, beta, C, ldc, kchunk, partial)
+  if (plan.narrow)                                                                           \
+    dgemm_narrow_kernel<TA_, TB_><<<grid, NT, 0, st>>>(m, n, k, alpha, A, lda, (int)ma, B,    \
+                                                       ldb, (int)mb, beta, C, ldc, kchunk,    \
+                                                       partial);                              \
+  else                                                                                       \
+    dgemm_kernel<TA_, TB_><<<grid, NT, 0, st>>>(m, n, k, alpha, A, lda, (int)ma, B, ldb,      \
+                                                (int)mb, beta, C, ldc, kchunk, partial)
   if (!ta && !tb) LLS_GEMM_CASE(false, false);
   else if (!ta && tb) LLS_GEMM_CASE(false, true);
   else if (ta && !tb) LLS_GEMM_CASE(true, false);
@@ -227,8 +356,8 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
   }
   if (partial) {
     TraceScope ts(kTrSplitK, st, (double)splits * m * n, 8.0 * (splits + 2.0) * m * n);
-    splitk_reduce_kernel<<<(unsigned)ceil_div(m * n, 256), 256, 0, st>>>(m, n, splits, alpha,
-                                                                        partial, beta, C, ldc);
+    splitk_reduce_kernel<<<(unsigned)ceil_div(m * n, 32), 256, 0, st>>>(m, n, splits, alpha,
+                                                                       partial, beta, C, ldc);
     LLS_LAUNCHED("splitk_reduce_kernel");
   }
   return ok_status();

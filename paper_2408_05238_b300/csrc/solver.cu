@@ -125,6 +125,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       need = std::max(need, oz_gemm_workspace_bytes(m, np, b));
       need = std::max(need, oz_gemm_workspace_bytes(b, np - b, mp));
       need = std::max(need, oz_gemm_workspace_bytes(mp, np - b, b));
+      need = std::max(need, oz_gemm_workspace_bytes(b, b, std::max(np, mp)));  // Gram W^T W
+      need = std::max(need, oz_gemm_workspace_bytes(k, b, b));                 // A01 V_SVD
     }
     LLS_TRY(h.oz_ws.reserve(need));
   }
@@ -168,8 +170,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     }
     // ---- a3: [Y, T_V, W_V] = unpivoted_QR(Y)
     LLS_TRY(panel_qr(np, b, Y, ldw, tauVi, pws, &ds->barrier_err, st));
-    LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, b, b, np, 1.0, Y, ldw, Y, ldw, 0.0, h.S.d(),
-                 nb, gws, st));
+    LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, b, b, np, 1.0, Y, ldw, Y, ldw, 0.0, h.S.d(),
+                  nb));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauVi, TVi, nb, st));
     // ---- a4: T(:, k:n) <- T(:, k:n) - (T(:, k:n) W_V) T_V W_V^T, all m rows
     double* Tk = T + k * ldt;
@@ -182,8 +184,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     // ---- a5: [[A11; A21], T_U, W_U] = unpivoted_QR([A11; A21])
     LLS_TRY(panel_qr(mp, b, ABR, ldt, tauUi, pws, &ds->barrier_err, st));
     LLS_TRY(copy_upper(b, ABR, ldt, f.Rblk.d() + i * blk, nb, st));
-    LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, b, b, mp, 1.0, ABR, ldt, ABR, ldt, 0.0,
-                 h.S.d(), nb, gws, st));
+    LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, b, b, mp, 1.0, ABR, ldt, ABR, ldt, 0.0,
+                  h.S.d(), nb));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauUi, TUi, nb, st));
     // ---- a6: [A12; A22] <- (I - W_U T_U W_U^T)^T [A12; A22]
     if (np > b) {
@@ -207,8 +209,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     const int64_t k = f.ks[i], b = f.bs[i];
     LLS_TRY(set_diag_block(b, f.sigma.d() + i * nb, T + k + k * ldt, ldt, st));
     if (k > 0) {  // A01 <- A01 V_SVD
-      LLS_TRY(gemm(false, false, kDense, kDense, k, b, b, 1.0, T + k * ldt, ldt,
-                   f.VS.d() + i * blk, nb, 0.0, h.P.d(), k, gws, st));
+      LLS_TRY(xgemm(false, false, kDense, kDense, k, b, b, 1.0, T + k * ldt, ldt,
+                    f.VS.d() + i * blk, nb, 0.0, h.P.d(), k));
       LLS_TRY(copy_matrix(k, b, h.P.d(), k, T + k * ldt, ldt, st));
     }
   }
@@ -216,8 +218,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     const int64_t k = f.ks[i], b = f.bs[i], np = n - k;
     if (np > b) {  // A12 <- U_SVD^T A12
       double* A12 = T + k + (k + b) * ldt;
-      LLS_TRY(gemm(true, false, kDense, kDense, b, np - b, b, 1.0, f.US.d() + i * blk, nb, A12, ldt,
-                   0.0, h.Q.d(), nb, gws, st));
+      LLS_TRY(xgemm(true, false, kDense, kDense, b, np - b, b, 1.0, f.US.d() + i * blk, nb, A12,
+                    ldt, 0.0, h.Q.d(), nb));
       LLS_TRY(copy_matrix(b, np - b, h.Q.d(), nb, A12, ldt, st));
     }
   }
@@ -285,8 +287,9 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       double* tz = f.RzTau.d() + bl.off_tau;
       LLS_TRY(rz_gather(bsz, L, T, ldt, j0, r, M, ldm, st));
       LLS_TRY(panel_qr(ldm, bsz, M, ldm, tz, pws, &ds->barrier_err, st));
-      LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, bsz, bsz, ldm, 1.0, M, ldm, M, ldm, 0.0,
-                   h.S.d(), nb, gws, st));
+      if (tc) LLS_TRY(h.oz_ws.reserve(oz_gemm_workspace_bytes(bsz, bsz, ldm)));
+      LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, bsz, bsz, ldm, 1.0, M, ldm, M, ldm, 0.0,
+                    h.S.d(), nb));
       LLS_TRY(wy_tfactor(bsz, h.S.d(), nb, tz, Tz, bsz, st));
       LLS_TRY(rz_scatter(bsz, M, ldm, T, ldt, j0, r, L, st));
       if (j0 > 0) {
@@ -298,10 +301,11 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
         LLS_TRY(copy_matrix(j0, bsz, Xc, j0, h.P.d(), j0, st));
         if (tc) LLS_TRY(h.oz_ws.reserve(std::max(oz_gemm_workspace_bytes(j0, bsz, L),
                                                   oz_gemm_workspace_bytes(j0, L, bsz))));
+        if (tc) LLS_TRY(h.oz_ws.reserve(oz_gemm_workspace_bytes(j0, bsz, bsz)));
         LLS_TRY(xgemm(false, false, kDense, kDense, j0, bsz, L, 1.0, D0, ldt, Wbot, ldm, 1.0,
                       h.P.d(), j0));
-        LLS_TRY(gemm(false, false, kDense, kDense, j0, bsz, bsz, 1.0, h.P.d(), j0, Tz, bsz, 0.0,
-                     h.P2.d(), j0, gws, st));
+        LLS_TRY(xgemm(false, false, kDense, kDense, j0, bsz, bsz, 1.0, h.P.d(), j0, Tz, bsz, 0.0,
+                      h.P2.d(), j0));
         LLS_TRY(xgemm(false, true, kDense, kDense, j0, L, bsz, -1.0, h.P2.d(), j0, Wbot, ldm, 1.0,
                       D0, ldt));
         // C01 (reversed) -= P2 W_top^T with W_top = I, then reversed back into T

@@ -38,7 +38,8 @@ def test_sketch_matches_oracle(lls, rows, cols, step):
 
 # ------------------------------------------------------------------- GEMM
 @pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
-@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (67, 45, 33), (130, 129, 4000), (64, 64, 16)])
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (67, 45, 33), (130, 129, 4000), (64, 64, 16),
+                                   (300, 16, 5000), (5000, 3, 128), (129, 9, 777), (128, 16, 20000)])
 def test_gemm_all_transposes(lls, ta, tb, m, n, k):
     g = np.random.default_rng(m * 7 + n + k)
     A = g.standard_normal((k, m) if ta else (m, k))
@@ -58,6 +59,12 @@ def test_gemm_split_k_is_deterministic(lls):
     r2 = host(lls.lls_k_gemm(1, 0, a, b))
     assert np.array_equal(r1, r2)
     assert np.allclose(r1, A.T @ Gm, rtol=0, atol=1e-12 * np.abs(A.T @ Gm).max())
+    # narrow outputs (n <= 16) take their own tile and a deeper split
+    Bn = Gm[:, :16]
+    n1 = host(lls.lls_k_gemm(1, 0, a, dev(Bn)))
+    n2 = host(lls.lls_k_gemm(1, 0, a, dev(Bn)))
+    assert np.array_equal(n1, n2)
+    assert np.allclose(n1, A.T @ Bn, rtol=0, atol=1e-12 * np.abs(A.T @ Bn).max())
 
 
 @pytest.mark.parametrize("ta", [0, 1])
