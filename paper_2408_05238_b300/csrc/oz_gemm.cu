@@ -50,7 +50,7 @@ constexpr int OZ_BK = 64;         // K per smem tile (128-byte swizzle rows)
 constexpr int OZ_KC = 256;        // K per CTA: keeps every FP32 sum below 2^24
 constexpr int OZ_XST = 5;         // X-tile ring depth (one slice of one K tile each)
 constexpr int OZ_ZST = 2;         // Z ring depth (all 8 slices of one K tile each)
-constexpr int OZ_THREADS = 256;  // 8 warps: all run the epilogue
+constexpr int OZ_THREADS = 512;  // 16 warps: all run the epilogue
 constexpr uint32_t OZ_XBYTES = OZ_BM * OZ_BK * 2;         // 16 KB
 constexpr uint32_t OZ_ZTILE = OZ_BN * OZ_BK * 2;          // 8 KB
 constexpr uint32_t OZ_ZBYTES = OZ_ZTILE * OZ_S;           // 64 KB
@@ -136,6 +136,53 @@ __global__ void oz_slice_kcontig_kernel(int64_t R, int64_t K, const double* __re
 #pragma unroll
       for (int s = 0; s < OZ_S; ++s) out[s * plane + r * ldk + k] = __int2bfloat16_rn(d[s]);
     }
+  }
+}
+
+// K-contiguous operand by chunks: grid (K chunks of OZ_KCH, rows), so a
+// handful of long rows (the b x K reflector blocks) still fills the GPU.
+// Pass 1: per-row maximum of |Op(r, k)|, one atomicMax per chunk.
+constexpr int OZ_KCH = 1024;
+
+__global__ void __launch_bounds__(256) oz_rowmax_kcontig_kernel(int64_t R, int64_t K,
+                                                                 const double* __restrict__ src,
+                                                                 int64_t ld, int ul,
+                                                                 unsigned long long* __restrict__ mx) {
+  __shared__ unsigned long long red[8];
+  const int64_t r = blockIdx.y;
+  const int64_t k0 = (int64_t)blockIdx.x * OZ_KCH;
+  unsigned long long m = 0;
+  for (int64_t k = k0 + threadIdx.x; k < min(K, k0 + OZ_KCH); k += 256) {
+    const unsigned long long b = abs_bits(op_load(src, ld, true, ul != 0, r, k));
+    m = b > m ? b : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = red[w] > m ? red[w] : m;
+    if (m) atomicMax(mx + r, m);
+  }
+}
+
+// Pass 2 (after oz_exps_kernel): the digits of one chunk of one row; each
+// plane's stores are contiguous in k.
+__global__ void __launch_bounds__(256) oz_slice_kcontig_chunk_kernel(
+    int64_t R, int64_t K, const double* __restrict__ src, int64_t ld, int ul,
+    const int* __restrict__ exps, __nv_bfloat16* __restrict__ out, int64_t ldk) {
+  const int64_t r = blockIdx.y;
+  const int64_t k0 = (int64_t)blockIdx.x * OZ_KCH;
+  const int e = exps[r];
+  const int64_t plane = R * ldk;
+  for (int64_t k = k0 + threadIdx.x; k < min(ldk, k0 + OZ_KCH); k += 256) {
+    int d[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < K) make_digits(op_load(src, ld, true, ul != 0, r, k), e, d);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) out[s * plane + r * ldk + k] = __int2bfloat16_rn(d[s]);
   }
 }
 
@@ -251,6 +298,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -260,36 +313,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-// v * 2^p as an FP64, assembled from bits: v rounded to 53 significant bits
-// (to nearest, ties to even), then the exponent set directly.  Returns false
-// when the result would leave the normal range.
+// v * 2^p as an FP64, assembled from bits with integer operations only (FP64
+// arithmetic and conversions are scarce on this part): |v| is normalised so
+// its top bit is bit 63, rounded to 53 bits (to nearest, ties away from
+// zero; a carry out of the mantissa lands in the exponent), and the exponent
+// set directly.  Returns false when the result would leave the normal range.
 __device__ __forceinline__ bool i64_scaled(long long v, int p, double& out) {
-  if (v == 0) {
+  const unsigned long long sgn = (unsigned long long)(v >> 63);
+  const unsigned long long a = ((unsigned long long)v ^ sgn) - sgn;
+  if (a == 0) {
     out = 0.0;
     return true;
   }
-  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  int e = 63 - __clzll((long long)a);  // a in [2^e, 2^(e+1))
-  unsigned long long mant;
-  if (e <= 52) {
-    mant = a << (52 - e);
-  } else {
-    const int sh = e - 52;
-    mant = a >> sh;
-    const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant >> 53) {
-        mant >>= 1;
-        ++e;
-      }
-    }
-  }
-  const int be = e + p + 1023;
-  if (be <= 0 || be >= 2047) return false;
-  out = __longlong_as_double((long long)(((unsigned long long)be << 52) |
-                                         (mant & ((1ull << 52) - 1)) |
-                                         (v < 0 ? (1ull << 63) : 0ull)));
+  const int lz = __clzll((long long)a);
+  const unsigned long long norm = a << lz;                       // bit 63 set
+  const unsigned long long mant = (norm >> 11) + ((norm >> 10) & 1ull);  // 2^52 .. 2^53
+  const int be = 63 - lz + p + 1023;                              // biased exponent
+  if ((unsigned)(be - 1) >= 2045u) return false;
+  out = __longlong_as_double(
+      (long long)((((unsigned long long)(be - 1)) << 52) + mant + (sgn << 63)));
   return true;
 }
 
@@ -297,6 +339,12 @@ __device__ __forceinline__ double pow2(int k) {
   if (k < -1022) return 0.0;
   if (k > 1023) k = 1023;
   return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// Out-of-range exponents (results near under/overflow): rarely taken, kept
+// out of line so the common path carries no FP64 conversion.
+__device__ __noinline__ double slow_scaled(long long v, int p) {
+  return (double)v * pow2(p / 2) * pow2(p - p / 2);
 }
 
 struct OzArgs {
@@ -387,25 +435,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         ok = false;
         break;
       }
-      const uint32_t zaddr = smem_u32(zring + zs * OZ_ZBYTES);
-      for (int s = 0; s < OZ_S; ++s, ++it) {
+      // Fully unrolled issue: descriptors differ only in their start-address
+      // field, so each MMA is one add and the instruction (a rolled loop with
+      // per-MMA descriptor arithmetic left the tensor pipe ~40% idle).
+      const uint64_t zdesc = sdesc_sw128(smem_u32(zring + zs * OZ_ZBYTES));
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s) {
         const int xs = it % OZ_XST;
         if (!mbar_wait(&xfull[xs], (it / OZ_XST) & 1, a.err)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t xaddr = smem_u32(xring + xs * OZ_XBYTES);
-        for (int t = 0; t < OZ_S - s; ++t) {
-          const uint32_t dcol = tmem + (uint32_t)((s + t) * OZ_BN);
+        const uint64_t xdesc = sdesc_sw128(smem_u32(xring + xs * OZ_XBYTES));
+        const uint32_t acc0 = (kb == 0 && s == 0) ? 0u : 1u;
 #pragma unroll
-          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-            const uint32_t acc = (kb == 0 && s == 0 && kk == 0) ? 0u : 1u;
-            mma_bf16(dcol, sdesc_sw128(xaddr + kk * 32),
-                     sdesc_sw128(zaddr + t * OZ_ZTILE + kk * 32), acc);
-          }
+        for (int t = 0; t < OZ_S - s; ++t) {
+#pragma unroll
+          for (int kk = 0; kk < OZ_BK / 16; ++kk)
+            mma_bf16(tmem + (uint32_t)((s + t) * OZ_BN), xdesc + (uint64_t)((kk * 32) >> 4),
+                     zdesc + (uint64_t)((t * OZ_ZTILE + kk * 32) >> 4), kk == 0 ? acc0 : 1u);
         }
         mma_commit(&xempty[xs]);
+        ++it;
       }
       if (ok) mma_commit(&zempty[zs]);
     }
@@ -419,68 +471,76 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 
   // ---- epilogue: exact integers -> FP64.  Warp w reads TMEM lanes
-  // 32 (w mod 4) .. +31 (its rows) and column groups 2 (w / 4), +1.
+  // 32 (w mod 4) .. +31 (its rows) and the 16 columns 16 (w / 4) .. +15, in
+  // two passes of 8.  The C values it updates are loaded first, while the
+  // tensor cores still work.
+  const int q = warp & 3;
+  const int il = q * 32 + lane;
+  const int i = m0 + il;
+  const bool row_ok = i < a.M;
+  const int cl0 = (warp >> 2) * 16;
+  const bool use_c = a.part == nullptr && a.beta != 0.0;
+  double cv[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int j = n0 + cl0 + c;
+    cv[c] = 0.0;
+    if (use_c && row_ok && j < a.N)
+      cv[c] = a.transC ? a.C[j + (int64_t)i * a.ldc] : a.C[i + (int64_t)j * a.ldc];
+  }
   __syncwarp();
   bool ready = nkb > 0 && mbar_wait(&done_bar, 0, a.err);
   ready = __all_sync(0xffffffffu, ready);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ready) {
-    const int q = warp & 3;
-    const int il = q * 32 + lane;
-    const int i = m0 + il;
-    const bool row_ok = i < a.M;
+  if (ready) {  // warp-uniform: the TMEM loads below are .sync.aligned
     const int ei = s_ex[il];
-    const bool use_c = a.part == nullptr && a.beta != 0.0;
-    for (int g = (warp >> 2) * 2; g < (warp >> 2) * 2 + 2; ++g) {
-      const int jb = n0 + g * 16;
-      // C of the 16 columns first: independent loads in flight during the TMEM reads
-      double cv[16];
+    const int bmode = a.part ? 3 : (a.beta == 0.0 ? 0 : (a.beta == 1.0 ? 1 : 2));
+    const double alpha = a.alpha, beta = a.beta;
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        cv[c] = 0.0;
-        if (use_c && row_ok && jb + c < a.N)
-          cv[c] = a.transC ? a.C[jb + c + (int64_t)i * a.ldc] : a.C[i + (int64_t)(jb + c) * a.ldc];
-      }
-      long long V[16];
+    for (int pass = 0; pass < 2; ++pass) {
+      const int cl = cl0 + pass * 8;  // first column of this pass within the tile
+      const int jb = n0 + cl;
+      long long V[8];
+      __syncwarp();
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
-        uint32_t r[4][16];
+        uint32_t r[4][8];
 #pragma unroll
-        for (int dd = 0; dd < 4; ++dd)
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((half * 4 + dd) * OZ_BN + g * 16),
-                    r[dd]);
+        for (int d = 0; d < 4; ++d) tmem_ld8(trow + (uint32_t)((half * 4 + d) * OZ_BN + cl), r[d]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          // |acc| <= 10.5e6 < 2^24: each pair a 128 + b fits in int32
-          const int a0 = __float2int_rn(__uint_as_float(r[0][c]));
-          const int a1 = __float2int_rn(__uint_as_float(r[1][c]));
-          const int a2 = __float2int_rn(__uint_as_float(r[2][c]));
-          const int a3 = __float2int_rn(__uint_as_float(r[3][c]));
-          const long long w = (long long)(a0 * 128 + a1) * 16384 + (a2 * 128 + a3);
+        for (int c = 0; c < 8; ++c) {
+          // |acc| <= 10.5e6 < 2^24: each pair x 128 + y fits in int32
+          const int x0 = __float2int_rn(__uint_as_float(r[0][c]));
+          const int x1 = __float2int_rn(__uint_as_float(r[1][c]));
+          const int x2 = __float2int_rn(__uint_as_float(r[2][c]));
+          const int x3 = __float2int_rn(__uint_as_float(r[3][c]));
+          const long long w = (long long)(x0 * 128 + x1) * 16384 + (x2 * 128 + x3);
           if (half == 0) V[c] = w * (1LL << 19);
           else V[c] += (w + (1LL << 8)) >> 9;
         }
       }
-      if (!row_ok) continue;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < 8; ++c) {
+        if (!row_ok) break;
         const int j = jb + c;
         if (j >= a.N) continue;
-        const int fj = s_fz[g * 16 + c];
+        const int fj = s_fz[cl + c];
         double v = 0.0;
         if (ei != kZeroExp && fj != kZeroExp) {
           const int p = ei + fj - 54;
-          if (!i64_scaled(V[c], p, v)) v = (double)V[c] * pow2(p / 2) * pow2(p - p / 2);
+          if (!i64_scaled(V[c], p, v)) v = slow_scaled(V[c], p);
         }
-        if (a.part) {
+        if (bmode == 3) {
           a.part[(int64_t)blockIdx.z * a.M * a.N + i + (int64_t)j * a.M] = v;
         } else {
           double* cp = a.transC ? a.C + j + (int64_t)i * a.ldc : a.C + i + (int64_t)j * a.ldc;
-          if (a.beta == 0.0) *cp = a.alpha * v;
-          else if (a.beta == 1.0) *cp = fma(a.alpha, v, cv[c]);
-          else *cp = fma(a.alpha, v, a.beta * cv[c]);
+          const double c0 = cv[pass * 8 + c];
+          if (bmode == 0) *cp = alpha * v;
+          else if (bmode == 1) *cp = fma(alpha, v, c0);
+          else *cp = fma(alpha, v, beta * c0);
         }
       }
     }
@@ -559,10 +619,22 @@ Status oz_slice(int64_t R, int64_t K, const double* src, int64_t ld, bool kconti
   const int64_t ldk = pad8(K);
   TraceScope ts(kTrConvert, st, 0.0, (8.0 + 16.0) * R * K);
   if (kcontig) {
-    int64_t warps = std::min<int64_t>(R, 148 * 64);
-    oz_slice_kcontig_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
-        R, K, src, ld, unit_lower ? 1 : 0, out, ldk, exps);
-    LLS_LAUNCHED("oz_slice_kcontig_kernel");
+    if (R > 65535) {
+      int64_t warps = std::min<int64_t>(R, 148 * 64);
+      oz_slice_kcontig_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(
+          R, K, src, ld, unit_lower ? 1 : 0, out, ldk, exps);
+      LLS_LAUNCHED("oz_slice_kcontig_kernel");
+      return ok_status();
+    }
+    LLS_CUDA(cudaMemsetAsync(maxbuf, 0, sizeof(unsigned long long) * R, st));
+    oz_rowmax_kcontig_kernel<<<dim3((unsigned)ceil_div(K, OZ_KCH), (unsigned)R), 256, 0, st>>>(
+        R, K, src, ld, unit_lower ? 1 : 0, maxbuf);
+    LLS_LAUNCHED("oz_rowmax_kcontig_kernel");
+    oz_exps_kernel<<<(unsigned)ceil_div(R, 256), 256, 0, st>>>(R, maxbuf, exps);
+    LLS_LAUNCHED("oz_exps_kernel");
+    oz_slice_kcontig_chunk_kernel<<<dim3((unsigned)ceil_div(ldk, OZ_KCH), (unsigned)R), 256, 0, st>>>(
+        R, K, src, ld, unit_lower ? 1 : 0, exps, out, ldk);
+    LLS_LAUNCHED("oz_slice_kcontig_chunk_kernel");
     return ok_status();
   }
   LLS_CUDA(cudaMemsetAsync(maxbuf, 0, sizeof(unsigned long long) * R, st));
@@ -607,8 +679,16 @@ Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int6
 
   // op(A) (m x k): row i, entry kk is A[i + kk lda] (ta = 0) or A[kk + i lda] (ta = 1)
   LLS_TRY(oz_slice(m, k, A, lda, /*kcontig=*/ta, ma == kUnitLower, Xs, ex, mxb, st));
-  // op(B) (k x n) as the n x k operand: column j, entry kk is B[kk + j ldb] (tb = 0)
-  LLS_TRY(oz_slice(n, k, B, ldb, /*kcontig=*/!tb, mb == kUnitLower, Zs, fz, mxb, st));
+  // op(B) (k x n) as the n x k operand: column j, entry kk is B[kk + j ldb] (tb = 0).
+  // A Gram product op(A) = op(B)^T reads the same stored operand the same
+  // way: its slices are reused.
+  const bool gram = A == B && lda == ldb && ta != tb && ma == mb && m == n;
+  if (gram) {
+    Zs = Xs;
+    fz = ex;
+  } else {
+    LLS_TRY(oz_slice(n, k, B, ldb, /*kcontig=*/!tb, mb == kUnitLower, Zs, fz, mxb, st));
+  }
 
   CUtensorMap mx, mz;
   LLS_TRY(make_slice_map(&mx, Xs, k, m, pad8(k), OZ_BM, 1));
