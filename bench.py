@@ -35,6 +35,11 @@ METRIC = "LLS TFLOP/s & solves/s, mixed vs FP64 at x err ≤1e-9; served p50/p99
 # FP64 pipe of B300: 2 DFMA (4 flops) per clock per SM, measured with a
 # DFMA-chain microbenchmark; 148 SMs.
 FP64_FLOPS_PER_CLK_PER_SM = 4.0
+try:
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as _f:
+        MEASURED_PEAKS = json.load(_f)
+except (OSError, ValueError):
+    MEASURED_PEAKS = {}
 NUM_SM = 148
 
 
@@ -45,11 +50,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--n", type=int, default=16384, help="matrix order (default: full workload)")
-    p.add_argument("--nrhs", type=int, default=16)
+    p.add_argument("--nrhs", type=int, default=None,
+                   help="right-hand sides (default: 16 for c2, 1 for c3)")
     p.add_argument("--nb", type=int, default=128)
     p.add_argument("--q", type=int, default=2)
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
-    p.add_argument("--workload", choices=["c2", "batched", "serving"], default="c2",
+    p.add_argument("--workload", choices=["c2", "c3", "batched", "serving"], default="c2",
                    help="c2: one 16384^2 solve per step (default); batched: many small "
                         "problems per step; serving: Poisson arrivals through lls_submit")
     p.add_argument("--count", type=int, default=1024, help="batched: problems per step")
@@ -61,10 +67,23 @@ def parse():
     return p.parse_args()
 
 
+def dense_shape(a):
+    """(m, n, rank, tol) of the single-matrix workloads.  c2: n x n, rank n/2,
+    sigma 1 .. 1e-6 then 1e-15.  c3: 2n x n, rank 12000 n / 16384, sigma
+    geometric 1 .. 1e-4 then 1e-14."""
+    if a.workload == "c3":
+        return 2 * a.n, a.n, round(12000 * a.n / 16384), 1e-6
+    return a.n, a.n, a.n // 2, 1e-10
+
+
 def workload_name(a) -> str:
-    return (f"randUTV LLS m=n={a.n}, rank {a.n // 2}, Haar Q1 diag(sigma) Q2^T, "
-            f"sigma 1..1e-6 then 1e-15, b = A x0 + 1e-8 noise, nrhs={a.nrhs}, nb={a.nb}, "
-            f"q={a.q}, tol=1e-10")
+    m, n, r, tol = dense_shape(a)
+    if a.workload == "c3":
+        spec = "sigma geometric 1..1e-4 then 1e-14"
+    else:
+        spec = "sigma 1..1e-6 then 1e-15"
+    return (f"randUTV LLS m={m}, n={n}, rank {r}, Haar Q1 diag(sigma) Q2^T, {spec}, "
+            f"b = A x0 + 1e-8 noise, nrhs={a.nrhs}, nb={a.nb}, q={a.q}, tol={tol:g}")
 
 
 def make_inputs(a, device):
@@ -73,13 +92,18 @@ def make_inputs(a, device):
 
     from paper_2408_05238_b300 import workloads as wl
 
-    n, r = a.n, a.n // 2
-    sigma = wl.step_spectrum(n, r, 6.0, 1e-15)
-    A, Q1, Q2 = wl.spectrum_matrix_torch(n, n, sigma, seed=1002, device=device)
+    m, n, r, _ = dense_shape(a)
+    if a.workload == "c3":
+        sigma = wl.geometric_spectrum(n, r, 1e-4, 1e-14)
+        seed = 1003
+    else:
+        sigma = wl.step_spectrum(n, r, 6.0, 1e-15)
+        seed = 1002
+    A, Q1, Q2 = wl.spectrum_matrix_torch(m, n, sigma, seed=seed, device=device)
     gen = torch.Generator(device=device)
-    gen.manual_seed(1102)
+    gen.manual_seed(seed + 100)
     X0 = torch.randn(n, a.nrhs, generator=gen, dtype=torch.float64, device=device)
-    noise = torch.randn(n, a.nrhs, generator=gen, dtype=torch.float64, device=device)
+    noise = torch.randn(m, a.nrhs, generator=gen, dtype=torch.float64, device=device)
     B = (A @ X0 + 1e-8 * noise).t().contiguous().t()
     return A, B, Q1, Q2, torch.as_tensor(sigma, device=device), r
 
@@ -165,14 +189,15 @@ def cpu_baseline(a, A_host, flops_total):
     from oracle import randutv_oracle as orc
     from paper_2408_05238_b300 import perf_model as pm
 
-    k, b = next(pm.steps(a.n, a.n, a.nb))
+    m, n = A_host.shape
+    k, b = next(pm.steps(m, n, a.nb))
     t0 = time.perf_counter()
     orc.randutv(A_host, a.q, a.nb, seed=2002, max_steps=1)
     dt = time.perf_counter() - t0
     threads = blas_threads()
-    tflops = pm.step_flops(a.n, a.n, k, b, a.q) / dt / 1e12
+    tflops = pm.step_flops(m, n, k, b, a.q) / dt / 1e12
     return {"value": tflops, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-            "sample": f"first randUTV step (nb={a.nb} columns) of the {a.n}x{a.n} matrix, "
+            "sample": f"first randUTV step (nb={a.nb} columns) of the {m}x{n} matrix, "
                       f"numpy FP64 with explicit U and V, {dt:.1f} s",
             "seconds": dt, "solves_per_s": tflops * 1e12 / flops_total}
 
@@ -189,7 +214,8 @@ def run_reference(a):
     A, B, _q1, _q2, _s, r = make_inputs(a, device)
     A_host = np.asfortranarray(A.cpu().numpy())
     del A, B, _q1, _q2
-    flops_total = pm.lls_flops(a.n, a.n, a.nb, a.q, r, a.nrhs)
+    m, n = A_host.shape
+    flops_total = pm.lls_flops(m, n, a.nb, a.q, r, a.nrhs)
     vals = []
     for i in range(a.warmup + a.steps):
         res = cpu_baseline(a, A_host, flops_total)
@@ -381,6 +407,8 @@ def run_serving(a):
 
 def main():
     a = parse()
+    if a.nrhs is None:
+        a.nrhs = 1 if a.workload == "c3" else 16
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":
@@ -404,8 +432,7 @@ def main():
     from paper_2408_05238_b300 import perf_model as pm
 
     A, B, Q1, Q2, sigma, r = make_inputs(a, "cuda")
-    m = n = a.n
-    tol = 1e-10
+    m, n, _, tol = dense_shape(a)
     X = lls.empty_colmajor(n, a.nrhs)
     prec = lls.LLS_MIXED_BF16 if a.precision == "mixed" else lls.LLS_FP64
     h = lls.lls_create(nb=a.nb, q=a.q, seed=2002, precision=prec)
@@ -457,11 +484,23 @@ def main():
               for j in range(a.nrhs))       # ||A||_2 = 1 for this construction
     del Q1, Q2, Xp, res
 
-    # roofline of the dominant kernel (FP64 DFMA GEMM, bound by the FP64 pipe)
-    g = trace.get("dgemm_kernel", (0, 0.0, 0.0, 0.0))
-    achieved = g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
+    # roofline of the dominant kernel: the FP64 DFMA GEMM (bound by the FP64
+    # pipe) on the FP64 path; the exact-slice GEMM (bound by the BF16 tensor
+    # pipe: 36 BF16 digit-plane products per FP64 multiply-add) on the mixed path
     sm_max = clocks.get("sm_max_mhz") or 2032.0
-    peak = FP64_FLOPS_PER_CLK_PER_SM * NUM_SM * sm_max * 1e6 / 1e12
+    if a.precision == "mixed":
+        kname = "oz_mma_kernel"
+        g = trace.get(kname, (0, 0.0, 0.0, 0.0))
+        achieved = 36.0 * g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
+        peak = MEASURED_PEAKS.get("bf16_tflops_sustained") or 1400.0
+        bound, psrc = "tensor", ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, "
+                                 "seconds-long loop)" if MEASURED_PEAKS else "fallback 1.4 PFLOP/s")
+    else:
+        kname = "dgemm_kernel"
+        g = trace.get(kname, (0, 0.0, 0.0, 0.0))
+        achieved = g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
+        peak = FP64_FLOPS_PER_CLK_PER_SM * NUM_SM * sm_max * 1e6 / 1e12
+        bound, psrc = "alu", "derived: 2 DFMA/clk/SM x 148 SMs x max SM clock"
     traced = sum(v[1] for v in trace.values()) or 1.0
     shares = {k: {"launches": v[0], "seconds": round(v[1], 4), "share": round(v[1] / traced, 4)}
               for k, v in trace.items()}
@@ -501,13 +540,12 @@ def main():
             "dtype": "f64" if a.precision == "fp64" else "bf16+f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "m": m, "n": n, "nrhs": a.nrhs, "nb": a.nb,
                        "q": a.q, "rank": ranks[-1], "precision": a.precision,
-                       "l2": "inputs larger than L2 (A = 2.1 GB), no flush",
+                       "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.1f} GB), no flush",
                        "parallelism": f"replicas x{world}"},
             "solves_per_s": total_solves / elapsed,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if peak else None, "traffic": None,
-                         "kernel": "dgemm_kernel",
-                         "peak_source": "derived: 2 DFMA/clk/SM x 148 SMs x max SM clock",
+                         "kernel": kname, "peak_source": psrc,
                          "launches": g[0], "avg_launch_ms": 1e3 * g[1] / max(g[0], 1)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "accuracy": {"x_rel_err_vs_pinv": x_err, "normal_eq_residual": ner},

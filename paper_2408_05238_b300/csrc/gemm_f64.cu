@@ -324,11 +324,12 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
   }
   const GemmPlan plan = plan_gemm(m, n, k);
   int splits = plan.splits;
+  // The split count is a function of the shape alone (never of the scratch
+  // on hand), so the summation order, and with it every bit of the result,
+  // is the same whoever calls: a caller must provide gemm_scratch_bytes().
   size_t need = splits > 1 ? (size_t)splits * m * n * sizeof(double) : 0;
-  if (need > scratch.bytes) {
-    // Not enough scratch: fall back to fewer splits that fit (or none).
-    while (splits > 1 && (size_t)splits * m * n * sizeof(double) > scratch.bytes) --splits;
-  }
+  if (need > scratch.bytes)
+    return make_error(LLS_ERR_NOMEM, "gemm: split-K scratch smaller than gemm_scratch_bytes()");
   int64_t kchunk = splits > 1 ? ceil_div(ceil_div(k, splits), BK) * BK : k;
   splits = (int)ceil_div(k, kchunk);
   double* partial = splits > 1 ? static_cast<double*>(scratch.ptr) : nullptr;

@@ -14,6 +14,14 @@ namespace lls {
 // unit lower trapezoidal (0 above the diagonal, 1 on it).
 enum OperandMode { kDense = 0, kUnitLower = 1 };
 
+// Raises fn's dynamic shared-memory limit to the device maximum, once per
+// device and kernel.  The limit is a property of the kernel, not of a
+// launch, so setting it per launch to that launch's size would race between
+// host threads (worker handles) launching the same kernel with different
+// sizes: one thread's smaller value could land between another's set and
+// launch.  Raising it once, to the maximum, is safe for every launch.
+Status allow_max_dyn_smem(const void* fn);
+
 // Reusable device scratch owned by the caller of a launcher.
 struct Scratch {
   void* ptr = nullptr;
@@ -91,6 +99,8 @@ Status copy_cols_reversed(int64_t rows, int64_t cols, const double* src, int64_t
 // Back substitution for one diagonal block: B (k x nrhs) <- R^{-1} B.
 Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double* B,
                   int64_t ldb, cudaStream_t st);
+// Scratch bytes trsm_upper needs for its split-K GEMM updates.
+size_t trsm_upper_scratch_bytes(int64_t r, int64_t nrhs);
 Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
                   int64_t ldb, Scratch scratch, cudaStream_t st);
 

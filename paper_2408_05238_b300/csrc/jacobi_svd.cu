@@ -219,9 +219,7 @@ Status jacobi_svd_batched(int count, int b, int b_last, const double* R, int64_t
              count};
   int bmax = std::max(b, b_last);
   size_t smem = sizeof(double) * (size_t)std::max(bmax * bmax, 2 * bmax);
-  if (smem > 48 * 1024)
-    LLS_CUDA(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  LLS_TRY(allow_max_dyn_smem((const void*)jacobi_svd_kernel));
   TraceScope ts(kTrSvd, st, 0.0, 8.0 * 3.0 * count * (double)bmax * bmax);
   jacobi_svd_kernel<<<count, SVD_THREADS, smem, st>>>(a);
   LLS_LAUNCHED("jacobi_svd_kernel");

@@ -1,0 +1,27 @@
+// Kernel launch configuration shared by the library's launchers.
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "internal.h"
+
+namespace lls {
+
+Status allow_max_dyn_smem(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  LLS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, fn})) return ok_status();
+  cudaFuncAttributes at;
+  LLS_CUDA(cudaFuncGetAttributes(&at, fn));
+  int optin = 0;
+  LLS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  LLS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)at.sharedSizeBytes));
+  done.insert({dev, fn});
+  return ok_status();
+}
+
+}  // namespace lls

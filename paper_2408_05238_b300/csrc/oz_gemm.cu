@@ -708,8 +708,7 @@ Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int6
   a.part = part;
   a.err = err;
   const size_t smem = 1024 + (size_t)OZ_XST * OZ_XBYTES + (size_t)OZ_ZST * OZ_ZBYTES;
-  LLS_CUDA(cudaFuncSetAttribute(oz_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  LLS_TRY(allow_max_dyn_smem((const void*)oz_mma_kernel));
   dim3 grid((unsigned)ceil_div(m, OZ_BM), (unsigned)ceil_div(n, OZ_BN), (unsigned)splits);
   if (grid.y > 65535u || grid.z > 65535u) return make_error(LLS_ERR_ARG, "oz_gemm: grid too large");
   {

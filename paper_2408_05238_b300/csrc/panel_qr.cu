@@ -468,9 +468,7 @@ Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scrat
     a.part = work;
     a.rowj = work + 2 * (size_t)sp.G * n;
     a.totg = a.rowj + 2 * (size_t)n;
-    if (sp.smem > 48 * 1024)
-      LLS_CUDA(cudaFuncSetAttribute(panel_qr_slab_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem));
+    LLS_TRY(allow_max_dyn_smem((const void*)panel_qr_slab_kernel));
     void* args[] = {&a};
     return coop_launch((const void*)panel_qr_slab_kernel, sp.G, PS_THREADS, args, sp.smem, st);
   }
@@ -489,9 +487,7 @@ Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scrat
   a.dot_final = a.part_dot + (size_t)G * n;
   size_t smem = sizeof(double) * (size_t)(a.rows_per + n);
   if (smem > 200 * 1024) return make_error(LLS_ERR_ARG, "panel_qr: panel too tall");
-  if (smem > 48 * 1024)
-    LLS_CUDA(cudaFuncSetAttribute(panel_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  LLS_TRY(allow_max_dyn_smem((const void*)panel_qr_kernel));
   void* args[] = {&a};
   return coop_launch((const void*)panel_qr_kernel, G, PQ_THREADS, args, smem, st);
 }
@@ -502,9 +498,7 @@ Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, do
   TraceScope ts(kTrTFactor, st, (double)k * k * k / 3.0, 16.0 * k * k);
   if (k <= TF_MAX) {
     const size_t smem = sizeof(double) * ((size_t)k * k + k);
-    if (smem > 48 * 1024)
-      LLS_CUDA(cudaFuncSetAttribute(wy_tfactor_smem_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LLS_TRY(allow_max_dyn_smem((const void*)wy_tfactor_smem_kernel));
     wy_tfactor_smem_kernel<<<1, 2 * TF_MAX, smem, st>>>((int)k, S, lds, tau, T, ldt);
     LLS_LAUNCHED("wy_tfactor_kernel");
     return ok_status();

@@ -25,6 +25,8 @@ struct Ticket {
   lls_problem req;
   int64_t bytes = 0;
   int status = LLS_PENDING;
+  int err_arg = 0;
+  std::string err_msg;  // the worker's message when status < 0
   bool done = false;
 };
 
@@ -130,6 +132,8 @@ void worker_loop(Handle::Pool* pool, int wi) {
       pool->admitted_bytes -= t->bytes;
       --pool->running;
       t->status = s.code;
+      t->err_arg = s.arg;
+      t->err_msg = s.msg;
       t->done = true;
     }
     pool->cv_done.notify_all();
@@ -227,7 +231,11 @@ int lls_solve_batched(lls_handle hh, int64_t count, lls_problem* problems) {
     pool.cv_done.wait(lock, [&] { return t->done; });
     problems[order[k]].status = t->status;
     problems[order[k]].factor_id = -1;
-    if (first == LLS_OK && t->status < 0) first = t->status;
+    if (first == LLS_OK && t->status < 0) {
+      first = t->status;
+      h->last_arg = t->err_arg;
+      h->last_msg = "problem " + std::to_string(order[k]) + ": " + t->err_msg;
+    }
     pool.tickets.erase(ids[k]);
   }
   return first;
@@ -267,6 +275,10 @@ int lls_poll(lls_handle hh, int64_t ticket, int* status) {
     return LLS_OK;
   }
   *status = it->second->status;
+  if (*status < 0) {
+    h->last_arg = it->second->err_arg;
+    h->last_msg = "ticket " + std::to_string(ticket) + ": " + it->second->err_msg;
+  }
   h->pool->tickets.erase(it);
   return LLS_OK;
 }

@@ -299,9 +299,20 @@ Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double*
   return ok_status();
 }
 
+constexpr int64_t kTrsmBlock = 64;
+
+size_t trsm_upper_scratch_bytes(int64_t r, int64_t nrhs) {
+  size_t need = 0;
+  for (int64_t j1 = r; j1 > 0; j1 -= kTrsmBlock) {
+    const int64_t j0 = std::max<int64_t>(0, j1 - kTrsmBlock);
+    if (j0 > 0) need = std::max(need, gemm_scratch_bytes(j0, nrhs, j1 - j0));
+  }
+  return need;
+}
+
 Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B, int64_t ldb,
                   Scratch scratch, cudaStream_t st) {
-  const int64_t TB = 64;
+  const int64_t TB = kTrsmBlock;
   int64_t j1 = r;
   while (j1 > 0) {
     int64_t j0 = std::max<int64_t>(0, j1 - TB);
@@ -320,7 +331,13 @@ extern "C" int lls_k_trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_
                                 int64_t ldb, void* stream) {
   if (r < 0 || nrhs < 0 || ldr < (r > 1 ? r : 1) || ldb < (r > 1 ? r : 1)) return LLS_ERR_ARG;
   if (r * nrhs > 0 && (!R || !B)) return LLS_ERR_ARG;
-  return lls::trsm_upper(r, nrhs, R, ldr, B, ldb, lls::Scratch{}, (cudaStream_t)stream).code;
+  cudaStream_t st = (cudaStream_t)stream;
+  lls::Scratch s;
+  s.bytes = lls::trsm_upper_scratch_bytes(r, nrhs);
+  if (s.bytes && cudaMallocAsync(&s.ptr, s.bytes, st) != cudaSuccess) return LLS_ERR_NOMEM;
+  int code = lls::trsm_upper(r, nrhs, R, ldr, B, ldb, s, st).code;
+  if (s.ptr) cudaFreeAsync(s.ptr, st);
+  return code;
 }
 
 extern "C" int lls_k_rank(int64_t len, const double* T, int64_t ldt, double tol, int64_t* out,

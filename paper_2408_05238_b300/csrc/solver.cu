@@ -113,7 +113,7 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   LLS_TRY(h.dstat.reserve(sizeof(DevStatus)));
   DevStatus* ds = h.dstat.as<DevStatus>();
   LLS_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevStatus), st));
-  Scratch gws = scratch_of(h.gemm_ws), pws = scratch_of(h.panel_ws);
+  Scratch pws = scratch_of(h.panel_ws);
   // Mixed precision: the trailing updates and Nullify's products run as
   // FP64-accurate GEMMs on the tensor cores (exact BF16 slices, oz_gemm.cu).
   const bool tc = h.opt.precision == LLS_MIXED_BF16;
@@ -130,13 +130,23 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     }
     LLS_TRY(h.oz_ws.reserve(need));
   }
+  // FP64 GEMM with its split-K scratch grown to this shape's plan first: the
+  // plan depends on the shape alone, so a result never depends on which
+  // handle (or worker) computed it or on what that handle ran before.
+  auto fgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
+                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
+                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
+    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
+    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
+                scratch_of(h.gemm_ws), st);
+  };
   auto xgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
                    int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
                    int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
     if (tc)
       return oz_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_, false,
                      scratch_of(h.oz_ws), &ds->barrier_err, st);
-    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_, gws, st);
+    return fgemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_);
   };
 
   // T <- A, with the finiteness check.
@@ -159,13 +169,13 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       LLS_TRY(sample_bf16(h, ABR, ldt, mp, np, b, q, h.opt.seed, i, Y, ldw));
     } else {
       LLS_TRY(launch_sketch(h.opt.seed, i, mp, b, h.G.d(), std::max<int64_t>(m, 1), st));
-      LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.G.d(),
-                   std::max<int64_t>(m, 1), 0.0, Y, ldw, gws, st));
+      LLS_TRY(fgemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.G.d(),
+                   std::max<int64_t>(m, 1), 0.0, Y, ldw));
       for (int it = 0; it < q; ++it) {
-        LLS_TRY(gemm(false, false, kDense, kDense, mp, b, np, 1.0, ABR, ldt, Y, ldw, 0.0, h.Wt.d(),
-                     std::max<int64_t>(mp, 1), gws, st));
-        LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.Wt.d(),
-                     std::max<int64_t>(mp, 1), 0.0, Y, ldw, gws, st));
+        LLS_TRY(fgemm(false, false, kDense, kDense, mp, b, np, 1.0, ABR, ldt, Y, ldw, 0.0, h.Wt.d(),
+                     std::max<int64_t>(mp, 1)));
+        LLS_TRY(fgemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.Wt.d(),
+                     std::max<int64_t>(mp, 1), 0.0, Y, ldw));
       }
     }
     // ---- a3: [Y, T_V, W_V] = unpivoted_QR(Y)
@@ -275,7 +285,6 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     LLS_TRY(h.gemm_ws.reserve(std::max(h.gemm_ws.bytes,
                                        std::max(gemm_scratch_bytes(nb, nb, L + nb),
                                                 gemm_scratch_bytes(r, nb, L)))));
-    gws = scratch_of(h.gemm_ws);
     LLS_TRY(h.panel_ws.reserve(panel_qr_scratch_bytes(L + nb, nb) + 64));
     pws = scratch_of(h.panel_ws);
     LLS_TRY(h.P.reserve(sizeof(double) * (size_t)std::max<int64_t>(r, 1) * nb));
@@ -348,7 +357,13 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   gneed = std::max(gneed, gemm_scratch_bytes(nb, nrhs, n));
   gneed = std::max(gneed, gemm_scratch_bytes(r, nrhs, nb));
   LLS_TRY(h.gemm_ws.reserve(gneed));
-  Scratch gws = scratch_of(h.gemm_ws);
+  auto fgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
+                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
+                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
+    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
+    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
+                scratch_of(h.gemm_ws), st);
+  };
   DevStatus* ds = h.dstat.as<DevStatus>();
   double* Bw = h.bw.d();
   double* Z = h.z.d();
@@ -362,18 +377,18 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   for (size_t i = 0; i < f.ks.size(); ++i) {
     const int64_t k = f.ks[i], b = f.bs[i], mp = m - k;
     const double* WU = T + k + k * ldt;
-    LLS_TRY(gemm(true, false, kUnitLower, kDense, b, nrhs, mp, 1.0, WU, ldt, Bw + k, m, 0.0, p, nb,
-                 gws, st));
-    LLS_TRY(gemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TU.d() + i * blk, nb, p, nb, 0.0,
-                 p2, nb, gws, st));
-    LLS_TRY(gemm(false, false, kUnitLower, kDense, mp, nrhs, b, -1.0, WU, ldt, p2, nb, 1.0, Bw + k,
-                 m, gws, st));
-    LLS_TRY(gemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.US.d() + i * blk, nb, Bw + k, m,
-                 0.0, p, nb, gws, st));
+    LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, mp, 1.0, WU, ldt, Bw + k, m, 0.0, p, nb));
+    LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TU.d() + i * blk, nb, p, nb, 0.0,
+                 p2, nb));
+    LLS_TRY(fgemm(false, false, kUnitLower, kDense, mp, nrhs, b, -1.0, WU, ldt, p2, nb, 1.0, Bw + k,
+                 m));
+    LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.US.d() + i * blk, nb, Bw + k, m,
+                 0.0, p, nb));
     LLS_TRY(copy_matrix(b, nrhs, p, nb, Bw + k, m, st));
   }
   // y = T_tl^{-1} c
-  LLS_TRY(trsm_upper(r, nrhs, T, ldt, Bw, m, gws, st));
+  LLS_TRY(h.gemm_ws.reserve(trsm_upper_scratch_bytes(r, nrhs)));
+  LLS_TRY(trsm_upper(r, nrhs, T, ldt, Bw, m, scratch_of(h.gemm_ws), st));
   // z = [y; 0]
   LLS_TRY(copy_matrix(r, nrhs, Bw, m, Z, ldw, st));
   if (r < n) LLS_TRY(fill_zero(n - r, nrhs, Z + r, ldw, st));
@@ -388,13 +403,12 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
       const double* Tz = f.RzT.d() + it->off_t;
       LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldw, zc, bsz, st));
       LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
-      LLS_TRY(gemm(true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldw, 1.0, p,
-                   bsz, gws, st));
-      LLS_TRY(gemm(false, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2, bsz,
-                   gws, st));
+      LLS_TRY(fgemm(true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldw, 1.0, p,
+                   bsz));
+      LLS_TRY(fgemm(false, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2, bsz));
       LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p2, bsz, zc, bsz, st));  // W_top = I
-      LLS_TRY(gemm(false, false, kDense, kDense, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0,
-                   Z + r, ldw, gws, st));
+      LLS_TRY(fgemm(false, false, kDense, kDense, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0,
+                   Z + r, ldw));
       LLS_TRY(copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldw, st));
     }
   }
@@ -402,15 +416,15 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii], np = n - k;
     const double* WVi = f.WV.d() + k + k * ldw;
-    LLS_TRY(gemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.VS.d() + ii * blk, nb, Z + k, ldw,
-                 0.0, p, nb, gws, st));
+    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.VS.d() + ii * blk, nb, Z + k, ldw,
+                 0.0, p, nb));
     LLS_TRY(copy_matrix(b, nrhs, p, nb, Z + k, ldw, st));
-    LLS_TRY(gemm(true, false, kUnitLower, kDense, b, nrhs, np, 1.0, WVi, ldw, Z + k, ldw, 0.0, p,
-                 nb, gws, st));
-    LLS_TRY(gemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.TV.d() + ii * blk, nb, p, nb, 0.0,
-                 p2, nb, gws, st));
-    LLS_TRY(gemm(false, false, kUnitLower, kDense, np, nrhs, b, -1.0, WVi, ldw, p2, nb, 1.0, Z + k,
-                 ldw, gws, st));
+    LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, np, 1.0, WVi, ldw, Z + k, ldw, 0.0, p,
+                 nb));
+    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.TV.d() + ii * blk, nb, p, nb, 0.0,
+                 p2, nb));
+    LLS_TRY(fgemm(false, false, kUnitLower, kDense, np, nrhs, b, -1.0, WVi, ldw, p2, nb, 1.0, Z + k,
+                 ldw));
   }
   LLS_TRY(copy_matrix(n, nrhs, Z, ldw, X, ldx, st));
   int flag = 0;

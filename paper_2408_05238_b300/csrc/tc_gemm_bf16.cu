@@ -363,8 +363,7 @@ Status tc_gemm_bf16(int M, int N, int K, const void* X, int64_t ldx, const void*
     a.ldd = ldd;
   }
   size_t smem = tc_gemm_smem_bytes(Ntile);
-  LLS_CUDA(cudaFuncSetAttribute(tc_gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  LLS_TRY(allow_max_dyn_smem((const void*)tc_gemm_bf16_kernel));
   dim3 grid((M + TC_BM - 1) / TC_BM, splits);
   {
     TraceScope ts(kTrBf16Gemm, st, 2.0 * M * N * K, 2.0 * ((double)M * K + (double)K * N) + 4.0 * M * N);

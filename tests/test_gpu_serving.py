@@ -24,8 +24,8 @@ def problems(count, seed):
     return wl.batched_problems(count, seed=seed, m_range=(200, 700), nrhs_choices=(1, 3, 8))
 
 
-def solve_alone(lls, p, nb=64, q=1, seed=2004):
-    h = lls.lls_create(nb=nb, q=q, seed=seed)
+def solve_alone(lls, p, nb=64, q=1, seed=2004, precision=0):
+    h = lls.lls_create(nb=nb, q=q, seed=seed, precision=precision)
     try:
         X, rank, _ = lls.lls_solve(h, dev(p.A), dev(p.B), p.tol)
         return X.cpu().numpy(), rank
@@ -33,9 +33,13 @@ def solve_alone(lls, p, nb=64, q=1, seed=2004):
         lls.lls_destroy(h)
 
 
-def test_batched_equals_alone_and_oracle(lls):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_equals_alone_and_oracle(lls, precision):
+    # precision 1 (BF16 sampling, exact-slice tensor-core updates) also runs
+    # kernels whose launch shapes differ between problems on several host
+    # threads at once
     ps = problems(24, 7)
-    h = lls.lls_create(nb=64, q=1, seed=2004)
+    h = lls.lls_create(nb=64, q=1, seed=2004, precision=precision)
     lls.lls_set_workers(h, 6)
     try:
         keep, plist, ranks = [], [], []
@@ -53,7 +57,7 @@ def test_batched_equals_alone_and_oracle(lls):
         lls.lls_destroy(h)
     for i, p in enumerate(ps):
         assert plist[i].status == 0
-        x_alone, r_alone = solve_alone(lls, p)
+        x_alone, r_alone = solve_alone(lls, p, precision=precision)
         assert ranks[i].value == r_alone == p.rank
         assert np.array_equal(keep[i][2].cpu().numpy(), x_alone)
     for p, (_, _, X) in list(zip(ps, keep))[:4]:
