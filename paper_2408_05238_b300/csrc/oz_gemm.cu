@@ -522,25 +522,48 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           else V[c] += (w + (1LL << 8)) >> 9;
         }
       }
+      if (row_ok) {
+        double v[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (!row_ok) break;
-        const int j = jb + c;
-        if (j >= a.N) continue;
-        const int fj = s_fz[cl + c];
-        double v = 0.0;
-        if (ei != kZeroExp && fj != kZeroExp) {
-          const int p = ei + fj - 54;
-          if (!i64_scaled(V[c], p, v)) v = slow_scaled(V[c], p);
+        for (int c = 0; c < 8; ++c) {
+          const int fj = s_fz[cl + c];
+          v[c] = 0.0;
+          if (ei != kZeroExp && fj != kZeroExp) {
+            const int p = ei + fj - 54;
+            if (!i64_scaled(V[c], p, v[c])) v[c] = slow_scaled(V[c], p);
+          }
         }
+        // one loop per output mode, so no FP64 instruction of another mode
+        // is issued predicated off (FP64 issue slots are scarce on this part)
+        const int ncols = min(8, a.N - jb);
         if (bmode == 3) {
-          a.part[(int64_t)blockIdx.z * a.M * a.N + i + (int64_t)j * a.M] = v;
+          double* P = a.part + (int64_t)blockIdx.z * a.M * a.N + i + (int64_t)jb * a.M;
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < ncols) P[(int64_t)c * a.M] = v[c];
+        } else if (!a.transC) {
+          double* cp = a.C + i + (int64_t)jb * a.ldc;
+          if (bmode == 0) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (c < ncols) cp[(int64_t)c * a.ldc] = alpha * v[c];
+          } else if (bmode == 1) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], cv[pass * 8 + c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], beta * cv[pass * 8 + c]);
+          }
         } else {
-          double* cp = a.transC ? a.C + j + (int64_t)i * a.ldc : a.C + i + (int64_t)j * a.ldc;
-          const double c0 = cv[pass * 8 + c];
-          if (bmode == 0) *cp = alpha * v;
-          else if (bmode == 1) *cp = fma(alpha, v, c0);
-          else *cp = fma(alpha, v, beta * c0);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (c >= ncols) break;
+            double* cp = a.C + jb + c + (int64_t)i * a.ldc;
+            const double c0 = cv[pass * 8 + c];
+            *cp = bmode == 0 ? alpha * v[c] : fma(alpha, v[c], (bmode == 1 ? 1.0 : beta) * c0);
+          }
         }
       }
     }
