@@ -21,6 +21,8 @@
 //
 // Panels whose slabs do not fit in shared memory use panel_qr_kernel, which
 // works on the panel in global memory with three barriers per column.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -297,6 +299,127 @@ __global__ void __launch_bounds__(PS_THREADS) panel_qr_slab_kernel(SlabArgs a) {
   }
 }
 
+// Cluster kernel (panels of up to a few thousand rows): the C CTAs of one
+// thread-block cluster (C <= 8) hold the panel in their shared memory and
+// exchange partial sums through distributed shared memory, with one hardware
+// cluster barrier per column.  A cluster is co-scheduled by construction, so
+// this kernel needs no cooperative launch and no grid barrier, and panels of
+// different streams run side by side.  Same arithmetic and reduction order
+// as the slab kernel (partials per CTA, then in CTA order).
+constexpr int PC_MAX_CLUSTER = 8;
+
+struct ClusterArgs {
+  int64_t m, lda;
+  int n, rows_per, ldsl;
+  double* A;
+  double* tau;
+};
+
+__global__ void __launch_bounds__(PS_THREADS) panel_qr_cluster_kernel(ClusterArgs a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ double sm[];
+  const int n = a.n, ldsl = a.ldsl;
+  double* slab = sm;                          // ldsl x n, column-major
+  double* part = slab + (size_t)ldsl * n;     // [2][n] this CTA's partial sums
+  double* rowb = part + 2 * n;                // [2][n] row j, when this CTA owns it
+  double* tot = rowb + 2 * n;                 // [n]
+  double* roww = tot + n;                     // [n]
+  __shared__ double sc[3];
+  const int C = (int)cluster.num_blocks(), cr = (int)cluster.block_rank(), t = threadIdx.x;
+  const int ci = t / PS_TPC, q = t % PS_TPC;
+  const int64_t m = a.m;
+  const int64_t r0 = (int64_t)cr * a.rows_per;
+  const int64_t r1 = m < r0 + a.rows_per ? m : r0 + a.rows_per;
+  const int nr = r1 > r0 ? (int)(r1 - r0) : 0;
+  const int kmax = m < (int64_t)n ? (int)m : n;
+
+  for (int idx = t; idx < nr * n; idx += PS_THREADS) {
+    const int p = idx % nr, c = idx / nr;
+    slab[p + c * ldsl] = a.A[r0 + p + (int64_t)c * a.lda];
+  }
+  __syncthreads();
+
+  auto publish = [&](int j) {
+    const int plo = (int)(j + 1 - r0 <= 0 ? 0 : (j + 1 - r0 >= nr ? nr : j + 1 - r0));
+    const int ncol = n - j;
+    double s0 = 0.0, s1 = 0.0;
+    if (ci < ncol) {
+      const double* xc = slab + (size_t)j * ldsl;
+      const double* ac = slab + (size_t)(j + ci) * ldsl;
+      int pb, pe;
+      quarter(plo, nr, q, pb, pe);
+      int p = pb;
+      for (; p + 1 < pe; p += 2) {
+        s0 = fma(xc[p], ac[p], s0);
+        s1 = fma(xc[p + 1], ac[p + 1], s1);
+      }
+      if (p < pe) s0 = fma(xc[p], ac[p], s0);
+    }
+    const double s = column_group_sum(s0 + s1);
+    if (ci < ncol && q == 0) part[(j & 1) * n + j + ci] = s;
+    if (r0 <= j && j < r0 + nr && t < ncol)
+      rowb[(j & 1) * n + j + t] = slab[(j - r0) + (size_t)(j + t) * ldsl];
+  };
+
+  if (kmax > 0) publish(0);
+  for (int j = 0; j < kmax; ++j) {
+    cluster.sync();  // partial sums (and row j) of column j are in
+    const int ncol = n - j;
+    const int owner = (int)(j / a.rows_per);
+    if (t < ncol) {
+      double s = 0.0;
+      for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(part, r)[(j & 1) * n + j + t];
+      tot[j + t] = s;
+      roww[j + t] = cluster.map_shared_rank(rowb, owner)[(j & 1) * n + j + t];
+    }
+    __syncthreads();
+    if (t == 0) {
+      const double ss = tot[j], alpha = roww[j];
+      double tau = 0.0, beta = alpha, scale = 0.0;
+      if (ss != 0.0) {
+        beta = -copysign(hypot(alpha, sqrt(ss)), alpha);
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      sc[0] = tau;
+      sc[1] = beta;
+      sc[2] = scale;
+    }
+    __syncthreads();
+    const double tau = sc[0], beta = sc[1], scale = sc[2];
+    for (int c = j + 1 + t; c < n; c += PS_THREADS) roww[c] = tau * fma(scale, tot[c], roww[c]);
+    const int lo = (int)(j - r0 <= 0 ? 0 : (j - r0 >= nr ? nr : j - r0));  // first own row >= j
+    const bool own_j = r0 <= j && j < r0 + nr;
+    for (int p = lo + (own_j ? 1 : 0) + t; p < nr; p += PS_THREADS) slab[p + (size_t)j * ldsl] *= scale;
+    __syncthreads();
+    if (tau != 0.0 && ci + 1 < ncol) {
+      const int c = j + 1 + ci;
+      const double tw = roww[c];
+      double* ac = slab + (size_t)c * ldsl;
+      const double* vc = slab + (size_t)j * ldsl;
+      int pb, pe;
+      quarter(lo, nr, q, pb, pe);
+      if (own_j && pb == lo && pb < pe) {
+        ac[pb] -= tw;  // row j: v_j = 1
+        ++pb;
+      }
+      for (int p = pb; p < pe; ++p) ac[p] = fma(-tw, vc[p], ac[p]);
+    }
+    __syncthreads();
+    if (own_j && t == 0) slab[lo + (size_t)j * ldsl] = beta;
+    if (cr == 0 && t == 0) a.tau[j] = tau;
+    __syncthreads();
+    if (j + 1 < kmax) publish(j + 1);
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
+
+  for (int idx = t; idx < nr * n; idx += PS_THREADS) {
+    const int p = idx % nr, c = idx / nr;
+    a.A[r0 + p + (int64_t)c * a.lda] = slab[p + c * ldsl];
+  }
+}
+
 // T factor of the compact WY form: T(j, j) = tau_j and
 // T(0:j, j) = -tau_j T(0:j, 0:j) S(0:j, j), S = W^T W (Schreiber-Van Loan).
 __global__ void wy_tfactor_kernel(int64_t k, const double* __restrict__ S, int64_t lds,
@@ -431,6 +554,30 @@ Status coop_launch(const void* fn, int G, int threads, void** args, size_t smem,
   return ok_status();
 }
 
+// Cluster plan: the fewest CTAs (at most PC_MAX_CLUSTER, at least enough
+// that each holds <= 64 rows when m allows) whose slabs fit in shared memory.
+struct ClusterPlan {
+  int C, rows_per, ldsl;
+  size_t smem;
+  bool fits;
+};
+
+ClusterPlan cluster_plan(int64_t m, int64_t n) {
+  ClusterPlan p{0, 0, 0, 0, false};
+  if (n > PS_THREADS / PS_TPC) return p;
+  for (int C = 1; C <= PC_MAX_CLUSTER; C *= 2) {
+    const int64_t rows = ceil_div(m, C);
+    if (rows > 64 && C < PC_MAX_CLUSTER) continue;  // spread the FP64 work first
+    const int ldsl = (int)(rows | 1);
+    const size_t smem = sizeof(double) * ((size_t)ldsl * n + 6 * (size_t)n);
+    if (smem <= (size_t)max_dyn_smem()) {
+      p = ClusterPlan{C, (int)rows, ldsl, smem, true};
+      return p;
+    }
+  }
+  return p;
+}
+
 }  // namespace
 
 size_t panel_qr_scratch_bytes(int64_t m, int64_t n) {
@@ -443,6 +590,30 @@ size_t panel_qr_scratch_bytes(int64_t m, int64_t n) {
 Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
                 int* err, cudaStream_t st) {
   if (m <= 0 || n <= 0) return ok_status();
+  {
+    const ClusterPlan cp = cluster_plan(m, n);
+    if (cp.fits) {
+      const int64_t k = std::min(m, n);
+      TraceScope ts(kTrPanelQR, st, 2.0 * m * n * k - 2.0 * k * k * k / 3.0, 16.0 * m * n);
+      ClusterArgs a{m, lda, (int)n, cp.rows_per, cp.ldsl, A, tau};
+      LLS_TRY(allow_max_dyn_smem((const void*)panel_qr_cluster_kernel));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cp.C);
+      cfg.blockDim = dim3(PS_THREADS);
+      cfg.dynamicSmemBytes = cp.smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cp.C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      LLS_CUDA(cudaLaunchKernelEx(&cfg, panel_qr_cluster_kernel, a));
+      LLS_LAUNCHED("panel_qr_cluster_kernel");
+      return ok_status();
+    }
+  }
   if (scratch.bytes < panel_qr_scratch_bytes(m, n))
     return make_error(LLS_ERR_NOMEM, "panel_qr: scratch too small");
   char* base = static_cast<char*>(scratch.ptr);
