@@ -155,6 +155,49 @@ struct SlabArgs {
   double* totg;  // [2][n + 4]: reduced sums of column j, then tau, beta, scale
 };
 
+// Reflector scalars of xLARFG from alpha and ss = ||x||^2 (ss > 0):
+// beta = -sign(alpha) sqrt(alpha^2 + ss), tau = (beta - alpha) / beta,
+// scale = 1 / (alpha - beta).  One thread computes them on every column, so
+// their dependent FP64 chain sits on the panel's critical path and FP64
+// instructions are scarce on this part: sqrt and the divisions are replaced
+// by Newton-Raphson iterations (reciprocal square root y <- y (3 - d y^2) / 2,
+// reciprocal r <- r (2 - d r)), two each, from single-precision seeds, after
+// scaling d by an even power of two into [1, 4) (exact, on the exponent bits).
+// With beta^2 = alpha^2 + ss to a few ulps the reflector is orthogonal to the
+// same order.  Subnormal or huge d takes the library functions instead.
+__device__ __forceinline__ void reflector_scalars(double alpha, double ss, double& tau,
+                                                  double& beta, double& scale) {
+  const double d = fma(alpha, alpha, ss);
+  const long long db = __double_as_longlong(d);
+  const int ex = (int)((db >> 52) & 0x7FF);
+  if (ex < 64 || ex > 1983) {  // outside the range the scaled seeds cover
+    beta = -copysign(hypot(alpha, sqrt(ss)), alpha);
+    tau = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+    return;
+  }
+  const int e2 = (ex - 1023) & ~1;                                   // even exponent
+  const double dm = __longlong_as_double(db - ((long long)e2 << 52));  // d 2^-e2 in [1, 4)
+  double y = (double)rsqrtf((float)dm);
+  y = y * fma(-0.5 * dm, y * y, 1.5);
+  y = y * fma(-0.5 * dm, y * y, 1.5);                                // 1/sqrt(dm)
+  const long long half = (long long)(e2 / 2) << 52;
+  const double rn = __longlong_as_double(__double_as_longlong(y) - half);       // 1/nrm
+  const double nrm = __longlong_as_double(__double_as_longlong(dm * y) + half);  // sqrt(d)
+  const double aa = fabs(alpha);
+  beta = -copysign(nrm, alpha);
+  tau = fma(aa, rn, 1.0);  // (beta - alpha) / beta = 1 + |alpha| / nrm
+  // scale = sign(alpha) / (|alpha| + nrm), with d2 = |alpha| + nrm in [nrm, 2 nrm]
+  const double d2 = aa + nrm;
+  const long long d2b = __double_as_longlong(d2);
+  const int e3 = (int)((d2b >> 52) & 0x7FF) - 1023;
+  const double d2m = __longlong_as_double(d2b - ((long long)e3 << 52));  // in [1, 2)
+  double r = (double)(1.0f / (float)d2m);
+  r = r * fma(-d2m, r, 2.0);
+  r = r * fma(-d2m, r, 2.0);
+  scale = copysign(__longlong_as_double(__double_as_longlong(r) - ((long long)e3 << 52)), alpha);
+}
+
 // Sum of the PS_TPC threads of one column, in a fixed pairing; commutative
 // adds make the result bit-identical in all of them.
 __device__ __forceinline__ double column_group_sum(double s) {
@@ -243,11 +286,7 @@ __global__ void __launch_bounds__(PS_THREADS) panel_qr_slab_kernel(SlabArgs a) {
           if (c == 0) {
             const double alpha = __ldcg(a.rowj + (size_t)(j & 1) * n + j);
             double tau = 0.0, beta = alpha, scale = 0.0;
-            if (s != 0.0) {
-              beta = -copysign(hypot(alpha, sqrt(s)), alpha);
-              tau = (beta - alpha) / beta;
-              scale = 1.0 / (alpha - beta);
-            }
+            if (s != 0.0) reflector_scalars(alpha, s, tau, beta, scale);
             TG[n] = tau;
             TG[n + 1] = beta;
             TG[n + 2] = scale;
@@ -377,11 +416,7 @@ __global__ void __launch_bounds__(PS_THREADS) panel_qr_cluster_kernel(ClusterArg
     if (t == 0) {
       const double ss = tot[j], alpha = roww[j];
       double tau = 0.0, beta = alpha, scale = 0.0;
-      if (ss != 0.0) {
-        beta = -copysign(hypot(alpha, sqrt(ss)), alpha);
-        tau = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
-      }
+      if (ss != 0.0) reflector_scalars(alpha, ss, tau, beta, scale);
       sc[0] = tau;
       sc[1] = beta;
       sc[2] = scale;
