@@ -60,6 +60,9 @@ def parse():
                         "problems per step; serving: Poisson arrivals through lls_submit")
     p.add_argument("--count", type=int, default=1024, help="batched: problems per step")
     p.add_argument("--workers", type=int, default=8)
+    p.add_argument("--autotune", action="store_true",
+                   help="batched/serving: tune (n_b, q) for every (m, n) bucket of the workload "
+                        "with lls_autotune before the timed region and solve with nb=0")
     p.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     p.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     p.add_argument("--no-e2e", action="store_true")
@@ -267,6 +270,27 @@ def batched_sizes(count, seed, m_range=(256, 2048), nrhs_choices=(1, 8, 32)):
     return out
 
 
+def autotune_buckets(lls, h, shapes, trials=2):
+    """lls_autotune once per (ceil log2 m, ceil log2 n) bucket of the shapes,
+    at the bucket's largest shape; returns {"bm,bn": [nb, q, seconds]}."""
+    buckets = {}
+    for m, n in shapes:
+        key = ((m - 1).bit_length(), (n - 1).bit_length())
+        bm, bn = buckets.get(key, (0, 0))
+        buckets[key] = (max(bm, m), max(bn, n))
+    out = {}
+    for key, (m, n) in sorted(buckets.items()):
+        t0 = time.perf_counter()
+        nb, q = lls.lls_autotune(h, m, n, trials)
+        out[f"{key[0]},{key[1]}"] = [nb, q, round(time.perf_counter() - t0, 2)]
+    return out
+
+
+def nbq(lls, h, m, n, tuned):
+    """(nb, q) the batched handle uses for an m x n problem."""
+    return lls.lls_tuning_lookup(h, m, n) if tuned else (64, 1)
+
+
 def run_batched(a):
     """lls_solve_batched over `count` independent X Y problems per step."""
     import ctypes as C
@@ -283,8 +307,9 @@ def run_batched(a):
         A, B, tol = gen_xy_problem(m, n, r, k, 1004 * 100000 + j, "cuda")
         probs.append((A, B, tol, lls.empty_colmajor(n, k), r))
     prec = lls.LLS_MIXED_BF16 if a.precision == "mixed" else lls.LLS_FP64
-    h = lls.lls_create(nb=64, q=1, seed=2004, precision=prec)
+    h = lls.lls_create(nb=0 if a.autotune else 64, q=1, seed=2004, precision=prec)
     lls.lls_set_workers(h, a.workers)
+    tuning = autotune_buckets(lls, h, [(m, n) for (m, n, _, _) in sizes]) if a.autotune else None
     ranks = [C.c_int64(-1) for _ in probs]
     plist = [lls.make_problem(A, B, tol, X, rank_out=C.pointer(rk))
              for (A, B, tol, X, _), rk in zip(probs, ranks)]
@@ -304,7 +329,8 @@ def run_batched(a):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     launches = lls.lls_launch_count() - launches0
-    flops = sum(pm.lls_flops(m, n, 64, 1, rk.value, k) for (m, n, r, k), rk in zip(sizes, ranks))
+    flops = sum(pm.lls_flops(m, n, *nbq(lls, h, m, n, a.autotune), rk.value, k)
+                for (m, n, r, k), rk in zip(sizes, ranks))
     wrong = sum(rk.value != r for (_, _, _, _, r), rk in zip(probs, ranks))
     lls.lls_destroy(h)
     out = {"metric": METRIC, "value": a.count * a.steps / dt, "unit": "solves/s",
@@ -312,8 +338,9 @@ def run_batched(a):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if a.precision == "fp64" else "bf16+f64", "data": "synthetic",
            "config": {"workload": f"batched: {a.count} X Y problems, m in [256, 2048], n in "
-                                  f"[128, m], rank in [n/4, n], nrhs in {{1, 8, 32}}, nb=64, q=1",
-                      "workers": a.workers, "precision": a.precision},
+                                  f"[128, m], rank in [n/4, n], nrhs in {{1, 8, 32}}, "
+                                  + ("nb, q autotuned per (m, n) bucket" if a.autotune else "nb=64, q=1"),
+                      "workers": a.workers, "precision": a.precision, "tuning": tuning},
            "tflops": flops * a.steps / dt / 1e12, "rank_mismatches": wrong,
            "gpu_launches": launches, "clocks": clk.summary()}
     print(json.dumps(out))

@@ -68,7 +68,8 @@ typedef struct lls_handle_s* lls_handle;
 
 /* Options (lls_default_options fills the defaults in brackets). */
 typedef struct {
-  int32_t nb;          /* block size n_b of Fig. 2, 1..128 [64] */
+  int32_t nb;          /* block size n_b of Fig. 2, 1..128 [64]; 0: n_b and q
+                          from the handle's tuning table (lls_autotune) */
   int32_t q;           /* power iterations of Y = (A^T A)^q A^T G, 0..4 [1] */
   int32_t precision;   /* LLS_FP64 | LLS_MIXED_BF16 [LLS_FP64] */
   int32_t nullify;     /* 1: run Nullify (minimum-norm x, Fig. 3) [1];
@@ -92,6 +93,33 @@ typedef struct {
   int32_t keep_factor;
   int32_t status;      /* written by lls_solve_batched: per-problem status */
 } lls_problem;
+
+/* ---- autotuning of n_b and q ---------------------------------------------
+ * With opt.nb == 0 a factorization of an m x n matrix takes n_b and q from
+ * the handle's tuning table entry for its bucket (ceil(log2 m), ceil(log2 n));
+ * a bucket without an entry uses n_b = 64, q = 1.  Worker handles of
+ * lls_solve_batched / lls_submit share the table.
+ *
+ * lls_autotune fills the entry of the bucket of (m, n).  On a synthetic m x n
+ * matrix X Y of rank min(m, n)/2 (X, Y Gaussian from the library's Philox
+ * generator, X's columns scaled so the singular values spread over four
+ * decades) with one Gaussian right-hand side and the default tol, it runs the
+ * reference choice n_b = 32, q = 2, then times `trials` solves (host wall
+ * clock, synchronous lls_solve on the handle's stream, current precision) for
+ * each n_b in {32, 64, 128} (n_b <= min(m, n) beyond 32) and q in {0, 1, 2},
+ * and keeps the fastest whose rank equals the reference's and whose x agrees
+ * with the reference x to 1e-9 relative.  nb_out, q_out (host, may be NULL)
+ * receive the choice.  Errors: LLS_ERR_ARG (m, n outside 1..2^20, trials < 1),
+ * LLS_ERR_NOMEM, and those of lls_solve. */
+int lls_autotune(lls_handle h, int64_t m, int64_t n, int32_t trials, int32_t* nb_out,
+                 int32_t* q_out);
+/* The (n_b, q) a tuned solve (opt.nb == 0) of an m x n matrix would use. */
+int lls_tuning_lookup(lls_handle h, int64_t m, int64_t n, int32_t* nb, int32_t* q);
+/* Write the table as text, one "bucket_m bucket_n n_b q" line per entry;
+ * read such a file and merge it into the table.  LLS_ERR_ARG when the file
+ * cannot be opened or a line is malformed (nothing is merged then). */
+int lls_tuning_save(lls_handle h, const char* path);
+int lls_tuning_load(lls_handle h, const char* path);
 
 /* Fill *opt with the defaults.  Returns LLS_OK or LLS_ERR_ARG (opt NULL). */
 int lls_default_options(lls_options* opt);

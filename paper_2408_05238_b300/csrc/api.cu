@@ -27,7 +27,7 @@ int finish(Handle* h, const Status& s) {
 Status arg_error(int idx, const char* what) { return lls::make_error(LLS_ERR_ARG, what, idx); }
 
 Status check_options(const lls_options& o) {
-  if (o.nb < 1 || o.nb > 128) return arg_error(2, "nb must be in 1..128");
+  if (o.nb < 0 || o.nb > 128) return arg_error(2, "nb must be in 0..128 (0: tuned)");
   if (o.q < 0 || o.q > 4) return arg_error(2, "q must be in 0..4");
   if (o.precision != LLS_FP64 && o.precision != LLS_MIXED_BF16)
     return arg_error(2, "unknown precision mode");
@@ -93,6 +93,7 @@ int lls_create(lls_handle* out, const lls_options* opt, void* cuda_stream) {
   Handle* h = new (std::nothrow) Handle();
   if (!h) return LLS_ERR_NOMEM;
   h->opt = o;
+  h->tune = std::make_shared<lls::TuneTable>();
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
     return LLS_ERR_CUDA;

@@ -56,6 +56,7 @@ namespace {
 
 // Device memory one request holds while it runs (factor + workspace).
 int64_t request_bytes(const lls_problem& p, int nb) {
+  if (nb <= 0) nb = 128;  // tuned block size: bound by the largest
   if (p.factor_id >= 0) return (int64_t)(8 * (p.m + 2 * p.n) * std::max<int64_t>(p.nrhs, 1));
   int64_t mx = std::max(p.m, p.n);
   int64_t ws = 8 * (int64_t)mx * nb * 6 + 8 * (int64_t)(p.m + p.n) * std::max<int64_t>(p.nrhs, 1);
@@ -126,6 +127,7 @@ void worker_loop(Handle::Pool* pool, int wi) {
       ++pool->running;
     }
     w.opt = pool->parent->opt;
+    w.tune = pool->parent->tune;
     Status s = run_request(*pool->parent, w, t->req);
     {
       std::lock_guard<std::mutex> lock(pool->mu);

@@ -66,8 +66,8 @@ size_t factor_bytes(int64_t m, int64_t n, int nb) {
 Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, int64_t lda,
                  double tol) {
   cudaStream_t st = h.stream;
-  const int nb = h.opt.nb;
-  const int q = h.opt.q;
+  int nb = 0, q = 0;
+  effective_nb_q(h.opt, h.tune.get(), m, n, &nb, &q);
   f.m = m;
   f.n = n;
   f.ldt = std::max<int64_t>(m, 1);

@@ -92,8 +92,22 @@ struct Factor {
   }
 };
 
+// Block size and power-iteration count per (m, n) bucket (ceil(log2 m),
+// ceil(log2 n)), filled by lls_autotune or lls_tuning_load and read when
+// opt.nb == 0.  Shared by a handle and its workers.
+struct TuneTable {
+  std::mutex mu;
+  std::map<std::pair<int, int>, std::pair<int, int>> entries;  // bucket -> (nb, q)
+};
+int tune_bucket(int64_t x);
+// (nb, q) a factorization of an m x n matrix uses: opt.nb and opt.q, or,
+// when opt.nb == 0, the table's entry for the bucket (nb 64, q 1 if none).
+void effective_nb_q(const lls_options& opt, const TuneTable* table, int64_t m, int64_t n,
+                    int* nb, int* q);
+
 struct Handle {
   lls_options opt{};
+  std::shared_ptr<TuneTable> tune;
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;

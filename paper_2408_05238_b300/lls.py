@@ -90,6 +90,10 @@ _sig("lls_poll", [_H, _I, C.POINTER(C.c_int)])
 _sig("lls_set_memory_cap", [_H, _I])
 _sig("lls_ticket_factor", [_H, _I, C.POINTER(_I)])
 _sig("lls_set_workers", [_H, C.c_int])
+_sig("lls_autotune", [_H, _I, _I, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)])
+_sig("lls_tuning_lookup", [_H, _I, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)])
+_sig("lls_tuning_save", [_H, C.c_char_p])
+_sig("lls_tuning_load", [_H, C.c_char_p])
 _sig("lls_status_string", [C.c_int], C.c_char_p)
 _sig("lls_last_error", [_H, C.POINTER(C.c_int), C.c_char_p, _I])
 _sig("lls_trace_enable", [_H, C.c_int])
@@ -301,6 +305,28 @@ def lls_ticket_factor(h, ticket: int):
 
 def lls_set_workers(h, workers: int):
     _check(h, _lib.lls_set_workers(h, int(workers)))
+
+
+def lls_autotune(h, m: int, n: int, trials: int = 2) -> tuple[int, int]:
+    """Time n_b x q candidates on a synthetic m x n matrix; returns the (n_b, q)
+    stored for the (m, n) bucket (lls_autotune)."""
+    nb, q = C.c_int32(0), C.c_int32(0)
+    _check(h, _lib.lls_autotune(h, m, n, int(trials), C.byref(nb), C.byref(q)))
+    return nb.value, q.value
+
+
+def lls_tuning_lookup(h, m: int, n: int) -> tuple[int, int]:
+    nb, q = C.c_int32(0), C.c_int32(0)
+    _check(h, _lib.lls_tuning_lookup(h, m, n, C.byref(nb), C.byref(q)))
+    return nb.value, q.value
+
+
+def lls_tuning_save(h, path: str):
+    _check(h, _lib.lls_tuning_save(h, os.fsencode(path)))
+
+
+def lls_tuning_load(h, path: str):
+    _check(h, _lib.lls_tuning_load(h, os.fsencode(path)))
 
 
 def lls_trace_enable(h, on: bool = True):

@@ -60,8 +60,9 @@ def test_null_handle_and_bad_create(lib):
     assert lib._lib.lls_destroy(None) == lib.LLS_ERR_ARG
     assert lib._lib.lls_solve(None, None, 0, 0, 1, None, 0, 1, 0.0, None, 1, None) == lib.LLS_ERR_ARG
     h = C.c_void_p()
-    bad = lib.lls_default_options(nb=0)
-    assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
+    for nb in (-1, 129):   # nb = 0 is valid: n_b and q from the tuning table
+        bad = lib.lls_default_options(nb=nb)
+        assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
     bad = lib.lls_default_options(q=9)
     assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
 

@@ -142,3 +142,42 @@ def test_serving_factor_reuse_and_memory_cap(lls):
         assert all(v == 0 for v in wait_all(lls, h, ts).values())
     finally:
         lls.lls_destroy(h)
+
+
+def test_autotune_table_drives_tuned_solves(lls, tmp_path):
+    h = lls.lls_create(nb=0, q=1, seed=2004)   # nb = 0: n_b and q from the tuning table
+    try:
+        assert lls.lls_tuning_lookup(h, 700, 300) == (64, 1)       # no entry yet: defaults
+        nb, q = lls.lls_autotune(h, 700, 300, trials=1)
+        assert nb in (32, 64, 128) and q in (0, 1, 2)
+        assert lls.lls_tuning_lookup(h, 1000, 400) == (nb, q)      # same bucket (1024, 512)
+        assert lls.lls_tuning_lookup(h, 2000, 400) == (64, 1)      # other bucket
+        path = str(tmp_path / "tune.txt")
+        lls.lls_tuning_save(h, path)
+        h2 = lls.lls_create(nb=0, q=1, seed=2004)
+        try:
+            lls.lls_tuning_load(h2, path)
+            assert lls.lls_tuning_lookup(h2, 700, 300) == (nb, q)
+        finally:
+            lls.lls_destroy(h2)
+        # a tuned solve equals the explicit choice bit for bit, and the oracle to 1e-9
+        p = problems(1, 21)[0]
+        A, B = dev(p.A), dev(p.B)
+        Xt, rt, _ = lls.lls_solve(h, A, B, p.tol)
+        mb, nbk = p.A.shape
+        tnb, tq = lls.lls_tuning_lookup(h, mb, nbk)
+        he = lls.lls_create(nb=tnb, q=tq, seed=2004)
+        try:
+            Xe, re_, _ = lls.lls_solve(he, A, B, p.tol)
+        finally:
+            lls.lls_destroy(he)
+        assert rt == re_ == p.rank
+        assert torch.equal(Xt, Xe)
+        ref = np.reshape(orc.solve(p.A, p.B, tq, tnb, p.tol, 2004).x, Xt.shape)
+        assert np.linalg.norm(Xt.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-9
+        bad = tmp_path / "bad.txt"
+        bad.write_text("1 2 300 1\n")
+        with pytest.raises(lls.LLSError):
+            lls.lls_tuning_load(h, str(bad))
+    finally:
+        lls.lls_destroy(h)
