@@ -367,9 +367,10 @@ def run_serving(a):
         A, _, tol = gen_xy_problem(m, n, r, 1, 1005 * 100000 + j, "cuda")
         pool.append((A, tol, r))
     prec = lls.LLS_MIXED_BF16 if a.precision == "mixed" else lls.LLS_FP64
-    h = lls.lls_create(nb=64, q=1, seed=2005, precision=prec)
+    h = lls.lls_create(nb=0 if a.autotune else 64, q=1, seed=2005, precision=prec)
     lls.lls_set_workers(h, a.workers)
     lls.lls_set_memory_cap(h, 120 << 30)
+    tuning = autotune_buckets(lls, h, [tuple(A.shape) for A, _, _ in pool]) if a.autotune else None
     # resident factors for the reuse requests (factored before the clock starts)
     factors = {}
     for j in range(0, len(pool), 3):
@@ -404,8 +405,9 @@ def run_serving(a):
             held[i] = (B, X, p)
             t_sub[i] = time.perf_counter() - t0
             pending.add(i)
-            flops += (pm.solve_flops(m, n, 64, r, k, True) if reuse
-                      else pm.lls_flops(m, n, 64, 1, r, k))
+            tnb, tq = nbq(lls, h, m, n, a.autotune)
+            flops += (pm.solve_flops(m, n, tnb, r, k, True) if reuse
+                      else pm.lls_flops(m, n, tnb, tq, r, k))
             i += 1
         for q in list(pending):
             s = lls.lls_poll(h, tickets[q])
@@ -424,8 +426,9 @@ def run_serving(a):
            "dtype": "f64" if a.precision == "fp64" else "bf16+f64", "data": "synthetic",
            "config": {"workload": f"serving: Poisson {a.rate}/s for {a.duration} s, X Y requests "
                                   f"m in [512, 8192], n <= m, rank in [n/8, n], nrhs in [1, 64], "
-                                  f"30% reuse a resident factor, 120 GB cap, nb=64, q=1",
-                      "workers": a.workers, "precision": a.precision},
+                                  f"30% reuse a resident factor, 120 GB cap, "
+                                  + ("nb, q autotuned per (m, n) bucket" if a.autotune else "nb=64, q=1"),
+                      "workers": a.workers, "precision": a.precision, "tuning": tuning},
            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
            "solves_per_s": nreq / wall, "offered_per_s": a.rate, "tflops": flops / wall / 1e12}
     print(json.dumps(out))

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(PS_THREADS) panel_qr_slab_kernel(SlabArgs a) {
 }
 
 // Cluster kernel (panels of up to a few thousand rows): the C CTAs of one
-// thread-block cluster (C <= 8) hold the panel in their shared memory and
+// thread-block cluster (C <= 16) hold the panel in their shared memory and
 // exchange partial sums through distributed shared memory, with one hardware
 // cluster barrier per column.  A cluster is co-scheduled by construction, so
 // this kernel needs no cooperative launch and no grid barrier, and panels of
@@ -589,7 +589,40 @@ Status coop_launch(const void* fn, int G, int threads, void** args, size_t smem,
   return ok_status();
 }
 
-// Cluster plan: the fewest CTAs (at most PC_MAX_CLUSTER, at least enough
+// Largest cluster the panel kernel may use on this device: 16 CTAs (a
+// non-portable size) when the device can hold one such cluster at the
+// kernel's maximum shared memory, else the portable 8.
+int max_cluster_ctas() {
+  static std::once_flag once;
+  static int v = PC_MAX_CLUSTER;
+  std::call_once(once, [] {
+    if (!allow_max_dyn_smem((const void*)panel_qr_cluster_kernel).ok()) return;
+    if (cudaFuncSetAttribute(panel_qr_cluster_kernel,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(PS_THREADS);
+    cfg.dynamicSmemBytes = (size_t)max_dyn_smem();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, panel_qr_cluster_kernel, &cfg) == cudaSuccess &&
+        clusters >= 1)
+      v = 16;
+    cudaGetLastError();
+  });
+  return v;
+}
+
+// Cluster plan: the fewest CTAs (at most max_cluster_ctas(), at least enough
 // that each holds <= 64 rows when m allows) whose slabs fit in shared memory.
 struct ClusterPlan {
   int C, rows_per, ldsl;
@@ -600,9 +633,10 @@ struct ClusterPlan {
 ClusterPlan cluster_plan(int64_t m, int64_t n) {
   ClusterPlan p{0, 0, 0, 0, false};
   if (n > PS_THREADS / PS_TPC) return p;
-  for (int C = 1; C <= PC_MAX_CLUSTER; C *= 2) {
+  const int cmax = max_cluster_ctas();
+  for (int C = 1; C <= cmax; C *= 2) {
     const int64_t rows = ceil_div(m, C);
-    if (rows > 64 && C < PC_MAX_CLUSTER) continue;  // spread the FP64 work first
+    if (rows > 64 && C < cmax) continue;  // spread the FP64 work first
     const int ldsl = (int)(rows | 1);
     const size_t smem = sizeof(double) * ((size_t)ldsl * n + 6 * (size_t)n);
     if (smem <= (size_t)max_dyn_smem()) {
