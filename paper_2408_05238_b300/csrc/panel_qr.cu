@@ -476,37 +476,44 @@ __global__ void wy_tfactor_kernel(int64_t k, const double* __restrict__ S, int64
   }
 }
 
-// The same recurrence with T in shared memory (k <= 128): per column j, two
-// threads per row i < j split the sum over l in [i, j) and combine in a
-// fixed order.
-constexpr int TF_MAX = 128;
+constexpr int TF_MAX = 128;  // largest k of the register-resident T-factor kernel
 
-__global__ void __launch_bounds__(2 * TF_MAX) wy_tfactor_smem_kernel(int k, const double* __restrict__ S,
-                                                                      int64_t lds,
-                                                                      const double* __restrict__ tau,
-                                                                      double* T, int64_t ldt) {
-  extern __shared__ double tsm[];
-  double* Ts = tsm;                   // k x k, leading dimension k
-  double* z = tsm + (size_t)k * k;    // S(0:j, j)
-  const int t = threadIdx.x, i = t >> 1, h = t & 1;
-  for (int j = 0; j < k; ++j) {
-    for (int l = t; l < j; l += blockDim.x) z[l] = S[l + (int64_t)j * lds];
-    __syncthreads();
-    const double tj = tau[j];
+// The same recurrence by rows: T(i, j) = -tau_j sum_{l=i}^{j-1} T(i, l) S(l, j)
+// needs only row i's own earlier entries, so the rows are independent.  One
+// warp per row (rows spread over CTAs, so the FP64 work of k^3/6 multiply-adds
+// uses many SMs): lane L keeps T(i, l) for l = L, L + 32, ... in registers,
+// each step j sums its lanes' terms and reduces across the warp in a fixed
+// order, and lane j mod 32 keeps the new entry.
+constexpr int TF_WARPS = 4;
+
+__global__ void __launch_bounds__(TF_WARPS * 32) wy_tfactor_rows_kernel(
+    int k, const double* __restrict__ S, int64_t lds, const double* __restrict__ tau, double* T,
+    int64_t ldt) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * TF_WARPS + (threadIdx.x >> 5);
+  if (i >= k) return;  // whole warps only: k rows, TF_WARPS rows per CTA
+  double t[TF_MAX / 32];  // indexed by compile-time u only, so it stays in registers
+  const double ti = tau[i];
+#pragma unroll
+  for (int u = 0; u < TF_MAX / 32; ++u) t[u] = (lane + 32 * u == i) ? ti : 0.0;
+  for (int j = i + 1; j < k; ++j) {
+    const double* Sj = S + (int64_t)j * lds;
     double s = 0.0;
-    if (i < j) {
-      const int mid = i + (j - i + 1) / 2;
-      const int lb = h ? mid : i, le = h ? j : mid;
-      for (int l = lb; l < le; ++l) s = fma(Ts[i + l * k], z[l], s);
+#pragma unroll
+    for (int u = 0; u < TF_MAX / 32; ++u) {
+      const int l = lane + 32 * u;
+      if (l >= i && l < j) s = fma(t[u], __ldg(Sj + l), s);
     }
-    const double other = __shfl_xor_sync(0xffffffffu, s, 1);
-    if (i < j && h == 0) Ts[i + j * k] = -tj * (s + other);
-    if (t == 0) Ts[j + j * k] = tj;
-    __syncthreads();
+    s = warp_sum(s);
+    const double tj = -tau[j] * s;
+#pragma unroll
+    for (int u = 0; u < TF_MAX / 32; ++u)
+      if (lane + 32 * u == j) t[u] = tj;
   }
-  for (int idx = t; idx < k * k; idx += blockDim.x) {
-    const int r = idx % k, c = idx / k;
-    T[r + (int64_t)c * ldt] = r <= c ? Ts[r + c * k] : 0.0;
+#pragma unroll
+  for (int u = 0; u < TF_MAX / 32; ++u) {
+    const int l = lane + 32 * u;
+    if (l < k) T[i + (int64_t)l * ldt] = l >= i ? t[u] : 0.0;
   }
 }
 
@@ -737,9 +744,8 @@ Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, do
   if (k <= 0) return ok_status();
   TraceScope ts(kTrTFactor, st, (double)k * k * k / 3.0, 16.0 * k * k);
   if (k <= TF_MAX) {
-    const size_t smem = sizeof(double) * ((size_t)k * k + k);
-    LLS_TRY(allow_max_dyn_smem((const void*)wy_tfactor_smem_kernel));
-    wy_tfactor_smem_kernel<<<1, 2 * TF_MAX, smem, st>>>((int)k, S, lds, tau, T, ldt);
+    wy_tfactor_rows_kernel<<<(unsigned)ceil_div(k, TF_WARPS), TF_WARPS * 32, 0, st>>>(
+        (int)k, S, lds, tau, T, ldt);
     LLS_LAUNCHED("wy_tfactor_kernel");
     return ok_status();
   }
