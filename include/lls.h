@@ -109,8 +109,9 @@ typedef struct {
  * each n_b in {32, 64, 128} (n_b <= min(m, n) beyond 32) and q in {0, 1, 2},
  * and keeps the fastest whose rank equals the reference's and whose x agrees
  * with the reference x to 1e-9 relative.  nb_out, q_out (host, may be NULL)
- * receive the choice.  Errors: LLS_ERR_ARG (m, n outside 1..2^20, trials < 1),
- * LLS_ERR_NOMEM, and those of lls_solve. */
+ * receive the choice.  Errors: LLS_ERR_ARG (m, n outside 1..2^20, trials < 1,
+ * or requests of this handle queued or running), LLS_ERR_NOMEM, and those of
+ * lls_solve. */
 int lls_autotune(lls_handle h, int64_t m, int64_t n, int32_t trials, int32_t* nb_out,
                  int32_t* q_out);
 /* The (n_b, q) a tuned solve (opt.nb == 0) of an m x n matrix would use. */

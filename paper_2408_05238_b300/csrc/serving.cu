@@ -180,6 +180,12 @@ int64_t enqueue(Handle& h, const lls_problem& req) {
 
 }  // namespace
 
+bool pool_busy(Handle& h) {
+  if (!h.pool) return false;
+  std::lock_guard<std::mutex> lock(h.pool->mu);
+  return h.pool->running > 0 || !h.pool->queue.empty();
+}
+
 void stop_pool(Handle& h) {
   if (!h.pool) return;
   {

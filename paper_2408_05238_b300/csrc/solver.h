@@ -158,6 +158,8 @@ size_t factor_bytes(int64_t m, int64_t n, int nb);
 
 // Stops and joins the worker pool (serving.cu); queued requests are dropped.
 void stop_pool(Handle& h);
+// True while the handle's worker pool has requests queued or running.
+bool pool_busy(Handle& h);
 
 Status jacobi_svd_batched(int count, int b, int b_last, const double* R, int64_t ldr,
                           int64_t strideR, double* sigma, int64_t strideS, double* U, int64_t ldu,

@@ -72,6 +72,12 @@ int lls_autotune(lls_handle hh, int64_t m, int64_t n, int32_t trials, int32_t* n
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || m < 1 || n < 1 || trials < 1 || m > (1LL << 20) || n > (1LL << 20))
     return LLS_ERR_ARG;
+  // the sweep changes the handle's options while it runs: not with requests in flight
+  if (lls::pool_busy(*h)) {
+    h->last_arg = 0;
+    h->last_msg = "lls_autotune: the handle has batched or served requests in flight";
+    return LLS_ERR_ARG;
+  }
   if (!h->tune) h->tune = std::make_shared<lls::TuneTable>();
   cudaStream_t st = h->stream;
   const int64_t r = std::max<int64_t>(1, std::min(m, n) / 2);
