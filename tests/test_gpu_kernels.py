@@ -123,8 +123,10 @@ def test_panel_qr_zero_and_rank_deficient_columns(lls):
 
 
 # ------------------------------------------------------------------ a7 SVD
-@pytest.mark.parametrize("b", [1, 2, 3, 17, 64, 128])
+@pytest.mark.parametrize("b", [1, 2, 3, 17, 33, 64, 97, 127, 128])
 def test_jacobi_svd(lls, b):
+    # b < 32: one CTA; 32 <= b <= 64: a cluster of 4 CTAs; b > 64: a cluster of 8
+    # (odd b leaves a padding column in the round-robin order)
     g = np.random.default_rng(b)
     R = np.triu(g.standard_normal((b, b))) @ np.diag(np.logspace(0, -10, b))
     sigma, Us, Vs, status = lls.lls_k_jacobi_svd(dev(R))
@@ -138,8 +140,8 @@ def test_jacobi_svd(lls, b):
     assert np.allclose(Us @ np.diag(sigma) @ Vs.T, np.triu(R), atol=1e-13 * ref[0])
 
 
-def test_jacobi_svd_singular_block_completes_u(lls):
-    b = 12
+@pytest.mark.parametrize("b", [12, 70])
+def test_jacobi_svd_singular_block_completes_u(lls, b):
     R = np.triu(np.random.default_rng(1).standard_normal((b, b)))
     R[:, [2, 5, 9]] = 0.0
     R[[4, 7], :] = 0.0
