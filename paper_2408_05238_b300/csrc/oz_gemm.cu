@@ -7,8 +7,8 @@
 //  1. Every row i of op(A) is scaled by 2^-e_i (2^e_i > max_k |op(A)_ik|) and
 //     every column j of op(B) by 2^-f_j, so each scaled entry x lies in
 //     (-1, 1).  With integer arithmetic only, x * 2^56 (rounded to an integer)
-//     is written in balanced base 128:  x = sum_{s=1..8} d_s 2^-7s with
-//     d_1 in [-128, 128] and d_2..d_8 in [-64, 64] -- integers that BF16
+//     is written in signed base 128:  x = sum_{s=1..8} d_s 2^-7s with
+//     d_1 in [-128, 128] and d_2..d_8 in [-64, 63] -- integers that BF16
 //     holds exactly.  The 8 digit planes ("slices") are stored K-major.
 //  2. C_ij = 2^(e_i + f_j) sum_{s,t} 2^-7(s+t) sum_k d_s(i,k) d'_t(k,j).  The
 //     36 products with s + t <= 9 run on tcgen05.mma kind::f16 (BF16 in,
@@ -86,8 +86,14 @@ __device__ __forceinline__ int exp_of_max(unsigned long long bits) {
   return ex - 1023 + 1;
 }
 
-// x * 2^(56 - e) rounded to an int64 (|result| < 2^56), then 8 balanced
-// base-128 digits, most significant first.
+// x * 2^(56 - e) rounded to an int64 X (|X| < 2^56), then 8 signed base-128
+// digits, most significant first.  With the bias B = 64 (1 + 128 + ... + 128^7),
+// X + B written in base 128 has the digits d_s + 64: every digit below the top
+// one is a plain 7-bit field of X + B (no carries to propagate), and the top
+// one is its arithmetic shift by 49.  d_1 lies in [-128, 128], d_2..d_8 in
+// [-64, 63], and X = sum_s d_s 128^(8 - s) exactly.
+constexpr long long kDigitBias = 0x81020408102040LL;  // 64 (128^8 - 1) / 127
+
 __device__ __forceinline__ void make_digits(double v, int e, int d[OZ_S]) {
   unsigned long long bits = (unsigned long long)__double_as_longlong(v);
   int ex = (int)((bits >> 52) & 0x7FF);
@@ -99,14 +105,18 @@ __device__ __forceinline__ void make_digits(double v, int e, int d[OZ_S]) {
     else if (sh > -60) X = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
     if (bits >> 63) X = -X;
   }
+  const long long Y = X + kDigitBias;
+  d[0] = (int)(Y >> 49) - 64;
+  const unsigned int lo = (unsigned int)Y, hi = (unsigned int)((unsigned long long)Y >> 32);
 #pragma unroll
-  for (int s = 0; s < OZ_S - 1; ++s) {
-    const int shift = 49 - 7 * s;
-    long long q = (X + (1LL << (shift - 1))) >> shift;
-    X -= q * (1LL << shift);
-    d[s] = (int)q;
+  for (int s = 1; s < OZ_S; ++s) {
+    const int shift = 49 - 7 * s;  // 42, 35, ..., 0
+    unsigned int f;
+    if (shift >= 32) f = hi >> (shift - 32);
+    else if (shift + 7 <= 32) f = lo >> shift;
+    else f = __funnelshift_r(lo, hi, shift);
+    d[s] = (int)(f & 127u) - 64;
   }
-  d[OZ_S - 1] = (int)X;
 }
 
 // K-contiguous operand: one warp per row r; max over k, then the digits.
