@@ -277,6 +277,17 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
   atomicExch(err, 1);
   return false;
 }
+// The same for the single producer and MMA-issuing threads, whose waits sit
+// on the tensor pipe's critical path: no sleep between polls (try_wait
+// itself suspends the thread for a while), a bounded number of polls.
+__device__ bool mbar_wait_spin(uint64_t* bar, uint32_t parity, int* err) {
+  for (long long i = 0; i < kOzWaitLimit / 4; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && *reinterpret_cast<volatile int*>(err) != 0) return false;
+  }
+  atomicExch(err, 1);
+  return false;
+}
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int c0, int c1, int c2) {
   asm volatile(
@@ -419,7 +430,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     for (int kb = 0; kb < nkb && ok; ++kb) {
       const int k = kbeg + kb * OZ_BK;
       const int zs = kb % OZ_ZST;
-      if (kb >= OZ_ZST && !mbar_wait(&zempty[zs], ((kb / OZ_ZST) - 1) & 1, a.err)) {
+      if (kb >= OZ_ZST && !mbar_wait_spin(&zempty[zs], ((kb / OZ_ZST) - 1) & 1, a.err)) {
         ok = false;
         break;
       }
@@ -427,7 +438,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       tma_load_3d(zring + zs * OZ_ZBYTES, &mapZ, &zfull[zs], k, n0, 0);
       for (int s = 0; s < OZ_S; ++s, ++it) {
         const int xs = it % OZ_XST;
-        if (it >= OZ_XST && !mbar_wait(&xempty[xs], ((it / OZ_XST) - 1) & 1, a.err)) {
+        if (it >= OZ_XST && !mbar_wait_spin(&xempty[xs], ((it / OZ_XST) - 1) & 1, a.err)) {
           ok = false;
           break;
         }
@@ -441,7 +452,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     bool ok = true;
     for (int kb = 0; kb < nkb && ok; ++kb) {
       const int zs = kb % OZ_ZST;
-      if (!mbar_wait(&zfull[zs], (kb / OZ_ZST) & 1, a.err)) {
+      if (!mbar_wait_spin(&zfull[zs], (kb / OZ_ZST) & 1, a.err)) {
         ok = false;
         break;
       }
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
       for (int s = 0; s < OZ_S; ++s) {
         const int xs = it % OZ_XST;
-        if (!mbar_wait(&xfull[xs], (it / OZ_XST) & 1, a.err)) {
+        if (!mbar_wait_spin(&xfull[xs], (it / OZ_XST) & 1, a.err)) {
           ok = false;
           break;
         }
