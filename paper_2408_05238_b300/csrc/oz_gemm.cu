@@ -188,11 +188,15 @@ __global__ void __launch_bounds__(256) oz_slice_kcontig_chunk_kernel(
   const int64_t k0 = (int64_t)blockIdx.x * OZ_KCH;
   const int e = exps[r];
   const int64_t plane = R * ldk;
-  for (int64_t k = k0 + threadIdx.x; k < min(ldk, k0 + OZ_KCH); k += 256) {
-    int d[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (k < K) make_digits(op_load(src, ld, true, ul != 0, r, k), e, d);
+  // two consecutive k per thread: one 4-byte store per plane (ldk and k0 are even)
+  for (int64_t k = k0 + 2 * threadIdx.x; k < min(ldk, k0 + OZ_KCH); k += 512) {
+    int d0[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0}, d1[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < K) make_digits(op_load(src, ld, true, ul != 0, r, k), e, d0);
+    if (k + 1 < K) make_digits(op_load(src, ld, true, ul != 0, r, k + 1), e, d1);
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) out[s * plane + r * ldk + k] = __int2bfloat16_rn(d[s]);
+    for (int s = 0; s < OZ_S; ++s)
+      *reinterpret_cast<__nv_bfloat162*>(out + s * plane + r * ldk + k) =
+          __halves2bfloat162(__int2bfloat16_rn(d0[s]), __int2bfloat16_rn(d1[s]));
   }
 }
 
@@ -219,28 +223,32 @@ __global__ void oz_exps_kernel(int64_t R, const unsigned long long* __restrict__
 
 // R-contiguous operand, pass 2: digits of a 32 (r) x 32 (k) tile, transposed
 // through shared memory so that the K-major slices are written coalesced.
-__global__ void oz_slice_rcontig_kernel(int64_t R, int64_t K, const double* __restrict__ src,
-                                        int64_t ld, int ul, const int* __restrict__ exps,
-                                        __nv_bfloat16* __restrict__ out, int64_t ldk) {
-  __shared__ short tile[OZ_S][32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t r = r0 + tx, k = k0 + i;
-    int d[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (r < R && k < K) make_digits(op_load(src, ld, false, ul != 0, r, k), exps[r], d);
+__global__ void __launch_bounds__(256) oz_slice_rcontig_kernel(
+    int64_t R, int64_t K, const double* __restrict__ src, int64_t ld, int ul,
+    const int* __restrict__ exps, __nv_bfloat16* __restrict__ out, int64_t ldk) {
+  __shared__ short tile[OZ_S][32][66];  // [plane][r][k], padded rows
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps
+  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
+  {
+    const int64_t r = r0 + lane;
+    const int e = r < R ? exps[r] : kZeroExp;
+    for (int kk = w; kk < 64; kk += 8) {  // coalesced: 32 consecutive rows per load
+      const int64_t k = k0 + kk;
+      int d[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (r < R && k < K) make_digits(op_load(src, ld, false, ul != 0, r, k), e, d);
 #pragma unroll
-    for (int s = 0; s < OZ_S; ++s) tile[s][i][tx] = (short)d[s];
+      for (int s = 0; s < OZ_S; ++s) tile[s][lane][kk] = (short)d[s];
+    }
   }
   __syncthreads();
   const int64_t plane = R * ldk;
-  for (int i = ty; i < 32; i += 8) {
-    const int64_t r = r0 + i, k = k0 + tx;
+  for (int rr = w; rr < 32; rr += 8) {  // one 128-byte store per row and plane
+    const int64_t r = r0 + rr, k = k0 + 2 * lane;
     if (r >= R || k >= ldk) continue;
-    for (int s = 0; s < OZ_S; ++s) {
-      int v = tile[s][tx][i];
-      out[s * plane + r * ldk + k] = __int2bfloat16_rn(v);
-    }
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s)
+      *reinterpret_cast<__nv_bfloat162*>(out + s * plane + r * ldk + k) = __halves2bfloat162(
+          __int2bfloat16_rn(tile[s][rr][2 * lane]), __int2bfloat16_rn(tile[s][rr][2 * lane + 1]));
   }
 }
 
@@ -687,7 +695,7 @@ Status oz_slice(int64_t R, int64_t K, const double* src, int64_t ld, bool kconti
   LLS_LAUNCHED("oz_rowmax_rcontig_kernel");
   oz_exps_kernel<<<(unsigned)ceil_div(R, 256), 256, 0, st>>>(R, maxbuf, exps);
   LLS_LAUNCHED("oz_exps_kernel");
-  dim3 g2((unsigned)ceil_div(R, 32), (unsigned)ceil_div(ldk, 32));
+  dim3 g2((unsigned)ceil_div(R, 32), (unsigned)ceil_div(ldk, 64));
   oz_slice_rcontig_kernel<<<g2, 256, 0, st>>>(R, K, src, ld, unit_lower ? 1 : 0, exps, out, ldk);
   LLS_LAUNCHED("oz_slice_rcontig_kernel");
   return ok_status();
