@@ -72,21 +72,21 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 }
 
 // Grid-wide barrier on a monotonically increasing arrival counter (reset to
-// 0 before each launch; a launch passes at most 2^31 / CTAs barriers): CTA
-// thread 0 adds 1 with release semantics and waits, with acquire loads,
-// until the counter reaches the next multiple of the CTA count.  The wait is
-// bounded (kBarrierSpinLimit polls); on expiry, or when another CTA has
-// already failed, it sets *err and every thread of the CTA gets false.
-__device__ inline bool grid_sync(const GridBarrier& bar) {
+// 0 before each launch; a launch passes at most 2^31 / CTAs barriers).  Each
+// CTA counts its own barriers in `epoch` (a variable of the calling kernel,
+// starting at 0), so thread 0 arrives with a fire-and-forget release add and
+// waits, with acquire loads, until the counter reaches (epoch + 1) x CTAs.
+// The wait is bounded (kBarrierSpinLimit polls); on expiry, or when another
+// CTA has already failed, it sets *err and every thread of the CTA gets false.
+__device__ inline bool grid_sync(const GridBarrier& bar, unsigned int& epoch) {
   __syncthreads();
   __shared__ int s_fail;
   if (threadIdx.x == 0) {
     s_fail = 0;
     const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int target = (epoch + 1) * nb;
     __threadfence();
-    unsigned int old;
-    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar.count) : "memory");
-    const unsigned int target = (old / nb + 1) * nb;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar.count) : "memory");
     long long it = 0;
     for (;;) {
       unsigned int cur;
@@ -101,6 +101,7 @@ __device__ inline bool grid_sync(const GridBarrier& bar) {
     }
     __threadfence();
   }
+  ++epoch;
   __syncthreads();
   return s_fail == 0;
 }

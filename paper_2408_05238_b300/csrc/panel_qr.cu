@@ -61,6 +61,7 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(PQ_THREADS) panel_qr_kernel(PanelArgs a) {
+  unsigned int epoch = 0;  // grid barriers passed by this CTA
   extern __shared__ double smem[];
   double* v_s = smem;               // rows_per
   double* d_s = smem + a.rows_per;  // n
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(PQ_THREADS) panel_qr_kernel(PanelArgs a) {
   };
 
   if (kmax > 0) own_ss(0);
-  if (!grid_sync(a.bar)) return;
+  if (!grid_sync(a.bar, epoch)) return;
 
   for (int64_t j = 0; j < kmax; ++j) {
     // ---- 2. reflector scalars (identical in every CTA) and local dots
@@ -114,14 +115,14 @@ __global__ void __launch_bounds__(PQ_THREADS) panel_qr_kernel(PanelArgs a) {
       s = warp_sum(s);
       if (lane == 0) a.part_dot[(int64_t)cta * n + c] = s;
     }
-    if (!grid_sync(a.bar)) return;
+    if (!grid_sync(a.bar, epoch)) return;
 
     // ---- 3a. cross-CTA reduction of the dot products (column c by CTA c mod G)
     for (int64_t c = j + 1 + cta; c < n; c += G) {
       double s = block_sum(t < G ? __ldcg(a.part_dot + (int64_t)t * n + c) : 0.0, red);
       if (t == 0) a.dot_final[c] = s;
     }
-    if (!grid_sync(a.bar)) return;
+    if (!grid_sync(a.bar, epoch)) return;
 
     // ---- 3b. rank-1 update of this CTA's rows, then the next column's norm
     for (int64_t c = j + 1 + t; c < n; c += PQ_THREADS) d_s[c] = tau * __ldcg(a.dot_final + c);
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(PQ_THREADS) panel_qr_kernel(PanelArgs a) {
     if (t == 0 && cta == 0) a.tau[j] = tau;
     __syncthreads();
     if (j + 1 < kmax) own_ss(j + 1);
-    if (!grid_sync(a.bar)) return;
+    if (!grid_sync(a.bar, epoch)) return;
   }
 }
 
@@ -216,6 +217,7 @@ __device__ __forceinline__ void quarter(int lo, int hi, int q, int& b, int& e) {
 }
 
 __global__ void __launch_bounds__(PS_THREADS) panel_qr_slab_kernel(SlabArgs a) {
+  unsigned int epoch = 0;  // grid barriers passed by this CTA
   extern __shared__ double sm[];
   const int n = a.n, ldsl = a.ldsl;
   double* slab = sm;                          // ldsl x n, column-major
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(PS_THREADS) panel_qr_slab_kernel(SlabArgs a) {
   if (kmax > 0) publish(0);
   const int warp = t >> 5, lane = t & 31;
   for (int j = 0; j < kmax; ++j) {
-    if (!grid_sync(a.bar)) return;  // partial sums of column j are in
+    if (!grid_sync(a.bar, epoch)) return;  // partial sums of column j are in
     const int ncol = n - j;
     // ---- column j + c is reduced by CTA c mod G, one warp per column, over
     // the CTAs in a fixed order; CTA 0 also derives the reflector.
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(PS_THREADS) panel_qr_slab_kernel(SlabArgs a) {
         }
       }
     }
-    if (!grid_sync(a.bar)) return;  // totals and the reflector are in
+    if (!grid_sync(a.bar, epoch)) return;  // totals and the reflector are in
     {
       const double* TG = a.totg + (size_t)(j & 1) * (n + 4);
       if (t < ncol) {
