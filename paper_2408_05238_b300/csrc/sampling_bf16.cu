@@ -124,8 +124,6 @@ Status sample_bf16(Handle& h, const double* A, int64_t lda, int64_t mp, int64_t 
   LLS_TRY(h.mixed_misc.reserve(64));
   unsigned long long* amax = h.mixed_misc.as<unsigned long long>();
   unsigned int* fmax = reinterpret_cast<unsigned int*>(amax + 1);
-  int* err = reinterpret_cast<int*>(amax + 2);  // reported through the panel barrier word
-  (void)err;
   DevStatus* ds = h.dstat.as<DevStatus>();
   Scratch tws{h.tc_ws.p, h.tc_ws.bytes};
   auto* A16 = h.A16.as<__nv_bfloat16>();
