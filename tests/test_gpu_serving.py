@@ -181,3 +181,32 @@ def test_autotune_table_drives_tuned_solves(lls, tmp_path):
             lls.lls_tuning_load(h, str(bad))
     finally:
         lls.lls_destroy(h)
+
+
+def test_tuned_batched_solves_use_the_table(lls, tmp_path):
+    # workers of a tuned handle (nb = 0) read the parent's table: a batch
+    # solved through the pool equals solves with the table's explicit choice
+    ps = problems(6, 31)
+    path = tmp_path / "tune.txt"
+    rows = ["# test table"]
+    for p in ps:
+        m, n = p.A.shape
+        rows.append(f"{(m - 1).bit_length()} {(n - 1).bit_length()} 32 2")
+    path.write_text("\n".join(rows) + "\n")
+    h = lls.lls_create(nb=0, q=1, seed=2004)
+    lls.lls_set_workers(h, 3)
+    lls.lls_tuning_load(h, str(path))
+    try:
+        held, plist = [], []
+        for p in ps:
+            A, B = dev(p.A), dev(p.B)
+            X = lls.empty_colmajor(p.A.shape[1], p.B.shape[1])
+            held.append((A, B, X))
+            plist.append(lls.make_problem(A, B, p.tol, X))
+        assert lls.lls_solve_batched(h, plist) == 0
+        torch.cuda.synchronize()
+    finally:
+        lls.lls_destroy(h)
+    for p, (_, _, X) in zip(ps, held):
+        x_explicit, _ = solve_alone(lls, p, nb=32, q=2)
+        assert np.array_equal(X.cpu().numpy(), x_explicit)
