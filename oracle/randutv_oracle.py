@@ -25,7 +25,7 @@ arXiv 2408.05238, Sec. 3):
 * ``pinv_solve``   -- Sec. 2.2 truncated-SVD least squares, used as the
                       brute-force pin on small inputs.
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here where it is silent or garbled:
 
 * The right update of Fig. 2 is applied to *all* m rows of the trailing
   columns (Fig. 2 prints only the A_BR block; without the rows above,
