@@ -435,6 +435,24 @@ def run_serving(a):
     return 0
 
 
+def max_over_ranks(seconds, dist, device):
+    """Barrier, then the largest of every rank's time (the job's wall time)."""
+    if not dist:
+        return seconds
+    import torch
+
+    dist.barrier()
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(flops_per_solve, steps, world, seconds):
+    """Whole-job figures of N independent replicas: (solves, TFLOP/s)."""
+    total = steps * world
+    return total, flops_per_solve * total / seconds / 1e12
+
+
 def main():
     a = parse()
     if a.nrhs is None:
@@ -494,15 +512,9 @@ def main():
     trace = lls.lls_trace_read(h)
     lls.lls_trace_enable(h, False)
     clocks = clk.summary()
-    if dist:
-        dist.barrier()
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
     flops = pm.lls_flops(m, n, a.nb, a.q, ranks[-1], a.nrhs)
-    total_solves = a.steps * world
-    value = flops * total_solves / elapsed / 1e12
+    total_solves, value = replica_throughput(flops, a.steps, world, elapsed)
 
     # accuracy of the timed result against the construction's pseudoinverse
     rr = ranks[-1]
@@ -546,10 +558,7 @@ def main():
         t0 = time.perf_counter()
         lls.lls_solve_host_ptr(h, A_h.data_ptr(), m, n, B_h.data_ptr(), a.nrhs, tol, X_h.data_ptr())
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist, "cuda")
         e2e = {"value": flops * world / dt / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 8 * (m * n + m * a.nrhs), "d2h_bytes_per_step": 8 * n * a.nrhs,
                "seconds_per_step": dt, "api": "lls_solve_host (pinned host buffers)"}
