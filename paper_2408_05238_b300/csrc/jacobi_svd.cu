@@ -52,6 +52,55 @@ __device__ __forceinline__ void pair_of(int round, int i, int bp, int& p, int& q
   }
 }
 
+// Rotation (c, s) of Rutishauser's formulas with the divisions and square
+// roots replaced by Newton-Raphson iterations (reciprocal r <- r (2 - x r),
+// reciprocal square root y <- y (3 - x y^2) / 2, two each from a
+// single-precision seed after an exact power-of-two scaling): fewer FP64
+// instructions on the SVD's serial path.  c^2 + s^2 = 1 to a few ulps, so the
+// accumulated V stays orthogonal to FP64 accuracy.
+__device__ __forceinline__ double rcp_newton(double x) {  // x > 0, normal
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  const double m = __longlong_as_double(b - ((long long)e << 52));  // [1, 2)
+  double r = (double)(1.0f / (float)m);
+  r = r * fma(-m, r, 2.0);
+  r = r * fma(-m, r, 2.0);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)e << 52));
+}
+__device__ __forceinline__ double rsqrt_newton(double x) {  // x >= 1, normal
+  const long long b = __double_as_longlong(x);
+  const int e2 = ((int)((b >> 52) & 0x7FF) - 1023) & ~1;
+  const double m = __longlong_as_double(b - ((long long)e2 << 52));  // [1, 4)
+  double y = (double)rsqrtf((float)m);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  y = y * fma(-0.5 * m, y * y, 1.5);
+  return __longlong_as_double(__double_as_longlong(y) - ((long long)(e2 / 2) << 52));
+}
+__device__ __forceinline__ void jacobi_rotation(double al, double be, double ga, double& c,
+                                                double& sn) {
+  const double g2 = fabs(2.0 * ga);
+  double t;
+  if (g2 < 1e-290 || g2 > 1e290) {  // outside the scaled seeds' range: library path
+    const double zeta = (be - al) / (2.0 * ga);
+    if (fabs(zeta) > 1e150) t = 0.5 / zeta;
+    else t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    c = 1.0 / sqrt(1.0 + t * t);
+    sn = c * t;
+    return;
+  }
+  // zeta = (be - al) / (2 ga): the magnitude from the reciprocal, the sign of ga applied
+  const double zeta = (ga < 0.0 ? -1.0 : 1.0) * ((be - al) * rcp_newton(g2));
+  if (fabs(zeta) > 1e150) {
+    t = 0.5 / zeta;
+  } else {
+    const double d = fma(zeta, zeta, 1.0);
+    const double w = d * rsqrt_newton(d);  // sqrt(1 + zeta^2)
+    t = copysign(rcp_newton(fabs(zeta) + w), zeta);
+  }
+  c = rsqrt_newton(fma(t, t, 1.0));
+  sn = c * t;
+}
+
 __global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(SvdBatch a) {
   extern __shared__ double As[];  // b x b, leading dimension b
   __shared__ int s_rot;
@@ -116,11 +165,8 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_svd_kernel(SvdBatch a) {
         ga += __shfl_xor_sync(mask, ga, o);
       }
       if (valid && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-        double zeta = (be - al) / (2.0 * ga);
-        double tt;
-        if (fabs(zeta) > 1e150) tt = 0.5 / zeta;
-        else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
+        double c, s;
+        jacobi_rotation(al, be, ga, c, s);
         double* ap = As + p * b;
         double* aq = As + q * b;
         for (int r = gl; r < b; r += tpp) {
@@ -284,14 +330,7 @@ __global__ void __launch_bounds__(SVDC_WARPS * 32) jacobi_svd_cluster_kernel(Svd
           ga = warp_sum(ga);
           if (al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
             double c = 0.0, sn = 0.0;
-            if (lane == 0) {
-              const double zeta = (be - al) / (2.0 * ga);
-              double tt;
-              if (fabs(zeta) > 1e150) tt = 0.5 / zeta;
-              else tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-              c = 1.0 / sqrt(1.0 + tt * tt);
-              sn = c * tt;
-            }
+            if (lane == 0) jacobi_rotation(al, be, ga, c, sn);
             c = __shfl_sync(0xffffffffu, c, 0);
             sn = __shfl_sync(0xffffffffu, sn, 0);
             for (int r = lane; r < b; r += 32) {
