@@ -33,3 +33,29 @@ def test_steps_cover_min_dimension():
     for m, n, nb in [(100, 37, 8), (37, 100, 8), (64, 64, 64), (5, 5, 7)]:
         ks = list(pm.steps(m, n, nb))
         assert sum(b for _, b in ks) == min(m, n)
+
+
+def test_c3_flops_match_survey_estimate():
+    """32768 x 16384, nb = 128, q = 1: about 54.2 TFLOP for the factorization."""
+    f = pm.randutv_flops(32768, 16384, 128, 1)
+    assert 53.7e12 < f < 54.7e12
+
+
+def test_bench_workload_shapes():
+    """The bench's single-matrix workloads: C2 square with rank n/2, C3 2n x n
+    with rank 12000 n / 16384."""
+    import argparse
+    import bench
+
+    c2 = argparse.Namespace(workload="c2", n=16384)
+    c3 = argparse.Namespace(workload="c3", n=16384)
+    assert bench.dense_shape(c2) == (16384, 16384, 8192, 1e-10)
+    assert bench.dense_shape(c3) == (32768, 16384, 12000, 1e-6)
+    assert bench.dense_shape(argparse.Namespace(workload="c3", n=1024))[:3] == (2048, 1024, 750)
+
+
+def test_bench_replica_throughput():
+    import bench
+
+    solves, tf = bench.replica_throughput(30.0e12, 2, 4, 60.0)
+    assert solves == 8 and tf == pytest.approx(4.0)
