@@ -543,9 +543,16 @@ def main():
         achieved = g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
         peak = FP64_FLOPS_PER_CLK_PER_SM * NUM_SM * sm_max * 1e6 / 1e12
         bound, psrc = "alu", "derived: 2 DFMA/clk/SM x 148 SMs x max SM clock"
-    traced = sum(v[1] for v in trace.values()) or 1.0
+    # kernel families and phases of the method are two views of the same time:
+    # shares are taken within each view
+    fam = {k: v for k, v in trace.items() if not k.startswith("phase:")}
+    phs = {k[len("phase:"):]: v for k, v in trace.items() if k.startswith("phase:")}
+    traced = sum(v[1] for v in fam.values()) or 1.0
     shares = {k: {"launches": v[0], "seconds": round(v[1], 4), "share": round(v[1] / traced, 4)}
-              for k, v in trace.items()}
+              for k, v in fam.items()}
+    phase_shares = {k: {"count": v[0], "seconds": round(v[1], 4),
+                        "share": round(v[1] / elapsed if elapsed else 0.0, 4)}
+                    for k, v in phs.items()}
 
     e2e = None
     if not a.no_e2e:
@@ -588,7 +595,7 @@ def main():
                          "launches": g[0], "avg_launch_ms": 1e3 * g[1] / max(g[0], 1)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "accuracy": {"x_rel_err_vs_pinv": x_err, "normal_eq_residual": ner},
-            "trace": shares,
+            "trace": shares, "phases": phase_shares,
         }
         print(json.dumps(out))
     if dist:

@@ -194,6 +194,12 @@ int lls_set_memory_cap(lls_handle h, int64_t bytes);
  * (LLS_PENDING before; call it before lls_poll forgets the ticket). */
 int lls_ticket_factor(lls_handle h, int64_t ticket, int64_t* factor_id);
 
+/* Withdraw a request that has not started: LLS_OK, and the ticket is
+ * forgotten (lls_poll then returns LLS_ERR_NOT_FOUND); LLS_ERR_NOT_FOUND when
+ * the ticket is unknown or its request has already started or finished
+ * (poll it as usual). */
+int lls_cancel(lls_handle h, int64_t ticket);
+
 /* Number of worker streams (1..64, default 4) used by lls_solve_batched and
  * lls_submit; waits for running requests and drops queued ones. */
 int lls_set_workers(lls_handle h, int workers);
@@ -209,16 +215,29 @@ typedef struct {
 
 /* Turn tracing on (1) or off (0) for later calls on h; turning it on clears
  * the counters.  Events are recorded on the handle's stream around every
- * kernel launch the calls make (the paper's per-task time table). */
+ * kernel launch the calls make (the paper's per-task time table), and
+ * around each phase of the method: entries named "phase:sample",
+ * "phase:qr_y", "phase:right_update", "phase:panel", "phase:left_update",
+ * "phase:block_svd", "phase:rank", "phase:nullify" and "phase:solve" (steps
+ * a1/a2 .. a10; a phase's time includes the kernels it launches, so phases
+ * and kernel families are two views of the same time). */
 int lls_trace_enable(lls_handle h, int on);
 
-/* Copy up to max per-family counters to out (host array); *count receives
- * the number of families with launches.  Waits for the recorded events. */
+/* Copy up to max per-family and per-phase counters to out (host array);
+ * *count receives the number of entries with launches (phases count their
+ * instances).  Waits for the recorded events. */
 int lls_trace_read(lls_handle h, lls_trace_stat* out, int64_t max, int64_t* count);
 
 /* Number of kernels this library has launched since it was loaded (all
  * handles and threads). */
 int64_t lls_launch_count(void);
+
+/* Testing hook (failure injection on the host): the (after + 1)-th device
+ * workspace allocation from now, in any handle, fails as if the device were
+ * out of memory (the call returns LLS_ERR_NOMEM and the handle stays usable);
+ * after = -1 turns the injection off.  Allocations inside the lls_k_* step
+ * entry points are not covered. */
+int lls_debug_fail_allocation(int64_t after);
 
 /* Static text for a status code. */
 const char* lls_status_string(int status);

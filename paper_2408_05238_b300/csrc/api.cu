@@ -294,3 +294,13 @@ int lls_last_error(lls_handle hh, int* arg_index, char* msg, int64_t len) {
 }
 
 }  // extern "C"
+
+namespace lls {
+std::atomic<int64_t> g_fail_alloc_countdown{-1};
+}  // namespace lls
+
+extern "C" int lls_debug_fail_allocation(int64_t after) {
+  if (after < -1) return LLS_ERR_ARG;
+  lls::g_fail_alloc_countdown.store(after < 0 ? -1 : after);
+  return LLS_OK;
+}

@@ -291,6 +291,22 @@ int lls_poll(lls_handle hh, int64_t ticket, int* status) {
   return LLS_OK;
 }
 
+int lls_cancel(lls_handle hh, int64_t ticket) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return LLS_ERR_ARG;
+  if (!h->pool) return LLS_ERR_NOT_FOUND;
+  Handle::Pool& pool = *h->pool;
+  {
+    std::lock_guard<std::mutex> lock(pool.mu);
+    auto q = std::find(pool.queue.begin(), pool.queue.end(), ticket);
+    if (q == pool.queue.end()) return LLS_ERR_NOT_FOUND;  // unknown, started or finished
+    pool.queue.erase(q);
+    pool.tickets.erase(ticket);
+  }
+  pool.cv_work.notify_all();  // the head of the queue may have changed
+  return LLS_OK;
+}
+
 int lls_ticket_factor(lls_handle hh, int64_t ticket, int64_t* factor_id) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || !factor_id) return LLS_ERR_ARG;

@@ -18,6 +18,7 @@
 //    row updates.
 #include <algorithm>
 #include <cstring>
+#include <optional>
 
 #include "lls_kernels.h"
 #include "oz_gemm.h"
@@ -165,6 +166,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     double* tauUi = f.tauU.d() + i * nb;
 
     // ---- a1/a2: sketch and sample Y = (A_BR^T A_BR)^q A_BR^T G
+    std::optional<TraceScope> phase;
+    phase.emplace(kTrPhaseSample, st);
     if (h.opt.precision == LLS_MIXED_BF16) {
       LLS_TRY(sample_bf16(h, ABR, ldt, mp, np, b, q, h.opt.seed, i, Y, ldw));
     } else {
@@ -179,11 +182,15 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       }
     }
     // ---- a3: [Y, T_V, W_V] = unpivoted_QR(Y)
+    phase.reset();
+    phase.emplace(kTrPhaseQrY, st);
     LLS_TRY(panel_qr(np, b, Y, ldw, tauVi, pws, &ds->barrier_err, st));
     LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, b, b, np, 1.0, Y, ldw, Y, ldw, 0.0, h.S.d(),
                   nb));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauVi, TVi, nb, st));
     // ---- a4: T(:, k:n) <- T(:, k:n) - (T(:, k:n) W_V) T_V W_V^T, all m rows
+    phase.reset();
+    phase.emplace(kTrPhaseRight, st);
     double* Tk = T + k * ldt;
     LLS_TRY(xgemm(false, false, kDense, kUnitLower, m, b, np, 1.0, Tk, ldt, Y, ldw, 0.0, h.P.d(),
                   m));
@@ -192,12 +199,16 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     LLS_TRY(xgemm(false, true, kDense, kUnitLower, m, np, b, -1.0, h.P2.d(), m, Y, ldw, 1.0, Tk,
                   ldt));
     // ---- a5: [[A11; A21], T_U, W_U] = unpivoted_QR([A11; A21])
+    phase.reset();
+    phase.emplace(kTrPhasePanel, st);
     LLS_TRY(panel_qr(mp, b, ABR, ldt, tauUi, pws, &ds->barrier_err, st));
     LLS_TRY(copy_upper(b, ABR, ldt, f.Rblk.d() + i * blk, nb, st));
     LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, b, b, mp, 1.0, ABR, ldt, ABR, ldt, 0.0,
                   h.S.d(), nb));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauUi, TUi, nb, st));
     // ---- a6: [A12; A22] <- (I - W_U T_U W_U^T)^T [A12; A22]
+    phase.reset();
+    phase.emplace(kTrPhaseLeft, st);
     if (np > b) {
       double* A12 = ABR + b * ldt;
       LLS_TRY(xgemm(true, false, kUnitLower, kDense, b, np - b, mp, 1.0, ABR, ldt, A12, ldt, 0.0,
@@ -210,6 +221,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   }
 
   // ---- a7: all diagonal-block SVDs in one launch, then their updates
+  std::optional<TraceScope> phase;
+  phase.emplace(kTrPhaseSvd, st);
   if (steps > 0) {
     LLS_TRY(jacobi_svd_batched((int)steps, nb, (int)f.bs.back(), f.Rblk.d(), nb, (int64_t)blk,
                                f.sigma.d(), nb, f.US.d(), nb, (int64_t)blk, f.VS.d(), nb,
@@ -235,10 +248,13 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   }
 
   // ---- a8: Compute_rank
+  phase.reset();
+  phase.emplace(kTrPhaseRank, st);
   if (mn > 0) {
     LLS_TRY(resolve_tol(tol, std::max(m, n), T, &ds->tol, st));
     LLS_TRY(rank_scan_dev(mn, T, ldt, &ds->tol, ds->rank, st));
   }
+  phase.reset();
   if (!h.hstat) LLS_CUDA(cudaMallocHost((void**)&h.hstat, sizeof(DevStatus)));
   LLS_CUDA(cudaMemcpyAsync(h.hstat, ds, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   LLS_CUDA(cudaStreamSynchronize(st));
@@ -266,6 +282,7 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   // Q = I - W T W^T from the right, and x gets Q from the left.
   const int64_t r = f.rank;
   if (h.opt.nullify && r > 0 && r < n) {
+    TraceScope nullify_phase(kTrPhaseNullify, st);
     const int64_t L = n - r;
     int64_t j1 = r;
     size_t off_m = 0, off_t = 0, off_tau = 0;
@@ -344,6 +361,7 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   const int64_t r = f.rank;
   if (n == 0 || nrhs == 0) return ok_status();
   if (r == 0 || m == 0) return fill_zero(n, nrhs, X, ldx, st);
+  TraceScope solve_phase(kTrPhaseSolve, st);
   LLS_TRY(h.bw.reserve(sizeof(double) * (size_t)m * nrhs));
   LLS_TRY(h.z.reserve(sizeof(double) * (size_t)n * nrhs));
   LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)nb * nrhs));

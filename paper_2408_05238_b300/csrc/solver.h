@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -14,6 +15,18 @@
 #include "trace.h"
 
 namespace lls {
+
+// Allocation-failure injection for tests (lls_debug_fail_allocation): while
+// >= 0, each workspace allocation decrements it and the one that finds it
+// at 0 fails as if the device were out of memory.
+extern std::atomic<int64_t> g_fail_alloc_countdown;
+inline bool injected_alloc_failure() {
+  int64_t c = g_fail_alloc_countdown.load(std::memory_order_relaxed);
+  while (c >= 0) {
+    if (g_fail_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+  }
+  return false;
+}
 
 // Owning device buffer.
 struct DevBuf {
@@ -37,6 +50,9 @@ struct DevBuf {
     if (need <= bytes) return ok_status();
     release();
     if (need == 0) return ok_status();
+    if (injected_alloc_failure())
+      return make_error(LLS_ERR_NOMEM, "device allocation of " + std::to_string(need) +
+                                           " bytes failed (injected)");
     cudaError_t e = cudaMalloc(&p, need);
     if (e != cudaSuccess) {
       p = nullptr;

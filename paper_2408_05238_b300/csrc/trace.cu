@@ -14,7 +14,12 @@ const char* trace_kind_name(int k) {
                                         "panel_qr_kernel",   "wy_tfactor_kernel",
                                         "sketch_kernel",     "jacobi_svd_kernel",
                                         "small_kernels",     "bf16_gemm_kernel",
-                                        "convert_kernels",   "oz_mma_kernel"};
+                                        "convert_kernels",   "oz_mma_kernel",
+                                        "phase:sample",      "phase:qr_y",
+                                        "phase:right_update", "phase:panel",
+                                        "phase:left_update", "phase:block_svd",
+                                        "phase:rank",        "phase:nullify",
+                                        "phase:solve"};
   return (k >= 0 && k < kTrCount) ? names[k] : "unknown";
 }
 

@@ -1,5 +1,6 @@
-// Per-kernel-family tracing: CUDA events recorded on the launching stream
-// around each launch, with the algorithmic flops and bytes of the launch.
+// Per-kernel-family and per-phase tracing: CUDA events recorded on the
+// launching stream around each launch (and around each phase of the method),
+// with the algorithmic flops and bytes of the launch.
 // Off unless a handle enables it; the counters mirror the paper's per-task
 // time table (average time and count per elementary task).
 #pragma once
@@ -23,8 +24,19 @@ enum TraceKind {
   kTrBf16Gemm,     // tcgen05 BF16 sampling GEMM
   kTrConvert,      // FP64 -> BF16 conversions and slicing
   kTrOzGemm,       // FP64-accurate GEMM on tensor cores (exact BF16 slices)
+  // phases of the method (each spans the kernels above that it launches)
+  kTrPhaseSample,   // a1/a2 sketch and sample Y
+  kTrPhaseQrY,      // a3 QR of Y and its T factor
+  kTrPhaseRight,    // a4 right update, all m rows
+  kTrPhasePanel,    // a5 panel QR of the block column and its T factor
+  kTrPhaseLeft,     // a6 left update
+  kTrPhaseSvd,      // a7 block SVDs and their updates
+  kTrPhaseRank,     // a8 rank decision
+  kTrPhaseNullify,  // a9 Nullify
+  kTrPhaseSolve,    // a10 solve
   kTrCount
 };
+constexpr int kTrFirstPhase = kTrPhaseSample;
 
 const char* trace_kind_name(int k);
 

@@ -90,6 +90,8 @@ _sig("lls_poll", [_H, _I, C.POINTER(C.c_int)])
 _sig("lls_set_memory_cap", [_H, _I])
 _sig("lls_ticket_factor", [_H, _I, C.POINTER(_I)])
 _sig("lls_set_workers", [_H, C.c_int])
+_sig("lls_cancel", [_H, _I])
+_sig("lls_debug_fail_allocation", [_I])
 _sig("lls_autotune", [_H, _I, _I, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)])
 _sig("lls_tuning_lookup", [_H, _I, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)])
 _sig("lls_tuning_save", [_H, C.c_char_p])
@@ -305,6 +307,16 @@ def lls_ticket_factor(h, ticket: int):
 
 def lls_set_workers(h, workers: int):
     _check(h, _lib.lls_set_workers(h, int(workers)))
+
+
+def lls_cancel(h, ticket: int) -> int:
+    """Withdraw a request that has not started (LLS_OK) or LLS_ERR_NOT_FOUND."""
+    return int(_lib.lls_cancel(h, ticket))
+
+
+def lls_debug_fail_allocation(after: int):
+    """Testing hook: the (after + 1)-th workspace allocation fails; -1 = off."""
+    _check(None, _lib.lls_debug_fail_allocation(after))
 
 
 def lls_autotune(h, m: int, n: int, trials: int = 2) -> tuple[int, int]:

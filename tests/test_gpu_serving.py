@@ -210,3 +210,49 @@ def test_tuned_batched_solves_use_the_table(lls, tmp_path):
     for p, (_, _, X) in zip(ps, held):
         x_explicit, _ = solve_alone(lls, p, nb=32, q=2)
         assert np.array_equal(X.cpu().numpy(), x_explicit)
+
+
+def test_cancel_withdraws_a_queued_request(lls):
+    # one worker and slow requests ahead: the last request is still queued
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    mats = [torch.randn(2048, 4096, generator=g, dtype=torch.float64, device="cuda").t()
+            for _ in range(4)]
+    h = lls.lls_create(nb=64, q=2, seed=2004)
+    lls.lls_set_workers(h, 1)
+    try:
+        held, tickets = [], []
+        for A in mats:
+            B = torch.randn(1, 4096, generator=g, dtype=torch.float64, device="cuda").t()
+            X = lls.empty_colmajor(2048, 1)
+            held.append((A, B, X))
+            tickets.append(lls.lls_submit(h, lls.make_problem(A, B, 1e-10, X)))
+        assert lls.lls_cancel(h, tickets[3]) == lls.LLS_OK
+        assert lls.lls_cancel(h, tickets[3]) == lls.LLS_ERR_NOT_FOUND   # already gone
+        st = wait_all(lls, h, tickets[:3])
+        assert all(v == 0 for v in st.values())
+        with pytest.raises(lls.LLSError) as e:
+            lls.lls_poll(h, tickets[3])
+        assert e.value.status == lls.LLS_ERR_NOT_FOUND
+        assert lls.lls_cancel(h, tickets[0]) == lls.LLS_ERR_NOT_FOUND   # finished and polled
+    finally:
+        lls.lls_destroy(h)
+
+
+def test_injected_allocation_failure_is_reported_and_recovered(lls):
+    p = problems(1, 41)[0]
+    A, B = dev(p.A), dev(p.B)
+    x_ref, r_ref = solve_alone(lls, p)
+    for after in (0, 3):            # the first, or a later, workspace allocation fails
+        h = lls.lls_create(nb=64, q=1, seed=2004)
+        try:
+            lls.lls_debug_fail_allocation(after)
+            with pytest.raises(lls.LLSError) as e:
+                lls.lls_solve(h, A, B, p.tol)
+            assert e.value.status == lls.LLS_ERR_NOMEM
+            lls.lls_debug_fail_allocation(-1)
+            X, r, _ = lls.lls_solve(h, A, B, p.tol)     # the same handle recovers
+            assert r == r_ref and np.array_equal(X.cpu().numpy(), x_ref)
+        finally:
+            lls.lls_debug_fail_allocation(-1)
+            lls.lls_destroy(h)

@@ -180,3 +180,27 @@ def test_repeat_solves_are_bit_identical(lls):
     a, _, _ = run(lls, p.A, p.B, p.tol, 64, 2, 9)
     b, _, _ = run(lls, p.A, p.B, p.tol, 64, 2, 9)
     assert np.array_equal(a, b)
+
+
+def test_trace_reports_kernel_families_and_phases(lls):
+    from paper_2408_05238_b300 import workloads as wl
+    p = wl.c1_problem()
+    A = torch.as_tensor(np.asfortranarray(p.A), device="cuda").t().contiguous().t()
+    B = torch.as_tensor(np.asfortranarray(p.B), device="cuda").t().contiguous().t()
+    h = lls.lls_create(nb=64, q=1, seed=2001)
+    try:
+        lls.lls_trace_enable(h, True)
+        _, rank, _ = lls.lls_solve(h, A, B, p.tol)
+        tr = lls.lls_trace_read(h)
+    finally:
+        lls.lls_destroy(h)
+    steps = -(-min(p.A.shape) // 64)
+    assert tr["dgemm_kernel"][0] > 0 and tr["panel_qr_kernel"][0] >= 2 * steps
+    for ph in ("sample", "qr_y", "right_update", "panel", "left_update"):
+        assert tr["phase:" + ph][0] == steps                    # once per step
+    for ph in ("block_svd", "rank", "solve"):
+        assert tr["phase:" + ph][0] == 1
+    assert 0 < rank < p.A.shape[1] and tr["phase:nullify"][0] == 1   # rank 400 of 1000
+    fam = sum(v[1] for k, v in tr.items() if not k.startswith("phase:"))
+    phases = sum(v[1] for k, v in tr.items() if k.startswith("phase:"))
+    assert 0.5 * fam < phases < 2.0 * fam + 0.05             # two views of the same time
