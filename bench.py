@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--nrhs", type=int, default=None,
                    help="right-hand sides (default: 16 for c2, 1 for c3)")
     p.add_argument("--nb", type=int, default=128)
-    p.add_argument("--q", type=int, default=2)
+    p.add_argument("--q", type=int, default=None, help="power iterations (default: 2 for c2, 1 for c3)")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     p.add_argument("--workload", choices=["c2", "c3", "batched", "serving"], default="c2",
                    help="c2: one 16384^2 solve per step (default); batched: many small "
@@ -457,6 +457,8 @@ def main():
     a = parse()
     if a.nrhs is None:
         a.nrhs = 1 if a.workload == "c3" else 16
+    if a.q is None:
+        a.q = 1 if a.workload == "c3" else 2
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":
