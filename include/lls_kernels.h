@@ -51,8 +51,9 @@ int lls_k_gemm(int transa, int transb, int unit_lower_a, int unit_lower_b,
 int lls_k_geqrf(int64_t m, int64_t n, double* A, int64_t lda, double* tau,
                 double* T, int64_t ldt, void* stream);
 
-/* SVD of the b x b block R (b <= 128) by one-sided Jacobi in one CTA
- * (Fig. 2, SVD(A_11)): R = Us diag(sigma) Vs^T, sigma descending >= 0.
+/* SVD of the b x b block R (b <= 128) by one-sided Jacobi (Fig. 2,
+ * SVD(A_11)): R = Us diag(sigma) Vs^T, sigma descending >= 0.  One CTA for
+ * b < 32, else a thread-block cluster of 4 (b <= 64) or 8 CTAs.
  * status (device int, may be NULL) receives 0, or LLS_ERR_SVD_NOCONV when
  * the sweep limit was hit. */
 int lls_k_jacobi_svd(int64_t b, const double* R, int64_t ldr, double* sigma,
@@ -83,10 +84,11 @@ int lls_k_gemm_bf16_tn(int64_t M, int64_t N, int64_t K, const void* X, int64_t l
 
 /* C = alpha op(A) op(B) + beta C with FP64 operands and result, computed on
  * the BF16 tensor cores by exact slicing (Ozaki-style): each row of op(A)
- * and column of op(B) is scaled by a power of two and split into 8 base-128
- * integer digit planes stored as BF16; the 36 digit-plane products with
- * s + t <= 9 accumulate exactly in FP32 (at most 256 K entries per partial
- * product), and the partial products are recombined and summed in FP64.
+ * and column of op(B) is scaled by a power of two and split into 8 signed
+ * base-128 integer digit planes stored as BF16; the 36 digit-plane products
+ * with s + t <= 9 accumulate exactly in FP32 (at most 256 K entries per
+ * partial product), are recombined exactly in 64-bit integers (one rounding
+ * at 2^-55 of the row/column scale) and summed in FP64.
  * Same operand conventions as lls_k_gemm.  Accuracy: at least that of an
  * FP64 GEMM relative to max_k |op(A)_ik| max_k |op(B)_kj|.  status (device
  * int) becomes nonzero if a device-side wait timed out.  Workspace is

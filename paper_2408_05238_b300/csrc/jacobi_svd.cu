@@ -1,12 +1,14 @@
 // SVD of the small diagonal block (Fig. 2, [A_11, U_SVD, V_SVD] = SVD(A_11);
-// step a7) by one-sided (Hestenes) Jacobi, one CTA per block.
+// step a7) by one-sided (Hestenes) Jacobi: one CTA per block, or, for
+// launches with few blocks, one thread-block cluster per block.
 //
 // The block (b x b, b <= 128) lives in shared memory; column pairs are
 // orthogonalized by plane rotations in the parallel round-robin order
 // (circle method: b - 1 rounds of b / 2 disjoint pairs per sweep), the
 // rotations are accumulated into V.  Rutishauser's formulas:
 //   zeta = (||a_q||^2 - ||a_p||^2) / (2 a_p^T a_q),
-//   t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t,
+//   t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t
+//   (divisions and square roots by Newton iterations, jacobi_rotation),
 //   (a_p, a_q) <- (c a_p - s a_q, s a_p + c a_q).
 // A pair is rotated when |a_p^T a_q| > sqrt(b) eps ||a_p|| ||a_q||; a sweep
 // without a rotation ends the iteration.  Then sigma_j = ||a_j||, U = A V /
