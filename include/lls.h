@@ -42,6 +42,8 @@ enum {
   LLS_OK = 0,
   LLS_PENDING = 1,              /* lls_poll: request not finished yet */
   LLS_WARN_RANK_NONPREFIX = 2,  /* some |T_jj| > tol after the first |T_jj| <= tol */
+  LLS_WARN_REFINE_NOCONV = 3,   /* refinement stopped with its last correction
+                                   above refine_tol (x is still the refined one) */
   LLS_ERR_ARG = -1,             /* invalid argument (see lls_last_error) */
   LLS_ERR_NOMEM = -2,           /* device or host allocation failed */
   LLS_ERR_CUDA = -3,            /* a CUDA runtime call failed */
@@ -73,9 +75,25 @@ typedef struct {
   int32_t q;           /* power iterations of Y = (A^T A)^q A^T G, 0..4 [1] */
   int32_t precision;   /* LLS_FP64 | LLS_MIXED_BF16 [LLS_FP64] */
   int32_t nullify;     /* 1: run Nullify (minimum-norm x, Fig. 3) [1];
-                          0: fast option (Remark after Fig. 4, Eq. (7)) */
+                          0: fast option (Remark after Fig. 4, Eq. (7)): a
+                          least-squares x whose excess norm is of the size
+                          of T_12; with LLS_MIXED_BF16 the BF16 sample fixes
+                          V_1 only to BF16 accuracy, so that excess is of
+                          order 1e-4..1e-2 relative (Nullify removes it) */
   uint64_t seed;       /* key of the Gaussian sketch generator [2001] */
-  int32_t reserved[4]; /* must be zero */
+  int32_t explicit_v;  /* 1: accumulate V (n x n) during the factorization
+                          (V <- V (I - W_V T_V W_V^T), V_01 <- V_01 V_SVD,
+                          Nullify's reflectors from the right, Fig. 2-3);
+                          solves then apply V as one GEMM and
+                          lls_factor_get can return it; 0: V is kept as its
+                          reflectors and applied by replaying them [0] */
+  int32_t max_refine;  /* iterative refinement steps after the solve,
+                          x <- x + P (b - A x) with the FP64 residual and
+                          P = V_1 T_11^{-1} U_1^T the factorization's solve
+                          operator, 0..16 [0] (see lls_refinement_info) */
+  double refine_tol;   /* refinement stops once every column has
+                          ||dx_j|| <= refine_tol ||x_j||, >= 0 [1e-12] */
+  int32_t reserved[2]; /* must be zero */
 } lls_options;
 
 /* One problem of lls_solve_batched / one request of lls_submit (device
@@ -133,7 +151,7 @@ int lls_create(lls_handle* h, const lls_options* opt, void* cuda_stream);
 /* Free the handle, its workspace and all resident factors. */
 int lls_destroy(lls_handle h);
 
-/* Change nb / q / precision / nullify / seed for later calls. */
+/* Change the options (every field of lls_options) for later calls. */
 int lls_set_options(lls_handle h, const lls_options* opt);
 
 /* Solve min ||A X - B|| with minimum ||X|| (per column), tol absolute:
@@ -161,6 +179,35 @@ int lls_solve_factored(lls_handle h, int64_t factor_id, const double* B, int64_t
 
 /* Release a resident factorization. */
 int lls_factor_release(lls_handle h, int64_t factor_id);
+
+/* What lls_factor_get copies. */
+enum {
+  LLS_FACTOR_T = 0,  /* T (m x n): upper trapezoid, zeros below the
+                        diagonal; after Nullify T(0:r, r:n) = 0 */
+  LLS_FACTOR_V = 1   /* V (n x n, orthogonal, A V = U T; after Nullify it
+                        includes Nullify's reflectors); needs a factor made
+                        with explicit_v = 1 */
+};
+
+/* Copy a resident factor's T or V (which = LLS_FACTOR_T / LLS_FACTOR_V) to
+ * the DEVICE buffer dst (column-major, ld >= max(1, rows)).  Synchronous.
+ * LLS_ERR_ARG: unknown `which`, ld too small, NULL dst, or V of a factor
+ * made without explicit_v (index 3); LLS_ERR_NOT_FOUND: unknown id. */
+int lls_factor_get(lls_handle h, int64_t factor_id, int32_t which, double* dst, int64_t ld);
+
+/* Refinement of the last lls_solve / lls_solve_host / lls_solve_factored on
+ * h: *steps (host, may be NULL) receives the number of corrections applied
+ * (0 when max_refine = 0 or the factor kept no copy of A), *correction
+ * (host, may be NULL) the last one's max_j ||dx_j|| / ||x_j||.  Refinement
+ * stops at max_refine steps, once the correction is <= refine_tol, or when
+ * a correction is not below half the previous one (the FP64 residual's
+ * rounding floor); the call returns LLS_WARN_REFINE_NOCONV when that last
+ * correction is still above refine_tol.  lls_solve refines with the
+ * caller's A; lls_solve_factored and requests with a resident factor refine
+ * only when the factor was made with max_refine > 0, in which case it holds
+ * a copy of A (m x n more device memory).  Batched and served requests
+ * refine the same way (their status carries the warning). */
+int lls_refinement_info(lls_handle h, int32_t* steps, double* correction);
 
 /* Copy |diag(T)| (min(m,n) values) of a resident factor to a HOST buffer;
  * rank_count (host, may be NULL) receives the number of entries > tol. */
@@ -238,6 +285,29 @@ int64_t lls_launch_count(void);
  * after = -1 turns the injection off.  Allocations inside the lls_k_* step
  * entry points are not covered. */
 int lls_debug_fail_allocation(int64_t after);
+
+/* Debug mode (guard words; for tests on small shapes).  With on = 1, every
+ * device buffer the library allocates from then on (solver workspace,
+ * factors, batched and serving workers; not the lls_k_* entry points'
+ * temporaries) carries 512 bytes of a fixed pattern before and after it,
+ * inside the same allocation.  After every kernel launch the library
+ * synchronizes the device and checks every live buffer's guards, and checks
+ * a buffer again when it is freed: a kernel that writes past either end of
+ * its buffer is reported (reads are not).  Turning it on clears the report;
+ * buffers allocated while it was off stay unguarded.  LLS_ERR_ARG unless on
+ * is 0 or 1. */
+int lls_debug_guard(int on);
+
+/* Number of guard violations seen since lls_debug_guard(1); msg (host, may
+ * be NULL) receives the first one: which guard, the buffer size, the offset
+ * and the kernel after which it was seen. */
+int64_t lls_debug_guard_report(char* msg, int64_t len);
+
+/* Checks the guard machinery itself: writes one byte just past the end and
+ * two bytes just before the start of a guarded buffer with cudaMemset (inside
+ * its allocation) and returns LLS_OK iff both writes are reported with the
+ * right offsets and an intact buffer is not. */
+int lls_debug_guard_selftest(void);
 
 /* Static text for a status code. */
 const char* lls_status_string(int status);

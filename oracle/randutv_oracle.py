@@ -22,6 +22,9 @@ arXiv 2408.05238, Sec. 3):
 * ``solve``        -- Fig. 4 (Solve_linear_system): x = V (T_tl^{-1} (U^T b)),
                       with the fast option of the Remark after Fig. 4 (skip
                       Nullify, Eq. (7) x_simple).
+* ``refine``       -- iterative refinement of a solution with the solve
+                      operator P = V_1 T_11^{-1} U_1^T of Fig. 4:
+                      x <- x + P (b - A x), the residual in FP64.
 * ``pinv_solve``   -- Sec. 2.2 truncated-SVD least squares, used as the
                       brute-force pin on small inputs.
 
@@ -70,6 +73,7 @@ __all__ = [
     "compute_rank",
     "nullify",
     "solve",
+    "refine",
     "pinv_solve",
     "pinv_solve_from_factors",
     "normal_equation_residual",
@@ -402,6 +406,30 @@ def solve(A: np.ndarray, B: np.ndarray, q: int, nb: int, tol: float, seed: int,
     if vec:
         X = X[:, 0]
     return Solution(X, r, count, diag, utv if keep else None)
+
+
+def refine(A: np.ndarray, B: np.ndarray, sol: Solution, x0: np.ndarray | None = None,
+           steps: int = 1) -> np.ndarray:
+    """``steps`` refinement steps x <- x + P (b - A x) from x0 (default:
+    sol.x), with P = V(:, :r) T(:r, :r)^{-1} U(:, :r)^T taken from the
+    factors of ``sol`` (``solve(..., keep=True)``; after Nullify when it ran).
+    Since U_1^T A V_1 = T_11 (A V = U T with T upper triangular), P A acts
+    as the identity on range(V_1): one step removes any error in that
+    subspace, and P b is a fixed point."""
+    if sol.utv is None:
+        raise ValueError("refine needs solve(..., keep=True)")
+    A = np.asarray(A, dtype=np.float64)
+    Bm = np.asarray(B, dtype=np.float64).reshape(A.shape[0], -1)
+    x = np.array(sol.x if x0 is None else x0, dtype=np.float64).reshape(A.shape[1], -1)
+    r = sol.rank
+    U, T, V = sol.utv.U, sol.utv.T, sol.utv.V
+    for _ in range(steps):
+        if r == 0:
+            break
+        res = Bm - A @ x
+        y = _back_substitution(T[:r, :r], (U.T @ res)[:r])
+        x = x + V[:, :r] @ y
+    return x.reshape(np.shape(sol.x if x0 is None else x0))
 
 
 # ---------------------------------------------------------------------------

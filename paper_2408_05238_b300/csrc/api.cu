@@ -1,5 +1,6 @@
 // C ABI entry points (include/lls.h): argument validation, handle and
 // factor management.  The numerical work is in solver.cu.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 
@@ -32,7 +33,11 @@ Status check_options(const lls_options& o) {
   if (o.precision != LLS_FP64 && o.precision != LLS_MIXED_BF16)
     return arg_error(2, "unknown precision mode");
   if (o.nullify != 0 && o.nullify != 1) return arg_error(2, "nullify must be 0 or 1");
-  for (int i = 0; i < 4; ++i)
+  if (o.explicit_v != 0 && o.explicit_v != 1) return arg_error(2, "explicit_v must be 0 or 1");
+  if (o.max_refine < 0 || o.max_refine > 16) return arg_error(2, "max_refine must be in 0..16");
+  if (!(o.refine_tol >= 0.0) || o.refine_tol == INFINITY)
+    return arg_error(2, "refine_tol must be finite and >= 0");
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return arg_error(2, "reserved option fields must be zero");
   return lls::ok_status();
 }
@@ -62,9 +67,9 @@ Status do_solve(Handle& h, const double* A, int64_t m, int64_t n, int64_t lda, c
   Status fs = lls::factorize(h, *h.scratch_factor, A, m, n, lda, tol);
   if (!fs.ok()) return fs;
   if (rank) *rank = h.scratch_factor->rank;
-  Status ss = lls::solve_factored(h, *h.scratch_factor, B, nrhs, ldb, X, ldx);
+  Status ss = lls::solve_refined(h, *h.scratch_factor, A, lda, B, nrhs, ldb, X, ldx);
   if (!ss.ok()) return ss;
-  return fs;  // may carry LLS_WARN_RANK_NONPREFIX
+  return fs.code != LLS_OK ? fs : ss;  // LLS_WARN_RANK_NONPREFIX, else LLS_WARN_REFINE_NOCONV
 }
 
 }  // namespace
@@ -79,6 +84,7 @@ int lls_default_options(lls_options* opt) {
   opt->precision = LLS_FP64;
   opt->nullify = 1;
   opt->seed = 2001;
+  opt->refine_tol = 1e-12;
   return LLS_OK;
 }
 
@@ -189,7 +195,7 @@ int lls_factor(lls_handle hh, const double* A, int64_t m, int64_t n, int64_t lda
   if (s.ok() && tol != tol) s = arg_error(6, "tol is NaN");
   if (!s.ok()) return finish(h, s);
   std::unique_ptr<lls::Factor> f(new lls::Factor());
-  s = lls::factorize(*h, *f, A, m, n, lda, tol);
+  s = lls::factorize(*h, *f, A, m, n, lda, tol, /*keep_a=*/true);
   if (!s.ok()) return finish(h, s);
   if (rank) *rank = f->rank;
   std::lock_guard<std::mutex> lock(h->factors_mu);
@@ -215,7 +221,7 @@ int lls_solve_factored(lls_handle hh, int64_t factor_id, const double* B, int64_
   Status s = check_matrix(B, f.m, nrhs, ldb, 3, 2, 4, 5);
   if (s.ok() && ldx < (f.n > 1 ? f.n : 1)) s = arg_error(7, "ldx < max(1, n)");
   if (s.ok() && f.n > 0 && nrhs > 0 && !X) s = arg_error(6, "NULL X");
-  if (s.ok()) s = lls::solve_factored(*h, f, B, nrhs, ldb, X, ldx);
+  if (s.ok()) s = lls::solve_refined(*h, f, nullptr, 0, B, nrhs, ldb, X, ldx);
   return finish(h, s);
 }
 
@@ -265,11 +271,45 @@ int lls_factor_diag(lls_handle hh, int64_t factor_id, double* diag, int64_t len,
   return finish(h, s);
 }
 
+int lls_factor_get(lls_handle hh, int64_t factor_id, int32_t which, double* dst, int64_t ld) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return LLS_ERR_ARG;
+  std::shared_ptr<lls::Factor> fp;
+  {
+    std::lock_guard<std::mutex> lock(h->factors_mu);
+    auto it = h->factors.find(factor_id);
+    if (it != h->factors.end()) fp = it->second;
+  }
+  if (!fp) return finish(h, lls::make_error(LLS_ERR_NOT_FOUND, "unknown factor id", 2));
+  lls::Factor& f = *fp;
+  if (which != LLS_FACTOR_T && which != LLS_FACTOR_V)
+    return finish(h, arg_error(3, "which must be LLS_FACTOR_T or LLS_FACTOR_V"));
+  if (which == LLS_FACTOR_V && !f.has_v)
+    return finish(h, arg_error(3, "V is kept only by factors made with explicit_v = 1"));
+  const int64_t rows = which == LLS_FACTOR_T ? f.m : f.n, cols = f.n;
+  if (ld < (rows > 1 ? rows : 1)) return finish(h, arg_error(5, "ld < max(1, rows)"));
+  if (rows > 0 && cols > 0 && !dst) return finish(h, arg_error(4, "NULL dst"));
+  Status s = which == LLS_FACTOR_T
+                 ? lls::copy_upper_trapezoid(rows, cols, f.T.d(), f.ldt, dst, ld, h->stream)
+                 : lls::copy_matrix(rows, cols, f.Vx.d(), cols > 1 ? cols : 1, dst, ld, h->stream);
+  if (s.ok()) s = lls::cuda_status(cudaStreamSynchronize(h->stream), "synchronize");
+  return finish(h, s);
+}
+
+int lls_refinement_info(lls_handle hh, int32_t* steps, double* correction) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h) return LLS_ERR_ARG;
+  if (steps) *steps = h->refine_steps;
+  if (correction) *correction = h->refine_corr;
+  return LLS_OK;
+}
+
 const char* lls_status_string(int status) {
   switch (status) {
     case LLS_OK: return "ok";
     case LLS_PENDING: return "pending";
     case LLS_WARN_RANK_NONPREFIX: return "warning: a diagonal entry above tol follows one below";
+    case LLS_WARN_REFINE_NOCONV: return "warning: refinement stopped above refine_tol";
     case LLS_ERR_ARG: return "invalid argument";
     case LLS_ERR_NOMEM: return "out of memory";
     case LLS_ERR_CUDA: return "CUDA error";

@@ -42,11 +42,20 @@ inline Status cuda_status(cudaError_t e, const char* what) {
 
 #define LLS_CUDA(call) LLS_TRY(::lls::cuda_status((call), #call))
 
+// Guard-word debug mode (guard.cu, lls_debug_guard): buffers allocated
+// while it is on carry guard bytes on both sides, checked after every launch.
+extern std::atomic<int> g_guard_mode;
+Status guard_alloc(size_t need, void** user);
+void guard_free(void* user);
+void guard_after_launch(const char* name);
+
 // Launch check after a <<<>>> launch.
-#define LLS_LAUNCHED(name)                                     \
-  do {                                                         \
-    ::lls::g_launches.fetch_add(1, std::memory_order_relaxed); \
-    LLS_CUDA(cudaGetLastError());                              \
+#define LLS_LAUNCHED(name)                                          \
+  do {                                                              \
+    ::lls::g_launches.fetch_add(1, std::memory_order_relaxed);      \
+    LLS_CUDA(cudaGetLastError());                                   \
+    if (::lls::g_guard_mode.load(std::memory_order_relaxed))        \
+      ::lls::guard_after_launch(name);                              \
   } while (0)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -71,6 +71,15 @@ Status fill_zero(int64_t m, int64_t n, double* dst, int64_t ldd, cudaStream_t st
 // dst (k x k) = upper triangle of src, zeros below.
 Status copy_upper(int64_t k, const double* src, int64_t lds, double* dst, int64_t ldd,
                   cudaStream_t st);
+// V (n x n) = I.
+Status set_identity(int64_t n, double* V, int64_t ldv, cudaStream_t st);
+// dst (m x n) = upper trapezoid of src, zeros below the diagonal.
+Status copy_upper_trapezoid(int64_t m, int64_t n, const double* src, int64_t lds, double* dst,
+                            int64_t ldd, cudaStream_t st);
+// X (n x nrhs) += D; norms (device, 2 nrhs) = per column ||d_j||^2, ||x_j||^2
+// of the updated X, each summed in a fixed order.
+Status refine_update(int64_t n, int64_t nrhs, const double* D, int64_t ldd, double* X, int64_t ldx,
+                     double* norms, cudaStream_t st);
 // Block (k x k) at D: diagonal = sigma, strictly upper part = 0, strictly
 // lower part untouched (it holds Householder vectors).
 Status set_diag_block(int64_t k, const double* sigma, double* D, int64_t ldd, cudaStream_t st);

@@ -576,9 +576,19 @@ SlabPlan slab_plan(int64_t m, int64_t n) {
   return p;
 }
 
+Status coop_launch_gated(const void* fn, int G, int threads, void** args, size_t smem,
+                         cudaStream_t st);
+
 // Launches a cooperative kernel behind the library-wide gate.
 Status coop_launch(const void* fn, int G, int threads, void** args, size_t smem,
                    cudaStream_t st) {
+  LLS_TRY(coop_launch_gated(fn, G, threads, args, smem, st));
+  if (g_guard_mode.load(std::memory_order_relaxed)) guard_after_launch("cooperative panel kernel");
+  return ok_status();
+}
+
+Status coop_launch_gated(const void* fn, int G, int threads, void** args, size_t smem,
+                         cudaStream_t st) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   CoopGate& gate = coop_gate();
   std::lock_guard<std::mutex> lock(gate.mu);

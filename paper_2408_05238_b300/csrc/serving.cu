@@ -55,12 +55,17 @@ Handle::~Handle() {
 namespace {
 
 // Device memory one request holds while it runs (factor + workspace).
-int64_t request_bytes(const lls_problem& p, int nb) {
+int64_t request_bytes(const lls_problem& p, const lls_options& opt) {
+  int nb = opt.nb;
   if (nb <= 0) nb = 128;  // tuned block size: bound by the largest
-  if (p.factor_id >= 0) return (int64_t)(8 * (p.m + 2 * p.n) * std::max<int64_t>(p.nrhs, 1));
+  const int64_t rhs = std::max<int64_t>(p.nrhs, 1);
+  const int64_t refine = opt.max_refine > 0 ? 8 * (int64_t)(p.m + p.n) * rhs : 0;
+  if (p.factor_id >= 0) return (int64_t)(8 * (p.m + 2 * p.n) * rhs) + refine;
   int64_t mx = std::max(p.m, p.n);
-  int64_t ws = 8 * (int64_t)mx * nb * 6 + 8 * (int64_t)(p.m + p.n) * std::max<int64_t>(p.nrhs, 1);
-  return (int64_t)factor_bytes(p.m, p.n, nb) + ws;
+  int64_t ws = 8 * (int64_t)mx * nb * 6 + 8 * (int64_t)(p.m + p.n) * rhs + refine;
+  return (int64_t)factor_bytes(p.m, p.n, nb, opt.explicit_v != 0,
+                               p.keep_factor && opt.max_refine > 0) +
+         ws;
 }
 
 Status run_request(Handle& parent, Handle& w, lls_problem& p) {
@@ -73,7 +78,7 @@ Status run_request(Handle& parent, Handle& w, lls_problem& p) {
     }
     if (!f) return make_error(LLS_ERR_NOT_FOUND, "unknown factor id");
     if (p.rank_out) *p.rank_out = f->rank;
-    return solve_factored(w, *f, p.B, p.nrhs, p.ldb, p.X, p.ldx);
+    return solve_refined(w, *f, nullptr, 0, p.B, p.nrhs, p.ldb, p.X, p.ldx);
   }
   if (p.n == 0 || p.nrhs == 0) {
     if (p.rank_out) *p.rank_out = 0;
@@ -92,10 +97,10 @@ Status run_request(Handle& parent, Handle& w, lls_problem& p) {
     w.scratch_factor.reset(new Factor());
   }
   Factor& fr = p.keep_factor ? *f : *w.scratch_factor;
-  Status fs = factorize(w, fr, p.A, p.m, p.n, p.lda, p.tol);
+  Status fs = factorize(w, fr, p.A, p.m, p.n, p.lda, p.tol, p.keep_factor != 0);
   if (!fs.ok()) return fs;
   if (p.rank_out) *p.rank_out = fr.rank;
-  Status ss = solve_factored(w, fr, p.B, p.nrhs, p.ldb, p.X, p.ldx);
+  Status ss = solve_refined(w, fr, p.A, p.lda, p.B, p.nrhs, p.ldb, p.X, p.ldx);
   if (!ss.ok()) return ss;
   if (p.keep_factor) {
     std::lock_guard<std::mutex> lock(parent.factors_mu);
@@ -103,7 +108,7 @@ Status run_request(Handle& parent, Handle& w, lls_problem& p) {
     parent.factors[id] = f;
     p.factor_id = id;
   }
-  return fs;
+  return fs.code != LLS_OK ? fs : ss;
 }
 
 void worker_loop(Handle::Pool* pool, int wi) {
@@ -166,7 +171,7 @@ int64_t enqueue(Handle& h, const lls_problem& req) {
   Handle::Pool& pool = *h.pool;
   auto t = std::make_shared<Ticket>();
   t->req = req;
-  t->bytes = request_bytes(req, h.opt.nb);
+  t->bytes = request_bytes(req, h.opt);
   int64_t id;
   {
     std::lock_guard<std::mutex> lock(pool.mu);
@@ -264,7 +269,7 @@ int lls_submit(lls_handle hh, const lls_problem* req, int64_t* ticket) {
       req->ldx < std::max<int64_t>(1, req->n) ||
       (req->factor_id < 0 && req->lda < std::max<int64_t>(1, req->m)))
     return LLS_ERR_ARG;
-  if (h->mem_cap > 0 && lls::request_bytes(*req, h->opt.nb) > h->mem_cap) return LLS_ERR_CAPACITY;
+  if (h->mem_cap > 0 && lls::request_bytes(*req, h->opt) > h->mem_cap) return LLS_ERR_CAPACITY;
   lls::Status ps = lls::ensure_pool(*h);
   if (!ps.ok()) return ps.code;
   *ticket = lls::enqueue(*h, *req);

@@ -158,6 +158,58 @@ __global__ void cols_reversed_kernel(int64_t rows, int64_t cols, const double* _
   }
 }
 
+__global__ void identity_kernel(int64_t n, double* V, int64_t ldv) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = idx % n, j = idx / n;
+    V[i + j * ldv] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void upper_trapezoid_kernel(int64_t m, int64_t n, const double* __restrict__ src,
+                                       int64_t lds, double* __restrict__ dst, int64_t ldd) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = idx % m, j = idx / m;
+    dst[i + j * ldd] = (i <= j) ? src[i + j * lds] : 0.0;
+  }
+}
+
+// Refinement update, one CTA per column j: x_j <- x_j + d_j, and
+// norms[2j] = ||d_j||^2, norms[2j+1] = ||x_j (new)||^2.  Each thread sums a
+// fixed strided subset, then a fixed-shape tree: the result is the same on
+// every run.
+constexpr int RF_THREADS = 256;
+__global__ void __launch_bounds__(RF_THREADS)
+refine_update_kernel(int64_t n, const double* __restrict__ D, int64_t ldd, double* __restrict__ X,
+                     int64_t ldx, double* __restrict__ norms) {
+  __shared__ double s_d[RF_THREADS], s_x[RF_THREADS];
+  const double* d = D + (int64_t)blockIdx.x * ldd;
+  double* x = X + (int64_t)blockIdx.x * ldx;
+  double sd = 0.0, sx = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += RF_THREADS) {
+    double di = d[i];
+    double xi = x[i] + di;
+    x[i] = xi;
+    sd = fma(di, di, sd);
+    sx = fma(xi, xi, sx);
+  }
+  s_d[threadIdx.x] = sd;
+  s_x[threadIdx.x] = sx;
+  __syncthreads();
+  for (int w = RF_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_d[threadIdx.x] += s_d[threadIdx.x + w];
+      s_x[threadIdx.x] += s_x[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    norms[2 * blockIdx.x] = s_d[0];
+    norms[2 * blockIdx.x + 1] = s_x[0];
+  }
+}
+
 // Back substitution on one diagonal block, one CTA per right-hand side:
 // y_i = b_i / R(i,i), then b_l -= R(l,i) y_i for l < i, from the bottom.
 __global__ void trsm_block_kernel(int64_t k, const double* __restrict__ R, int64_t ldr, double* B,
@@ -219,6 +271,33 @@ Status copy_upper(int64_t k, const double* src, int64_t lds, double* dst, int64_
   TraceScope ts(kTrSmall, st);
   copy_upper_kernel<<<grid_for(k * k), EW, 0, st>>>(k, src, lds, dst, ldd);
   LLS_LAUNCHED("copy_upper_kernel");
+  return ok_status();
+}
+
+Status set_identity(int64_t n, double* V, int64_t ldv, cudaStream_t st) {
+  if (n <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
+  identity_kernel<<<grid_for(n * n), EW, 0, st>>>(n, V, ldv);
+  LLS_LAUNCHED("identity_kernel");
+  return ok_status();
+}
+
+Status copy_upper_trapezoid(int64_t m, int64_t n, const double* src, int64_t lds, double* dst,
+                            int64_t ldd, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
+  upper_trapezoid_kernel<<<grid_for(m * n), EW, 0, st>>>(m, n, src, lds, dst, ldd);
+  LLS_LAUNCHED("upper_trapezoid_kernel");
+  return ok_status();
+}
+
+Status refine_update(int64_t n, int64_t nrhs, const double* D, int64_t ldd, double* X, int64_t ldx,
+                     double* norms, cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return ok_status();
+  if (nrhs > (1 << 20)) return make_error(LLS_ERR_ARG, "too many right-hand sides");
+  TraceScope ts(kTrSmall, st);
+  refine_update_kernel<<<(unsigned)nrhs, RF_THREADS, 0, st>>>(n, D, ldd, X, ldx, norms);
+  LLS_LAUNCHED("refine_update_kernel");
   return ok_status();
 }
 

@@ -3,10 +3,11 @@
 // the other translation units on the handle's stream.
 //
 // Differences from the paper's formulation (same mathematics):
-//  * U and V are never formed.  Each step keeps its reflectors (W_U below the
-//    diagonal of T, W_V in a side buffer), their compact-WY factors and the
-//    diagonal block's singular vectors; U^T b and V y are applied from them
-//    (the paper's v23t variant applies U to B on the fly, Sec. 3.4).
+//  * U is never formed, V only on request (explicit_v).  Each step keeps its
+//    reflectors (W_U below the diagonal of T, W_V in a side buffer), their
+//    compact-WY factors and the diagonal block's singular vectors; U^T b and,
+//    without an explicit V, V y are applied from them (the paper's v23t
+//    variant applies U to B on the fly, Sec. 3.4).
 //  * The right update of step i runs over all m rows of columns k..n-1
 //    (Fig. 2 prints only the A_BR block; the rows above must change too for
 //    A V = U T to hold).
@@ -17,8 +18,10 @@
 //    as one batched launch after the loop, then all column updates, then all
 //    row updates.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <optional>
+#include <vector>
 
 #include "lls_kernels.h"
 #include "oz_gemm.h"
@@ -51,13 +54,15 @@ size_t loop_gemm_scratch(int64_t m, int64_t n, int nb, int64_t max_nrhs) {
 
 }  // namespace
 
-size_t factor_bytes(int64_t m, int64_t n, int nb) {
+size_t factor_bytes(int64_t m, int64_t n, int nb, bool explicit_v, bool keep_a) {
   int64_t steps = ceil_div(std::min(m, n), nb);
   size_t blk = (size_t)nb * nb * sizeof(double);
   size_t b = (size_t)m * n * sizeof(double) + (size_t)n * n * sizeof(double);
   b += 5 * steps * blk + 3 * steps * nb * sizeof(double);
   // Nullify panels at worst (r ~ n/2): n/2 x (nb + n/2)
   b += (size_t)(n / 2 + nb) * (size_t)(n / 2 + nb) * sizeof(double);
+  if (explicit_v) b += (size_t)n * n * sizeof(double);
+  if (keep_a) b += (size_t)m * n * sizeof(double);
   return b;
 }
 
@@ -65,7 +70,7 @@ size_t factor_bytes(int64_t m, int64_t n, int nb) {
 // randUTV + rank (+ Nullify when opt.nullify)
 // ---------------------------------------------------------------------------
 Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, int64_t lda,
-                 double tol) {
+                 double tol, bool keep_a) {
   cudaStream_t st = h.stream;
   int nb = 0, q = 0;
   effective_nb_q(h.opt, h.tune.get(), m, n, &nb, &q);
@@ -76,6 +81,10 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   f.q = q;
   f.precision = h.opt.precision;
   f.nullified = false;
+  f.has_v = h.opt.explicit_v != 0;
+  f.has_a = keep_a && h.opt.max_refine > 0;
+  if (!f.has_v) f.Vx.release();
+  if (!f.has_a) f.A0.release();
   f.ks.clear();
   f.bs.clear();
   f.rz.clear();
@@ -99,6 +108,9 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   LLS_TRY(f.tauV.reserve(sizeof(double) * nb * std::max<int64_t>(steps, 1)));
   LLS_TRY(f.tauU.reserve(sizeof(double) * nb * std::max<int64_t>(steps, 1)));
   LLS_TRY(f.sigma.reserve(sizeof(double) * nb * std::max<int64_t>(steps, 1)));
+  const int64_t ldv = std::max<int64_t>(n, 1);
+  if (f.has_v) LLS_TRY(f.Vx.reserve(sizeof(double) * (size_t)ldv * n));
+  if (f.has_a) LLS_TRY(f.A0.reserve(sizeof(double) * (size_t)ldt * n));
 
   // workspace
   const int64_t mx = std::max(m, n);
@@ -128,6 +140,11 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       need = std::max(need, oz_gemm_workspace_bytes(mp, np - b, b));
       need = std::max(need, oz_gemm_workspace_bytes(b, b, std::max(np, mp)));  // Gram W^T W
       need = std::max(need, oz_gemm_workspace_bytes(k, b, b));                 // A01 V_SVD
+      if (f.has_v) {  // V's right update and V_SVD
+        need = std::max(need, oz_gemm_workspace_bytes(n, b, np));
+        need = std::max(need, oz_gemm_workspace_bytes(n, np, b));
+        need = std::max(need, oz_gemm_workspace_bytes(n, b, b));
+      }
     }
     LLS_TRY(h.oz_ws.reserve(need));
   }
@@ -150,8 +167,10 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     return fgemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_);
   };
 
-  // T <- A, with the finiteness check.
+  // T <- A, with the finiteness check; V <- I; the refinement copy of A.
   LLS_TRY(copy_check(m, n, A, lda, f.T.d(), ldt, &ds->nonfinite, st));
+  if (f.has_v) LLS_TRY(set_identity(n, f.Vx.d(), ldv, st));
+  if (f.has_a) LLS_TRY(copy_matrix(m, n, f.T.d(), ldt, f.A0.d(), ldt, st));
 
   double* T = f.T.d();
   double* WV = f.WV.d();
@@ -198,6 +217,15 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
                   m));
     LLS_TRY(xgemm(false, true, kDense, kUnitLower, m, np, b, -1.0, h.P2.d(), m, Y, ldw, 1.0, Tk,
                   ldt));
+    if (f.has_v) {  // V(:, k:n) <- V(:, k:n) (I - W_V T_V W_V^T), all n rows
+      double* Vk = f.Vx.d() + k * ldv;
+      LLS_TRY(xgemm(false, false, kDense, kUnitLower, n, b, np, 1.0, Vk, ldv, Y, ldw, 0.0, h.P.d(),
+                    ldv));
+      LLS_TRY(xgemm(false, false, kDense, kDense, n, b, b, 1.0, h.P.d(), ldv, TVi, nb, 0.0,
+                    h.P2.d(), ldv));
+      LLS_TRY(xgemm(false, true, kDense, kUnitLower, n, np, b, -1.0, h.P2.d(), ldv, Y, ldw, 1.0, Vk,
+                    ldv));
+    }
     // ---- a5: [[A11; A21], T_U, W_U] = unpivoted_QR([A11; A21])
     phase.reset();
     phase.emplace(kTrPhasePanel, st);
@@ -235,6 +263,11 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       LLS_TRY(xgemm(false, false, kDense, kDense, k, b, b, 1.0, T + k * ldt, ldt,
                     f.VS.d() + i * blk, nb, 0.0, h.P.d(), k));
       LLS_TRY(copy_matrix(k, b, h.P.d(), k, T + k * ldt, ldt, st));
+    }
+    if (f.has_v) {  // V(:, k:k+b) <- V(:, k:k+b) V_SVD (later steps never touch these columns)
+      LLS_TRY(xgemm(false, false, kDense, kDense, n, b, b, 1.0, f.Vx.d() + k * ldv, ldv,
+                    f.VS.d() + i * blk, nb, 0.0, h.P.d(), ldv));
+      LLS_TRY(copy_matrix(n, b, h.P.d(), ldv, f.Vx.d() + k * ldv, ldv, st));
     }
   }
   for (int64_t i = 0; i < steps; ++i) {
@@ -298,14 +331,39 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     LLS_TRY(f.RzM.reserve(sizeof(double) * off_m));
     LLS_TRY(f.RzT.reserve(sizeof(double) * off_t));
     LLS_TRY(f.RzTau.reserve(sizeof(double) * off_tau));
-    LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)std::max<int64_t>(r, 1) * nb));
+    const int64_t xrows = f.has_v ? std::max(r, n) : r;  // rows updated per block: T's, V's
+    LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)std::max<int64_t>(xrows, 1) * nb));
     LLS_TRY(h.gemm_ws.reserve(std::max(h.gemm_ws.bytes,
                                        std::max(gemm_scratch_bytes(nb, nb, L + nb),
-                                                gemm_scratch_bytes(r, nb, L)))));
+                                                gemm_scratch_bytes(xrows, nb, L)))));
     LLS_TRY(h.panel_ws.reserve(panel_qr_scratch_bytes(L + nb, nb) + 64));
     pws = scratch_of(h.panel_ws);
-    LLS_TRY(h.P.reserve(sizeof(double) * (size_t)std::max<int64_t>(r, 1) * nb));
-    LLS_TRY(h.P2.reserve(sizeof(double) * (size_t)std::max<int64_t>(r, 1) * nb));
+    LLS_TRY(h.P.reserve(sizeof(double) * (size_t)std::max<int64_t>(xrows, 1) * nb));
+    LLS_TRY(h.P2.reserve(sizeof(double) * (size_t)std::max<int64_t>(xrows, 1) * nb));
+    // [X_rev | X_tail] <- [X_rev | X_tail] (I - W T_z W^T) with W = [I; W_bot]:
+    // the block's reflectors applied from the right to `rows` rows of a
+    // matrix X (ld ldx) whose columns j0..j0+bsz-1 are taken reversed and
+    // whose columns r..n-1 form the tail (Update of Fig. 3).
+    auto apply_rz_right = [&](int64_t rows, double* Xm, int64_t ldx, int64_t j0, int64_t bsz,
+                              const double* Wbot, int64_t ldm, const double* Tz) -> Status {
+      double* Xc = h.xc.d();
+      double* D0 = Xm + r * ldx;
+      LLS_TRY(copy_cols_reversed(rows, bsz, Xm + j0 * ldx, ldx, Xc, rows, st));
+      LLS_TRY(copy_matrix(rows, bsz, Xc, rows, h.P.d(), rows, st));
+      if (tc) LLS_TRY(h.oz_ws.reserve(std::max(oz_gemm_workspace_bytes(rows, bsz, L),
+                                                oz_gemm_workspace_bytes(rows, L, bsz))));
+      if (tc) LLS_TRY(h.oz_ws.reserve(oz_gemm_workspace_bytes(rows, bsz, bsz)));
+      LLS_TRY(xgemm(false, false, kDense, kDense, rows, bsz, L, 1.0, D0, ldx, Wbot, ldm, 1.0,
+                    h.P.d(), rows));
+      LLS_TRY(xgemm(false, false, kDense, kDense, rows, bsz, bsz, 1.0, h.P.d(), rows, Tz, bsz, 0.0,
+                    h.P2.d(), rows));
+      LLS_TRY(xgemm(false, true, kDense, kDense, rows, L, bsz, -1.0, h.P2.d(), rows, Wbot, ldm, 1.0,
+                    D0, ldx));
+      // X_rev -= P2 W_top^T with W_top = I, then reversed back into X
+      LLS_TRY(axpy_matrix(rows, bsz, -1.0, h.P2.d(), rows, Xc, rows, st));
+      LLS_TRY(copy_cols_reversed(rows, bsz, Xc, rows, Xm + j0 * ldx, ldx, st));
+      return ok_status();
+    };
     for (const auto& bl : f.rz) {
       const int64_t j0 = bl.j0, bsz = bl.bsz, ldm = bsz + L;
       double* M = f.RzM.d() + bl.off_m;
@@ -318,26 +376,10 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
                     h.S.d(), nb));
       LLS_TRY(wy_tfactor(bsz, h.S.d(), nb, tz, Tz, bsz, st));
       LLS_TRY(rz_scatter(bsz, M, ldm, T, ldt, j0, r, L, st));
-      if (j0 > 0) {
-        // X~ = [C01 reversed | D0]; X~ <- X~ - (X~ W) T W^T with W = [I; W_bot]
-        double* Xc = h.xc.d();
-        double* D0 = T + r * ldt;
-        const double* Wbot = M + bsz;
-        LLS_TRY(copy_cols_reversed(j0, bsz, T + j0 * ldt, ldt, Xc, j0, st));
-        LLS_TRY(copy_matrix(j0, bsz, Xc, j0, h.P.d(), j0, st));
-        if (tc) LLS_TRY(h.oz_ws.reserve(std::max(oz_gemm_workspace_bytes(j0, bsz, L),
-                                                  oz_gemm_workspace_bytes(j0, L, bsz))));
-        if (tc) LLS_TRY(h.oz_ws.reserve(oz_gemm_workspace_bytes(j0, bsz, bsz)));
-        LLS_TRY(xgemm(false, false, kDense, kDense, j0, bsz, L, 1.0, D0, ldt, Wbot, ldm, 1.0,
-                      h.P.d(), j0));
-        LLS_TRY(xgemm(false, false, kDense, kDense, j0, bsz, bsz, 1.0, h.P.d(), j0, Tz, bsz, 0.0,
-                      h.P2.d(), j0));
-        LLS_TRY(xgemm(false, true, kDense, kDense, j0, L, bsz, -1.0, h.P2.d(), j0, Wbot, ldm, 1.0,
-                      D0, ldt));
-        // C01 (reversed) -= P2 W_top^T with W_top = I, then reversed back into T
-        LLS_TRY(axpy_matrix(j0, bsz, -1.0, h.P2.d(), j0, Xc, j0, st));
-        LLS_TRY(copy_cols_reversed(j0, bsz, Xc, j0, T + j0 * ldt, ldt, st));
-      }
+      // Update(C_01, D_0): the rows of T above the block
+      if (j0 > 0) LLS_TRY(apply_rz_right(j0, T, ldt, j0, bsz, M + bsz, ldm, Tz));
+      // Update(E_1, F): all n rows of an explicit V
+      if (f.has_v) LLS_TRY(apply_rz_right(n, f.Vx.d(), ldv, j0, bsz, M + bsz, ldm, Tz));
     }
     f.nullified = true;
     LLS_CUDA(cudaMemcpyAsync(&h.hstat->barrier_err, &ds->barrier_err, sizeof(int),
@@ -407,6 +449,15 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   // y = T_tl^{-1} c
   LLS_TRY(h.gemm_ws.reserve(trsm_upper_scratch_bytes(r, nrhs)));
   LLS_TRY(trsm_upper(r, nrhs, T, ldt, Bw, m, scratch_of(h.gemm_ws), st));
+  if (f.has_v) {  // x = V(:, 0:r) y, V with Nullify's reflectors included
+    LLS_TRY(fgemm(false, false, kDense, kDense, n, nrhs, r, 1.0, f.Vx.d(), ldw, Bw, m, 0.0, X,
+                  ldx));
+    int flag = 0;
+    LLS_CUDA(cudaMemcpyAsync(&flag, &ds->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LLS_CUDA(cudaStreamSynchronize(st));
+    if (flag) return make_error(LLS_ERR_NONFINITE, "B has a NaN or Inf entry", 6);
+    return ok_status();
+  }
   // z = [y; 0]
   LLS_TRY(copy_matrix(r, nrhs, Bw, m, Z, ldw, st));
   if (r < n) LLS_TRY(fill_zero(n - r, nrhs, Z + r, ldw, st));
@@ -450,6 +501,56 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   LLS_CUDA(cudaStreamSynchronize(st));
   if (flag) return make_error(LLS_ERR_NONFINITE, "B has a NaN or Inf entry", 6);
   return ok_status();
+}
+
+// ---------------------------------------------------------------------------
+// Iterative refinement: x <- x + P (b - A x), P = V_1 T_11^{-1} U_1^T applied
+// by solve_factored, the residual in FP64 with the original A.
+// ---------------------------------------------------------------------------
+Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const double* B,
+                     int64_t nrhs, int64_t ldb, double* X, int64_t ldx) {
+  h.refine_steps = 0;
+  h.refine_corr = 0.0;
+  LLS_TRY(solve_factored(h, f, B, nrhs, ldb, X, ldx));
+  const int64_t m = f.m, n = f.n;
+  if (!A && f.has_a) {
+    A = f.A0.d();
+    lda = f.ldt;
+  }
+  if (h.opt.max_refine <= 0 || !A || m == 0 || n == 0 || nrhs == 0 || f.rank == 0)
+    return ok_status();
+  cudaStream_t st = h.stream;
+  LLS_TRY(h.rr.reserve(sizeof(double) * (size_t)m * nrhs));
+  LLS_TRY(h.dd.reserve(sizeof(double) * (size_t)n * nrhs));
+  LLS_TRY(h.nrm.reserve(sizeof(double) * 2 * (size_t)nrhs));
+  LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(m, nrhs, n)));
+  std::vector<double> norms(2 * (size_t)nrhs);
+  double prev = 0.0;
+  for (int it = 1; it <= h.opt.max_refine; ++it) {
+    // r = b - A x
+    LLS_TRY(copy_matrix(m, nrhs, B, ldb, h.rr.d(), m, st));
+    LLS_TRY(gemm(false, false, kDense, kDense, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, h.rr.d(), m,
+                 scratch_of(h.gemm_ws), st));
+    // d = P r; x += d
+    LLS_TRY(solve_factored(h, f, h.rr.d(), nrhs, m, h.dd.d(), n));
+    LLS_TRY(refine_update(n, nrhs, h.dd.d(), n, X, ldx, h.nrm.d(), st));
+    LLS_CUDA(cudaMemcpyAsync(norms.data(), h.nrm.d(), sizeof(double) * 2 * nrhs,
+                             cudaMemcpyDeviceToHost, st));
+    LLS_CUDA(cudaStreamSynchronize(st));
+    double corr = 0.0;
+    for (int64_t j = 0; j < nrhs; ++j) {
+      const double dn = std::sqrt(norms[2 * j]), xn = std::sqrt(norms[2 * j + 1]);
+      const double c = xn > 0.0 ? dn / xn : (dn > 0.0 ? INFINITY : 0.0);
+      corr = std::max(corr, c);
+    }
+    h.refine_steps = it;
+    h.refine_corr = corr;
+    if (corr <= h.opt.refine_tol) return ok_status();
+    if (it > 1 && corr > 0.5 * prev) break;  // no longer contracting: rounding floor
+    prev = corr;
+  }
+  return make_error(LLS_WARN_REFINE_NOCONV, "refinement correction " + std::to_string(h.refine_corr) +
+                                                " above refine_tol");
 }
 
 }  // namespace lls

@@ -28,10 +28,11 @@ inline bool injected_alloc_failure() {
   return false;
 }
 
-// Owning device buffer.
+// Owning device buffer (with guard words while lls_debug_guard is on).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  bool guarded = false;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
@@ -40,10 +41,12 @@ struct DevBuf {
     // Work queued on any stream may still use the old buffer.
     if (p) {
       cudaDeviceSynchronize();
-      cudaFree(p);
+      if (guarded) guard_free(p);
+      else cudaFree(p);
     }
     p = nullptr;
     bytes = 0;
+    guarded = false;
   }
   // Grow to at least `need` bytes (contents are not kept).
   Status reserve(size_t need) {
@@ -53,6 +56,16 @@ struct DevBuf {
     if (injected_alloc_failure())
       return make_error(LLS_ERR_NOMEM, "device allocation of " + std::to_string(need) +
                                            " bytes failed (injected)");
+    if (g_guard_mode.load(std::memory_order_relaxed)) {
+      Status s = guard_alloc(need, &p);
+      if (!s.ok()) {
+        p = nullptr;
+        return s;
+      }
+      guarded = true;
+      bytes = need;
+      return ok_status();
+    }
     cudaError_t e = cudaMalloc(&p, need);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -88,10 +101,16 @@ struct DevStatus {
 //  US, VS  per step nb x nb singular vectors of the diagonal block (ld nb).
 //  Rz*     Nullify: per row block, the (bsz + n - r) x bsz reflector panel
 //          M (Householder vectors below its diagonal) and its T factor.
+//  Vx      with explicit_v: V itself (n x n, ld n), Nullify's reflectors
+//          included.
+//  A0      with max_refine > 0 on a factor kept for reuse: a copy of A
+//          (m x n, ld m) for the refinement residual.
 struct Factor {
   int64_t m = 0, n = 0, ldt = 0;
   int nb = 0, q = 0, precision = 0;
   bool nullified = false;
+  bool has_v = false, has_a = false;
+  DevBuf Vx, A0;
   std::vector<int64_t> ks, bs;
   DevBuf T, WV, TV, TU, US, VS, tauV, tauU, Rblk, sigma;
   int64_t rank = 0, rank_count = 0;
@@ -104,7 +123,8 @@ struct Factor {
   DevBuf RzM, RzT, RzTau;
   size_t bytes() const {
     return T.bytes + WV.bytes + TV.bytes + TU.bytes + US.bytes + VS.bytes + tauV.bytes +
-           tauU.bytes + Rblk.bytes + sigma.bytes + RzM.bytes + RzT.bytes + RzTau.bytes;
+           tauU.bytes + Rblk.bytes + sigma.bytes + RzM.bytes + RzT.bytes + RzTau.bytes +
+           Vx.bytes + A0.bytes;
   }
 };
 
@@ -129,6 +149,11 @@ struct Handle {
   bool own_stream = false;
   // workspace
   DevBuf G, Wt, P, P2, Q, Q2, S, gemm_ws, panel_ws, bw, z, sp, sp2, xc;
+  // iterative refinement: residual, correction, per-column norms; what the
+  // last refined solve did (lls_refinement_info)
+  DevBuf rr, dd, nrm;
+  int refine_steps = 0;
+  double refine_corr = 0.0;
   DevBuf dstat;           // DevStatus
   // mixed precision sampling: bf16 copies of A_BR and A_BR^T, bf16 sketch /
   // product, fp32 product, tensor-core split-K partials, scalars
@@ -165,12 +190,19 @@ struct TraceGuard {
   ~TraceGuard() { g_tracer = prev; }
 };
 
+// keep_a: with opt.max_refine > 0, keep a copy of A in the factor so that
+// later solves with it can refine.
 Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, int64_t lda,
-                 double tol);
+                 double tol, bool keep_a = false);
 Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64_t ldb, double* X,
                       int64_t ldx);
+// solve_factored, then opt.max_refine refinement steps x <- x + P (b - A x)
+// with A (ld lda), or f's own copy when A is NULL; no refinement when
+// max_refine = 0 or neither is there.  Records the steps in h.
+Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const double* B,
+                     int64_t nrhs, int64_t ldb, double* X, int64_t ldx);
 // Device bytes a factorization of m x n (and a solve with nrhs) will hold.
-size_t factor_bytes(int64_t m, int64_t n, int nb);
+size_t factor_bytes(int64_t m, int64_t n, int nb, bool explicit_v = false, bool keep_a = false);
 
 // Stops and joins the worker pool (serving.cu); queued requests are dropped.
 void stop_pool(Handle& h);

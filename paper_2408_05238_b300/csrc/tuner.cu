@@ -98,6 +98,8 @@ int lls_autotune(lls_handle hh, int64_t m, int64_t n, int32_t trials, int32_t* n
     lls::decay_cols_kernel<<<(unsigned)lls::ceil_div(m * r, 256), 256, 0, st>>>(m, r,
                                                                                (double*)X.p, m);
     s = lls::cuda_status(cudaGetLastError(), "decay_cols_kernel");
+    lls::g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (lls::g_guard_mode.load(std::memory_order_relaxed)) lls::guard_after_launch("decay_cols_kernel");
   }
   const size_t wsb = lls::gemm_scratch_bytes(m, n, r);
   if (s.ok() && wsb && cudaMalloc(&ws.p, wsb) != cudaSuccess) s = lls::make_error(LLS_ERR_NOMEM, "tuner");

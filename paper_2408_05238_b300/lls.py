@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "liblls.so")
 LLS_OK = 0
 LLS_PENDING = 1
 LLS_WARN_RANK_NONPREFIX = 2
+LLS_WARN_REFINE_NOCONV = 3
 LLS_ERR_ARG = -1
 LLS_ERR_NOMEM = -2
 LLS_ERR_CUDA = -3
@@ -30,11 +31,15 @@ LLS_ERR_NOT_FOUND = -7
 LLS_ERR_CAPACITY = -8
 LLS_FP64 = 0
 LLS_MIXED_BF16 = 1
+LLS_FACTOR_T = 0
+LLS_FACTOR_V = 1
 
 
 class lls_options(C.Structure):
     _fields_ = [("nb", C.c_int32), ("q", C.c_int32), ("precision", C.c_int32),
-                ("nullify", C.c_int32), ("seed", C.c_uint64), ("reserved", C.c_int32 * 4)]
+                ("nullify", C.c_int32), ("seed", C.c_uint64), ("explicit_v", C.c_int32),
+                ("max_refine", C.c_int32), ("refine_tol", C.c_double),
+                ("reserved", C.c_int32 * 2)]
 
 
 class lls_problem(C.Structure):
@@ -84,6 +89,8 @@ _sig("lls_factor", [_H, _P, _I, _I, _I, _D, C.POINTER(_I), C.POINTER(_I)])
 _sig("lls_solve_factored", [_H, _I, _P, _I, _I, _P, _I])
 _sig("lls_factor_release", [_H, _I])
 _sig("lls_factor_diag", [_H, _I, _P, _I, C.POINTER(_I)])
+_sig("lls_factor_get", [_H, _I, C.c_int32, _P, _I])
+_sig("lls_refinement_info", [_H, C.POINTER(C.c_int32), C.POINTER(_D)])
 _sig("lls_solve_batched", [_H, _I, C.POINTER(lls_problem)])
 _sig("lls_submit", [_H, C.POINTER(lls_problem), C.POINTER(_I)])
 _sig("lls_poll", [_H, _I, C.POINTER(C.c_int)])
@@ -92,6 +99,9 @@ _sig("lls_ticket_factor", [_H, _I, C.POINTER(_I)])
 _sig("lls_set_workers", [_H, C.c_int])
 _sig("lls_cancel", [_H, _I])
 _sig("lls_debug_fail_allocation", [_I])
+_sig("lls_debug_guard", [C.c_int])
+_sig("lls_debug_guard_report", [C.c_char_p, _I], C.c_int64)
+_sig("lls_debug_guard_selftest", [])
 _sig("lls_autotune", [_H, _I, _I, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)])
 _sig("lls_tuning_lookup", [_H, _I, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)])
 _sig("lls_tuning_save", [_H, C.c_char_p])
@@ -256,6 +266,21 @@ def lls_factor_diag(h, factor_id: int, length: int):
     return d[:length], cnt.value
 
 
+def lls_factor_get(h, factor_id: int, which: int, rows: int, cols: int) -> torch.Tensor:
+    """T (which = LLS_FACTOR_T, rows x cols = m x n) or V (LLS_FACTOR_V, n x n)
+    of a resident factor as a new column-major CUDA tensor."""
+    out = empty_colmajor(rows, cols)
+    _check(h, _lib.lls_factor_get(h, factor_id, int(which), _ptr(out), max(1, rows)))
+    return out
+
+
+def lls_refinement_info(h) -> tuple[int, float]:
+    """(steps, last correction) of the last solve's iterative refinement."""
+    steps, corr = C.c_int32(0), _D(0.0)
+    _check(h, _lib.lls_refinement_info(h, C.byref(steps), C.byref(corr)))
+    return steps.value, corr.value
+
+
 def make_problem(A, B, tol, X, factor_id=-1, keep_factor=0, rank_out=None) -> lls_problem:
     p = lls_problem()
     m, n = (A.shape if A is not None else (B.shape[0], X.shape[0]))
@@ -317,6 +342,23 @@ def lls_cancel(h, ticket: int) -> int:
 def lls_debug_fail_allocation(after: int):
     """Testing hook: the (after + 1)-th workspace allocation fails; -1 = off."""
     _check(None, _lib.lls_debug_fail_allocation(after))
+
+
+def lls_debug_guard(on: bool):
+    """Guard words around every buffer allocated from now on, checked after
+    every launch (debug mode)."""
+    _check(None, _lib.lls_debug_guard(1 if on else 0))
+
+
+def lls_debug_guard_report() -> tuple[int, str]:
+    """(violations since the mode was turned on, the first one's description)."""
+    buf = C.create_string_buffer(512)
+    n = _lib.lls_debug_guard_report(buf, 512)
+    return int(n), buf.value.decode(errors="replace")
+
+
+def lls_debug_guard_selftest() -> int:
+    return int(_lib.lls_debug_guard_selftest())
 
 
 def lls_autotune(h, m: int, n: int, trials: int = 2) -> tuple[int, int]:

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for code in (0, 1, 2, -1, -2, -3, -4, -5, -6, -7, -8):
+    for code in (0, 1, 2, 3, -1, -2, -3, -4, -5, -6, -7, -8):
         s = lib.status_string(code)
         assert s and s != "unknown status"
     assert lib.status_string(12345) == "unknown status"
@@ -52,6 +52,10 @@ def test_status_strings(lib):
 def test_default_options(lib):
     o = lib.lls_default_options()
     assert (o.nb, o.q, o.precision, o.nullify, o.seed) == (64, 1, 0, 1, 2001)
+    assert (o.explicit_v, o.max_refine, o.refine_tol) == (0, 0, 1e-12)
+    assert list(o.reserved) == [0, 0]
+    # the ctypes mirror has the C struct's size (4 int32, uint64, 2 int32, double, 2 int32)
+    assert C.sizeof(lib.lls_options) == 48
     assert lib._lib.lls_default_options(None) == lib.LLS_ERR_ARG
 
 
@@ -65,6 +69,24 @@ def test_null_handle_and_bad_create(lib):
         assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
     bad = lib.lls_default_options(q=9)
     assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
+
+
+@pytest.mark.parametrize("field,value", [("explicit_v", 2), ("explicit_v", -1), ("max_refine", -1),
+                                         ("max_refine", 17), ("refine_tol", -1e-3),
+                                         ("refine_tol", float("nan")), ("refine_tol", float("inf")),
+                                         ("nullify", 2), ("precision", 7)])
+def test_bad_options_rejected_before_any_cuda_call(lib, field, value):
+    h = C.c_void_p()
+    bad = lib.lls_default_options(**{field: value})
+    assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
+    bad = lib.lls_default_options()
+    bad.reserved[1] = 1
+    assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
+
+
+def test_new_entry_points_reject_null_handle(lib):
+    assert lib._lib.lls_factor_get(None, 0, 0, None, 1) == lib.LLS_ERR_ARG
+    assert lib._lib.lls_refinement_info(None, None, None) == lib.LLS_ERR_ARG
 
 
 def test_kernel_entry_points_reject_bad_sizes(lib):

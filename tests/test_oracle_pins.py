@@ -317,3 +317,45 @@ def test_pinv_from_factors_equals_svd_pinv():
     x1 = orc.pinv_solve_from_factors(Q1, sigma, Q2, B, 60)
     x2 = orc.pinv_solve(A, B, 60)
     assert np.linalg.norm(x1 - x2) / np.linalg.norm(x2) < 1e-9
+
+
+# -------------------------------------------------------------------- refinement
+@pytest.mark.parametrize("nullify", [True, False])
+def test_refine_removes_error_in_row_space_in_one_step(nullify):
+    """U_1^T A V_1 = T_11 (A V = U T, T upper triangular), so P A = I on
+    range(V_1): one refinement step from x + V_1 c returns x for any c."""
+    A, X, Y = wl.lowrank_xy(120, 90, 35, seed=21, noise=1e-14)
+    b = np.random.default_rng(3).standard_normal(120)
+    nrm = wl.norm2_of_product(X, Y)
+    sol = orc.solve(A, b, 1, 16, 1e-10 * nrm, seed=5, do_nullify=nullify, keep=True)
+    assert sol.rank == 35
+    V1 = sol.utv.V[:, :35]
+    x_bad = sol.x + V1 @ np.random.default_rng(4).standard_normal(35)
+    assert np.linalg.norm(x_bad - sol.x) > 0.1 * np.linalg.norm(sol.x)
+    x1 = orc.refine(A, b, sol, x0=x_bad, steps=1)
+    assert np.linalg.norm(x1 - sol.x) / np.linalg.norm(sol.x) < 1e-12
+
+
+def test_refine_fixed_point_and_pseudoinverse():
+    """P b is a fixed point: refining the solution changes it only by
+    rounding, and the refined x is still the truncated-SVD solution."""
+    A, X, Y = wl.lowrank_xy(100, 80, 30, seed=8, noise=1e-14)
+    B = np.random.default_rng(5).standard_normal((100, 2))
+    nrm = wl.norm2_of_product(X, Y)
+    sol = orc.solve(A, B, 1, 16, 1e-10 * nrm, seed=9, keep=True)
+    x2 = orc.refine(A, B, sol, steps=2)
+    assert np.linalg.norm(x2 - sol.x) / np.linalg.norm(sol.x) < 1e-13
+    x_ref = orc.pinv_solve(A, B, 30)
+    assert np.linalg.norm(x2 - x_ref) / np.linalg.norm(x_ref) < 1e-12
+
+
+def test_refine_leaves_nullspace_components():
+    """After Nullify T_12 = 0, so P A V_2 = 0: refinement cannot remove a
+    nullspace component (the minimum-norm property comes from P b itself)."""
+    A, X, Y = wl.lowrank_xy(70, 60, 20, seed=17, noise=1e-14)
+    b = np.random.default_rng(6).standard_normal(70)
+    sol = orc.solve(A, b, 1, 8, 1e-10 * wl.norm2_of_product(X, Y), seed=2, keep=True)
+    V2 = sol.utv.V[:, 20:]
+    c = np.random.default_rng(7).standard_normal(40)
+    x1 = orc.refine(A, b, sol, x0=sol.x + V2 @ c, steps=1)
+    assert np.linalg.norm(x1 - (sol.x + V2 @ c)) < 1e-9 * np.linalg.norm(c)
