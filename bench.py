@@ -321,7 +321,7 @@ def run_batched(a):
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
-    launches0 = lls.lls_launch_count()
+    launches0, allocs0 = lls.lls_launch_count(), lls.lls_alloc_count()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         t0 = time.perf_counter()
         for _ in range(a.steps):
@@ -329,6 +329,7 @@ def run_batched(a):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
     launches = lls.lls_launch_count() - launches0
+    allocs = lls.lls_alloc_count() - allocs0
     flops = sum(pm.lls_flops(m, n, *nbq(lls, h, m, n, a.autotune), rk.value, k)
                 for (m, n, r, k), rk in zip(sizes, ranks))
     wrong = sum(rk.value != r for (_, _, _, _, r), rk in zip(probs, ranks))
@@ -342,7 +343,7 @@ def run_batched(a):
                                   + ("nb, q autotuned per (m, n) bucket" if a.autotune else "nb=64, q=1"),
                       "workers": a.workers, "precision": a.precision, "tuning": tuning},
            "tflops": flops * a.steps / dt / 1e12, "rank_mismatches": wrong,
-           "gpu_launches": launches, "clocks": clk.summary()}
+           "gpu_launches": launches, "device_allocations": allocs, "clocks": clk.summary()}
     print(json.dumps(out))
     return 0
 

@@ -279,6 +279,11 @@ int lls_trace_read(lls_handle h, lls_trace_stat* out, int64_t max, int64_t* coun
  * handles and threads). */
 int64_t lls_launch_count(void);
 
+/* Number of device allocations (workspace and factor buffers growing) this
+ * library has made since it was loaded.  A steady-state loop of solves of
+ * shapes seen before makes none. */
+int64_t lls_alloc_count(void);
+
 /* Testing hook (failure injection on the host): the (after + 1)-th device
  * workspace allocation from now, in any handle, fails as if the device were
  * out of memory (the call returns LLS_ERR_NOMEM and the handle stays usable);

@@ -63,11 +63,11 @@ Status do_solve(Handle& h, const double* A, int64_t m, int64_t n, int64_t lda, c
   if (rank) *rank = 0;
   if (n == 0 || nrhs == 0) return lls::ok_status();
   if (m == 0) return lls::fill_zero(n, nrhs, X, ldx, h.stream);
-  if (!h.scratch_factor) h.scratch_factor.reset(new lls::Factor());
-  Status fs = lls::factorize(h, *h.scratch_factor, A, m, n, lda, tol);
+  lls::Factor& f = h.scratch();
+  Status fs = lls::factorize(h, f, A, m, n, lda, tol);
   if (!fs.ok()) return fs;
-  if (rank) *rank = h.scratch_factor->rank;
-  Status ss = lls::solve_refined(h, *h.scratch_factor, A, lda, B, nrhs, ldb, X, ldx);
+  if (rank) *rank = f.rank;
+  Status ss = lls::solve_refined(h, f, A, lda, B, nrhs, ldb, X, ldx);
   if (!ss.ok()) return ss;
   return fs.code != LLS_OK ? fs : ss;  // LLS_WARN_RANK_NONPREFIX, else LLS_WARN_REFINE_NOCONV
 }
@@ -113,6 +113,7 @@ int lls_create(lls_handle* out, const lls_options* opt, void* cuda_stream) {
     }
     h->own_stream = true;
   }
+  h->bind_workspace();
   *out = reinterpret_cast<lls_handle>(h);
   return LLS_OK;
 }

@@ -48,6 +48,10 @@ Handle::Handle() = default;
 
 Handle::~Handle() {
   stop_pool(*this);
+  // Stream-ordered frees of the workspace before the stream goes away.
+  for (DevBuf* b : workspace()) b->release();
+  scratch_factor.reset();
+  if (stream) cudaStreamSynchronize(stream);
   if (hstat) cudaFreeHost(hstat);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
@@ -91,12 +95,8 @@ Status run_request(Handle& parent, Handle& w, lls_problem& p) {
     return s;
   }
   std::shared_ptr<Factor> f;
-  if (p.keep_factor) {
-    f = std::make_shared<Factor>();
-  } else if (!w.scratch_factor) {
-    w.scratch_factor.reset(new Factor());
-  }
-  Factor& fr = p.keep_factor ? *f : *w.scratch_factor;
+  if (p.keep_factor) f = std::make_shared<Factor>();  // shared later: not stream-bound
+  Factor& fr = p.keep_factor ? *f : w.scratch();
   Status fs = factorize(w, fr, p.A, p.m, p.n, p.lda, p.tol, p.keep_factor != 0);
   if (!fs.ok()) return fs;
   if (p.rank_out) *p.rank_out = fr.rank;
@@ -159,6 +159,7 @@ Status ensure_pool(Handle& h) {
     if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
       return make_error(LLS_ERR_CUDA, "cannot create a worker stream");
     w->own_stream = true;
+    w->bind_workspace();
     pool->workers.push_back(std::move(w));
   }
   Handle::Pool* raw = pool.get();

@@ -52,6 +52,18 @@ size_t loop_gemm_scratch(int64_t m, int64_t n, int nb, int64_t max_nrhs) {
   return need;
 }
 
+// Waits for the handle's stream and reports B's finiteness check (read
+// through the handle's pinned status mirror: a copy into pageable memory
+// would go through the driver's shared staging buffer).
+Status read_nonfinite_flag(Handle& h, const DevStatus* ds) {
+  if (!h.hstat) LLS_CUDA(cudaMallocHost((void**)&h.hstat, sizeof(DevStatus)));
+  LLS_CUDA(cudaMemcpyAsync(&h.hstat->nonfinite, &ds->nonfinite, sizeof(int),
+                           cudaMemcpyDeviceToHost, h.stream));
+  LLS_CUDA(cudaStreamSynchronize(h.stream));
+  if (h.hstat->nonfinite) return make_error(LLS_ERR_NONFINITE, "B has a NaN or Inf entry", 6);
+  return ok_status();
+}
+
 }  // namespace
 
 size_t factor_bytes(int64_t m, int64_t n, int nb, bool explicit_v, bool keep_a) {
@@ -452,11 +464,7 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   if (f.has_v) {  // x = V(:, 0:r) y, V with Nullify's reflectors included
     LLS_TRY(fgemm(false, false, kDense, kDense, n, nrhs, r, 1.0, f.Vx.d(), ldw, Bw, m, 0.0, X,
                   ldx));
-    int flag = 0;
-    LLS_CUDA(cudaMemcpyAsync(&flag, &ds->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LLS_CUDA(cudaStreamSynchronize(st));
-    if (flag) return make_error(LLS_ERR_NONFINITE, "B has a NaN or Inf entry", 6);
-    return ok_status();
+    return read_nonfinite_flag(h, ds);
   }
   // z = [y; 0]
   LLS_TRY(copy_matrix(r, nrhs, Bw, m, Z, ldw, st));
@@ -496,11 +504,7 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
                  ldw));
   }
   LLS_TRY(copy_matrix(n, nrhs, Z, ldw, X, ldx, st));
-  int flag = 0;
-  LLS_CUDA(cudaMemcpyAsync(&flag, &ds->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LLS_CUDA(cudaStreamSynchronize(st));
-  if (flag) return make_error(LLS_ERR_NONFINITE, "B has a NaN or Inf entry", 6);
-  return ok_status();
+  return read_nonfinite_flag(h, ds);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,20 +29,38 @@ inline bool injected_alloc_failure() {
 }
 
 // Owning device buffer (with guard words while lls_debug_guard is on).
+//
+// A buffer bound to a stream (bind) is only ever used by work on that
+// stream: it is allocated and freed stream-ordered (cudaMallocAsync /
+// cudaFreeAsync), so growing it never waits for other streams.  An unbound
+// buffer may be used from any stream (resident factors shared by the
+// worker pool): freeing it first waits for the whole device.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
   bool guarded = false;
+  cudaStream_t stream = nullptr;
+  bool ordered = false;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
+  // Only while empty.
+  void bind(cudaStream_t s) {
+    stream = s;
+    ordered = true;
+  }
   void release() {
-    // Work queued on any stream may still use the old buffer.
     if (p) {
-      cudaDeviceSynchronize();
-      if (guarded) guard_free(p);
-      else cudaFree(p);
+      if (guarded) {
+        cudaDeviceSynchronize();
+        guard_free(p);
+      } else if (ordered) {
+        cudaFreeAsync(p, stream);  // after the work queued on `stream` that uses it
+      } else {
+        cudaDeviceSynchronize();  // work queued on any stream may still use it
+        cudaFree(p);
+      }
     }
     p = nullptr;
     bytes = 0;
@@ -56,6 +74,7 @@ struct DevBuf {
     if (injected_alloc_failure())
       return make_error(LLS_ERR_NOMEM, "device allocation of " + std::to_string(need) +
                                            " bytes failed (injected)");
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     if (g_guard_mode.load(std::memory_order_relaxed)) {
       Status s = guard_alloc(need, &p);
       if (!s.ok()) {
@@ -66,7 +85,7 @@ struct DevBuf {
       bytes = need;
       return ok_status();
     }
-    cudaError_t e = cudaMalloc(&p, need);
+    cudaError_t e = ordered ? cudaMallocAsync(&p, need, stream) : cudaMalloc(&p, need);
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
@@ -121,6 +140,13 @@ struct Factor {
   };
   std::vector<RzBlock> rz;
   DevBuf RzM, RzT, RzTau;
+  // Stream-ordered allocation for a factor that only one stream uses (a
+  // handle's reusable scratch factor); only while empty.
+  void bind(cudaStream_t s) {
+    for (DevBuf* b : {&T, &WV, &TV, &TU, &US, &VS, &tauV, &tauU, &Rblk, &sigma, &RzM, &RzT, &RzTau,
+                      &Vx, &A0})
+      b->bind(s);
+  }
   size_t bytes() const {
     return T.bytes + WV.bytes + TV.bytes + TU.bytes + US.bytes + VS.bytes + tauV.bytes +
            tauU.bytes + Rblk.bytes + sigma.bytes + RzM.bytes + RzT.bytes + RzTau.bytes +
@@ -179,6 +205,24 @@ struct Handle {
   std::unique_ptr<Pool> pool;
   Handle();  // both defined where Pool is complete (serving.cu)
   ~Handle();
+  // Every workspace buffer above (all used on `stream` only).
+  std::vector<DevBuf*> workspace() {
+    return {&G,  &Wt, &P,  &P2,  &Q,   &Q2,  &S,   &gemm_ws, &panel_ws,   &bw,   &z,   &sp,   &sp2,
+            &xc, &rr, &dd, &nrm, &dstat, &G16, &A16, &A16t,  &Z16,        &F32,  &tc_ws, &mixed_misc,
+            &oz_ws};
+  }
+  // Binds the workspace to `stream` (call once the stream is set).
+  void bind_workspace() {
+    for (DevBuf* b : workspace()) b->bind(stream);
+  }
+  // The handle's reusable factor for lls_solve / batched problems.
+  Factor& scratch() {
+    if (!scratch_factor) {
+      scratch_factor.reset(new Factor());
+      scratch_factor->bind(stream);
+    }
+    return *scratch_factor;
+  }
 };
 
 // Makes h's tracer the active one on this thread for the duration of a call.

@@ -8,6 +8,7 @@ namespace lls {
 
 thread_local Tracer* g_tracer = nullptr;
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_allocs{0};
 
 const char* trace_kind_name(int k) {
   static const char* names[kTrCount] = {"dgemm_kernel",      "splitk_reduce_kernel",
@@ -104,5 +105,6 @@ int lls_trace_read(lls_handle hh, lls_trace_stat* out, int64_t max, int64_t* cou
 }
 
 int64_t lls_launch_count(void) { return lls::g_launches.load(); }
+int64_t lls_alloc_count(void) { return lls::g_allocs.load(); }
 
 }  // extern "C"

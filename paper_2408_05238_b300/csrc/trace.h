@@ -62,6 +62,8 @@ struct Tracer {
 extern thread_local Tracer* g_tracer;
 // Kernels launched by the library since load (all handles, all threads).
 extern std::atomic<int64_t> g_launches;
+// Device allocations made by DevBuf (lls_alloc_count).
+extern std::atomic<int64_t> g_allocs;
 
 // Records a start event in the constructor and a stop event in the
 // destructor when a tracer is active.

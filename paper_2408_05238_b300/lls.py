@@ -111,6 +111,7 @@ _sig("lls_last_error", [_H, C.POINTER(C.c_int), C.c_char_p, _I])
 _sig("lls_trace_enable", [_H, C.c_int])
 _sig("lls_trace_read", [_H, C.POINTER(lls_trace_stat), _I, C.POINTER(_I)])
 _sig("lls_launch_count", [], C.c_int64)
+_sig("lls_alloc_count", [], C.c_int64)
 _sig("lls_k_philox", [C.c_uint64, _I, _I, _I, _P, _P])
 _sig("lls_k_sketch", [C.c_uint64, _I, _I, _I, _P, _I, _P])
 _sig("lls_k_gemm", [C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P,
@@ -398,6 +399,10 @@ def lls_trace_read(h) -> dict:
 
 def lls_launch_count() -> int:
     return int(_lib.lls_launch_count())
+
+
+def lls_alloc_count() -> int:
+    return int(_lib.lls_alloc_count())
 
 
 # --------------------------------------------------------------------------- step-level API
