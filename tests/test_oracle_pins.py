@@ -359,3 +359,46 @@ def test_refine_leaves_nullspace_components():
     c = np.random.default_rng(7).standard_normal(40)
     x1 = orc.refine(A, b, sol, x0=sol.x + V2 @ c, steps=1)
     assert np.linalg.norm(x1 - (sol.x + V2 @ c)) < 1e-9 * np.linalg.norm(c)
+
+
+# -------------------------------------------------------------------- properties
+from hypothesis import HealthCheck, given, settings, strategies as st  # noqa: E402
+
+
+@settings(max_examples=30, deadline=None, suppress_health_check=[HealthCheck.too_slow])
+@given(m=st.integers(1, 36), n=st.integers(1, 36), nb=st.integers(1, 40), q=st.integers(0, 2),
+       r=st.integers(0, 36), seed=st.integers(0, 2**31 - 1), nullify=st.booleans())
+def test_solve_properties_on_random_small_problems(m, n, nb, q, r, seed, nullify):
+    """Over random shapes, block sizes (including nb > min(m, n) and nb = 1),
+    power counts and ranks: the factorization invariants hold, the rank is the
+    construction's, and with Nullify x is the truncated-SVD solution; without
+    it x is still a least-squares solution of the rank-r system."""
+    r = min(r, m, n)
+    g = np.random.default_rng(seed)
+    if r > 0:
+        X = g.standard_normal((m, r))
+        Y = g.standard_normal((r, n))
+        A = X @ Y
+    else:
+        A = np.zeros((m, n))
+    b = g.standard_normal(m)
+    s = np.linalg.svd(A, compute_uv=False) if min(m, n) else np.zeros(0)
+    smax = s[0] if s.size else 0.0
+    if r > 0 and s[r - 1] < 1e-6 * smax:       # nearly dependent draw: rank not well defined
+        return
+    tol = 1e-9 * smax
+    res = orc.randutv(A, q, nb, seed=seed % 1000)
+    if min(m, n) > 0:
+        _check_utv(A, res, nb, tol_fact=1e-12)
+    sol = orc.solve(A, b, q, nb, tol, seed=seed % 1000, do_nullify=nullify)
+    assert sol.rank == r and sol.rank_count == r
+    if r == 0:
+        assert np.all(sol.x == 0)
+        return
+    x_ref = orc.pinv_solve(A, b, r)
+    if nullify:
+        assert np.linalg.norm(sol.x - x_ref) <= 1e-9 * np.linalg.norm(x_ref)
+    else:
+        # same residual as the minimum-norm solution, norm no smaller
+        assert np.linalg.norm(A @ sol.x - A @ x_ref) <= 1e-9 * max(np.linalg.norm(b), 1.0)
+        assert np.linalg.norm(sol.x) >= np.linalg.norm(x_ref) * (1 - 1e-9)
