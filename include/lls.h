@@ -145,6 +145,9 @@ int lls_default_options(lls_options* opt);
 
 /* Create a handle on the current CUDA device.  opt NULL = defaults.
  * cuda_stream: a cudaStream_t to borrow, or NULL for a handle-owned stream.
+ * A borrowed stream must outlive the handle: the handle's workspace is
+ * allocated and freed in stream order on it (cudaMallocAsync /
+ * cudaFreeAsync), up to lls_destroy.
  * Errors: LLS_ERR_ARG (bad option; index 2), LLS_ERR_CUDA, LLS_ERR_NOMEM. */
 int lls_create(lls_handle* h, const lls_options* opt, void* cuda_stream);
 
