@@ -254,6 +254,50 @@ int lls_cancel(lls_handle h, int64_t ticket);
  * lls_submit; waits for running requests and drops queued ones. */
 int lls_set_workers(lls_handle h, int workers);
 
+/* ---- out-of-core planning ---------------------------------------------
+ * The host<->device traffic of a solve whose m x n matrix stays in host
+ * memory and moves through a device cache of `cache_panels` whole column
+ * panels (nb columns, all m rows; the paper's block cache, Sec. 3.4, with
+ * device memory as the cache and host memory as the disk).  The plan visits
+ * the trailing panels in passes: per step of Fig. 2 the sampling passes
+ * (the first product A^T G taken in the previous step's update pass; q + 1
+ * passes for q >= 1), the pass forming T(:, k:n) W_V, and the update pass
+ * (right and left updates, modifying the panels); then one pass for the
+ * block-SVD updates; with nullify = 1 and 0 < rank < n, per panel-aligned
+ * row block of Nullify (Fig. 3) its panel and two passes over the panels of
+ * T(0:r, r:n); and the solve's reads (Fig. 4).  Consecutive passes alternate
+ * direction.  policy LLS_OOC_FARTHEST evicts the panel whose next use lies
+ * latest in the future (the paper's "LFU" policy, Belady's MIN: the access
+ * list is known before the solve starts), LLS_OOC_LRU the least recently
+ * used one; a modified panel is written back when evicted and at the end.
+ * Host computation only (no device is touched).  LLS_ERR_ARG for m, n < 0,
+ * nb < 1, q outside 0..4, rank outside 0..min(m, n), nullify not 0/1,
+ * cache_panels < 1, an unknown policy, more than 2^24 panels or out NULL. */
+enum { LLS_OOC_FARTHEST = 0, LLS_OOC_LRU = 1 };
+typedef struct {
+  int64_t panels;      /* column panels of nb columns (the last may be narrower) */
+  int64_t passes;      /* passes over panels in the plan */
+  int64_t accesses;    /* panel visits */
+  int64_t hits;        /* visits that found the panel on the device */
+  int64_t loads;       /* host->device panel copies (the other visits) */
+  int64_t stores;      /* device->host write-backs of modified panels */
+  double load_bytes;   /* bytes of those copies (whole panels, m rows) */
+  double store_bytes;
+  double side_bytes;   /* W_V of every step and Nullify's reflector panels:
+                          written to host memory once, read back once */
+} lls_ooc_stats;
+int lls_ooc_plan(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank, int32_t nullify,
+                 int64_t cache_panels, int32_t policy, lls_ooc_stats* out);
+
+/* The cache of lls_ooc_plan run over any access list: access t touches panel
+ * panels[t] (0 <= panels[t] < num_panels) and modifies it when writes[t] is
+ * nonzero (writes may be NULL: no modification); every panel is rows x cols
+ * FP64.  Fills loads, stores, hits, accesses, panels and the byte counts
+ * (passes and side_bytes are 0).  LLS_ERR_ARG on a bad argument. */
+int lls_ooc_simulate(const int64_t* panels, const int8_t* writes, int64_t count,
+                     int64_t num_panels, int64_t rows, int64_t cols, int64_t cache_panels,
+                     int32_t policy, lls_ooc_stats* out);
+
 /* ---- tracing (per-kernel-family CUDA-event timing) --------------------- */
 typedef struct {
   char name[32];     /* kernel family, e.g. "dgemm_kernel" */

@@ -33,6 +33,8 @@ LLS_FP64 = 0
 LLS_MIXED_BF16 = 1
 LLS_FACTOR_T = 0
 LLS_FACTOR_V = 1
+LLS_OOC_FARTHEST = 0
+LLS_OOC_LRU = 1
 
 
 class lls_options(C.Structure):
@@ -53,6 +55,13 @@ class lls_problem(C.Structure):
 class lls_trace_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("seconds", C.c_double),
                 ("flops", C.c_double), ("bytes", C.c_double)]
+
+
+class lls_ooc_stats(C.Structure):
+    _fields_ = [("panels", C.c_int64), ("passes", C.c_int64), ("accesses", C.c_int64),
+                ("hits", C.c_int64), ("loads", C.c_int64), ("stores", C.c_int64),
+                ("load_bytes", C.c_double), ("store_bytes", C.c_double),
+                ("side_bytes", C.c_double)]
 
 
 class LLSError(RuntimeError):
@@ -111,6 +120,10 @@ _sig("lls_last_error", [_H, C.POINTER(C.c_int), C.c_char_p, _I])
 _sig("lls_trace_enable", [_H, C.c_int])
 _sig("lls_trace_read", [_H, C.POINTER(lls_trace_stat), _I, C.POINTER(_I)])
 _sig("lls_launch_count", [], C.c_int64)
+_sig("lls_ooc_plan", [_I, _I, C.c_int32, C.c_int32, _I, C.c_int32, _I, C.c_int32,
+                      C.POINTER(lls_ooc_stats)])
+_sig("lls_ooc_simulate", [C.POINTER(_I), C.POINTER(C.c_int8), _I, _I, _I, _I, _I, C.c_int32,
+                          C.POINTER(lls_ooc_stats)])
 _sig("lls_alloc_count", [], C.c_int64)
 _sig("lls_k_philox", [C.c_uint64, _I, _I, _I, _P, _P])
 _sig("lls_k_sketch", [C.c_uint64, _I, _I, _I, _P, _I, _P])
@@ -343,6 +356,28 @@ def lls_cancel(h, ticket: int) -> int:
 def lls_debug_fail_allocation(after: int):
     """Testing hook: the (after + 1)-th workspace allocation fails; -1 = off."""
     _check(None, _lib.lls_debug_fail_allocation(after))
+
+
+def lls_ooc_plan(m: int, n: int, nb: int, q: int, rank: int, nullify: int, cache_panels: int,
+                 policy: int = LLS_OOC_FARTHEST) -> dict:
+    """Host<->device panel traffic of an out-of-core solve (lls_ooc_plan)."""
+    st = lls_ooc_stats()
+    _check(None, _lib.lls_ooc_plan(m, n, nb, q, rank, nullify, cache_panels, policy, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in lls_ooc_stats._fields_}
+
+
+def lls_ooc_simulate(panels, writes=None, num_panels: int | None = None, rows: int = 1,
+                     cols: int = 1, cache_panels: int = 1, policy: int = LLS_OOC_FARTHEST) -> dict:
+    """The planner's cache over an arbitrary panel access list (lls_ooc_simulate)."""
+    n = len(panels)
+    pa = (_I * max(n, 1))(*panels)
+    wa = (C.c_int8 * max(n, 1))(*([1 if w else 0 for w in writes] if writes is not None else []))
+    if num_panels is None:
+        num_panels = (max(panels) + 1) if n else 1
+    st = lls_ooc_stats()
+    _check(None, _lib.lls_ooc_simulate(pa, wa if writes is not None else None, n, num_panels, rows,
+                                       cols, cache_panels, policy, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in lls_ooc_stats._fields_}
 
 
 def lls_debug_guard(on: bool):
