@@ -264,8 +264,9 @@ int lls_set_workers(lls_handle h, int workers);
  * passes for q >= 1), the pass forming T(:, k:n) W_V, and the update pass
  * (right and left updates, modifying the panels); then one pass for the
  * block-SVD updates; with nullify = 1 and 0 < rank < n, per panel-aligned
- * row block of Nullify (Fig. 3) its panel and two passes over the panels of
- * T(0:r, r:n); and the solve's reads (Fig. 4).  Consecutive passes alternate
+ * row block of Nullify (Fig. 3) a read and a write pass over its own panel
+ * and the panels of T(0:r, r:n) (plus one gathering pass before the first
+ * block); and the solve's reads (Fig. 4).  Consecutive passes alternate
  * direction.  policy LLS_OOC_FARTHEST evicts the panel whose next use lies
  * latest in the future (the paper's "LFU" policy, Belady's MIN: the access
  * list is known before the solve starts), LLS_OOC_LRU the least recently
@@ -288,6 +289,48 @@ typedef struct {
 } lls_ooc_stats;
 int lls_ooc_plan(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank, int32_t nullify,
                  int64_t cache_panels, int32_t policy, lls_ooc_stats* out);
+
+/* What a planned access does (the kinds named in lls_ooc_plan's passes). */
+enum {
+  LLS_OOC_K_SAMPLE_ATG = 0,     /* step 0: Y_j = A_j^T G */
+  LLS_OOC_K_SAMPLE_AY = 1,      /* W += A_j Y_j */
+  LLS_OOC_K_SAMPLE_ATW_AY = 2,  /* Y_j = A_j^T W, then W' += A_j Y_j */
+  LLS_OOC_K_SAMPLE_ATW = 3,     /* Y_j = A_j^T W */
+  LLS_OOC_K_PRODUCT_TWV = 4,    /* P += T(:, panel) W_V(panel rows) */
+  LLS_OOC_K_UPDATE = 5,         /* right update; panel QR (panel = step) or left update;
+                                   the next step's A_j^T G */
+  LLS_OOC_K_SVD = 6,            /* the block SVDs' V_s and U_s^T updates */
+  LLS_OOC_K_NULL_GATHER = 7,    /* rows of D = T(0:r, r:n) of the first Nullify block */
+  LLS_OOC_K_NULL_READ = 8,      /* Nullify block `step`: reflectors (its own panel), P */
+  LLS_OOC_K_NULL_WRITE = 9,     /* Nullify block `step`: updates, the next block's rows */
+  LLS_OOC_K_SOLVE_UTB = 10,     /* c = U^T b with the panel's W_U */
+  LLS_OOC_K_SOLVE_TRSM = 11,    /* back substitution with the panel's columns of T_11 */
+  LLS_OOC_K_FLUSH = 12          /* final write-back of a modified panel */
+};
+
+/* One entry of an out-of-core schedule: before the access, the panel in
+ * `slot` (evict, or -1) is written back to host memory if store = 1, then
+ * `panel` is copied into `slot` if load = 1; the access (kind, for step or
+ * Nullify row block `step`) then works on the panel in `slot`, modifying it
+ * if write = 1.  FLUSH entries write back `panel` from `slot`. */
+typedef struct {
+  int32_t kind;
+  int32_t write;
+  int64_t step;
+  int64_t panel;
+  int64_t slot;
+  int64_t evict;
+  int32_t store;
+  int32_t load;
+} lls_ooc_action;
+
+/* The schedule behind lls_ooc_plan (same arguments): *count receives the
+ * number of entries; with actions not NULL they are copied there
+ * (LLS_ERR_CAPACITY, nothing copied, when max_actions is smaller).  Slots
+ * are numbered 0..min(cache_panels, panels)-1. */
+int lls_ooc_schedule(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank,
+                     int32_t nullify, int64_t cache_panels, int32_t policy,
+                     lls_ooc_action* actions, int64_t max_actions, int64_t* count);
 
 /* The cache of lls_ooc_plan run over any access list: access t touches panel
  * panels[t] (0 <= panels[t] < num_panels) and modifies it when writes[t] is

@@ -64,6 +64,12 @@ class lls_ooc_stats(C.Structure):
                 ("side_bytes", C.c_double)]
 
 
+class lls_ooc_action(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("write", C.c_int32), ("step", C.c_int64),
+                ("panel", C.c_int64), ("slot", C.c_int64), ("evict", C.c_int64),
+                ("store", C.c_int32), ("load", C.c_int32)]
+
+
 class LLSError(RuntimeError):
     def __init__(self, status: int, arg: int = 0, msg: str = ""):
         self.status, self.arg, self.msg = status, arg, msg
@@ -122,6 +128,8 @@ _sig("lls_trace_read", [_H, C.POINTER(lls_trace_stat), _I, C.POINTER(_I)])
 _sig("lls_launch_count", [], C.c_int64)
 _sig("lls_ooc_plan", [_I, _I, C.c_int32, C.c_int32, _I, C.c_int32, _I, C.c_int32,
                       C.POINTER(lls_ooc_stats)])
+_sig("lls_ooc_schedule", [_I, _I, C.c_int32, C.c_int32, _I, C.c_int32, _I, C.c_int32,
+                          C.POINTER(lls_ooc_action), _I, C.POINTER(_I)])
 _sig("lls_ooc_simulate", [C.POINTER(_I), C.POINTER(C.c_int8), _I, _I, _I, _I, _I, C.c_int32,
                           C.POINTER(lls_ooc_stats)])
 _sig("lls_alloc_count", [], C.c_int64)
@@ -364,6 +372,28 @@ def lls_ooc_plan(m: int, n: int, nb: int, q: int, rank: int, nullify: int, cache
     st = lls_ooc_stats()
     _check(None, _lib.lls_ooc_plan(m, n, nb, q, rank, nullify, cache_panels, policy, C.byref(st)))
     return {k: getattr(st, k) for k, _ in lls_ooc_stats._fields_}
+
+
+OOC_KINDS = ["sample_atg", "sample_ay", "sample_atw_ay", "sample_atw", "product_twv", "update",
+             "svd", "null_gather", "null_read", "null_write", "solve_utb", "solve_trsm", "flush"]
+
+
+def lls_ooc_schedule(m: int, n: int, nb: int, q: int, rank: int, nullify: int, cache_panels: int,
+                     policy: int = LLS_OOC_FARTHEST) -> list[dict]:
+    """The planned access list with cache slots, loads and write-backs."""
+    cnt = _I(0)
+    _check(None, _lib.lls_ooc_schedule(m, n, nb, q, rank, nullify, cache_panels, policy, None, 0,
+                                       C.byref(cnt)))
+    arr = (lls_ooc_action * max(cnt.value, 1))()
+    _check(None, _lib.lls_ooc_schedule(m, n, nb, q, rank, nullify, cache_panels, policy, arr,
+                                       cnt.value, C.byref(cnt)))
+    names = [f for f, _ in lls_ooc_action._fields_]
+    out = []
+    for a in arr[:cnt.value]:
+        d = {f: getattr(a, f) for f in names}
+        d["kind"] = OOC_KINDS[d["kind"]]
+        out.append(d)
+    return out
 
 
 def lls_ooc_simulate(panels, writes=None, num_panels: int | None = None, rows: int = 1,

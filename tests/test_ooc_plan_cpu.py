@@ -118,9 +118,11 @@ def plan_counts(m, n, nb, q, r, nullify):
         passes += 1
         accesses += P
         if nullify and 0 < r < n:
-            blocks = (r - 1) // nb + 1
-            passes += 3 * blocks
-            accesses += blocks * (1 + 2 * (P - r // nb))
+            pr, top = r // nb, (r - 1) // nb
+            passes += 1 + 2 * (top + 1)             # gather, then read + write per block
+            accesses += P - pr
+            for p in range(top + 1):                # the block's panel + D's other panels
+                accesses += 2 * (1 + P - max(pr, p + 1))
         if r > 0:
             passes += 2
             accesses += s + (r - 1) // nb + 1
