@@ -327,9 +327,14 @@ typedef struct {
 /* The schedule behind lls_ooc_plan (same arguments): *count receives the
  * number of entries; with actions not NULL they are copied there
  * (LLS_ERR_CAPACITY, nothing copied, when max_actions is smaller).  Slots
- * are numbered 0..min(cache_panels, panels)-1. */
+ * are numbered 0..min(cache_panels, panels)-1.  phase 0 is the whole solve;
+ * phase 1 the factorization (step loop and block-SVD pass, which do not
+ * depend on the rank), ending with every modified panel written back; phase
+ * 2 Nullify and the solve's reads for the given rank, starting from an empty
+ * cache -- the split lls_solve_ooc runs, since the rank is known only after
+ * phase 1.  LLS_ERR_ARG also for phase outside 0..2. */
 int lls_ooc_schedule(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank,
-                     int32_t nullify, int64_t cache_panels, int32_t policy,
+                     int32_t nullify, int64_t cache_panels, int32_t policy, int32_t phase,
                      lls_ooc_action* actions, int64_t max_actions, int64_t* count);
 
 /* The cache of lls_ooc_plan run over any access list: access t touches panel

@@ -83,8 +83,8 @@ struct PassList {
   }
 };
 
-PassList build_accesses(int64_t m, int64_t n, int64_t nb, int q, int64_t r, bool nullify) {
-  PassList pl;
+// The factorization: the step loop and the block-SVD pass.
+void add_factor_accesses(PassList& pl, int64_t m, int64_t n, int64_t nb, int q) {
   const int64_t P = (n + nb - 1) / nb;
   const int64_t steps = (std::min(m, n) + nb - 1) / nb;
   for (int64_t i = 0; i < steps; ++i) {
@@ -106,8 +106,16 @@ PassList build_accesses(int64_t m, int64_t n, int64_t nb, int q, int64_t r, bool
     }
     pl.pass(i, hi, true, true, LLS_OOC_K_UPDATE, i);  // panel i first
   }
-  if (steps == 0) return pl;  // m = 0 or n = 0: nothing is read
+  if (steps == 0) return;  // m = 0 or n = 0: nothing is read
   pl.pass(0, P - 1, !pl.forward, true, LLS_OOC_K_SVD, -1);
+}
+
+// Nullify (with rank r) and the solve's reads.
+void add_finish_accesses(PassList& pl, int64_t m, int64_t n, int64_t nb, int64_t r,
+                         bool nullify) {
+  const int64_t P = (n + nb - 1) / nb;
+  const int64_t steps = (std::min(m, n) + nb - 1) / nb;
+  if (steps == 0) return;
   if (nullify && r > 0 && r < n) {
     const int64_t pr = r / nb;         // first panel holding columns of D
     const int64_t top = (r - 1) / nb;  // panel of the last row block of C
@@ -138,6 +146,12 @@ PassList build_accesses(int64_t m, int64_t n, int64_t nb, int q, int64_t r, bool
     pl.pass(0, steps - 1, true, false, LLS_OOC_K_SOLVE_UTB, -1);
     pl.pass(0, (r - 1) / nb, false, false, LLS_OOC_K_SOLVE_TRSM, -1);
   }
+}
+
+PassList build_accesses(int64_t m, int64_t n, int64_t nb, int q, int64_t r, bool nullify) {
+  PassList pl;
+  add_factor_accesses(pl, m, n, nb, q);
+  add_finish_accesses(pl, m, n, nb, r, nullify);
   return pl;
 }
 
@@ -252,6 +266,24 @@ double side_bytes(int64_t m, int64_t n, int64_t nb, int64_t rank, bool nullify) 
 }  // namespace
 }  // namespace lls
 
+namespace lls {
+
+std::vector<lls_ooc_action> ooc_schedule_phase(int64_t m, int64_t n, int64_t nb, int q,
+                                               int64_t r, bool nullify, int64_t cache_panels,
+                                               int32_t policy, int phase) {
+  PassList pl;
+  if (phase != 2) add_factor_accesses(pl, m, n, nb, q);
+  if (phase != 1) add_finish_accesses(pl, m, n, nb, r, nullify);
+  std::vector<lls_ooc_action> acts;
+  lls_ooc_stats st{};
+  const int64_t P = (n + nb - 1) / nb;
+  simulate(pl.acc, P, m, cache_panels, policy,
+           [&](int64_t j) { return std::min<int64_t>(nb, n - j * nb); }, &st, &acts);
+  return acts;
+}
+
+}  // namespace lls
+
 extern "C" int lls_ooc_plan(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank,
                             int32_t nullify, int64_t cache_panels, int32_t policy,
                             lls_ooc_stats* out) {
@@ -269,16 +301,14 @@ extern "C" int lls_ooc_plan(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t
 
 extern "C" int lls_ooc_schedule(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank,
                                 int32_t nullify, int64_t cache_panels, int32_t policy,
-                                lls_ooc_action* actions, int64_t max_actions, int64_t* count) {
-  if (!count || max_actions < 0 || (max_actions > 0 && !actions)) return LLS_ERR_ARG;
+                                int32_t phase, lls_ooc_action* actions, int64_t max_actions,
+                                int64_t* count) {
+  if (!count || max_actions < 0 || (max_actions > 0 && !actions) || phase < 0 || phase > 2)
+    return LLS_ERR_ARG;
   int e = lls::check_plan_args(m, n, nb, q, rank, nullify, cache_panels, policy);
   if (e != LLS_OK) return e;
-  const int64_t P = (n + nb - 1) / nb;
-  lls::PassList pl = lls::build_accesses(m, n, nb, q, rank, nullify != 0);
-  std::vector<lls_ooc_action> acts;
-  lls_ooc_stats st{};
-  lls::simulate(pl.acc, P, m, cache_panels, policy,
-                [&](int64_t j) { return std::min<int64_t>(nb, n - j * nb); }, &st, &acts);
+  std::vector<lls_ooc_action> acts =
+      lls::ooc_schedule_phase(m, n, nb, q, rank, nullify != 0, cache_panels, policy, phase);
   *count = (int64_t)acts.size();
   if (!actions) return LLS_OK;
   if (max_actions < (int64_t)acts.size()) return LLS_ERR_CAPACITY;

@@ -129,7 +129,7 @@ _sig("lls_launch_count", [], C.c_int64)
 _sig("lls_ooc_plan", [_I, _I, C.c_int32, C.c_int32, _I, C.c_int32, _I, C.c_int32,
                       C.POINTER(lls_ooc_stats)])
 _sig("lls_ooc_schedule", [_I, _I, C.c_int32, C.c_int32, _I, C.c_int32, _I, C.c_int32,
-                          C.POINTER(lls_ooc_action), _I, C.POINTER(_I)])
+                          C.c_int32, C.POINTER(lls_ooc_action), _I, C.POINTER(_I)])
 _sig("lls_ooc_simulate", [C.POINTER(_I), C.POINTER(C.c_int8), _I, _I, _I, _I, _I, C.c_int32,
                           C.POINTER(lls_ooc_stats)])
 _sig("lls_alloc_count", [], C.c_int64)
@@ -379,14 +379,14 @@ OOC_KINDS = ["sample_atg", "sample_ay", "sample_atw_ay", "sample_atw", "product_
 
 
 def lls_ooc_schedule(m: int, n: int, nb: int, q: int, rank: int, nullify: int, cache_panels: int,
-                     policy: int = LLS_OOC_FARTHEST) -> list[dict]:
+                     policy: int = LLS_OOC_FARTHEST, phase: int = 0) -> list[dict]:
     """The planned access list with cache slots, loads and write-backs."""
     cnt = _I(0)
-    _check(None, _lib.lls_ooc_schedule(m, n, nb, q, rank, nullify, cache_panels, policy, None, 0,
-                                       C.byref(cnt)))
+    _check(None, _lib.lls_ooc_schedule(m, n, nb, q, rank, nullify, cache_panels, policy, phase,
+                                       None, 0, C.byref(cnt)))
     arr = (lls_ooc_action * max(cnt.value, 1))()
-    _check(None, _lib.lls_ooc_schedule(m, n, nb, q, rank, nullify, cache_panels, policy, arr,
-                                       cnt.value, C.byref(cnt)))
+    _check(None, _lib.lls_ooc_schedule(m, n, nb, q, rank, nullify, cache_panels, policy, phase,
+                                       arr, cnt.value, C.byref(cnt)))
     names = [f for f, _ in lls_ooc_action._fields_]
     out = []
     for a in arr[:cnt.value]:

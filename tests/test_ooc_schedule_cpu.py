@@ -72,12 +72,20 @@ class StreamedSolve:
         return np.concatenate(cols, axis=1)
 
     # driver -----------------------------------------------------------------
-    def run(self):
-        sched = self.lls.lls_ooc_schedule(self.m, self.n, self.nb, self.q, self.rank_for_plan,
-                                          self.nullify, self.cache, self.policy)
-        self.max_slot = max([a["slot"] for a in sched], default=-1)
+    def run(self, phases=(0,)):
+        sched = []
+        for ph in phases:
+            part = self.lls.lls_ooc_schedule(self.m, self.n, self.nb, self.q, self.rank_for_plan,
+                                             self.nullify, self.cache, self.policy, ph)
+            if ph == 1:   # ends with every modified panel written back: the cache starts empty
+                part.append({"kind": "drop"})
+            sched += part
+        self.max_slot = max([a.get("slot", -1) for a in sched], default=-1)
         self.T_after_svd = None
         for a in sched:
+            if a["kind"] == "drop":
+                self.slots, self.resident = {}, {}
+                continue
             if self.pass_key and self.pass_key[0] == "svd" and a["kind"] != "svd":
                 self.T_after_svd = self.snapshot()
             if a["evict"] >= 0 and a["kind"] != "flush":
@@ -305,9 +313,10 @@ def make_input(kind, m, n, r, seed):
     return A, 1e-3
 
 
+@pytest.mark.parametrize("phases", [(0,), (1, 2)], ids=["whole", "two-phase"])
 @pytest.mark.parametrize("kind,m,n,r,nb,q,nullify,cache,policy", CASES)
 def test_streamed_solve_follows_schedule_and_matches_oracle(lls, kind, m, n, r, nb, q, nullify,
-                                                             cache, policy):
+                                                             cache, policy, phases):
     A, tol = make_input(kind, m, n, r, seed=m + 3 * n + (r or 0))
     B = np.random.default_rng(n).standard_normal((m, 2))
     seed = 77
@@ -322,7 +331,7 @@ def test_streamed_solve_follows_schedule_and_matches_oracle(lls, kind, m, n, r, 
 
     ss = StreamedSolve(A, B, nb, q, tol, seed, nullify, cache, policy, lls)
     ss.rank_for_plan = ss.r = r
-    sched = ss.run()
+    sched = ss.run(phases)
     assert ss.rank == r and ss.rank_count == ref.rank_count
     # T after the block-SVD pass: the oracle's randUTV T
     T = np.triu(ss.T_after_svd)
@@ -332,12 +341,12 @@ def test_streamed_solve_follows_schedule_and_matches_oracle(lls, kind, m, n, r, 
     assert np.linalg.norm(T_end - ref.utv.T) <= 1e-11 * np.linalg.norm(ref.utv.T)
     x = ss.solution()
     assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
-    # the schedule's traffic is the plan's
     plan = lls.lls_ooc_plan(m, n, nb, q, r, nullify, cache, policy)
-    assert sum(a["load"] for a in sched) == plan["loads"]
-    assert sum(a["store"] for a in sched) == plan["stores"]
-    assert sum(a["kind"] != "flush" for a in sched) == plan["accesses"]
     assert ss.max_slot < min(cache, plan["panels"])
+    if phases == (0,):   # the schedule's traffic is the plan's
+        assert sum(a["load"] for a in sched) == plan["loads"]
+        assert sum(a["store"] for a in sched) == plan["stores"]
+        assert sum(a["kind"] != "flush" for a in sched) == plan["accesses"]
 
 
 def test_schedule_api_errors(lls):
@@ -345,10 +354,22 @@ def test_schedule_api_errors(lls):
 
     cnt = C.c_int64(0)
     L = lls._lib
-    assert L.lls_ooc_schedule(10, 10, 4, 1, 5, 1, 2, 0, None, 0, None) == lls.LLS_ERR_ARG
-    assert L.lls_ooc_schedule(10, 10, 4, 1, 11, 1, 2, 0, None, 0, C.byref(cnt)) == lls.LLS_ERR_ARG
-    assert L.lls_ooc_schedule(10, 10, 4, 1, 5, 1, 2, 0, None, 0, C.byref(cnt)) == lls.LLS_OK
+    assert L.lls_ooc_schedule(10, 10, 4, 1, 5, 1, 2, 0, 0, None, 0, None) == lls.LLS_ERR_ARG
+    assert L.lls_ooc_schedule(10, 10, 4, 1, 11, 1, 2, 0, 0, None, 0, C.byref(cnt)) == \
+        lls.LLS_ERR_ARG
+    assert L.lls_ooc_schedule(10, 10, 4, 1, 5, 1, 2, 0, 3, None, 0, C.byref(cnt)) == \
+        lls.LLS_ERR_ARG
+    assert L.lls_ooc_schedule(10, 10, 4, 1, 5, 1, 2, 0, 0, None, 0, C.byref(cnt)) == lls.LLS_OK
     assert cnt.value > 0
     small = (lls.lls_ooc_action * 1)()
-    assert L.lls_ooc_schedule(10, 10, 4, 1, 5, 1, 2, 0, small, 1, C.byref(cnt)) == \
+    assert L.lls_ooc_schedule(10, 10, 4, 1, 5, 1, 2, 0, 0, small, 1, C.byref(cnt)) == \
         lls.LLS_ERR_CAPACITY
+    # phase 1 ends with nothing modified left on the device
+    acts = lls.lls_ooc_schedule(60, 40, 8, 1, 20, 1, 2, 0, 1)
+    dirty = set()
+    for a in acts:
+        if a["store"]:
+            dirty.discard(a["evict"])
+        if a["kind"] != "flush" and a["write"]:
+            dirty.add(a["panel"])
+    assert not dirty
