@@ -337,6 +337,24 @@ int lls_ooc_schedule(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank,
                      int32_t nullify, int64_t cache_panels, int32_t policy, int32_t phase,
                      lls_ooc_action* actions, int64_t max_actions, int64_t* count);
 
+/* Out-of-core solve: as lls_solve_host (A m x n, B m x nrhs and X n x nrhs
+ * in HOST memory, column-major; pinned memory is not required), with A
+ * copied into a pinned host store and at most cache_panels column panels of
+ * nb columns of it on the device at any time, moved by the schedule of
+ * lls_ooc_schedule (phase 1, then phase 2 once the rank is known) under
+ * `policy`.  Device memory used: cache_panels * m * nb doubles plus
+ * O((m + n) nb + nb^2 s) for the sketch, the samples, the WY products and
+ * the per-step factors; each step's W_V and Nullify's reflector panels go to
+ * pinned host memory.  Same arithmetic as lls_solve (FP64; the handle's nb,
+ * q, nullify and seed), so x agrees with lls_solve's to rounding.  Copies
+ * and compute run in stream order on the handle's stream.
+ * Errors: those of lls_solve_host; LLS_ERR_ARG also for cache_panels < 1
+ * (index 13), an unknown policy (14), or a handle whose options ask for
+ * LLS_MIXED_BF16, explicit_v or max_refine (index 1). */
+int lls_solve_ooc(lls_handle h, const double* A, int64_t m, int64_t n, int64_t lda,
+                  const double* B, int64_t nrhs, int64_t ldb, double tol, double* X,
+                  int64_t ldx, int64_t* rank, int64_t cache_panels, int32_t policy);
+
 /* The cache of lls_ooc_plan run over any access list: access t touches panel
  * panels[t] (0 <= panels[t] < num_panels) and modifies it when writes[t] is
  * nonzero (writes may be NULL: no modification); every panel is rows x cols

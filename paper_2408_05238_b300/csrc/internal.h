@@ -71,6 +71,10 @@ Status fill_zero(int64_t m, int64_t n, double* dst, int64_t ldd, cudaStream_t st
 // dst (k x k) = upper triangle of src, zeros below.
 Status copy_upper(int64_t k, const double* src, int64_t lds, double* dst, int64_t ldd,
                   cudaStream_t st);
+// Upper triangle (diagonal included) of src (k x k) into dst; dst's strictly
+// lower part is left as it is.
+Status copy_upper_into(int64_t k, const double* src, int64_t lds, double* dst, int64_t ldd,
+                       cudaStream_t st);
 // V (n x n) = I.
 Status set_identity(int64_t n, double* V, int64_t ldv, cudaStream_t st);
 // dst (m x n) = upper trapezoid of src, zeros below the diagonal.

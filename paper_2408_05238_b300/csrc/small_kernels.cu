@@ -158,6 +158,15 @@ __global__ void cols_reversed_kernel(int64_t rows, int64_t cols, const double* _
   }
 }
 
+__global__ void upper_into_kernel(int64_t k, const double* __restrict__ src, int64_t lds,
+                                  double* __restrict__ dst, int64_t ldd) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < k * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = idx % k, j = idx / k;
+    if (i <= j) dst[i + j * ldd] = src[i + j * lds];
+  }
+}
+
 __global__ void identity_kernel(int64_t n, double* V, int64_t ldv) {
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -271,6 +280,15 @@ Status copy_upper(int64_t k, const double* src, int64_t lds, double* dst, int64_
   TraceScope ts(kTrSmall, st);
   copy_upper_kernel<<<grid_for(k * k), EW, 0, st>>>(k, src, lds, dst, ldd);
   LLS_LAUNCHED("copy_upper_kernel");
+  return ok_status();
+}
+
+Status copy_upper_into(int64_t k, const double* src, int64_t lds, double* dst, int64_t ldd,
+                       cudaStream_t st) {
+  if (k <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
+  upper_into_kernel<<<grid_for(k * k), EW, 0, st>>>(k, src, lds, dst, ldd);
+  LLS_LAUNCHED("upper_into_kernel");
   return ok_status();
 }
 

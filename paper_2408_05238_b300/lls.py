@@ -130,6 +130,7 @@ _sig("lls_ooc_plan", [_I, _I, C.c_int32, C.c_int32, _I, C.c_int32, _I, C.c_int32
                       C.POINTER(lls_ooc_stats)])
 _sig("lls_ooc_schedule", [_I, _I, C.c_int32, C.c_int32, _I, C.c_int32, _I, C.c_int32,
                           C.c_int32, C.POINTER(lls_ooc_action), _I, C.POINTER(_I)])
+_sig("lls_solve_ooc", [_H, _P, _I, _I, _I, _P, _I, _I, _D, _P, _I, C.POINTER(_I), _I, C.c_int32])
 _sig("lls_ooc_simulate", [C.POINTER(_I), C.POINTER(C.c_int8), _I, _I, _I, _I, _I, C.c_int32,
                           C.POINTER(lls_ooc_stats)])
 _sig("lls_alloc_count", [], C.c_int64)
@@ -394,6 +395,22 @@ def lls_ooc_schedule(m: int, n: int, nb: int, q: int, rank: int, nullify: int, c
         d["kind"] = OOC_KINDS[d["kind"]]
         out.append(d)
     return out
+
+
+def lls_solve_ooc(h, A, B, tol: float, cache_panels: int, policy: int = LLS_OOC_FARTHEST):
+    """Out-of-core solve of host arrays (numpy, float64): returns (X, rank, status)."""
+    import numpy as np
+
+    A = np.asfortranarray(A, dtype=np.float64)
+    B2 = np.asfortranarray(B if np.ndim(B) == 2 else np.reshape(B, (-1, 1)), dtype=np.float64)
+    m, n = A.shape
+    nrhs = B2.shape[1]
+    X = np.zeros((n, nrhs), order="F")
+    rank = _I(0)
+    code = _check(h, _lib.lls_solve_ooc(h, A.ctypes.data, m, n, max(1, m), B2.ctypes.data, nrhs,
+                                        max(1, m), float(tol), X.ctypes.data, max(1, n),
+                                        C.byref(rank), int(cache_panels), int(policy)))
+    return X, rank.value, code
 
 
 def lls_ooc_simulate(panels, writes=None, num_panels: int | None = None, rows: int = 1,
