@@ -345,7 +345,8 @@ int lls_ooc_schedule(int64_t m, int64_t n, int32_t nb, int32_t q, int64_t rank,
  * `policy`.  Device memory used: cache_panels * m * nb doubles plus
  * O((m + n) nb + nb^2 s) for the sketch, the samples, the WY products and
  * the per-step factors; each step's W_V and Nullify's reflector panels go to
- * pinned host memory.  Same arithmetic as lls_solve (FP64; the handle's nb,
+ * pinned host memory (host memory used: m n for the copy of A, n^2 for the
+ * W_V and (r / nb)(nb + n - r) nb for the reflector panels, in doubles).  Same arithmetic as lls_solve (FP64; the handle's nb,
  * q, nullify and seed), so x agrees with lls_solve's to rounding.  Copies
  * and compute run in stream order on the handle's stream.
  * Errors: those of lls_solve_host; LLS_ERR_ARG also for cache_panels < 1
