@@ -311,12 +311,14 @@ enum {
 /* One entry of an out-of-core schedule: before the access, the panel in
  * `slot` (evict, or -1) is written back to host memory if store = 1, then
  * `panel` is copied into `slot` if load = 1; the access (kind, for step or
- * Nullify row block `step`) then works on the panel in `slot`, modifying it
- * if write = 1.  FLUSH entries write back `panel` from `slot`. */
+ * Nullify row block `step`, in pass number `pass` of the schedule) then works
+ * on the panel in `slot`, modifying it if write = 1.  FLUSH entries (pass -1)
+ * write back `panel` from `slot`. */
 typedef struct {
   int32_t kind;
   int32_t write;
   int64_t step;
+  int64_t pass;
   int64_t panel;
   int64_t slot;
   int64_t evict;

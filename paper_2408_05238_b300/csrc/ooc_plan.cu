@@ -61,14 +61,17 @@ struct Access {
   bool write;
   int32_t kind = -1;  // LLS_OOC_K_*
   int64_t step = -1;  // step of Fig. 2, row block of Nullify, or -1
+  int64_t pass = -1;  // index of the pass the access belongs to
 };
 
 struct PassList {
   std::vector<Access> acc;
   int64_t passes = 0;
   bool forward = true;  // direction of the last pass added
+  // An access of the pass being built (its index is the number of passes
+  // completed so far).
   void one(int64_t j, bool write, int32_t kind, int64_t step) {
-    acc.push_back({j, write, kind, step});
+    acc.push_back({j, write, kind, step, passes});
   }
   // Visits panels [lo, hi] in the given direction as one pass.
   void pass(int64_t lo, int64_t hi, bool fwd, bool write, int32_t kind, int64_t step) {
@@ -186,7 +189,7 @@ void simulate(const std::vector<Access>& acc, int64_t P, int64_t m, int64_t cach
   double load_bytes = 0.0, store_bytes = 0.0;
   for (int64_t t = 0; t < N; ++t) {
     const int64_t j = acc[t].panel;
-    lls_ooc_action a{acc[t].kind, acc[t].write ? 1 : 0, acc[t].step, j, -1, -1, 0, 0};
+    lls_ooc_action a{acc[t].kind, acc[t].write ? 1 : 0, acc[t].step, acc[t].pass, j, -1, -1, 0, 0};
     if (slot[j] >= 0) {
       ++hits;
       order.erase({key[j], j});
@@ -222,7 +225,7 @@ void simulate(const std::vector<Access>& acc, int64_t P, int64_t m, int64_t cach
     if (slot[j] >= 0 && dirty[j]) {
       ++stores;
       store_bytes += 8.0 * (double)m * (double)width(j);
-      if (actions) actions->push_back({LLS_OOC_K_FLUSH, 0, -1, j, slot[j], j, 1, 0});
+      if (actions) actions->push_back({LLS_OOC_K_FLUSH, 0, -1, -1, j, slot[j], j, 1, 0});
     }
   }
   out->panels = P;
@@ -325,7 +328,7 @@ extern "C" int lls_ooc_simulate(const int64_t* panels, const int8_t* writes, int
   std::vector<lls::Access> acc((size_t)count);
   for (int64_t t = 0; t < count; ++t) {
     if (panels[t] < 0 || panels[t] >= num_panels) return LLS_ERR_ARG;
-    acc[(size_t)t] = {panels[t], writes ? writes[t] != 0 : false};
+    acc[(size_t)t] = {panels[t], writes ? writes[t] != 0 : false, -1, -1, -1};
   }
   lls::simulate(acc, num_panels, rows, cache_panels, policy, [&](int64_t) { return cols; }, out,
                 nullptr);

@@ -444,8 +444,7 @@ struct OocSolve {
 
   // ---- the schedule --------------------------------------------------------
   Status run(const std::vector<lls_ooc_action>& acts) {
-    int32_t last_kind = -1;
-    int64_t last_step = -2;
+    int64_t last_pass = -2;
     for (const lls_ooc_action& a : acts) {
       if (a.panel < 0 || a.panel >= P || a.slot < 0 || a.slot >= C ||
           (a.evict >= 0 && a.evict >= P))
@@ -456,9 +455,8 @@ struct OocSolve {
       }
       if (a.evict >= 0 && a.store) LLS_TRY(store(a.evict, a.slot));
       if (a.load) LLS_TRY(load(a.panel, a.slot));
-      const bool first = a.kind != last_kind || a.step != last_step;
-      last_kind = a.kind;
-      last_step = a.step;
+      const bool first = a.pass != last_pass;  // the first access of its pass
+      last_pass = a.pass;
       double* X = slot(a.slot);
       const Span xs = slot_span(a.slot);
       const int64_t j = a.panel, s = a.step;

@@ -66,7 +66,7 @@ class lls_ooc_stats(C.Structure):
 
 class lls_ooc_action(C.Structure):
     _fields_ = [("kind", C.c_int32), ("write", C.c_int32), ("step", C.c_int64),
-                ("panel", C.c_int64), ("slot", C.c_int64), ("evict", C.c_int64),
+                ("pass_", C.c_int64), ("panel", C.c_int64), ("slot", C.c_int64), ("evict", C.c_int64),
                 ("store", C.c_int32), ("load", C.c_int32)]
 
 

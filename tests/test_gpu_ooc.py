@@ -24,6 +24,7 @@ def rel(a, b):
     (150, 100, 40, 16, 1, 1, 3, FAR),     # tall; D starts inside the last block's panel
     (100, 150, 40, 16, 1, 1, 2, LRU),     # wide: a narrow last step inside its panel
     (120, 120, 48, 16, 2, 1, 4, FAR),     # r a multiple of nb; q = 2
+    (110, 90, 30, 16, 3, 1, 3, LRU),      # q = 3: two fused sampling passes in a row
     (90, 60, 60, 13, 0, 1, 2, FAR),       # full column rank: no Nullify; q = 0
     (80, 70, 25, 8, 1, 0, 3, LRU),        # the fast option
     (64, 64, 1, 8, 1, 1, 1, FAR),         # rank 1, a cache of one panel

@@ -101,7 +101,7 @@ class StreamedSolve:
                 self.slots[a["slot"]] = self.host[a["panel"]].copy()
                 self.resident[a["panel"]] = a["slot"]
             assert self.resident.get(a["panel"]) == a["slot"], "panel not in its slot"
-            key = (a["kind"], a["step"])
+            key = (a["kind"], a["pass_"])
             first = key != self.pass_key
             self.pass_key = key
             before = None if a["write"] else self.slots[a["slot"]].copy()
@@ -293,6 +293,8 @@ CASES = [  # input, m, n, r, nb, q, nullify, cache panels, policy
     ("xy", 150, 100, 40, 16, 1, 1, 3, FAR),     # tall; D starts inside the last block's panel
     ("xy", 100, 150, 40, 16, 1, 1, 2, LRU),     # wide: a narrow last step inside its panel
     ("xy", 120, 120, 48, 16, 2, 1, 4, FAR),     # r a multiple of nb; q = 2
+    ("xy", 110, 90, 30, 16, 3, 1, 3, LRU),      # q = 3: two fused sampling passes in a row
+    ("xy", 90, 110, 30, 16, 4, 1, 2, FAR),      # q = 4
     ("xy", 90, 60, 60, 13, 0, 1, 2, FAR),       # full column rank: no Nullify; q = 0
     ("xy", 80, 70, 25, 8, 1, 0, 3, LRU),        # the fast option
     ("xy", 64, 64, 1, 8, 1, 1, 1, FAR),         # rank 1, a cache of one panel
