@@ -1,0 +1,352 @@
+// Host stand-ins for the library's launchers (test infrastructure, never
+// loaded by the package).  Linked with the library's host-side orchestration
+// (solver.cu, ooc_solve.cu, ooc_plan.cu) and stand_in_runtime.cpp, they let
+// the CPU tests run the solver's and the out-of-core executor's sequence of
+// launches, pointers, leading dimensions and copies against the oracle.
+// Each stand-in is a plain loop version of what its launcher computes:
+// column-major GEMM with the unit-lower operand mode, Householder QR in the
+// LAPACK sign convention, the compact-WY T factor, one-sided Jacobi SVD,
+// copies, the Nullify gather/scatter index maps, back substitution.  The
+// sketch is a fixed deterministic hash matrix (the tests give the oracle the
+// same one).  Fresh allocations are filled with NaN so that a read of memory
+// nothing wrote shows up in the result.
+#include <algorithm>
+#include <cstdio>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "solver.h"
+#include "lls.h"
+
+namespace lls {
+std::atomic<int> g_guard_mode{0};
+std::atomic<int64_t> g_allocs{0};
+std::atomic<int64_t> g_fail_alloc_countdown{-1};
+std::atomic<int64_t> g_launches{0};
+thread_local Tracer* g_tracer = nullptr;
+Status guard_alloc(size_t, void**) { return make_error(LLS_ERR_CUDA, "no guard words in the host harness"); }
+void guard_free(void*) {}
+struct Handle::Pool {};
+Handle::Handle() = default;
+Handle::~Handle() {}
+Tracer::~Tracer() {}
+
+void effective_nb_q(const lls_options& opt, const TuneTable*, int64_t, int64_t, int* nb, int* q) {
+  *nb = opt.nb;
+  *q = opt.q;
+}
+size_t gemm_scratch_bytes(int64_t, int64_t, int64_t) { return 0; }
+size_t panel_qr_scratch_bytes(int64_t, int64_t) { return 0; }
+
+static double rd(const double* A, int64_t lda, OperandMode md, int64_t r, int64_t c) {
+  if (md == kUnitLower) return r > c ? A[r + c * lda] : (r == c ? 1.0 : 0.0);
+  return A[r + c * lda];
+}
+Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t n, int64_t k,
+            double alpha, const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+            double* C, int64_t ldc, Scratch, cudaStream_t) {
+  std::vector<double> out((size_t)(m * n), 0.0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int64_t p = 0; p < k; ++p) {
+        double a = ta ? rd(A, lda, ma, p, i) : rd(A, lda, ma, i, p);
+        double b = tb ? rd(B, ldb, mb, j, p) : rd(B, ldb, mb, p, j);
+        s += a * b;
+      }
+      out[i + j * m] = alpha * s + (beta == 0.0 ? 0.0 : beta * C[i + j * ldc]);
+    }
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) C[i + j * ldc] = out[i + j * m];
+  return ok_status();
+}
+Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch, int*,
+                cudaStream_t) {
+  const int64_t k = std::min(m, n);
+  for (int64_t j = 0; j < k; ++j) {
+    double alpha = A[j + j * lda], sig = 0.0;
+    for (int64_t i = j + 1; i < m; ++i) sig += A[i + j * lda] * A[i + j * lda];
+    sig = std::sqrt(sig);
+    if (sig == 0.0) { tau[j] = 0.0; continue; }
+    double beta = -std::copysign(std::hypot(alpha, sig), alpha);
+    double t = (beta - alpha) / beta, sc = 1.0 / (alpha - beta);
+    for (int64_t i = j + 1; i < m; ++i) A[i + j * lda] *= sc;
+    A[j + j * lda] = beta;
+    tau[j] = t;
+    for (int64_t c = j + 1; c < n; ++c) {
+      double d = A[j + c * lda];
+      for (int64_t i = j + 1; i < m; ++i) d += A[i + j * lda] * A[i + c * lda];
+      d *= t;
+      A[j + c * lda] -= d;
+      for (int64_t i = j + 1; i < m; ++i) A[i + c * lda] -= d * A[i + j * lda];
+    }
+  }
+  return ok_status();
+}
+Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, double* T,
+                  int64_t ldt, cudaStream_t) {
+  for (int64_t j = 0; j < k; ++j)
+    for (int64_t i = 0; i < k; ++i) T[i + j * ldt] = 0.0;
+  for (int64_t j = 0; j < k; ++j) {
+    T[j + j * ldt] = tau[j];
+    for (int64_t i = 0; i < j; ++i) {
+      double s = 0.0;
+      for (int64_t l = i; l < j; ++l) s += T[i + l * ldt] * S[l + j * lds];
+      T[i + j * ldt] = -tau[j] * s;
+    }
+  }
+  return ok_status();
+}
+// one-sided Jacobi SVD of a b x b block, sigma descending
+static void svd_block(int64_t b, const double* R, int64_t ldr, double* s, double* U, int64_t ldu,
+                      double* V, int64_t ldv) {
+  std::vector<double> A((size_t)(b * b)), W((size_t)(b * b), 0.0);
+  for (int64_t j = 0; j < b; ++j)
+    for (int64_t i = 0; i < b; ++i) A[i + j * b] = R[i + j * ldr];
+  for (int64_t i = 0; i < b; ++i) W[i + i * b] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rot = false;
+    for (int64_t p = 0; p < b; ++p)
+      for (int64_t q = p + 1; q < b; ++q) {
+        double a = 0, bb = 0, c = 0;
+        for (int64_t i = 0; i < b; ++i) {
+          a += A[i + p * b] * A[i + p * b];
+          bb += A[i + q * b] * A[i + q * b];
+          c += A[i + p * b] * A[i + q * b];
+        }
+        if (std::fabs(c) <= 1e-16 * std::sqrt(a * bb)) continue;
+        rot = true;
+        double z = (bb - a) / (2 * c), t = std::copysign(1.0, z) / (std::fabs(z) + std::hypot(1.0, z));
+        double cs = 1 / std::hypot(1.0, t), sn = cs * t;
+        for (int64_t i = 0; i < b; ++i) {
+          double x = A[i + p * b], y = A[i + q * b];
+          A[i + p * b] = cs * x - sn * y;
+          A[i + q * b] = sn * x + cs * y;
+          x = W[i + p * b];
+          y = W[i + q * b];
+          W[i + p * b] = cs * x - sn * y;
+          W[i + q * b] = sn * x + cs * y;
+        }
+      }
+    if (!rot) break;
+  }
+  std::vector<int64_t> ord((size_t)b);
+  std::vector<double> nrm((size_t)b);
+  for (int64_t j = 0; j < b; ++j) {
+    double s2 = 0;
+    for (int64_t i = 0; i < b; ++i) s2 += A[i + j * b] * A[i + j * b];
+    nrm[(size_t)j] = std::sqrt(s2);
+    ord[(size_t)j] = j;
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return nrm[x] > nrm[y]; });
+  for (int64_t jj = 0; jj < b; ++jj) {
+    int64_t j = ord[(size_t)jj];
+    s[jj] = nrm[(size_t)j];
+    for (int64_t i = 0; i < b; ++i) {
+      V[i + jj * ldv] = W[i + j * b];
+      U[i + jj * ldu] = nrm[(size_t)j] > 0 ? A[i + j * b] / nrm[(size_t)j] : (i == jj ? 1.0 : 0.0);
+    }
+  }
+}
+Status jacobi_svd_batched(int count, int b, int b_last, const double* R, int64_t ldr,
+                          int64_t strideR, double* sigma, int64_t strideS, double* U, int64_t ldu,
+                          int64_t strideU, double* V, int64_t ldv, int64_t strideV, int*,
+                          cudaStream_t) {
+  for (int i = 0; i < count; ++i)
+    svd_block(i == count - 1 ? b_last : b, R + i * strideR, ldr, sigma + i * strideS,
+              U + i * strideU, ldu, V + i * strideV, ldv);
+  return ok_status();
+}
+Status launch_sketch(uint64_t seed, int64_t step, int64_t rows, int64_t cols, double* G,
+                     int64_t ldg, cudaStream_t) {
+  for (int64_t j = 0; j < cols; ++j)
+    for (int64_t i = 0; i < rows; ++i) {
+      double v = std::sin(12.9898 * i + 78.233 * j + 37.719 * step + (double)(seed % 1000)) * 43758.5453;
+      G[i + j * ldg] = v - std::floor(v) - 0.5;
+    }
+  return ok_status();
+}
+Status copy_matrix(int64_t m, int64_t n, const double* s, int64_t lds, double* d, int64_t ldd,
+                   cudaStream_t) {
+  std::vector<double> t((size_t)(m * n));
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) t[i + j * m] = s[i + j * lds];
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) d[i + j * ldd] = t[i + j * m];
+  return ok_status();
+}
+Status copy_upper(int64_t k, const double* s, int64_t lds, double* d, int64_t ldd, cudaStream_t) {
+  for (int64_t j = 0; j < k; ++j)
+    for (int64_t i = 0; i < k; ++i) d[i + j * ldd] = i <= j ? s[i + j * lds] : 0.0;
+  return ok_status();
+}
+Status copy_upper_into(int64_t k, const double* s, int64_t lds, double* d, int64_t ldd,
+                       cudaStream_t) {
+  for (int64_t j = 0; j < k; ++j)
+    for (int64_t i = 0; i <= j; ++i) d[i + j * ldd] = s[i + j * lds];
+  return ok_status();
+}
+Status set_diag_block(int64_t k, const double* sigma, double* D, int64_t ldd, cudaStream_t) {
+  for (int64_t j = 0; j < k; ++j)
+    for (int64_t i = 0; i <= j; ++i) D[i + j * ldd] = i == j ? sigma[i] : 0.0;
+  return ok_status();
+}
+Status fill_zero(int64_t m, int64_t n, double* d, int64_t ldd, cudaStream_t) {
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) d[i + j * ldd] = 0.0;
+  return ok_status();
+}
+Status axpy_matrix(int64_t m, int64_t n, double a, const double* X, int64_t ldx, double* Y,
+                   int64_t ldy, cudaStream_t) {
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) Y[i + j * ldy] += a * X[i + j * ldx];
+  return ok_status();
+}
+Status copy_cols_reversed(int64_t rows, int64_t cols, const double* s, int64_t lds, double* d,
+                          int64_t ldd, cudaStream_t) {
+  for (int64_t j = 0; j < cols; ++j)
+    for (int64_t i = 0; i < rows; ++i) d[i + j * ldd] = s[i + (cols - 1 - j) * lds];
+  return ok_status();
+}
+Status copy_rows_reversed(int64_t rows, int64_t cols, const double* s, int64_t lds, double* d,
+                          int64_t ldd, cudaStream_t) {
+  for (int64_t j = 0; j < cols; ++j)
+    for (int64_t i = 0; i < rows; ++i) d[i + j * ldd] = s[(rows - 1 - i) + j * lds];
+  return ok_status();
+}
+Status rz_gather(int64_t bsz, int64_t L, const double* T, int64_t ldt, int64_t j0, int64_t r,
+                 double* M, int64_t ldm, cudaStream_t) {
+  const int64_t rows = bsz + L, j1 = j0 + bsz;
+  for (int64_t j = 0; j < bsz; ++j)
+    for (int64_t pp = 0; pp < rows; ++pp) {
+      int64_t trow = j1 - 1 - j;
+      double v;
+      if (pp < bsz) v = (pp <= j) ? T[trow + (j1 - 1 - pp) * ldt] : 0.0;
+      else v = T[trow + (r + pp - bsz) * ldt];
+      M[pp + j * ldm] = v;
+    }
+  return ok_status();
+}
+Status rz_scatter(int64_t bsz, const double* M, int64_t ldm, double* T, int64_t ldt, int64_t j0,
+                  int64_t r, int64_t L, cudaStream_t) {
+  const int64_t j1 = j0 + bsz, rows = bsz + L;
+  for (int64_t j = 0; j < bsz; ++j)
+    for (int64_t pp = 0; pp < rows; ++pp) {
+      int64_t trow = j1 - 1 - j;
+      if (pp < bsz) {
+        if (pp <= j) T[trow + (j1 - 1 - pp) * ldt] = M[pp + j * ldm];
+      } else {
+        T[trow + (r + pp - bsz) * ldt] = 0.0;
+      }
+    }
+  return ok_status();
+}
+Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double* B, int64_t ldb,
+                  cudaStream_t) {
+  for (int64_t c = 0; c < nrhs; ++c)
+    for (int64_t i = k - 1; i >= 0; --i) {
+      double y = B[i + c * ldb] / R[i + i * ldr];
+      B[i + c * ldb] = y;
+      for (int64_t l = 0; l < i; ++l) B[l + c * ldb] -= R[l + i * ldr] * y;
+    }
+  return ok_status();
+}
+}  // namespace lls
+
+extern "C" void* harness_handle(int nb, int q, int nullify, unsigned long long seed) {
+  lls::Handle* h = new lls::Handle();
+  std::memset(&h->opt, 0, sizeof(h->opt));
+  h->opt.precision = LLS_FP64;
+  h->opt.nb = nb;
+  h->opt.q = q;
+  h->opt.nullify = nullify;
+  h->opt.seed = seed;
+  h->stream = nullptr;
+  return h;
+}
+
+namespace lls {
+cudaEvent_t Tracer::get() { return nullptr; }
+Status copy_check(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
+                  int* flag, cudaStream_t) {
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) {
+      double v = src[i + j * lds];
+      if (!std::isfinite(v)) *flag = 1;
+      if (dst) dst[i + j * ldd] = v;
+    }
+  return ok_status();
+}
+size_t oz_gemm_workspace_bytes(int64_t, int64_t, int64_t) { return 0; }
+Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t n, int64_t k,
+               double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double beta, double* C, int64_t ldc, bool, Scratch s, int*, cudaStream_t st) {
+  return gemm(ta, tb, ma, mb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s, st);
+}
+Status sample_bf16(Handle&, const double*, int64_t, int64_t, int64_t, int64_t, int, uint64_t,
+                   int64_t, double*, int64_t) {
+  return make_error(LLS_ERR_ARG, "no mixed precision in the host harness");
+}
+Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, cudaStream_t) {
+  *tol_dev = tol >= 0.0 ? tol : (double)mn * 2.220446049250313e-16 * std::fabs(*T00);
+  return ok_status();
+}
+Status rank_scan_dev(int64_t len, const double* T, int64_t ldt, const double* tol_dev,
+                     int64_t* out, cudaStream_t) {
+  int64_t first = len, cnt = 0, nan = 0;
+  for (int64_t j = 0; j < len; ++j) {
+    double d = std::fabs(T[j + j * ldt]);
+    bool nz = d > *tol_dev;
+    cnt += nz;
+    nan |= std::isnan(d);
+    if (!nz && j < first) first = j;
+  }
+  out[0] = first;
+  out[1] = cnt;
+  out[2] = nan;
+  return ok_status();
+}
+Status refine_update(int64_t n, int64_t nrhs, const double* D, int64_t ldd, double* X, int64_t ldx,
+                     double* norms, cudaStream_t) {
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double sd = 0, sx = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      X[i + c * ldx] += D[i + c * ldd];
+      sd += D[i + c * ldd] * D[i + c * ldd];
+      sx += X[i + c * ldx] * X[i + c * ldx];
+    }
+    norms[2 * c] = sd;
+    norms[2 * c + 1] = sx;
+  }
+  return ok_status();
+}
+Status set_identity(int64_t n, double* V, int64_t ldv, cudaStream_t) {
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) V[i + j * ldv] = i == j ? 1.0 : 0.0;
+  return ok_status();
+}
+size_t trsm_upper_scratch_bytes(int64_t, int64_t) { return 0; }
+Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B, int64_t ldb,
+                  Scratch, cudaStream_t st) {
+  return trsm_block(r, nrhs, R, ldr, B, ldb, st);
+}
+}  // namespace lls
+
+extern "C" int harness_solve(void* hh, const double* A, int64_t m, int64_t n, int64_t lda,
+                           const double* B, int64_t nrhs, int64_t ldb, double tol, double* X,
+                           int64_t ldx, int64_t* rank, int explicit_v, int max_refine) {
+  lls::Handle& h = *(lls::Handle*)hh;
+  h.opt.explicit_v = explicit_v;
+  h.opt.max_refine = max_refine;
+  h.opt.refine_tol = 1e-12;
+  lls::Factor f;
+  lls::Status s = lls::factorize(h, f, A, m, n, lda, tol, max_refine > 0);
+  if (!s.ok()) return s.code;
+  *rank = f.rank;
+  lls::Status ss = lls::solve_refined(h, f, nullptr, 0, B, nrhs, ldb, X, ldx);
+  if (!ss.ok()) return ss.code;
+  return s.code != 0 ? s.code : ss.code;
+}
