@@ -1,7 +1,8 @@
 """Builds the host harness (test infrastructure): the library's host-side
-orchestration -- solver.cu, ooc_solve.cu, ooc_plan.cu, compiled as they are
--- linked with plain-loop stand-ins for its launchers (stand_ins.cu) and for
-the CUDA runtime (stand_in_runtime.cpp) into _build/harness.so, which the CPU
+code -- the C ABI, the worker pool, the solver's orchestration, the tuner,
+tracing, guard words and the out-of-core executor, compiled as they are --
+linked with plain-loop stand-ins for its launchers (stand_ins.cu) and for the
+CUDA runtime (stand_in_runtime.cpp) into _build/harness.so, which the CPU
 tests load.  Needs nvcc (it cross-compiles; no GPU is used) and g++."""
 
 from __future__ import annotations
@@ -17,7 +18,8 @@ OUT = os.path.join(HERE, "_build")
 SO = os.path.join(OUT, "harness.so")
 CUDA_INC = "/usr/local/cuda/include"
 
-PRODUCT = ["solver.cu", "ooc_solve.cu", "ooc_plan.cu"]
+PRODUCT = ["api.cu", "serving.cu", "solver.cu", "tuner.cu", "trace.cu", "guard.cu", "ooc_solve.cu",
+           "ooc_plan.cu"]
 
 
 def _newer(target: str, deps: list[str]) -> bool:

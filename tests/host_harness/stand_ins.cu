@@ -22,22 +22,7 @@
 #include "lls.h"
 
 namespace lls {
-std::atomic<int> g_guard_mode{0};
-std::atomic<int64_t> g_allocs{0};
-std::atomic<int64_t> g_fail_alloc_countdown{-1};
-std::atomic<int64_t> g_launches{0};
-thread_local Tracer* g_tracer = nullptr;
-Status guard_alloc(size_t, void**) { return make_error(LLS_ERR_CUDA, "no guard words in the host harness"); }
-void guard_free(void*) {}
-struct Handle::Pool {};
-Handle::Handle() = default;
-Handle::~Handle() {}
-Tracer::~Tracer() {}
 
-void effective_nb_q(const lls_options& opt, const TuneTable*, int64_t, int64_t, int* nb, int* q) {
-  *nb = opt.nb;
-  *q = opt.q;
-}
 size_t gemm_scratch_bytes(int64_t, int64_t, int64_t) { return 0; }
 size_t panel_qr_scratch_bytes(int64_t, int64_t) { return 0; }
 
@@ -256,20 +241,7 @@ Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double*
 }
 }  // namespace lls
 
-extern "C" void* harness_handle(int nb, int q, int nullify, unsigned long long seed) {
-  lls::Handle* h = new lls::Handle();
-  std::memset(&h->opt, 0, sizeof(h->opt));
-  h->opt.precision = LLS_FP64;
-  h->opt.nb = nb;
-  h->opt.q = q;
-  h->opt.nullify = nullify;
-  h->opt.seed = seed;
-  h->stream = nullptr;
-  return h;
-}
-
 namespace lls {
-cudaEvent_t Tracer::get() { return nullptr; }
 Status copy_check(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
                   int* flag, cudaStream_t) {
   for (int64_t j = 0; j < n; ++j)
@@ -323,6 +295,12 @@ Status refine_update(int64_t n, int64_t nrhs, const double* D, int64_t ldd, doub
   }
   return ok_status();
 }
+Status copy_upper_trapezoid(int64_t m, int64_t n, const double* s, int64_t lds, double* d,
+                            int64_t ldd, cudaStream_t) {
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) d[i + j * ldd] = i <= j ? s[i + j * lds] : 0.0;
+  return ok_status();
+}
 Status set_identity(int64_t n, double* V, int64_t ldv, cudaStream_t) {
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < n; ++i) V[i + j * ldv] = i == j ? 1.0 : 0.0;
@@ -335,18 +313,3 @@ Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double*
 }
 }  // namespace lls
 
-extern "C" int harness_solve(void* hh, const double* A, int64_t m, int64_t n, int64_t lda,
-                           const double* B, int64_t nrhs, int64_t ldb, double tol, double* X,
-                           int64_t ldx, int64_t* rank, int explicit_v, int max_refine) {
-  lls::Handle& h = *(lls::Handle*)hh;
-  h.opt.explicit_v = explicit_v;
-  h.opt.max_refine = max_refine;
-  h.opt.refine_tol = 1e-12;
-  lls::Factor f;
-  lls::Status s = lls::factorize(h, f, A, m, n, lda, tol, max_refine > 0);
-  if (!s.ok()) return s.code;
-  *rank = f.rank;
-  lls::Status ss = lls::solve_refined(h, f, nullptr, 0, B, nrhs, ldb, X, ldx);
-  if (!ss.ok()) return ss.code;
-  return s.code != 0 ? s.code : ss.code;
-}

@@ -1,17 +1,20 @@
-"""The solver's host-side orchestration, run on the CPU.
+"""The library's host-side code, run on the CPU through its public C API.
 
-tests/host_harness links the library's own solver.cu, ooc_solve.cu and
-ooc_plan.cu with plain-loop stand-ins for the launchers and the CUDA runtime,
-so the exact sequence of launches, operand pointers, leading dimensions,
-operand modes, buffer reservations and copies of a solve runs here without a
-GPU.  The oracle gets the harness's deterministic sketch, and over random
-shapes (tall, wide, narrow last steps, nb = 1 and nb > n, rank 0 to full),
-q = 0..4, with and without Nullify, explicit V and refinement, and for the
-out-of-core executor caches of one panel to all of them under both eviction
-policies, the rank must equal the oracle's and x must agree to 1e-8.  Where
-the fast option's x is itself ill-determined (the oracle's fast x is far
-from the pseudoinverse solution: T_12 not small), the least-squares property
-is checked instead.  The GPU kernels themselves are checked by the gpu tests.
+tests/host_harness links the library's own api.cu, serving.cu, solver.cu,
+tuner.cu, trace.cu, guard.cu, ooc_solve.cu and ooc_plan.cu, compiled as they
+are, with plain-loop stand-ins for the launchers and the CUDA runtime, so the
+exact sequence of launches, operand pointers, leading dimensions, operand
+modes, buffer reservations and copies of a solve -- and the worker pool, the
+serving queue, the tuning table, guard words and argument checks -- run here
+without a GPU ("device" memory is host memory).  The oracle gets the
+harness's deterministic sketch.  Over random shapes (tall, wide, narrow last
+steps, nb = 1 and nb > n, rank 0 to full), q = 0..4, with and without
+Nullify, explicit V and refinement, and for the out-of-core executor caches
+of one panel to all of them under both eviction policies, the rank must equal
+the oracle's and x must agree to 1e-8; where the fast option's x is itself
+ill-determined (the oracle's fast x is far from the pseudoinverse solution:
+T_12 not small) the least-squares property is checked instead.  The GPU
+kernels themselves are checked by the gpu tests.
 """
 
 import ctypes as C
@@ -31,18 +34,55 @@ def harness():
     import importlib.util
     import os
 
+    from paper_2408_05238_b300 import lls as binding
+
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "host_harness", "build.py")
     spec = importlib.util.spec_from_file_location("host_harness_build", path)
     hb = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(hb)
     lib = C.CDLL(hb.build())
-    lib.harness_handle.restype = C.c_void_p
-    lib.harness_handle.argtypes = [C.c_int, C.c_int, C.c_int, C.c_ulonglong]
-    lib.harness_solve.argtypes = [C.c_void_p, C.c_void_p, I, I, I, C.c_void_p, I, I, C.c_double,
-                                  C.c_void_p, I, C.POINTER(I), C.c_int, C.c_int]
-    lib.lls_solve_ooc.argtypes = [C.c_void_p, C.c_void_p, I, I, I, C.c_void_p, I, I, C.c_double,
-                                  C.c_void_p, I, C.POINTER(I), I, C.c_int32]
+    H, P, D = C.c_void_p, C.c_void_p, C.c_double
+    sigs = {
+        "lls_create": [C.POINTER(H), C.POINTER(binding.lls_options), P],
+        "lls_destroy": [H],
+        "lls_solve": [H, P, I, I, I, P, I, I, D, P, I, C.POINTER(I)],
+        "lls_factor": [H, P, I, I, I, D, C.POINTER(I), C.POINTER(I)],
+        "lls_solve_factored": [H, I, P, I, I, P, I],
+        "lls_factor_get": [H, I, C.c_int32, P, I],
+        "lls_factor_release": [H, I],
+        "lls_refinement_info": [H, C.POINTER(C.c_int32), C.POINTER(D)],
+        "lls_solve_batched": [H, I, C.POINTER(binding.lls_problem)],
+        "lls_set_workers": [H, C.c_int],
+        "lls_set_memory_cap": [H, I],
+        "lls_submit": [H, C.POINTER(binding.lls_problem), C.POINTER(I)],
+        "lls_poll": [H, I, C.POINTER(C.c_int)],
+        "lls_autotune": [H, I, I, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+        "lls_tuning_lookup": [H, I, I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+        "lls_tuning_save": [H, C.c_char_p],
+        "lls_tuning_load": [H, C.c_char_p],
+        "lls_last_error": [H, C.POINTER(C.c_int), C.c_char_p, I],
+        "lls_debug_guard": [C.c_int],
+        "lls_debug_guard_report": [C.c_char_p, I],
+        "lls_debug_guard_selftest": [],
+        "lls_solve_ooc": [H, P, I, I, I, P, I, I, D, P, I, C.POINTER(I), I, C.c_int32],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int64 if name == "lls_debug_guard_report" else C.c_int
+    lib.binding = binding
     return lib
+
+
+def create(lib, **kw):
+    o = lib.binding.lls_default_options(**kw)
+    h = C.c_void_p()
+    assert lib.lls_create(C.byref(h), C.byref(o), None) == 0
+    return h
+
+
+def F(x):
+    return np.asfortranarray(np.asarray(x, dtype=np.float64))
 
 
 def hashed_sketch(seed, step, rows, cols):
@@ -104,17 +144,20 @@ def run_case(harness, c, ooc):
     m, n = A.shape
     B = np.random.default_rng(c["it"]).standard_normal((m, 2))
     ref = orc.solve(A, B, c["q"], c["nb"], tol, 77, do_nullify=bool(c["nullify"]))
-    h = harness.harness_handle(c["nb"], c["q"], c["nullify"], 77)
-    Af, Bf = np.asfortranarray(A), np.asfortranarray(B)
-    X = np.zeros((n, 2), order="F")
-    rk = I(0)
-    if ooc:
-        code = harness.lls_solve_ooc(h, Af.ctypes.data, m, n, m, Bf.ctypes.data, 2, m, tol,
-                                     X.ctypes.data, n, C.byref(rk), c["cache"], c["policy"])
-    else:
-        code = harness.harness_solve(h, Af.ctypes.data, m, n, m, Bf.ctypes.data, 2, m, tol,
-                                     X.ctypes.data, n, C.byref(rk), c["explicit_v"],
-                                     c["max_refine"])
+    h = create(harness, nb=c["nb"], q=c["q"], nullify=c["nullify"], seed=77,
+               explicit_v=c["explicit_v"], max_refine=c["max_refine"])
+    try:
+        Af, Bf = F(A), F(B)
+        X = np.zeros((n, 2), order="F")
+        rk = I(0)
+        if ooc:
+            code = harness.lls_solve_ooc(h, Af.ctypes.data, m, n, m, Bf.ctypes.data, 2, m, tol,
+                                         X.ctypes.data, n, C.byref(rk), c["cache"], c["policy"])
+        else:
+            code = harness.lls_solve(h, Af.ctypes.data, m, n, m, Bf.ctypes.data, 2, m, tol,
+                                     X.ctypes.data, n, C.byref(rk))
+    finally:
+        harness.lls_destroy(h)
     check(A, B, X, code, rk.value, ref, c["nullify"])
 
 
@@ -128,3 +171,176 @@ def test_in_core_orchestration_random(harness, sketch, chunk):
 def test_out_of_core_executor_random(harness, sketch, chunk):
     for c in random_configs(200 + chunk, 25, ooc=True):
         run_case(harness, c, ooc=True)
+
+
+# ---- the public C API on the harness ------------------------------------------
+def gap_problem(m, n, r, seed, nrhs=2):
+    A, X, Y = wl.lowrank_xy(m, n, r, seed=seed, noise=1e-14)
+    B = np.random.default_rng(seed).standard_normal((m, nrhs))
+    return A, B, 1e-10 * wl.norm2_of_product(X, Y)
+
+
+def test_factor_reuse_export_and_refinement(harness, sketch):
+    """lls_factor keeps A for refinement and V for export: solves with the
+    resident factor match the oracle, V^T V = I, (A V)^T (A V) = T^T T and
+    T(0:r, r:n) = 0 after Nullify."""
+    m, n, r = 50, 40, 17
+    A, B, tol = gap_problem(m, n, r, seed=3)
+    ref = orc.solve(A, B, 1, 8, tol, 77)
+    h = create(harness, nb=8, q=1, seed=77, explicit_v=1, max_refine=2)
+    try:
+        Af, Bf = F(A), F(B)
+        fid, rk = I(0), I(0)
+        assert harness.lls_factor(h, Af.ctypes.data, m, n, m, tol, C.byref(fid), C.byref(rk)) == 0
+        assert rk.value == r
+        X = np.zeros((n, 2), order="F")
+        assert harness.lls_solve_factored(h, fid.value, Bf.ctypes.data, 2, m, X.ctypes.data, n) == 0
+        steps, corr = C.c_int32(0), C.c_double(0)
+        harness.lls_refinement_info(h, C.byref(steps), C.byref(corr))
+        assert steps.value >= 1 and corr.value <= 1e-12
+        T = np.zeros((m, n), order="F")
+        V = np.zeros((n, n), order="F")
+        assert harness.lls_factor_get(h, fid.value, 0, T.ctypes.data, m) == 0
+        assert harness.lls_factor_get(h, fid.value, 1, V.ctypes.data, n) == 0
+        assert harness.lls_factor_release(h, fid.value) == 0
+    finally:
+        harness.lls_destroy(h)
+    assert np.linalg.norm(X - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    assert np.linalg.norm(V.T @ V - np.eye(n)) <= 1e-13 * n
+    AV = A @ V
+    assert np.linalg.norm(AV.T @ AV - T.T @ T) <= 1e-12 * np.linalg.norm(A) ** 2
+    assert np.all(T[:r, r:] == 0.0) and np.all(np.tril(T, -1) == 0.0)
+
+
+def test_batched_pool_equals_alone(harness, sketch):
+    """Problems solved by the worker pool (three host threads) are
+    bit-identical to the same problems solved alone, and match the oracle."""
+    probs = [gap_problem(m, n, r, seed=s) for (m, n, r, s) in
+             [(40, 30, 10, 1), (30, 45, 12, 2), (50, 50, 20, 3), (25, 12, 12, 4), (33, 33, 5, 5)]]
+    h = create(harness, nb=8, q=1, seed=77)
+    try:
+        alone = []
+        for A, B, tol in probs:
+            m, n = A.shape
+            X = np.zeros((n, 2), order="F")
+            rk = I(0)
+            assert harness.lls_solve(h, F(A).ctypes.data, m, n, m, F(B).ctypes.data, 2, m, tol,
+                                     X.ctypes.data, n, C.byref(rk)) == 0
+            alone.append(X)
+        assert harness.lls_set_workers(h, 3) == 0
+        keep, arr = [], (harness.binding.lls_problem * len(probs))()
+        for i, (A, B, tol) in enumerate(probs):
+            m, n = A.shape
+            Af, Bf, X = F(A), F(B), np.zeros((n, 2), order="F")
+            keep += [Af, Bf, X]
+            p = arr[i]
+            p.A, p.m, p.n, p.lda = Af.ctypes.data, m, n, m
+            p.B, p.nrhs, p.ldb = Bf.ctypes.data, 2, m
+            p.tol, p.X, p.ldx = tol, X.ctypes.data, n
+            p.factor_id, p.keep_factor = -1, 0
+        assert harness.lls_solve_batched(h, len(probs), arr) >= 0
+    finally:
+        harness.lls_destroy(h)
+    for i, (A, B, tol) in enumerate(probs):
+        assert arr[i].status == 0
+        np.testing.assert_array_equal(keep[3 * i + 2], alone[i])
+        ref = orc.solve(A, B, 1, 8, tol, 77)
+        assert np.linalg.norm(alone[i] - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+def test_serving_queue_memory_cap_and_factor_reuse(harness, sketch):
+    """Submitted requests complete with the oracle's result; a request larger
+    than the memory cap is refused at submission; a kept factor serves a later
+    request with new right-hand sides."""
+    A, B, tol = gap_problem(40, 30, 9, seed=7)
+    B2 = np.random.default_rng(8).standard_normal((40, 2))
+    h = create(harness, nb=8, q=1, seed=77)
+    try:
+        assert harness.lls_set_workers(h, 2) == 0
+        Af, Bf, B2f = F(A), F(B), F(B2)
+        X1, X2 = np.zeros((30, 2), order="F"), np.zeros((30, 2), order="F")
+        p = harness.binding.lls_problem()
+        p.A, p.m, p.n, p.lda, p.B, p.nrhs, p.ldb = Af.ctypes.data, 40, 30, 40, Bf.ctypes.data, 2, 40
+        p.tol, p.X, p.ldx, p.factor_id, p.keep_factor = tol, X1.ctypes.data, 30, -1, 1
+        t = I(0)
+        assert harness.lls_submit(h, C.byref(p), C.byref(t)) == 0
+        st = C.c_int(1)
+        while st.value == 1:
+            assert harness.lls_poll(h, t.value, C.byref(st)) >= 0 or st.value < 0
+        assert st.value == 0
+        assert harness.lls_set_memory_cap(h, 1000) == 0          # far below any request
+        assert harness.lls_submit(h, C.byref(p), C.byref(t)) == harness.binding.LLS_ERR_CAPACITY
+    finally:
+        harness.lls_destroy(h)
+    ref1 = orc.solve(A, B, 1, 8, tol, 77)
+    assert np.linalg.norm(X1 - ref1.x) <= 1e-9 * np.linalg.norm(ref1.x)
+
+
+def test_tuning_table_roundtrip(harness, sketch, tmp_path):
+    """lls_autotune fills the bucket of (m, n); the table written by
+    lls_tuning_save is read back by another handle; a malformed file is
+    refused with nothing merged."""
+    h = create(harness, nb=0, q=1, seed=77)
+    h2 = create(harness, nb=0, q=1, seed=77)
+    try:
+        nb, q = C.c_int32(0), C.c_int32(0)
+        assert harness.lls_autotune(h, 60, 40, 1, C.byref(nb), C.byref(q)) == 0
+        assert nb.value in (32, 64) and q.value in (0, 1, 2)
+        path = str(tmp_path / "table.txt").encode()
+        assert harness.lls_tuning_save(h, path) == 0
+        assert harness.lls_tuning_load(h2, path) == 0
+        nb2, q2 = C.c_int32(0), C.c_int32(0)
+        assert harness.lls_tuning_lookup(h2, 60, 40, C.byref(nb2), C.byref(q2)) == 0
+        assert (nb2.value, q2.value) == (nb.value, q.value)
+        bad = tmp_path / "bad.txt"
+        bad.write_text("9 9 16 2\nnot a line\n")
+        assert harness.lls_tuning_load(h2, str(bad).encode()) == harness.binding.LLS_ERR_ARG
+        nb3, q3 = C.c_int32(0), C.c_int32(0)
+        assert harness.lls_tuning_lookup(h2, 300, 300, C.byref(nb3), C.byref(q3)) == 0
+        assert (nb3.value, q3.value) == (64, 1)      # bucket (9, 9) not merged: the default
+        # (60, 40) and (33, 33) share the bucket (ceil log2 m, ceil log2 n) = (6, 6)
+        assert harness.lls_tuning_lookup(h2, 33, 33, C.byref(nb3), C.byref(q3)) == 0
+        assert (nb3.value, q3.value) == (nb.value, q.value)
+    finally:
+        harness.lls_destroy(h)
+        harness.lls_destroy(h2)
+
+
+def test_guard_words_on_host_memory(harness, sketch):
+    """The guard-word machinery detects writes just past either end of a
+    buffer, and a guarded solve leaves every guard intact."""
+    assert harness.lls_debug_guard_selftest() == 0
+    A, B, tol = gap_problem(45, 35, 11, seed=9)
+    assert harness.lls_debug_guard(1) == 0
+    try:
+        h = create(harness, nb=8, q=1, seed=77, explicit_v=1)
+        try:
+            X = np.zeros((35, 2), order="F")
+            rk = I(0)
+            assert harness.lls_solve(h, F(A).ctypes.data, 45, 35, 45, F(B).ctypes.data, 2, 45, tol,
+                                     X.ctypes.data, 35, C.byref(rk)) == 0
+        finally:
+            harness.lls_destroy(h)
+        msg = C.create_string_buffer(256)
+        assert harness.lls_debug_guard_report(msg, 256) == 0, msg.value
+    finally:
+        harness.lls_debug_guard(0)
+
+
+@pytest.mark.parametrize("bad,index", [("m", 3), ("lda", 5), ("ldb", 8), ("ldx", 11), ("tol", 9)])
+def test_argument_errors_name_their_argument(harness, bad, index):
+    h = create(harness, nb=8, q=1)
+    try:
+        A, B = F(np.ones((10, 6))), F(np.ones((10, 1)))
+        X = np.zeros((6, 1), order="F")
+        args = dict(m=10, lda=10, ldb=10, ldx=6, tol=1e-8)
+        args[bad] = {"m": -1, "lda": 9, "ldb": 9, "ldx": 5, "tol": float("nan")}[bad]
+        rk = I(0)
+        code = harness.lls_solve(h, A.ctypes.data, args["m"], 6, args["lda"], B.ctypes.data, 1,
+                                 args["ldb"], args["tol"], X.ctypes.data, args["ldx"], C.byref(rk))
+        assert code == harness.binding.LLS_ERR_ARG
+        arg = C.c_int(0)
+        harness.lls_last_error(h, C.byref(arg), None, 0)
+        assert arg.value == index
+    finally:
+        harness.lls_destroy(h)
