@@ -17,8 +17,9 @@ def test_randutv_flops_closed_form():
     assert pm.randutv_flops(m, n, nb, q) == pytest.approx((10 + 4 * q) * S + right_extra - left_fix)
 
 
-def test_c2_flops_match_survey_estimate():
-    """16384^2, nb = 128, q = 2: about 29.3 TFLOP for the factorization."""
+def test_c2_flops_match_closed_form_estimate():
+    """16384^2, nb = 128, q = 2: (10 + 4q) S + 2n^3/3 with S ~ mn^2/2 - n^3/6 gives
+    about 29.3 TFLOP for the factorization."""
     f = pm.randutv_flops(16384, 16384, 128, 2)
     assert 29.0e12 < f < 29.6e12
 
@@ -35,8 +36,8 @@ def test_steps_cover_min_dimension():
         assert sum(b for _, b in ks) == min(m, n)
 
 
-def test_c3_flops_match_survey_estimate():
-    """32768 x 16384, nb = 128, q = 1: about 54.2 TFLOP for the factorization."""
+def test_c3_flops_match_closed_form_estimate():
+    """32768 x 16384, nb = 128, q = 1: the same closed form gives about 54.2 TFLOP."""
     f = pm.randutv_flops(32768, 16384, 128, 1)
     assert 53.7e12 < f < 54.7e12
 
