@@ -258,9 +258,23 @@ Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int6
                double beta, double* C, int64_t ldc, bool, Scratch s, int*, cudaStream_t st) {
   return gemm(ta, tb, ma, mb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s, st);
 }
-Status sample_bf16(Handle&, const double*, int64_t, int64_t, int64_t, int64_t, int, uint64_t,
-                   int64_t, double*, int64_t) {
-  return make_error(LLS_ERR_ARG, "no mixed precision in the host harness");
+// The mixed-precision sample, in FP64 here (the BF16 products are a kernel
+// matter): Y = (A^T A)^q A^T G with the harness's sketch, so the mixed path's
+// orchestration around it runs with exact products.
+Status sample_bf16(Handle&, const double* A, int64_t lda, int64_t mp, int64_t np, int64_t b, int q,
+                   uint64_t seed, int64_t step, double* Y, int64_t ldy) {
+  std::vector<double> G((size_t)std::max<int64_t>(mp * b, 1)), W((size_t)std::max<int64_t>(mp * b, 1));
+  LLS_TRY(launch_sketch(seed, step, mp, b, G.data(), std::max<int64_t>(mp, 1), nullptr));
+  const int64_t ldg = std::max<int64_t>(mp, 1);
+  LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, A, lda, G.data(), ldg, 0.0, Y, ldy,
+               Scratch{}, nullptr));
+  for (int it = 0; it < q; ++it) {
+    LLS_TRY(gemm(false, false, kDense, kDense, mp, b, np, 1.0, A, lda, Y, ldy, 0.0, W.data(), ldg,
+                 Scratch{}, nullptr));
+    LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, A, lda, W.data(), ldg, 0.0, Y, ldy,
+                 Scratch{}, nullptr));
+  }
+  return ok_status();
 }
 Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, cudaStream_t) {
   *tol_dev = tol >= 0.0 ? tol : (double)mn * 2.220446049250313e-16 * std::fabs(*T00);

@@ -8,8 +8,10 @@ modes, buffer reservations and copies of a solve -- and the worker pool, the
 serving queue, the tuning table, guard words and argument checks -- run here
 without a GPU ("device" memory is host memory).  The oracle gets the
 harness's deterministic sketch.  Over random shapes (tall, wide, narrow last
-steps, nb = 1 and nb > n, rank 0 to full), q = 0..4, with and without
-Nullify, explicit V and refinement, and for the out-of-core executor caches
+steps, nb = 1 and nb > n, rank 0 to full), q = 0..4, both precision modes
+(the mixed mode's products are exact here: its orchestration is what is
+checked), with and without Nullify, explicit V and refinement, and for the
+out-of-core executor caches
 of one panel to all of them under both eviction policies, the rank must equal
 the oracle's and x must agree to 1e-8; where the fast option's x is itself
 ill-determined (the oracle's fast x is far from the pseudoinverse solution:
@@ -134,6 +136,7 @@ def random_configs(seed, count, ooc):
         r = g.randint(0, min(m, n))
         P = -(-n // nb)
         yield dict(it=it, kind=kind, m=m, n=n, r=r, nb=nb, q=q, nullify=g.randint(0, 1),
+                   precision=0 if ooc else g.randint(0, 1),
                    explicit_v=0 if ooc else g.randint(0, 1),
                    max_refine=0 if ooc else g.choice([0, 0, 1, 2]),
                    cache=g.randint(1, P + 1), policy=g.randint(0, 1))
@@ -145,7 +148,7 @@ def run_case(harness, c, ooc):
     B = np.random.default_rng(c["it"]).standard_normal((m, 2))
     ref = orc.solve(A, B, c["q"], c["nb"], tol, 77, do_nullify=bool(c["nullify"]))
     h = create(harness, nb=c["nb"], q=c["q"], nullify=c["nullify"], seed=77,
-               explicit_v=c["explicit_v"], max_refine=c["max_refine"])
+               precision=c["precision"], explicit_v=c["explicit_v"], max_refine=c["max_refine"])
     try:
         Af, Bf = F(A), F(B)
         X = np.zeros((n, 2), order="F")
