@@ -347,3 +347,41 @@ def test_argument_errors_name_their_argument(harness, bad, index):
         assert arg.value == index
     finally:
         harness.lls_destroy(h)
+
+
+def test_host_entry_point_and_phase_trace(harness, sketch):
+    """lls_solve_host (host buffers, copies inside) gives lls_solve's x, and
+    the per-phase trace counts one sample, QR of Y, right update, panel and
+    left update per step (left update: every step with columns to its right),
+    one block-SVD phase, one rank phase, one Nullify and one solve."""
+    binding = harness.binding
+    harness.lls_solve_host.argtypes = harness.lls_solve.argtypes
+    harness.lls_solve_host.restype = C.c_int
+    harness.lls_trace_enable.argtypes = [C.c_void_p, C.c_int]
+    harness.lls_trace_read.argtypes = [C.c_void_p, C.POINTER(binding.lls_trace_stat), I,
+                                       C.POINTER(I)]
+    m, n, r, nb = 50, 44, 15, 8
+    A, B, tol = gap_problem(m, n, r, seed=12)
+    h = create(harness, nb=nb, q=1, seed=77)
+    try:
+        X1, X2 = np.zeros((n, 2), order="F"), np.zeros((n, 2), order="F")
+        rk = I(0)
+        assert harness.lls_solve(h, F(A).ctypes.data, m, n, m, F(B).ctypes.data, 2, m, tol,
+                                 X1.ctypes.data, n, C.byref(rk)) == 0
+        assert harness.lls_trace_enable(h, 1) == 0
+        assert harness.lls_solve_host(h, F(A).ctypes.data, m, n, m, F(B).ctypes.data, 2, m, tol,
+                                      X2.ctypes.data, n, C.byref(rk)) == 0
+        stats = (binding.lls_trace_stat * 64)()
+        cnt = I(0)
+        assert harness.lls_trace_read(h, stats, 64, C.byref(cnt)) == 0
+        phases = {s.name.decode(): s.launches for s in stats[:cnt.value]
+                  if s.name.decode().startswith("phase:")}
+    finally:
+        harness.lls_destroy(h)
+    np.testing.assert_array_equal(X1, X2)
+    steps = -(-min(m, n) // nb)
+    assert phases["phase:sample"] == phases["phase:qr_y"] == steps
+    assert phases["phase:right_update"] == phases["phase:panel"] == steps
+    assert phases["phase:left_update"] == steps
+    assert phases["phase:block_svd"] == phases["phase:rank"] == 1
+    assert phases["phase:nullify"] == 1 and phases["phase:solve"] == 1
