@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     p.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-mixed", action="store_true",
+                   help="fp64 runs: skip the mixed-precision arm timed beside it")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -386,6 +388,7 @@ def run_serving(a):
         k = int(g.integers(1, 65))
         reqs.append((j, reuse, k))
     held, tickets, t_sub, t_done, flops = {}, {}, {}, {}, 0.0
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))).__enter__()
     t0 = time.perf_counter()
     i = 0
     pending = set()
@@ -418,6 +421,7 @@ def run_serving(a):
                 pending.discard(q)
                 held.pop(q)
         time.sleep(0.0005)
+    clk.__exit__(None, None, None)
     wall = max(t_done.values())
     lat = np.array([t_done[q] - t_sub[q] for q in range(nreq)])
     lls.lls_destroy(h)
@@ -431,7 +435,8 @@ def run_serving(a):
                                   + ("nb, q autotuned per (m, n) bucket" if a.autotune else "nb=64, q=1"),
                       "workers": a.workers, "precision": a.precision, "tuning": tuning},
            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-           "solves_per_s": nreq / wall, "offered_per_s": a.rate, "tflops": flops / wall / 1e12}
+           "solves_per_s": nreq / wall, "offered_per_s": a.rate, "tflops": flops / wall / 1e12,
+           "clocks": clk.summary()}
     print(json.dumps(out))
     return 0
 
@@ -452,6 +457,110 @@ def replica_throughput(flops_per_solve, steps, world, seconds):
     """Whole-job figures of N independent replicas: (solves, TFLOP/s)."""
     total = steps * world
     return total, flops_per_solve * total / seconds / 1e12
+
+
+PRECISIONS = {"fp64": "LLS_FP64", "mixed": "LLS_MIXED_BF16"}
+DTYPES = {"fp64": "f64", "mixed": "bf16+f64"}
+# DRAM bytes per algorithmic byte of a kernel family, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over the family's launches
+# in one solve of a 4096-order case of the same construction, divided by the
+# algorithmic bytes the library's trace assigns to those launches; None
+# until captured for the kernel as it stands).  Full-size captures are
+# limited to one-pass metrics, so the bench line scales this ratio by the
+# algorithmic bytes of its own launches.
+TRAFFIC_PER_ALG_BYTE = {"dgemm_kernel": None, "oz_mma_kernel": None}
+
+
+def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, local):
+    """K timed solves of one precision mode on the resident inputs: value,
+    accuracy against the construction's pseudoinverse, roofline of the
+    dominant kernel, traces and the clocks seen during the timed region."""
+    import torch
+
+    m, n, _, tol = dense_shape(a)
+    X = lls.empty_colmajor(n, a.nrhs)
+    h = lls.lls_create(nb=a.nb, q=a.q, seed=2002, precision=getattr(lls, PRECISIONS[precision]))
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        lls.lls_solve(h, A, B, tol, X)
+    torch.cuda.synchronize()
+
+    lls.lls_trace_enable(h, True)
+    launches0 = lls.lls_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ranks = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("lls_timed")   # lets a profiler select the timed solves
+        ev0.record(stream)
+        for _ in range(steps):
+            _, rk, _ = lls.lls_solve(h, A, B, tol, X)
+            ranks.append(rk)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    launches = lls.lls_launch_count() - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    trace = lls.lls_trace_read(h)
+    lls.lls_trace_enable(h, False)
+    clocks = clk.summary()
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
+    world = dist.get_world_size() if dist else 1
+    flops = pm.lls_flops(m, n, a.nb, a.q, ranks[-1], a.nrhs)
+    total_solves, value = replica_throughput(flops, steps, world, elapsed)
+
+    # accuracy of the timed result against the construction's pseudoinverse
+    rr = ranks[-1]
+    Xp = Q2[:, :rr] @ ((Q1[:, :rr].t() @ B) / sigma[:rr, None])
+    x_err = float(torch.linalg.norm(X - Xp) / torch.linalg.norm(Xp))
+    res = A.t() @ (B - A @ X)
+    ner = max(float(torch.linalg.norm(res[:, j]) /
+                    (torch.linalg.norm(X[:, j]) + torch.linalg.norm(B[:, j])))
+              for j in range(a.nrhs))       # ||A||_2 = 1 for this construction
+    del Xp, res
+
+    # roofline of the dominant kernel: the FP64 DFMA GEMM (bound by the FP64
+    # pipe) on the FP64 path; the exact-slice GEMM (bound by the BF16 tensor
+    # pipe: 36 BF16 digit-plane products per FP64 multiply-add) on the mixed path
+    sm_max = clocks.get("sm_max_mhz") or 2032.0
+    if precision == "mixed":
+        kname = "oz_mma_kernel"
+        g = trace.get(kname, (0, 0.0, 0.0, 0.0))
+        achieved = 36.0 * g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
+        peak = MEASURED_PEAKS.get("bf16_tflops_sustained") or 1400.0
+        bound, psrc = "tensor", ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, "
+                                 "seconds-long loop)" if MEASURED_PEAKS else "fallback 1.4 PFLOP/s")
+    else:
+        kname = "dgemm_kernel"
+        g = trace.get(kname, (0, 0.0, 0.0, 0.0))
+        achieved = g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
+        peak = FP64_FLOPS_PER_CLK_PER_SM * NUM_SM * sm_max * 1e6 / 1e12
+        bound, psrc = "alu", "derived: 2 DFMA/clk/SM x 148 SMs x max SM clock"
+    ratio = TRAFFIC_PER_ALG_BYTE.get(kname)
+    traffic = ratio * g[3] / g[0] if (ratio and g[0]) else None
+    # kernel families and phases of the method are two views of the same time:
+    # shares are taken within each view
+    fam = {k: v for k, v in trace.items() if not k.startswith("phase:")}
+    phs = {k[len("phase:"):]: v for k, v in trace.items() if k.startswith("phase:")}
+    traced = sum(v[1] for v in fam.values()) or 1.0
+    shares = {k: {"launches": v[0], "seconds": round(v[1], 4), "share": round(v[1] / traced, 4)}
+              for k, v in fam.items()}
+    phase_shares = {k: {"count": v[0], "seconds": round(v[1], 4),
+                        "share": round(v[1] / elapsed if elapsed else 0.0, 4)}
+                    for k, v in phs.items()}
+    return {"h": h, "X": X, "flops": flops, "rank": ranks[-1], "elapsed": elapsed,
+            "value": value, "solves_per_s": total_solves / elapsed,
+            "ms_per_step": 1e3 * elapsed / steps, "launches": launches, "clocks": clocks,
+            "accuracy": {"x_rel_err_vs_pinv": x_err, "normal_eq_residual": ner},
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak else None, "traffic": traffic,
+                         "kernel": kname, "peak_source": psrc,
+                         "launches": g[0], "avg_launch_ms": 1e3 * g[1] / max(g[0], 1),
+                         "alg_bytes_per_launch": g[3] / max(g[0], 1)},
+            "trace": shares, "phases": phase_shares}
 
 
 def main():
@@ -484,78 +593,9 @@ def main():
 
     A, B, Q1, Q2, sigma, r = make_inputs(a, "cuda")
     m, n, _, tol = dense_shape(a)
-    X = lls.empty_colmajor(n, a.nrhs)
-    prec = lls.LLS_MIXED_BF16 if a.precision == "mixed" else lls.LLS_FP64
-    h = lls.lls_create(nb=a.nb, q=a.q, seed=2002, precision=prec)
-    stream = torch.cuda.current_stream()
-
-    for _ in range(a.warmup):
-        lls.lls_solve(h, A, B, tol, X)
-    torch.cuda.synchronize()
-
-    lls.lls_trace_enable(h, True)
-    launches0 = lls.lls_launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ranks = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        torch.cuda.nvtx.range_push("lls_timed")   # lets a profiler select the timed solves
-        ev0.record(stream)
-        for _ in range(a.steps):
-            _, rk, _ = lls.lls_solve(h, A, B, tol, X)
-            ranks.append(rk)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-    launches = lls.lls_launch_count() - launches0
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    trace = lls.lls_trace_read(h)
-    lls.lls_trace_enable(h, False)
-    clocks = clk.summary()
-    elapsed = max_over_ranks(elapsed, dist, "cuda")
-    flops = pm.lls_flops(m, n, a.nb, a.q, ranks[-1], a.nrhs)
-    total_solves, value = replica_throughput(flops, a.steps, world, elapsed)
-
-    # accuracy of the timed result against the construction's pseudoinverse
-    rr = ranks[-1]
-    Xp = Q2[:, :rr] @ ((Q1[:, :rr].t() @ B) / sigma[:rr, None])
-    x_err = float(torch.linalg.norm(X - Xp) / torch.linalg.norm(Xp))
-    res = A.t() @ (B - A @ X)
-    ner = max(float(torch.linalg.norm(res[:, j]) /
-                    (torch.linalg.norm(X[:, j]) + torch.linalg.norm(B[:, j])))
-              for j in range(a.nrhs))       # ||A||_2 = 1 for this construction
-    del Q1, Q2, Xp, res
-
-    # roofline of the dominant kernel: the FP64 DFMA GEMM (bound by the FP64
-    # pipe) on the FP64 path; the exact-slice GEMM (bound by the BF16 tensor
-    # pipe: 36 BF16 digit-plane products per FP64 multiply-add) on the mixed path
-    sm_max = clocks.get("sm_max_mhz") or 2032.0
-    if a.precision == "mixed":
-        kname = "oz_mma_kernel"
-        g = trace.get(kname, (0, 0.0, 0.0, 0.0))
-        achieved = 36.0 * g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
-        peak = MEASURED_PEAKS.get("bf16_tflops_sustained") or 1400.0
-        bound, psrc = "tensor", ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, "
-                                 "seconds-long loop)" if MEASURED_PEAKS else "fallback 1.4 PFLOP/s")
-    else:
-        kname = "dgemm_kernel"
-        g = trace.get(kname, (0, 0.0, 0.0, 0.0))
-        achieved = g[2] / g[1] / 1e12 if g[1] > 0 else 0.0
-        peak = FP64_FLOPS_PER_CLK_PER_SM * NUM_SM * sm_max * 1e6 / 1e12
-        bound, psrc = "alu", "derived: 2 DFMA/clk/SM x 148 SMs x max SM clock"
-    # kernel families and phases of the method are two views of the same time:
-    # shares are taken within each view
-    fam = {k: v for k, v in trace.items() if not k.startswith("phase:")}
-    phs = {k[len("phase:"):]: v for k, v in trace.items() if k.startswith("phase:")}
-    traced = sum(v[1] for v in fam.values()) or 1.0
-    shares = {k: {"launches": v[0], "seconds": round(v[1], 4), "share": round(v[1] / traced, 4)}
-              for k, v in fam.items()}
-    phase_shares = {k: {"count": v[0], "seconds": round(v[1], 4),
-                        "share": round(v[1] / elapsed if elapsed else 0.0, 4)}
-                    for k, v in phs.items()}
+    main_arm = time_dense(a, lls, pm, a.precision, A, B, Q1, Q2, sigma, a.steps, a.warmup, dist,
+                          local)
+    h, flops = main_arm["h"], main_arm["flops"]
 
     e2e = None
     if not a.no_e2e:
@@ -573,6 +613,24 @@ def main():
                "h2d_bytes_per_step": 8 * (m * n + m * a.nrhs), "d2h_bytes_per_step": 8 * n * a.nrhs,
                "seconds_per_step": dt, "api": "lls_solve_host (pinned host buffers)"}
         del A_h, B_h, X_h
+    lls.lls_destroy(h)
+    del main_arm["h"], main_arm["X"]
+
+    # the same workload in the other precision modes, timed the same way
+    # (same K and W), reported beside the headline arm
+    others = {}
+    if a.precision == "fp64" and not a.no_mixed:
+        for prec in ("mixed",):
+            arm = time_dense(a, lls, pm, prec, A, B, Q1, Q2, sigma, a.steps, a.warmup, dist, local)
+            lls.lls_destroy(arm.pop("h"))
+            del arm["X"]
+            others[prec] = {"value": arm["value"], "unit": "TFLOP/s", "dtype": DTYPES[prec],
+                            "ms_per_step": arm["ms_per_step"], "steps": a.steps, "warmup": a.warmup,
+                            "solves_per_s": arm["solves_per_s"], "rank": arm["rank"],
+                            "accuracy": arm["accuracy"], "roofline": arm["roofline"],
+                            "clocks": arm["clocks"], "gpu_launches": arm["launches"],
+                            "phases": arm["phases"], "trace": arm["trace"]}
+    del Q1, Q2
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -580,26 +638,23 @@ def main():
         cpu = cpu_baseline(a, A_host, flops)
         del A_host
 
-    lls.lls_destroy(h)
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * elapsed / a.steps,
+            "metric": METRIC, "value": main_arm["value"], "unit": "TFLOP/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": main_arm["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if a.precision == "fp64" else "bf16+f64", "data": "synthetic",
+            "dtype": DTYPES[a.precision], "data": "synthetic",
             "config": {"workload": workload_name(a), "m": m, "n": n, "nrhs": a.nrhs, "nb": a.nb,
-                       "q": a.q, "rank": ranks[-1], "precision": a.precision,
+                       "q": a.q, "rank": main_arm["rank"], "precision": a.precision,
                        "l2": f"inputs larger than L2 (A = {8 * m * n / 1e9:.1f} GB), no flush",
                        "parallelism": f"replicas x{world}"},
-            "solves_per_s": total_solves / elapsed,
-            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if peak else None, "traffic": None,
-                         "kernel": kname, "peak_source": psrc,
-                         "launches": g[0], "avg_launch_ms": 1e3 * g[1] / max(g[0], 1)},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "accuracy": {"x_rel_err_vs_pinv": x_err, "normal_eq_residual": ner},
-            "trace": shares, "phases": phase_shares,
+            "solves_per_s": main_arm["solves_per_s"],
+            "roofline": main_arm["roofline"],
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main_arm["launches"],
+            "clocks": main_arm["clocks"], "accuracy": main_arm["accuracy"],
+            "trace": main_arm["trace"], "phases": main_arm["phases"],
         }
+        out.update(others)
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()

@@ -77,9 +77,10 @@ typedef struct {
   int32_t nullify;     /* 1: run Nullify (minimum-norm x, Fig. 3) [1];
                           0: fast option (Remark after Fig. 4, Eq. (7)): a
                           least-squares x whose excess norm is of the size
-                          of T_12; with LLS_MIXED_BF16 the BF16 sample fixes
-                          V_1 only to BF16 accuracy, so that excess is of
-                          order 1e-4..1e-2 relative (Nullify removes it) */
+                          of T_12, only with precision LLS_FP64 (LLS_ERR_ARG,
+                          index 2, otherwise: a BF16 sample fixes V_1 only to
+                          BF16 accuracy, so T_12 and the excess norm would be
+                          of order 1e-4..1e-2 relative) */
   uint64_t seed;       /* key of the Gaussian sketch generator [2001] */
   int32_t explicit_v;  /* 1: accumulate V (n x n) during the factorization
                           (V <- V (I - W_V T_V W_V^T), V_01 <- V_01 V_SVD,
@@ -406,6 +407,15 @@ int64_t lls_alloc_count(void);
  * after = -1 turns the injection off.  Allocations inside the lls_k_* step
  * entry points are not covered. */
 int lls_debug_fail_allocation(int64_t after);
+
+/* Testing hook (failure detection without a GPU fault): a CTA of the
+ * cooperative panel kernels waiting at their grid barrier gives up after
+ * `polls` polls (default about 4 million, a few seconds) instead of
+ * hanging; the kernel then exits and the call that launched it returns
+ * LLS_ERR_TIMEOUT.  polls = 0 makes every wait that does not pass at once
+ * run out; polls < 0 restores the default.  Applies to kernels launched
+ * after the call, by every handle. */
+int lls_debug_barrier_limit(int64_t polls);
 
 /* Debug mode (guard words; for tests on small shapes).  With on = 1, every
  * device buffer the library allocates from then on (solver workspace,

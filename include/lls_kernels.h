@@ -105,17 +105,17 @@ int lls_k_gemm_oz(int transa, int transb, int unit_lower_a, int unit_lower_b,
  * can synchronize the device.  The paper has no counterpart; this is a
  * library convenience.
  *
- * The kernel's scratch (grid-barrier words and per-CTA partial sums) lives
- * in one fixed array of the library (under 520 KB, held by every GPU that
- * loads the library until the process exits), so this call allocates
- * nothing.  n may be at most 128; larger n returns LLS_ERR_CAPACITY and
+ * The kernel's scratch (the grid barrier's arrival counter and per-CTA
+ * partial sums) lives in one fixed array of the library (528,512 bytes,
+ * about 516 KiB, held by every GPU that loads the library until the process
+ * exits), so this call allocates nothing.  n may be at most 128; larger n returns LLS_ERR_CAPACITY and
  * launches nothing.  status is a caller-owned device int: it is set to 0 and
  * becomes nonzero if a grid barrier of the kernel timed out (then A and tau
  * are not valid).  The call only enqueues work on `stream`; it does not
  * synchronize.  The first call on each device looks up the array's device
  * address (once, with that device current), so make that first call before
  * any stream capture.  All calls share the one array, which keeps the last
- * call's contents (the barrier words are cleared by each call): calls that
+ * call's contents (the barrier counter is cleared by each call): calls that
  * overlap on the GPU -- on different streams, or from several threads --
  * race on it, so issue them one after another. */
 int lls_k_panel_qr_noalloc(int64_t m, int64_t n, double* A, int64_t lda, double* tau,

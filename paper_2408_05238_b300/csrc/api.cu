@@ -33,6 +33,12 @@ Status check_options(const lls_options& o) {
   if (o.precision != LLS_FP64 && o.precision != LLS_MIXED_BF16)
     return arg_error(2, "unknown precision mode");
   if (o.nullify != 0 && o.nullify != 1) return arg_error(2, "nullify must be 0 or 1");
+  // The fast option keeps T_12.  Its x is the minimum-norm one only when the
+  // sample resolves range(V_1) to FP64 accuracy (T_12 at rounding level, the
+  // Remark after Fig. 4); a BF16 sample leaves T_12 of BF16 size.
+  if (o.nullify == 0 && o.precision != LLS_FP64)
+    return arg_error(2, "the fast option (nullify = 0) needs precision LLS_FP64: a BF16 sample "
+                        "leaves T_12 of BF16 size, so x would not be the minimum-norm solution");
   if (o.explicit_v != 0 && o.explicit_v != 1) return arg_error(2, "explicit_v must be 0 or 1");
   if (o.max_refine < 0 || o.max_refine > 16) return arg_error(2, "max_refine must be in 0..16");
   if (!(o.refine_tol >= 0.0) || o.refine_tol == INFINITY)
@@ -339,6 +345,11 @@ int lls_last_error(lls_handle hh, int* arg_index, char* msg, int64_t len) {
 namespace lls {
 std::atomic<int64_t> g_fail_alloc_countdown{-1};
 }  // namespace lls
+
+extern "C" int lls_debug_barrier_limit(int64_t polls) {
+  lls::g_barrier_spin_limit.store(polls < 0 ? lls::kBarrierSpinLimit : (long long)polls);
+  return LLS_OK;
+}
 
 extern "C" int lls_debug_fail_allocation(int64_t after) {
   if (after < -1) return LLS_ERR_ARG;

@@ -68,9 +68,13 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // ---------------------------------------------------------------------------
 constexpr long long kBarrierSpinLimit = 1LL << 22;  // a few seconds of polling at most
 
+// limit: polls a waiting CTA makes before it gives up; launchers take it
+// from g_barrier_spin_limit (kBarrierSpinLimit unless a test lowered it
+// through lls_debug_barrier_limit).
 struct GridBarrier {
   unsigned int* count;
   int* err;
+  long long limit = kBarrierSpinLimit;
 };
 
 __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
@@ -85,7 +89,7 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 // CTA counts its own barriers in `epoch` (a variable of the calling kernel,
 // starting at 0), so thread 0 arrives with a fire-and-forget release add and
 // waits, with acquire loads, until the counter reaches (epoch + 1) x CTAs.
-// The wait is bounded (kBarrierSpinLimit polls); on expiry, or when another
+// The wait is bounded (bar.limit polls); on expiry, or when another
 // CTA has already failed, it sets *err and every thread of the CTA gets false.
 __device__ inline bool grid_sync(const GridBarrier& bar, unsigned int& epoch) {
   __syncthreads();
@@ -101,7 +105,7 @@ __device__ inline bool grid_sync(const GridBarrier& bar, unsigned int& epoch) {
       unsigned int cur;
       asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar.count) : "memory");
       if ((int)(cur - target) >= 0) break;
-      if (++it > kBarrierSpinLimit || ((it & 255) == 0 && ld_volatile_i32(bar.err) != 0)) {
+      if (++it > bar.limit || ((it & 255) == 0 && ld_volatile_i32(bar.err) != 0)) {
         atomicExch(bar.err, 1);
         s_fail = 1;
         break;

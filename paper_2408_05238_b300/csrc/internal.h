@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace lls {
@@ -46,6 +48,17 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
             cudaStream_t st);
 
 // panel_qr.cu ----------------------------------------------------------------
+// Most CTAs a cooperative panel kernel uses.
+constexpr int kPanelMaxCtas = 256;
+// Scratch of the cooperative panel kernels with G CTAs and n columns: the
+// grid-barrier arrival counter (first 64 bytes), then the partial sums of
+// the larger of the two kernels' layouts (global-memory kernel: one norm
+// per CTA, one dot per CTA and column, one reduced dot per column;
+// shared-memory kernel: two buffers of one value per CTA and column, two
+// copies of one row, two of the column totals).
+constexpr size_t panel_qr_scratch_layout_bytes(int64_t G, int64_t n) {
+  return 64 + sizeof(double) * (size_t)std::max(G + G * n + n, 2 * G * n + 2 * n + 2 * (n + 4));
+}
 size_t panel_qr_scratch_bytes(int64_t m, int64_t n);
 // Householder QR of the m x n panel in place; tau[min(m,n)]; err (device
 // int) is raised if a grid barrier timed out.

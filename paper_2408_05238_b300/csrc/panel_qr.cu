@@ -33,7 +33,7 @@ namespace lls {
 namespace {
 
 constexpr int PQ_THREADS = 256;
-constexpr int PQ_MAX_CTAS = 256;
+constexpr int PQ_MAX_CTAS = kPanelMaxCtas;
 
 struct PanelArgs {
   int64_t m, n, lda, rows_per;
@@ -669,10 +669,7 @@ ClusterPlan cluster_plan(int64_t m, int64_t n) {
 }  // namespace
 
 size_t panel_qr_scratch_bytes(int64_t m, int64_t n) {
-  int G = panel_ctas(m);
-  size_t global_kernel = (size_t)G + (size_t)G * n + (size_t)n;
-  size_t slab_kernel = 2 * (size_t)G * n + 2 * (size_t)n + 2 * ((size_t)n + 4);
-  return 64 + sizeof(double) * std::max(global_kernel, slab_kernel);
+  return panel_qr_scratch_layout_bytes(panel_ctas(m), n);
 }
 
 Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
@@ -708,6 +705,7 @@ Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scrat
   GridBarrier bar;
   bar.count = reinterpret_cast<unsigned int*>(base);
   bar.err = err;
+  bar.limit = g_barrier_spin_limit.load(std::memory_order_relaxed);
   double* work = reinterpret_cast<double*>(base + 64);
   const int64_t k = std::min(m, n);
   TraceScope ts(kTrPanelQR, st, 2.0 * m * n * k - 2.0 * k * k * k / 3.0, 16.0 * m * n);

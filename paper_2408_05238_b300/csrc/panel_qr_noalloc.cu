@@ -2,12 +2,14 @@
 // fixed device array owned by the library, for callers that must not
 // allocate device memory (see include/lls_kernels.h).
 //
-// Scratch use of the panel kernels: one grid-barrier word, one barrier-error
-// word, and partial sums -- for the shared-memory kernel two buffers of one
-// value per CTA and column, two copies of one row and two of the column
+// Scratch of the cooperative panel kernels: the grid-barrier arrival
+// counter and the partial sums (for the shared-memory kernel two buffers of
+// one value per CTA and column, two copies of one row and two of the column
 // totals; for the global-memory kernel one norm per CTA, one dot product per
-// CTA and column and one reduced dot per column.  With at most 256 CTAs and
-// 128 columns that is under 520 KB; the array below holds it.
+// CTA and column and one reduced dot per column).  A barrier time-out is
+// reported in the caller's status word, not in the array.  The array is
+// sized by panel_qr.cu's own layout for its largest grid (kPanelMaxCtas
+// CTAs) and 128 columns: 528,512 bytes (about 516 KiB).
 #include <mutex>
 
 #include "internal.h"
@@ -16,7 +18,8 @@
 namespace {
 
 constexpr int64_t kNoAllocMaxCols = 128;
-constexpr size_t kNoAllocBytes = 64 + sizeof(double) * (2 * 256 * 128 + 4 * 128 + 8);
+constexpr size_t kNoAllocBytes = lls::panel_qr_scratch_layout_bytes(lls::kPanelMaxCtas, kNoAllocMaxCols);
+static_assert(kNoAllocBytes == 528512, "documented size of the fixed scratch array");
 
 // Every device that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_panel_scratch[kNoAllocBytes];

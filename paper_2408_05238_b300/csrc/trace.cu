@@ -9,6 +9,7 @@ namespace lls {
 thread_local Tracer* g_tracer = nullptr;
 std::atomic<int64_t> g_launches{0};
 std::atomic<int64_t> g_allocs{0};
+std::atomic<long long> g_barrier_spin_limit{kBarrierSpinLimit};
 
 const char* trace_kind_name(int k) {
   static const char* names[kTrCount] = {"dgemm_kernel",      "splitk_reduce_kernel",

@@ -64,6 +64,9 @@ extern thread_local Tracer* g_tracer;
 extern std::atomic<int64_t> g_launches;
 // Device allocations made by DevBuf (lls_alloc_count).
 extern std::atomic<int64_t> g_allocs;
+// Poll limit of the grid barrier of the cooperative panel kernels
+// (kBarrierSpinLimit; lls_debug_barrier_limit lowers it for tests).
+extern std::atomic<long long> g_barrier_spin_limit;
 
 // Records a start event in the constructor and a stop event in the
 // destructor when a tracer is active.

@@ -114,6 +114,7 @@ _sig("lls_ticket_factor", [_H, _I, C.POINTER(_I)])
 _sig("lls_set_workers", [_H, C.c_int])
 _sig("lls_cancel", [_H, _I])
 _sig("lls_debug_fail_allocation", [_I])
+_sig("lls_debug_barrier_limit", [_I])
 _sig("lls_debug_guard", [C.c_int])
 _sig("lls_debug_guard_report", [C.c_char_p, _I], C.c_int64)
 _sig("lls_debug_guard_selftest", [])
@@ -425,6 +426,11 @@ def lls_ooc_simulate(panels, writes=None, num_panels: int | None = None, rows: i
     _check(None, _lib.lls_ooc_simulate(pa, wa if writes is not None else None, n, num_panels, rows,
                                        cols, cache_panels, policy, C.byref(st)))
     return {k: getattr(st, k) for k, _ in lls_ooc_stats._fields_}
+
+
+def lls_debug_barrier_limit(polls: int):
+    """Grid-barrier poll limit of the cooperative panel kernels (< 0: default)."""
+    _kcheck(_lib.lls_debug_barrier_limit(int(polls)))
 
 
 def lls_debug_guard(on: bool):

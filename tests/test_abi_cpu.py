@@ -84,6 +84,19 @@ def test_bad_options_rejected_before_any_cuda_call(lib, field, value):
     assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
 
 
+def test_fast_option_with_a_bf16_sample_is_refused(lib):
+    """nullify = 0 keeps T_12, which a BF16 sample leaves at BF16 size: the
+    fast option is accepted with the FP64 sample only (argument 2)."""
+    h = C.c_void_p()
+    bad = lib.lls_default_options(nullify=0, precision=lib.LLS_MIXED_BF16)
+    assert lib._lib.lls_create(C.byref(h), C.byref(bad), None) == lib.LLS_ERR_ARG
+
+
+def test_barrier_limit_hook_accepts_and_restores(lib):
+    assert lib._lib.lls_debug_barrier_limit(0) == lib.LLS_OK
+    assert lib._lib.lls_debug_barrier_limit(-1) == lib.LLS_OK
+
+
 def test_new_entry_points_reject_null_handle(lib):
     assert lib._lib.lls_factor_get(None, 0, 0, None, 1) == lib.LLS_ERR_ARG
     assert lib._lib.lls_refinement_info(None, None, None) == lib.LLS_ERR_ARG

@@ -83,7 +83,11 @@ def test_gemm_unit_lower_operands(lls, ta):
 
 
 # -------------------------------------------------------------- a3/a5 panel QR
-@pytest.mark.parametrize("m,n", [(2000, 64), (129, 7), (300, 128), (16384, 128), (8, 12), (5000, 1)])
+# (2000, 64), (300, 128), (129, 7): one thread-block cluster; (16384, 128): the
+# cooperative shared-memory (slab) kernel; (40000, 128): slabs too tall for
+# shared memory, the cooperative global-memory kernel
+@pytest.mark.parametrize("m,n", [(2000, 64), (129, 7), (300, 128), (16384, 128), (40000, 128),
+                                 (8, 12), (5000, 1)])
 def test_panel_qr_matches_oracle(lls, m, n):
     Y = np.random.default_rng(m + n).standard_normal((m, n))
     A, tau, T = lls.lls_k_geqrf(dev(Y))

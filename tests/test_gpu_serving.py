@@ -256,3 +256,39 @@ def test_injected_allocation_failure_is_reported_and_recovered(lls):
         finally:
             lls.lls_debug_fail_allocation(-1)
             lls.lls_destroy(h)
+
+
+@pytest.mark.slow
+def test_batched_on_the_full_size_distribution(lls):
+    """128 problems of the batched workload's own size distribution (m in
+    [256, 2048], n in [128, m], rank in [n/4, n], nrhs in {1, 8, 32}) in one
+    lls_solve_batched call on 8 workers: every rank equals the construction's
+    and a random subset matches the oracle's solve."""
+    ps = wl.batched_problems(128, seed=1004)
+    h = lls.lls_create(nb=64, q=1, seed=2004)
+    lls.lls_set_workers(h, 8)
+    try:
+        keep, plist, ranks = [], [], []
+        for p in ps:
+            A, B = dev(p.A), dev(p.B)
+            X = lls.empty_colmajor(p.A.shape[1], p.B.shape[1])
+            r = C.c_int64(-1)
+            ranks.append(r)
+            keep.append((A, B, X))
+            plist.append(lls.make_problem(A, B, p.tol, X, rank_out=C.pointer(r)))
+        code = lls.lls_solve_batched(h, plist)
+        torch.cuda.synchronize()
+        assert code == 0
+    finally:
+        lls.lls_destroy(h)
+    assert [pl.status for pl in plist] == [0] * len(ps)
+    assert [r.value for r in ranks] == [p.rank for p in ps]
+    pick = np.random.default_rng(0).choice([i for i, p in enumerate(ps) if p.A.shape[0] <= 1200],
+                                           size=4, replace=False)
+    for i in pick:
+        p = ps[i]
+        ref = orc.solve(p.A, p.B, 1, 64, p.tol, 2004)
+        x = keep[i][2].cpu().numpy()
+        assert ref.rank == p.rank
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-9
+        assert orc.normal_equation_residual(p.A, x, p.B, p.norm2) <= 1e-13

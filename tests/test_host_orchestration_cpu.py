@@ -135,8 +135,10 @@ def random_configs(seed, count, ooc):
             q, nb = 0, min(nb, 12)
         r = g.randint(0, min(m, n))
         P = -(-n // nb)
-        yield dict(it=it, kind=kind, m=m, n=n, r=r, nb=nb, q=q, nullify=g.randint(0, 1),
-                   precision=0 if ooc else g.randint(0, 1),
+        nullify = g.randint(0, 1)
+        precision = 0 if ooc else g.randint(0, 1)
+        yield dict(it=it, kind=kind, m=m, n=n, r=r, nb=nb, q=q, nullify=nullify,
+                   precision=precision if nullify else 0,   # the fast option is FP64-only
                    explicit_v=0 if ooc else g.randint(0, 1),
                    max_refine=0 if ooc else g.choice([0, 0, 1, 2]),
                    cache=g.randint(1, P + 1), policy=g.randint(0, 1))

@@ -362,6 +362,36 @@ def test_refine_leaves_nullspace_components():
 
 
 # -------------------------------------------------------------------- properties
+def test_normal_equation_residual_closed_forms():
+    """The normalisation of the normal-equation residual (reading c15),
+    ||A^T (b - A x)|| / (||A||_2 (||A||_2 ||x|| + ||b||)) per column, max over
+    columns, pinned by values worked out by hand on A = [[3, 0], [0, 1], [0, 0]]
+    (||A||_2 = 3):
+      column 0: x = (1, 2), b = (1, 1, 5): A x = (3, 2, 0), b - A x = (-2, -1, 5),
+                A^T (b - A x) = (-6, -1), norm sqrt(37); ||x|| = sqrt(5),
+                ||b|| = 3 sqrt(3)  ->  sqrt(37) / (9 (sqrt(5) + sqrt(3))) = 0.170323...
+      column 1: x = 0, b = (0, 4, 0): A^T b = (0, 4), norm 4; ||b|| = 4
+                ->  4 / (3 (0 + 4)) = 1/3.
+    A dropped or extra ||A||_2, a transposed A, the wrong column or norms
+    taken over all columns at once each give another number."""
+    A = np.array([[3.0, 0.0], [0.0, 1.0], [0.0, 0.0]])
+    x0, b0 = np.array([1.0, 2.0]), np.array([1.0, 1.0, 5.0])
+    x1, b1 = np.zeros(2), np.array([0.0, 4.0, 0.0])
+    assert orc.normal_equation_residual(A, x0, b0, 3.0) == pytest.approx(0.170323153, rel=1e-8)
+    assert orc.normal_equation_residual(A, x1, b1, 3.0) == pytest.approx(1.0 / 3.0, rel=1e-15)
+    X, B = np.stack([x0, x1], axis=1), np.stack([b0, b1], axis=1)
+    assert orc.normal_equation_residual(A, X, B, 3.0) == pytest.approx(1.0 / 3.0, rel=1e-15)
+    assert orc.normal_equation_residual(A, X[:, ::-1], B[:, ::-1], 3.0) == pytest.approx(1.0 / 3.0,
+                                                                                         rel=1e-15)
+    # the exact least-squares solution of b = (3, 1, 7): x = (1, 1), A^T r = 0 exactly
+    assert orc.normal_equation_residual(A, np.array([1.0, 1.0]), np.array([3.0, 1.0, 7.0]), 3.0) == 0.0
+    # invariant under (A, b, ||A||) -> (c A, c b, c ||A||): numerator and
+    # denominator both scale with c^2 (an extra or missing ||A|| breaks it)
+    for c in (0.25, 8.0):
+        assert orc.normal_equation_residual(c * A, x0, c * b0, 3.0 * c) == pytest.approx(0.170323153,
+                                                                                          rel=1e-8)
+
+
 from hypothesis import HealthCheck, given, settings, strategies as st  # noqa: E402
 
 

@@ -2,8 +2,15 @@
 device memory (their memory is owned by another allocator, or they must not
 block on cudaMalloc / cudaFree).  Its scratch is a fixed array inside the
 library; its results must equal those of lls_k_geqrf, which allocates its
-scratch, on two calls in a row (the second call starts from the first
-call's leftovers in that array).
+scratch.
+
+Each pair below makes two calls in a row whose panels both use that array,
+so the second call starts from the first call's leftovers in it: the
+shared-memory (slab) kernel twice at different column counts, the slab
+kernel followed by the global-memory kernel (a 40000-row panel's slabs do
+not fit in shared memory), and the global-memory kernel followed by a small
+panel.  Panels of at most a few thousand rows run on one thread-block
+cluster and use no scratch at all.
 
 Collected last on purpose: a failure here leaves every other test run."""
 
@@ -18,7 +25,9 @@ def dev(x):
     return torch.as_tensor(np.asfortranarray(x), dtype=torch.float64, device="cuda").t().contiguous().t()
 
 
-@pytest.mark.parametrize("shapes", [((2000, 64), (16384, 128)), ((300, 128), (129, 7))])
+@pytest.mark.parametrize("shapes", [((8192, 96), (16384, 128)),
+                                    ((16384, 128), (40000, 128)),
+                                    ((40000, 128), (300, 128), (129, 7))])
 def test_noalloc_panel_qr_matches_allocating_entry_point(lls, shapes):
     for call, (m, n) in enumerate(shapes):
         Y = np.random.default_rng(10 * m + n + call).standard_normal((m, n))
