@@ -54,7 +54,12 @@ def parse():
                    help="right-hand sides (default: 16 for c2, 1 for c3)")
     p.add_argument("--nb", type=int, default=128)
     p.add_argument("--q", type=int, default=None, help="power iterations (default: 2 for c2, 1 for c3)")
-    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--precision", choices=["fp64", "mixed", "3xtf32", "tf32"], default="fp64",
+                   help="fp64; mixed: BF16 sampling + exact-slice FP64-accurate tensor-core "
+                        "updates; 3xtf32 / tf32: BF16 sampling + split-TF32 / plain TF32 "
+                        "updates with the minimum-norm FP64 refinement")
+    p.add_argument("--max-refine", type=int, default=None,
+                   help="refinement steps (default 0 for fp64 and mixed, 10 for the TF32 modes)")
     p.add_argument("--workload", choices=["c2", "c3", "batched", "serving"], default="c2",
                    help="c2: one 16384^2 solve per step (default); batched: many small "
                         "problems per step; serving: Poisson arrivals through lls_submit")
@@ -308,8 +313,9 @@ def run_batched(a):
     for j, (m, n, r, k) in enumerate(sizes):
         A, B, tol = gen_xy_problem(m, n, r, k, 1004 * 100000 + j, "cuda")
         probs.append((A, B, tol, lls.empty_colmajor(n, k), r))
-    prec = lls.LLS_MIXED_BF16 if a.precision == "mixed" else lls.LLS_FP64
-    h = lls.lls_create(nb=0 if a.autotune else 64, q=1, seed=2004, precision=prec)
+    prec = getattr(lls, PRECISIONS[a.precision])
+    h = lls.lls_create(nb=0 if a.autotune else 64, q=1, seed=2004, precision=prec,
+                       max_refine=default_refine(a.precision), refine_tol=1e-12)
     lls.lls_set_workers(h, a.workers)
     tuning = autotune_buckets(lls, h, [(m, n) for (m, n, _, _) in sizes]) if a.autotune else None
     ranks = [C.c_int64(-1) for _ in probs]
@@ -339,7 +345,7 @@ def run_batched(a):
     out = {"metric": METRIC, "value": a.count * a.steps / dt, "unit": "solves/s",
            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if a.precision == "fp64" else "bf16+f64", "data": "synthetic",
+           "dtype": DTYPES[a.precision], "data": "synthetic",
            "config": {"workload": f"batched: {a.count} X Y problems, m in [256, 2048], n in "
                                   f"[128, m], rank in [n/4, n], nrhs in {{1, 8, 32}}, "
                                   + ("nb, q autotuned per (m, n) bucket" if a.autotune else "nb=64, q=1"),
@@ -369,8 +375,9 @@ def run_serving(a):
         r = int(g.integers(-(-n // 8), n + 1))
         A, _, tol = gen_xy_problem(m, n, r, 1, 1005 * 100000 + j, "cuda")
         pool.append((A, tol, r))
-    prec = lls.LLS_MIXED_BF16 if a.precision == "mixed" else lls.LLS_FP64
-    h = lls.lls_create(nb=0 if a.autotune else 64, q=1, seed=2005, precision=prec)
+    prec = getattr(lls, PRECISIONS[a.precision])
+    h = lls.lls_create(nb=0 if a.autotune else 64, q=1, seed=2005, precision=prec,
+                       max_refine=default_refine(a.precision), refine_tol=1e-12)
     lls.lls_set_workers(h, a.workers)
     lls.lls_set_memory_cap(h, 120 << 30)
     tuning = autotune_buckets(lls, h, [tuple(A.shape) for A, _, _ in pool]) if a.autotune else None
@@ -428,7 +435,7 @@ def run_serving(a):
     out = {"metric": METRIC, "value": float(np.percentile(lat, 50) * 1e3), "unit": "ms p50 latency",
            "n_gpus": 1, "steps": nreq, "warmup": 0, "ms_per_step": 1e3 * wall / nreq,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if a.precision == "fp64" else "bf16+f64", "data": "synthetic",
+           "dtype": DTYPES[a.precision], "data": "synthetic",
            "config": {"workload": f"serving: Poisson {a.rate}/s for {a.duration} s, X Y requests "
                                   f"m in [512, 8192], n <= m, rank in [n/8, n], nrhs in [1, 64], "
                                   f"30% reuse a resident factor, 120 GB cap, "
@@ -459,8 +466,14 @@ def replica_throughput(flops_per_solve, steps, world, seconds):
     return total, flops_per_solve * total / seconds / 1e12
 
 
-PRECISIONS = {"fp64": "LLS_FP64", "mixed": "LLS_MIXED_BF16"}
-DTYPES = {"fp64": "f64", "mixed": "bf16+f64"}
+PRECISIONS = {"fp64": "LLS_FP64", "mixed": "LLS_MIXED_BF16", "3xtf32": "LLS_MIXED_BF16_3xTF32",
+              "tf32": "LLS_MIXED_BF16_TF32"}
+DTYPES = {"fp64": "f64", "mixed": "bf16+f64", "3xtf32": "bf16+tf32x3+f64", "tf32": "bf16+tf32+f64"}
+TF32_OF_BF16 = 1.1 / 2.25    # nominal dense TF32 / BF16 tensor rate of the part
+
+
+def default_refine(precision):
+    return 10 if precision in ("3xtf32", "tf32") else 0
 # DRAM bytes per algorithmic byte of a kernel family, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the family's launches
 # in one solve of a 4096-order case of the same construction, divided by the
@@ -471,7 +484,8 @@ DTYPES = {"fp64": "f64", "mixed": "bf16+f64"}
 TRAFFIC_PER_ALG_BYTE = {"dgemm_kernel": None, "oz_mma_kernel": None}
 
 
-def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, local):
+def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, local,
+               max_refine=None):
     """K timed solves of one precision mode on the resident inputs: value,
     accuracy against the construction's pseudoinverse, roofline of the
     dominant kernel, traces and the clocks seen during the timed region."""
@@ -479,7 +493,10 @@ def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, 
 
     m, n, _, tol = dense_shape(a)
     X = lls.empty_colmajor(n, a.nrhs)
-    h = lls.lls_create(nb=a.nb, q=a.q, seed=2002, precision=getattr(lls, PRECISIONS[precision]))
+    refine = default_refine(precision) if max_refine is None else max_refine
+    h = lls.lls_create(nb=a.nb, q=a.q, seed=2002 if a.workload == "c2" else 2003,
+                       precision=getattr(lls, PRECISIONS[precision]), max_refine=refine,
+                       refine_tol=1e-12)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         lls.lls_solve(h, A, B, tol, X)
@@ -533,6 +550,16 @@ def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, 
         peak = MEASURED_PEAKS.get("bf16_tflops_sustained") or 1400.0
         bound, psrc = "tensor", ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, "
                                  "seconds-long loop)" if MEASURED_PEAKS else "fallback 1.4 PFLOP/s")
+    elif precision in ("3xtf32", "tf32"):
+        # the split-TF32 GEMM streams FP32 planes and FP64 C: HBM-bound (its
+        # TF32 tensor rate is reported beside, against the nominal ratio of
+        # the measured BF16 peak)
+        kname = "tf32_mma_kernel"
+        g = trace.get(kname, (0, 0.0, 0.0, 0.0))
+        achieved = g[3] / g[1] / 1e9 if g[1] > 0 else 0.0
+        peak = MEASURED_PEAKS.get("hbm_gbs") or 6400.0
+        bound, psrc = "hbm", ("MEASURED_PEAKS.json hbm_gbs (STREAM-style copy)" if MEASURED_PEAKS
+                              else "fallback 6.4 TB/s")
     else:
         kname = "dgemm_kernel"
         g = trace.get(kname, (0, 0.0, 0.0, 0.0))
@@ -541,6 +568,20 @@ def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, 
         bound, psrc = "alu", "derived: 2 DFMA/clk/SM x 148 SMs x max SM clock"
     ratio = TRAFFIC_PER_ALG_BYTE.get(kname)
     traffic = ratio * g[3] / g[0] if (ratio and g[0]) else None
+    roof = {"bound": bound, "achieved": achieved, "peak": peak,
+            "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "kernel": kname, "peak_source": psrc,
+            "launches": g[0], "avg_launch_ms": 1e3 * g[1] / max(g[0], 1),
+            "alg_bytes_per_launch": g[3] / max(g[0], 1)}
+    if bound == "hbm" and g[1] > 0:
+        terms = 3.0 if precision == "3xtf32" else 1.0
+        tf_peak = (MEASURED_PEAKS.get("bf16_tflops_sustained") or 1400.0) * TF32_OF_BF16
+        roof["tensor"] = {"achieved": terms * g[2] / g[1] / 1e12, "peak": tf_peak,
+                          "unit": "TFLOP/s TF32",
+                          "frac": terms * g[2] / g[1] / 1e12 / tf_peak,
+                          "peak_source": "bf16_tflops_sustained x nominal TF32/BF16 (1.1/2.25)"}
+    refine_steps, refine_corr = lls.lls_refinement_info(h)
     # kernel families and phases of the method are two views of the same time:
     # shares are taken within each view
     fam = {k: v for k, v in trace.items() if not k.startswith("phase:")}
@@ -554,13 +595,23 @@ def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, 
     return {"h": h, "X": X, "flops": flops, "rank": ranks[-1], "elapsed": elapsed,
             "value": value, "solves_per_s": total_solves / elapsed,
             "ms_per_step": 1e3 * elapsed / steps, "launches": launches, "clocks": clocks,
-            "accuracy": {"x_rel_err_vs_pinv": x_err, "normal_eq_residual": ner},
-            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if peak else None, "traffic": traffic,
-                         "kernel": kname, "peak_source": psrc,
-                         "launches": g[0], "avg_launch_ms": 1e3 * g[1] / max(g[0], 1),
-                         "alg_bytes_per_launch": g[3] / max(g[0], 1)},
-            "trace": shares, "phases": phase_shares}
+            "accuracy": {"x_rel_err_vs_pinv": x_err, "normal_eq_residual": ner,
+                         "rank_expected": int(dense_shape(a)[2]), "refine_steps": refine_steps,
+                         "refine_last_correction": refine_corr},
+            "roofline": roof, "trace": shares, "phases": phase_shares}
+
+
+def side_arm(arm, prec, steps, warmup, note=None):
+    """The JSON object of an arm timed beside the headline one."""
+    out = {"value": arm["value"], "unit": "TFLOP/s", "dtype": DTYPES[prec],
+           "ms_per_step": arm["ms_per_step"], "steps": steps, "warmup": warmup,
+           "solves_per_s": arm["solves_per_s"], "rank": arm["rank"],
+           "accuracy": arm["accuracy"], "roofline": arm["roofline"],
+           "clocks": arm["clocks"], "gpu_launches": arm["launches"],
+           "phases": arm["phases"], "trace": arm["trace"]}
+    if note:
+        out["note"] = note
+    return out
 
 
 def main():
@@ -594,7 +645,7 @@ def main():
     A, B, Q1, Q2, sigma, r = make_inputs(a, "cuda")
     m, n, _, tol = dense_shape(a)
     main_arm = time_dense(a, lls, pm, a.precision, A, B, Q1, Q2, sigma, a.steps, a.warmup, dist,
-                          local)
+                          local, a.max_refine)
     h, flops = main_arm["h"], main_arm["flops"]
 
     e2e = None
@@ -616,20 +667,15 @@ def main():
     lls.lls_destroy(h)
     del main_arm["h"], main_arm["X"]
 
-    # the same workload in the other precision modes, timed the same way
-    # (same K and W), reported beside the headline arm
+    # the same workload in the mixed precision mode, timed the same way (same
+    # K and W), reported beside the headline arm
     others = {}
-    if a.precision == "fp64" and not a.no_mixed:
-        for prec in ("mixed",):
-            arm = time_dense(a, lls, pm, prec, A, B, Q1, Q2, sigma, a.steps, a.warmup, dist, local)
-            lls.lls_destroy(arm.pop("h"))
-            del arm["X"]
-            others[prec] = {"value": arm["value"], "unit": "TFLOP/s", "dtype": DTYPES[prec],
-                            "ms_per_step": arm["ms_per_step"], "steps": a.steps, "warmup": a.warmup,
-                            "solves_per_s": arm["solves_per_s"], "rank": arm["rank"],
-                            "accuracy": arm["accuracy"], "roofline": arm["roofline"],
-                            "clocks": arm["clocks"], "gpu_launches": arm["launches"],
-                            "phases": arm["phases"], "trace": arm["trace"]}
+    default_run = a.precision == "fp64" and a.workload == "c2" and not a.no_mixed
+    if default_run:
+        arm = time_dense(a, lls, pm, "mixed", A, B, Q1, Q2, sigma, a.steps, a.warmup, dist, local)
+        lls.lls_destroy(arm.pop("h"))
+        del arm["X"]
+        others["mixed"] = side_arm(arm, "mixed", a.steps, a.warmup)
     del Q1, Q2
 
     cpu = None
@@ -637,6 +683,31 @@ def main():
         A_host = np.asfortranarray(A.cpu().numpy())
         cpu = cpu_baseline(a, A_host, flops)
         del A_host
+
+    if default_run:
+        # the 32768 x 16384 mixed-precision workload: 3xTF32 updates with the
+        # minimum-norm refinement (K, W as above), the exact-slice updates (at
+        # most 5 timed solves after 3 warm-ups), and one plain-TF32 solve whose
+        # rank and error are reported (a failure record, not a throughput)
+        del A, B
+        torch.cuda.empty_cache()
+        import copy
+
+        c3 = copy.copy(a)
+        c3.workload, c3.nrhs, c3.q = "c3", 1, 1
+        A3, B3, Q13, Q23, sigma3, _ = make_inputs(c3, "cuda")
+        for prec, k_, w_, key in (("3xtf32", a.steps, a.warmup, "c3_3xtf32"),
+                                  ("mixed", min(a.steps, 5), max(3, min(a.warmup, 3)), "c3_mixed"),
+                                  ("tf32", 1, 1, "c3_tf32")):
+            arm = time_dense(c3, lls, pm, prec, A3, B3, Q13, Q23, sigma3, k_, w_, dist, local)
+            lls.lls_destroy(arm.pop("h"))
+            del arm["X"]
+            note = ("accuracy record of plain TF32 updates (rank expected "
+                    f"{arm['accuracy']['rank_expected']}, found {arm['rank']}); not a "
+                    "throughput claim") if prec == "tf32" else None
+            others[key] = side_arm(arm, prec, k_, w_, note)
+            others[key]["workload"] = workload_name(c3)
+        del A3, B3, Q13, Q23
 
     if rank == 0:
         out = {

@@ -57,13 +57,29 @@ enum {
 /* ---- precision modes --------------------------------------------------- */
 enum {
   LLS_FP64 = 0,        /* every step in FP64 */
-  LLS_MIXED_BF16 = 1   /* sampling products (step a2) in BF16 on the tcgen05
+  LLS_MIXED_BF16 = 1,  /* sampling products (step a2) in BF16 on the tcgen05
                           tensor cores with FP32 accumulation; the trailing
                           WY updates and Nullify's products as FP64-accurate
                           tensor-core GEMMs (exact BF16 digit slices, FP32
                           accumulation, FP64 recombination, see
                           lls_k_gemm_oz); panels, block SVDs, rank and the
                           solve in FP64 */
+  LLS_MIXED_BF16_3xTF32 = 2,  /* BF16 sampling as above; the trailing WY
+                          updates and Nullify's products on the TF32 tensor
+                          cores with split operands, hi*hi + hi*lo + lo*hi,
+                          FP32 accumulation (lls_k_gemm_tf32, terms = 3), so
+                          the factorization carries errors of about 2^-21
+                          ||A||; panels, block SVDs, rank and the solve in
+                          FP64.  The accuracy of x is won back by max_refine
+                          steps of the minimum-norm refinement (see
+                          max_refine); the rank is revealed when tol and the
+                          kept singular values lie well above that noise
+                          (e.g. tol = 1e-6 ||A||) */
+  LLS_MIXED_BF16_TF32 = 3     /* the same with plain TF32 products (terms = 1):
+                          errors of about 2^-11 ||A||, which hide singular
+                          values below about 1e-3 ||A|| -- the rank of such
+                          matrices is not revealed and refinement cannot
+                          repair it; kept as the baseline of the split */
 };
 
 typedef struct lls_handle_s* lls_handle;
@@ -73,7 +89,8 @@ typedef struct {
   int32_t nb;          /* block size n_b of Fig. 2, 1..128 [64]; 0: n_b and q
                           from the handle's tuning table (lls_autotune) */
   int32_t q;           /* power iterations of Y = (A^T A)^q A^T G, 0..4 [1] */
-  int32_t precision;   /* LLS_FP64 | LLS_MIXED_BF16 [LLS_FP64] */
+  int32_t precision;   /* LLS_FP64 | LLS_MIXED_BF16 | LLS_MIXED_BF16_3xTF32 |
+                          LLS_MIXED_BF16_TF32 [LLS_FP64] */
   int32_t nullify;     /* 1: run Nullify (minimum-norm x, Fig. 3) [1];
                           0: fast option (Remark after Fig. 4, Eq. (7)): a
                           least-squares x whose excess norm is of the size
@@ -88,10 +105,20 @@ typedef struct {
                           solves then apply V as one GEMM and
                           lls_factor_get can return it; 0: V is kept as its
                           reflectors and applied by replaying them [0] */
-  int32_t max_refine;  /* iterative refinement steps after the solve,
+  int32_t max_refine;  /* iterative refinement steps after the solve, 0..16
+                          [0] (see lls_refinement_info).  LLS_FP64 and
+                          LLS_MIXED_BF16 (FP64-accurate factors):
                           x <- x + P (b - A x) with the FP64 residual and
                           P = V_1 T_11^{-1} U_1^T the factorization's solve
-                          operator, 0..16 [0] (see lls_refinement_info) */
+                          operator.  The TF32 modes (factors accurate to the
+                          TF32 split only): x_0 = 0,
+                          x <- x + A^T P^T P P^T A^T (b - A x), whose every
+                          correction lies in range(A^T) and whose fixed point
+                          is the minimum-norm least-squares solution itself;
+                          it contracts by about the factors' relative error
+                          times the condition number of T_11 per step (with
+                          max_refine = 0 these modes return x = P b at TF32
+                          accuracy) */
   double refine_tol;   /* refinement stops once every column has
                           ||dx_j|| <= refine_tol ||x_j||, >= 0 [1e-12] */
   int32_t reserved[2]; /* must be zero */

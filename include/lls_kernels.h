@@ -65,6 +65,13 @@ int lls_k_jacobi_svd(int64_t b, const double* R, int64_t ldr, double* sigma,
 int lls_k_trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
                      double* B, int64_t ldb, void* stream);
 
+/* B <- R^{-T} B for the upper triangular r x r matrix R (only its upper
+ * triangle is read), B r x nrhs: the T_11^{-T} of the transposed solve
+ * operator P^T = U_1 T_11^{-T} V_1^T used by the refinement of the TF32
+ * modes (see lls_options.max_refine). */
+int lls_k_trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
+                           double* B, int64_t ldb, void* stream);
+
 /* Compute_rank (Fig. 4) of diag(T) (len entries, T with leading dimension
  * ldt): out[0] = length of the leading run of |T_jj| > tol, out[1] = number
  * of |T_jj| > tol, out[2] = 1 if a diagonal entry is NaN (device int64[3]). */
@@ -97,6 +104,25 @@ int lls_k_gemm_oz(int transa, int transb, int unit_lower_a, int unit_lower_b,
                   int64_t m, int64_t n, int64_t k, double alpha,
                   const double* A, int64_t lda, const double* B, int64_t ldb,
                   double beta, double* C, int64_t ldc, int* status, void* stream);
+
+/* C = alpha op(A) op(B) + beta C with FP64 operands and result on the TF32
+ * tensor cores (tcgen05 kind::tf32), the product of the trailing WY updates
+ * of the TF32 precision modes (Fig. 2, right and left updates; Fig. 3,
+ * Nullify's updates).  Every entry x of op(A) and op(B) is split into TF32
+ * terms hi = x rounded to 11 significant bits and lo = (x - hi) rounded to
+ * 11 bits; terms = 3 sums hi*hi + hi*lo + lo*hi (3xTF32, about 2^-21
+ * relative to sum_k |a_k b_k|), terms = 1 only hi*hi (plain TF32, about
+ * 2^-11).  FP32 accumulation in tensor memory over K ranges of 1024, the
+ * ranges summed in FP64.  Entries must lie inside FP32's range (|x| <
+ * 2^128, else the result is not finite; below 2^-126 they count as zero).
+ * Same operand conventions as lls_k_gemm; LLS_ERR_ARG for terms other than
+ * 1 or 3.  status (device int) becomes nonzero if a device-side wait timed
+ * out.  Workspace is allocated and freed on the stream inside the call. */
+int lls_k_gemm_tf32(int transa, int transb, int unit_lower_a, int unit_lower_b,
+                    int64_t m, int64_t n, int64_t k, double alpha,
+                    const double* A, int64_t lda, const double* B, int64_t ldb,
+                    double beta, double* C, int64_t ldc, int terms, int* status,
+                    void* stream);
 
 /* The Householder panel QR of lls_k_geqrf (R, W and tau in place; no T
  * factor) for callers that cannot allocate device memory: code whose device

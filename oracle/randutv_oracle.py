@@ -25,6 +25,9 @@ arXiv 2408.05238, Sec. 3):
 * ``refine``       -- iterative refinement of a solution with the solve
                       operator P = V_1 T_11^{-1} U_1^T of Fig. 4:
                       x <- x + P (b - A x), the residual in FP64.
+* ``refine_min_norm`` -- refinement from 0 with M = A^T P^T P P^T A^T, whose
+                      fixed point is the minimum-norm least-squares solution
+                      even when the factors are only approximate.
 * ``pinv_solve``   -- Sec. 2.2 truncated-SVD least squares, used as the
                       brute-force pin on small inputs.
 
@@ -74,6 +77,7 @@ __all__ = [
     "nullify",
     "solve",
     "refine",
+    "refine_min_norm",
     "pinv_solve",
     "pinv_solve_from_factors",
     "normal_equation_residual",
@@ -430,6 +434,66 @@ def refine(A: np.ndarray, B: np.ndarray, sol: Solution, x0: np.ndarray | None = 
         y = _back_substitution(T[:r, :r], (U.T @ res)[:r])
         x = x + V[:, :r] @ y
     return x.reshape(np.shape(sol.x if x0 is None else x0))
+
+
+def _forward_substitution_transposed(R: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Solve R^T Y = C for upper triangular R (R^T lower triangular), one row
+    at a time from the top."""
+    r = R.shape[0]
+    Y = np.zeros_like(C)
+    for i in range(r):
+        Y[i] = (C[i] - R[:i, i] @ Y[:i]) / R[i, i]
+    return Y
+
+
+MIN_NORM_GAP = 1e-2
+
+
+def refine_min_norm(A: np.ndarray, B: np.ndarray, sol: Solution, steps: int = 1) -> np.ndarray:
+    """Refinement that also restores the minimum-norm property when the
+    factors are only approximate (the TF32 update modes): from x_0 = 0,
+
+        x_{k+1} = x_k + M (b - A x_k),   M = A^T P^T P P^T A^T,
+
+    with P = V_1 T_11^{-1} U_1^T the solve operator of the factors of ``sol``
+    (``solve(..., keep=True)``) and the residual and the products with A in
+    FP64.  For exact factors of a rank-r matrix P = A^+ and M = A^+ (as
+    (A A^T)^+ = (A^+)^T A^+): one step from 0 gives the pseudoinverse
+    solution.  For approximate factors every correction lies in range(A^T)
+    (the leading A^T) and M annihilates every residual orthogonal to
+    range(A) (the trailing A^T), so the fixed point is the minimum-norm
+    least-squares solution itself -- not merely the solution within
+    range(V_1) that ``refine`` converges to -- and the iteration contracts
+    by about the relative error of P A on range(A^T).
+
+    The fixed point is the truncated solution only when A is of numerical
+    rank r: its singular values beyond the rank enter M through A (by about
+    sigma_{r+1} / sigma_r).  So, as the library does, the diagonal blocks'
+    singular values (``sol.diag``, before Nullify) are checked first: when
+    the largest dropped one exceeds MIN_NORM_GAP times the smallest kept one
+    there is no gap at the rank, and ``sol.x`` is returned unrefined."""
+    if sol.utv is None:
+        raise ValueError("refine_min_norm needs solve(..., keep=True)")
+    A = np.asarray(A, dtype=np.float64)
+    Bm = np.asarray(B, dtype=np.float64).reshape(A.shape[0], -1)
+    r = sol.rank
+    U, T, V = sol.utv.U, sol.utv.T, sol.utv.V
+    x = np.zeros((A.shape[1], Bm.shape[1]))
+    if r == 0:
+        return x.reshape(np.shape(sol.x))
+    if r < sol.diag.size and sol.diag[r:].max() > MIN_NORM_GAP * sol.diag[:r].min():
+        return np.array(sol.x, dtype=np.float64)
+
+    def apply_p(R):   # V_1 T_11^{-1} U_1^T R
+        return V[:, :r] @ _back_substitution(T[:r, :r], U[:, :r].T @ R)
+
+    def apply_pt(S):  # U_1 T_11^{-T} V_1^T S
+        return U[:, :r] @ _forward_substitution_transposed(T[:r, :r], V[:, :r].T @ S)
+
+    for _ in range(steps):
+        res = Bm - A @ x
+        x = x + A.T @ apply_pt(apply_p(apply_pt(A.T @ res)))
+    return x.reshape(np.shape(sol.x))
 
 
 # ---------------------------------------------------------------------------

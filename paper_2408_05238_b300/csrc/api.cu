@@ -30,7 +30,7 @@ Status arg_error(int idx, const char* what) { return lls::make_error(LLS_ERR_ARG
 Status check_options(const lls_options& o) {
   if (o.nb < 0 || o.nb > 128) return arg_error(2, "nb must be in 0..128 (0: tuned)");
   if (o.q < 0 || o.q > 4) return arg_error(2, "q must be in 0..4");
-  if (o.precision != LLS_FP64 && o.precision != LLS_MIXED_BF16)
+  if (o.precision < LLS_FP64 || o.precision > LLS_MIXED_BF16_TF32)
     return arg_error(2, "unknown precision mode");
   if (o.nullify != 0 && o.nullify != 1) return arg_error(2, "nullify must be 0 or 1");
   // The fast option keeps T_12.  Its x is the minimum-norm one only when the

@@ -108,6 +108,9 @@ Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, c
 // Rank scan with a device tolerance.
 Status rank_scan_dev(int64_t len, const double* T, int64_t ldt, const double* tol_dev,
                      int64_t* out, cudaStream_t st);
+// Gap at the rank of a diagonal d (len entries, contiguous): out (device,
+// 2 doubles) = {min_{j < r} |d_j|, max_{j >= r} |d_j|}.
+Status diag_gap(int64_t len, const double* d, int64_t r, double* out, cudaStream_t st);
 // Reversed-index gather / scatter used by Nullify (see nullify in solver.cu).
 Status rz_gather(int64_t bsz, int64_t L, const double* T, int64_t ldt, int64_t j0,
                  int64_t r, double* M, int64_t ldm, cudaStream_t st);
@@ -127,6 +130,11 @@ Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double*
                   int64_t ldb, cudaStream_t st);
 // Scratch bytes trsm_upper needs for its split-K GEMM updates.
 size_t trsm_upper_scratch_bytes(int64_t r, int64_t nrhs);
+// B <- R^{-T} B (forward substitution with the transpose of the upper
+// triangular r x r matrix R), blocked like trsm_upper.
+size_t trsm_upper_trans_scratch_bytes(int64_t r, int64_t nrhs);
+Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
+                        int64_t ldb, Scratch scratch, cudaStream_t st);
 Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
                   int64_t ldb, Scratch scratch, cudaStream_t st);
 

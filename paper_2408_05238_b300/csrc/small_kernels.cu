@@ -237,7 +237,63 @@ __global__ void trsm_block_kernel(int64_t k, const double* __restrict__ R, int64
   for (int64_t i = threadIdx.x; i < k; i += blockDim.x) b[i] = x[i];
 }
 
+// B <- R^{-T} B for one k x k diagonal block: forward substitution with the
+// transpose of the upper triangular R (R^T(l, i) = R(i, l)), one CTA per
+// right-hand side.
+__global__ void trsm_block_trans_kernel(int64_t k, const double* __restrict__ R, int64_t ldr,
+                                        double* B, int64_t ldb) {
+  extern __shared__ double x[];
+  double* b = B + (int64_t)blockIdx.x * ldb;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) x[i] = b[i];
+  __syncthreads();
+  for (int64_t i = 0; i < k; ++i) {
+    double yi = x[i] / R[i + i * ldr];
+    for (int64_t l = i + 1 + threadIdx.x; l < k; l += blockDim.x) x[l] = fma(-R[i + l * ldr], yi, x[l]);
+    __syncthreads();
+    if (threadIdx.x == 0) x[i] = yi;
+    __syncthreads();
+  }
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) b[i] = x[i];
+}
+
+// out[0] = min_{j < r} |d_j|, out[1] = max_{r <= j < len} |d_j| (0 when the
+// range is empty), one CTA.
+__global__ void diag_gap_kernel(int64_t len, const double* __restrict__ d, int64_t r,
+                                double* out) {
+  __shared__ double smin[32], smax[32];
+  double mn = INFINITY, mx = 0.0;
+  for (int64_t j = threadIdx.x; j < len; j += blockDim.x) {
+    const double v = fabs(d[j]);
+    if (j < r) mn = fmin(mn, v);
+    else mx = fmax(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    smin[threadIdx.x >> 5] = mn;
+    smax[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mn = fmin(mn, smin[w]);
+      mx = fmax(mx, smax[w]);
+    }
+    out[0] = r > 0 ? mn : 0.0;
+    out[1] = mx;
+  }
+}
+
 }  // namespace
+
+Status diag_gap(int64_t len, const double* d, int64_t r, double* out, cudaStream_t st) {
+  TraceScope ts(kTrSmall, st);
+  diag_gap_kernel<<<1, 1024, 0, st>>>(len, d, r, out);
+  LLS_LAUNCHED("diag_gap_kernel");
+  return ok_status();
+}
 
 Status copy_check(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
                   int* flag, cudaStream_t st) {
@@ -422,7 +478,49 @@ Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double*
   return ok_status();
 }
 
+size_t trsm_upper_trans_scratch_bytes(int64_t r, int64_t nrhs) {
+  size_t need = 0;
+  for (int64_t j0 = 0; j0 < r; j0 += kTrsmBlock) {
+    const int64_t j1 = std::min(r, j0 + kTrsmBlock);
+    if (j1 < r) need = std::max(need, gemm_scratch_bytes(r - j1, nrhs, j1 - j0));
+  }
+  return need;
+}
+
+Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
+                        int64_t ldb, Scratch scratch, cudaStream_t st) {
+  if (r <= 0 || nrhs <= 0) return ok_status();
+  if (nrhs > 2147483647) return make_error(LLS_ERR_ARG, "trsm: too many right-hand sides");
+  for (int64_t j0 = 0; j0 < r; j0 += kTrsmBlock) {
+    const int64_t j1 = std::min(r, j0 + kTrsmBlock);
+    {
+      TraceScope ts(kTrSmall, st);
+      trsm_block_trans_kernel<<<(unsigned)nrhs, 128, sizeof(double) * (j1 - j0), st>>>(
+          j1 - j0, R + j0 + j0 * ldr, ldr, B + j0, ldb);
+      LLS_LAUNCHED("trsm_block_trans_kernel");
+    }
+    // B(j1:r) -= R(j0:j1, j1:r)^T B(j0:j1)
+    if (j1 < r)
+      LLS_TRY(gemm(true, false, kDense, kDense, r - j1, nrhs, j1 - j0, -1.0, R + j0 + j1 * ldr, ldr,
+                   B + j0, ldb, 1.0, B + j1, ldb, scratch, st));
+  }
+  return ok_status();
+}
+
 }  // namespace lls
+
+extern "C" int lls_k_trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
+                                      double* B, int64_t ldb, void* stream) {
+  if (r < 0 || nrhs < 0 || ldr < (r > 1 ? r : 1) || ldb < (r > 1 ? r : 1)) return LLS_ERR_ARG;
+  if (r * nrhs > 0 && (!R || !B)) return LLS_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  lls::Scratch s;
+  s.bytes = lls::trsm_upper_trans_scratch_bytes(r, nrhs);
+  if (s.bytes && cudaMallocAsync(&s.ptr, s.bytes, st) != cudaSuccess) return LLS_ERR_NOMEM;
+  int code = lls::trsm_upper_trans(r, nrhs, R, ldr, B, ldb, s, st).code;
+  if (s.ptr) cudaFreeAsync(s.ptr, st);
+  return code;
+}
 
 extern "C" int lls_k_trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
                                 int64_t ldb, void* stream) {

@@ -26,6 +26,7 @@
 #include "lls_kernels.h"
 #include "oz_gemm.h"
 #include "solver.h"
+#include "tf32_gemm.h"
 
 namespace lls {
 
@@ -139,23 +140,30 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   DevStatus* ds = h.dstat.as<DevStatus>();
   LLS_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevStatus), st));
   Scratch pws = scratch_of(h.panel_ws);
-  // Mixed precision: the trailing updates and Nullify's products run as
-  // FP64-accurate GEMMs on the tensor cores (exact BF16 slices, oz_gemm.cu).
-  const bool tc = h.opt.precision == LLS_MIXED_BF16;
+  // Mixed precision: the trailing updates and Nullify's products run on the
+  // tensor cores, as FP64-accurate GEMMs (exact BF16 slices, oz_gemm.cu) or
+  // with TF32 split operands (tf32_gemm.cu: 3xTF32 or plain TF32).
+  const bool oz = h.opt.precision == LLS_MIXED_BF16;
+  const int tf_terms = h.opt.precision == LLS_MIXED_BF16_3xTF32 ? 3
+                       : h.opt.precision == LLS_MIXED_BF16_TF32 ? 1 : 0;
+  const bool tc = oz || tf_terms > 0;
+  auto tc_ws_bytes = [&](int64_t mm, int64_t nn, int64_t kk) {
+    return oz ? oz_gemm_workspace_bytes(mm, nn, kk) : tf32_gemm_workspace_bytes(mm, nn, kk, tf_terms);
+  };
   if (tc) {
     size_t need = 0;
     for (int64_t i = 0; i < steps; ++i) {
       const int64_t k = f.ks[i], b = f.bs[i], mp = m - k, np = n - k;
-      need = std::max(need, oz_gemm_workspace_bytes(m, b, np));
-      need = std::max(need, oz_gemm_workspace_bytes(m, np, b));
-      need = std::max(need, oz_gemm_workspace_bytes(b, np - b, mp));
-      need = std::max(need, oz_gemm_workspace_bytes(mp, np - b, b));
-      need = std::max(need, oz_gemm_workspace_bytes(b, b, std::max(np, mp)));  // Gram W^T W
-      need = std::max(need, oz_gemm_workspace_bytes(k, b, b));                 // A01 V_SVD
+      need = std::max(need, tc_ws_bytes(m, b, np));
+      need = std::max(need, tc_ws_bytes(m, np, b));
+      need = std::max(need, tc_ws_bytes(b, np - b, mp));
+      need = std::max(need, tc_ws_bytes(mp, np - b, b));
+      need = std::max(need, tc_ws_bytes(b, b, std::max(np, mp)));  // Gram W^T W
+      need = std::max(need, tc_ws_bytes(k, b, b));                 // A01 V_SVD
       if (f.has_v) {  // V's right update and V_SVD
-        need = std::max(need, oz_gemm_workspace_bytes(n, b, np));
-        need = std::max(need, oz_gemm_workspace_bytes(n, np, b));
-        need = std::max(need, oz_gemm_workspace_bytes(n, b, b));
+        need = std::max(need, tc_ws_bytes(n, b, np));
+        need = std::max(need, tc_ws_bytes(n, np, b));
+        need = std::max(need, tc_ws_bytes(n, b, b));
       }
     }
     LLS_TRY(h.oz_ws.reserve(need));
@@ -173,9 +181,12 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   auto xgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
                    int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
                    int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
-    if (tc)
+    if (oz)
       return oz_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_, false,
                      scratch_of(h.oz_ws), &ds->barrier_err, st);
+    if (tf_terms)
+      return tf32_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
+                       tf_terms, scratch_of(h.oz_ws), &ds->barrier_err, st);
     return fgemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_);
   };
 
@@ -199,7 +210,7 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     // ---- a1/a2: sketch and sample Y = (A_BR^T A_BR)^q A_BR^T G
     std::optional<TraceScope> phase;
     phase.emplace(kTrPhaseSample, st);
-    if (h.opt.precision == LLS_MIXED_BF16) {
+    if (h.opt.precision != LLS_FP64) {
       LLS_TRY(sample_bf16(h, ABR, ldt, mp, np, b, q, h.opt.seed, i, Y, ldw));
     } else {
       LLS_TRY(launch_sketch(h.opt.seed, i, mp, b, h.G.d(), std::max<int64_t>(m, 1), st));
@@ -362,9 +373,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       double* D0 = Xm + r * ldx;
       LLS_TRY(copy_cols_reversed(rows, bsz, Xm + j0 * ldx, ldx, Xc, rows, st));
       LLS_TRY(copy_matrix(rows, bsz, Xc, rows, h.P.d(), rows, st));
-      if (tc) LLS_TRY(h.oz_ws.reserve(std::max(oz_gemm_workspace_bytes(rows, bsz, L),
-                                                oz_gemm_workspace_bytes(rows, L, bsz))));
-      if (tc) LLS_TRY(h.oz_ws.reserve(oz_gemm_workspace_bytes(rows, bsz, bsz)));
+      if (tc) LLS_TRY(h.oz_ws.reserve(std::max(tc_ws_bytes(rows, bsz, L), tc_ws_bytes(rows, L, bsz))));
+      if (tc) LLS_TRY(h.oz_ws.reserve(tc_ws_bytes(rows, bsz, bsz)));
       LLS_TRY(xgemm(false, false, kDense, kDense, rows, bsz, L, 1.0, D0, ldx, Wbot, ldm, 1.0,
                     h.P.d(), rows));
       LLS_TRY(xgemm(false, false, kDense, kDense, rows, bsz, bsz, 1.0, h.P.d(), rows, Tz, bsz, 0.0,
@@ -383,7 +393,7 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       double* tz = f.RzTau.d() + bl.off_tau;
       LLS_TRY(rz_gather(bsz, L, T, ldt, j0, r, M, ldm, st));
       LLS_TRY(panel_qr(ldm, bsz, M, ldm, tz, pws, &ds->barrier_err, st));
-      if (tc) LLS_TRY(h.oz_ws.reserve(oz_gemm_workspace_bytes(bsz, bsz, ldm)));
+      if (tc) LLS_TRY(h.oz_ws.reserve(tc_ws_bytes(bsz, bsz, ldm)));
       LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, bsz, bsz, ldm, 1.0, M, ldm, M, ldm, 0.0,
                     h.S.d(), nb));
       LLS_TRY(wy_tfactor(bsz, h.S.d(), nb, tz, Tz, bsz, st));
@@ -508,8 +518,182 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
 }
 
 // ---------------------------------------------------------------------------
+// out (m x nrhs) = P^T S = U_1 T_11^{-T} V_1^T S for S (n x nrhs): the
+// transpose of the solve operator of Fig. 4, replayed from the factors in the
+// opposite order to solve_factored -- V^T (each step's reflectors with T_V^T,
+// then V_SVD^T, first step first), Nullify's reflectors with their T factors
+// transposed (first block processed first), a forward substitution with
+// T_11^T, then U = H_0 U_SVD,0 H_1 U_SVD,1 ... applied to [y; 0] last step
+// first.  S must not be the handle's z buffer.
+// ---------------------------------------------------------------------------
+Status apply_solve_transpose(Handle& h, Factor& f, const double* S, int64_t lds, int64_t nrhs,
+                             double* out, int64_t ldo) {
+  cudaStream_t st = h.stream;
+  const int64_t m = f.m, n = f.n, ldt = f.ldt, ldw = std::max<int64_t>(n, 1);
+  const int nb = f.nb;
+  const size_t blk = (size_t)nb * nb;
+  const int64_t r = f.rank;
+  if (m == 0 || nrhs == 0) return ok_status();
+  if (r == 0 || n == 0) return fill_zero(m, nrhs, out, ldo, st);
+  LLS_TRY(h.z.reserve(sizeof(double) * (size_t)n * nrhs));
+  LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)nb * nrhs));
+  LLS_TRY(h.sp2.reserve(sizeof(double) * (size_t)nb * nrhs));
+  LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)nb * nrhs));
+  auto fgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
+                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
+                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
+    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
+    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
+                scratch_of(h.gemm_ws), st);
+  };
+  double* Z = h.z.d();
+  double* p = h.sp.d();
+  double* p2 = h.sp2.d();
+  const double* T = f.T.d();
+  if (f.has_v) {  // z(0:r) = V(:, 0:r)^T S, V with Nullify's reflectors included
+    LLS_TRY(fgemm(true, false, kDense, kDense, r, nrhs, n, 1.0, f.Vx.d(), ldw, S, lds, 0.0, Z, ldw));
+  } else {
+    LLS_TRY(copy_matrix(n, nrhs, S, lds, Z, ldw, st));
+    for (size_t i = 0; i < f.ks.size(); ++i) {
+      const int64_t k = f.ks[i], b = f.bs[i], np = n - k;
+      const double* WVi = f.WV.d() + k + k * ldw;
+      LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, np, 1.0, WVi, ldw, Z + k, ldw, 0.0, p,
+                    nb));
+      LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TV.d() + i * blk, nb, p, nb, 0.0,
+                    p2, nb));
+      LLS_TRY(fgemm(false, false, kUnitLower, kDense, np, nrhs, b, -1.0, WVi, ldw, p2, nb, 1.0, Z + k,
+                    ldw));
+      LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.VS.d() + i * blk, nb, Z + k, ldw,
+                    0.0, p, nb));
+      LLS_TRY(copy_matrix(b, nrhs, p, nb, Z + k, ldw, st));
+    }
+    if (f.nullified) {
+      const int64_t L = n - r;
+      double* zc = h.xc.d();
+      for (const auto& bl : f.rz) {
+        const int64_t j0 = bl.j0, bsz = bl.bsz, ldm = bsz + L;
+        const double* M = f.RzM.d() + bl.off_m;
+        const double* Tz = f.RzT.d() + bl.off_t;
+        LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldw, zc, bsz, st));
+        LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
+        LLS_TRY(fgemm(true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldw, 1.0,
+                      p, bsz));
+        LLS_TRY(fgemm(true, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2,
+                      bsz));
+        LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p2, bsz, zc, bsz, st));  // W_top = I
+        LLS_TRY(fgemm(false, false, kDense, kDense, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0,
+                      Z + r, ldw));
+        LLS_TRY(copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldw, st));
+      }
+    }
+  }
+  // y = T_11^{-T} z(0:r)
+  LLS_TRY(h.gemm_ws.reserve(trsm_upper_trans_scratch_bytes(r, nrhs)));
+  LLS_TRY(trsm_upper_trans(r, nrhs, T, ldt, Z, ldw, scratch_of(h.gemm_ws), st));
+  // out = U [y; 0], last step first
+  LLS_TRY(copy_matrix(r, nrhs, Z, ldw, out, ldo, st));
+  if (r < m) LLS_TRY(fill_zero(m - r, nrhs, out + r, ldo, st));
+  for (size_t ii = f.ks.size(); ii-- > 0;) {
+    const int64_t k = f.ks[ii], b = f.bs[ii], mp = m - k;
+    const double* WU = T + k + k * ldt;
+    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.US.d() + ii * blk, nb, out + k, ldo,
+                  0.0, p, nb));
+    LLS_TRY(copy_matrix(b, nrhs, p, nb, out + k, ldo, st));
+    LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, mp, 1.0, WU, ldt, out + k, ldo, 0.0, p,
+                  nb));
+    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.TU.d() + ii * blk, nb, p, nb, 0.0,
+                  p2, nb));
+    LLS_TRY(fgemm(false, false, kUnitLower, kDense, mp, nrhs, b, -1.0, WU, ldt, p2, nb, 1.0, out + k,
+                  ldo));
+  }
+  return ok_status();
+}
+
+namespace {
+
+// Per-column ||dx|| / ||x|| of the last correction (max over columns) from
+// the norms refine_update wrote.
+double max_correction(const std::vector<double>& norms, int64_t nrhs) {
+  double corr = 0.0;
+  for (int64_t j = 0; j < nrhs; ++j) {
+    const double dn = std::sqrt(norms[2 * j]), xn = std::sqrt(norms[2 * j + 1]);
+    const double c = xn > 0.0 ? dn / xn : (dn > 0.0 ? INFINITY : 0.0);
+    corr = std::max(corr, c);
+  }
+  return corr;
+}
+
+// Ratio of the largest dropped to the smallest kept singular value of the
+// diagonal blocks above which the minimum-norm refinement is not applied.
+constexpr double kMinNormGap = 1e-2;
+
+// The refinement of the TF32 modes, whose factors carry the TF32 split's
+// errors (range(V_1) is then off the row space by about that error times
+// the condition number of T_11, which x <- x + P r cannot repair): from
+// x_0 = 0, x <- x + A^T P^T P P^T A^T (b - A x).  Every correction is A^T
+// times something, so x stays in range(A^T); M = A^T P^T P P^T A^T equals
+// A^+ for exact factors and annihilates residuals orthogonal to range(A), so
+// for a matrix of numerical rank r the fixed point is the minimum-norm
+// least-squares solution.  Without a gap at the rank (singular values
+// beyond it comparable to the kept ones) A itself is not of rank r, M
+// differs from P by about sigma_{r+1} / sigma_r and the fixed point from the
+// truncated solution P b: the diagonal blocks' singular values are checked
+// first and, without a gap of kMinNormGap, x = P b is kept (warning).
+Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const double* B,
+                       int64_t nrhs, int64_t ldb, double* X, int64_t ldx) {
+  cudaStream_t st = h.stream;
+  const int64_t m = f.m, n = f.n;
+  LLS_TRY(h.nrm.reserve(sizeof(double) * std::max<int64_t>(2 * nrhs, 2)));
+  LLS_TRY(diag_gap(std::min(m, n), f.sigma.d(), f.rank, h.nrm.d(), st));
+  double gap[2];
+  LLS_CUDA(cudaMemcpyAsync(gap, h.nrm.d(), sizeof(gap), cudaMemcpyDeviceToHost, st));
+  LLS_CUDA(cudaStreamSynchronize(st));
+  if (gap[1] > kMinNormGap * gap[0])
+    return make_error(LLS_WARN_REFINE_NOCONV,
+                      "no gap at the rank (largest dropped / smallest kept singular value " +
+                          std::to_string(gap[1] / gap[0]) + "): refinement not applied");
+  LLS_TRY(h.rr.reserve(sizeof(double) * (size_t)m * nrhs));
+  LLS_TRY(h.rt.reserve(sizeof(double) * (size_t)m * nrhs));
+  LLS_TRY(h.rs.reserve(sizeof(double) * (size_t)n * nrhs));
+  LLS_TRY(h.dd.reserve(sizeof(double) * (size_t)n * nrhs));
+  LLS_TRY(h.nrm.reserve(sizeof(double) * 2 * (size_t)nrhs));
+  LLS_TRY(h.gemm_ws.reserve(std::max(gemm_scratch_bytes(m, nrhs, n), gemm_scratch_bytes(n, nrhs, m))));
+  std::vector<double> norms(2 * (size_t)nrhs);
+  LLS_TRY(fill_zero(n, nrhs, X, ldx, st));
+  double prev = 0.0;
+  for (int it = 1; it <= h.opt.max_refine; ++it) {
+    LLS_TRY(copy_matrix(m, nrhs, B, ldb, h.rr.d(), m, st));  // r = b - A x
+    LLS_TRY(gemm(false, false, kDense, kDense, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, h.rr.d(), m,
+                 scratch_of(h.gemm_ws), st));
+    LLS_TRY(gemm(true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, h.rr.d(), m, 0.0, h.rs.d(), n,
+                 scratch_of(h.gemm_ws), st));                   // A^T r
+    LLS_TRY(apply_solve_transpose(h, f, h.rs.d(), n, nrhs, h.rt.d(), m));   // P^T A^T r
+    LLS_TRY(solve_factored(h, f, h.rt.d(), nrhs, m, h.dd.d(), n));        // P P^T A^T r
+    LLS_TRY(apply_solve_transpose(h, f, h.dd.d(), n, nrhs, h.rt.d(), m));   // P^T P P^T A^T r
+    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(n, nrhs, m)));
+    LLS_TRY(gemm(true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, h.rt.d(), m, 0.0, h.dd.d(), n,
+                 scratch_of(h.gemm_ws), st));                   // dx = A^T (...)
+    LLS_TRY(refine_update(n, nrhs, h.dd.d(), n, X, ldx, h.nrm.d(), st));
+    LLS_CUDA(cudaMemcpyAsync(norms.data(), h.nrm.d(), sizeof(double) * 2 * nrhs,
+                             cudaMemcpyDeviceToHost, st));
+    LLS_CUDA(cudaStreamSynchronize(st));
+    const double corr = max_correction(norms, nrhs);
+    h.refine_steps = it;
+    h.refine_corr = corr;
+    if (corr <= h.opt.refine_tol) return ok_status();
+    if (it > 1 && corr > 0.5 * prev) break;  // no longer contracting: rounding floor
+    prev = corr;
+  }
+  return make_error(LLS_WARN_REFINE_NOCONV, "refinement correction " + std::to_string(h.refine_corr) +
+                                                " above refine_tol");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // Iterative refinement: x <- x + P (b - A x), P = V_1 T_11^{-1} U_1^T applied
-// by solve_factored, the residual in FP64 with the original A.
+// by solve_factored, the residual in FP64 with the original A; for factors
+// made in a TF32 mode, refine_min_norm above.
 // ---------------------------------------------------------------------------
 Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const double* B,
                      int64_t nrhs, int64_t ldb, double* X, int64_t ldx) {
@@ -523,6 +707,8 @@ Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const d
   }
   if (h.opt.max_refine <= 0 || !A || m == 0 || n == 0 || nrhs == 0 || f.rank == 0)
     return ok_status();
+  if (f.precision == LLS_MIXED_BF16_3xTF32 || f.precision == LLS_MIXED_BF16_TF32)
+    return refine_min_norm(h, f, A, lda, B, nrhs, ldb, X, ldx);
   cudaStream_t st = h.stream;
   LLS_TRY(h.rr.reserve(sizeof(double) * (size_t)m * nrhs));
   LLS_TRY(h.dd.reserve(sizeof(double) * (size_t)n * nrhs));
@@ -541,12 +727,7 @@ Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const d
     LLS_CUDA(cudaMemcpyAsync(norms.data(), h.nrm.d(), sizeof(double) * 2 * nrhs,
                              cudaMemcpyDeviceToHost, st));
     LLS_CUDA(cudaStreamSynchronize(st));
-    double corr = 0.0;
-    for (int64_t j = 0; j < nrhs; ++j) {
-      const double dn = std::sqrt(norms[2 * j]), xn = std::sqrt(norms[2 * j + 1]);
-      const double c = xn > 0.0 ? dn / xn : (dn > 0.0 ? INFINITY : 0.0);
-      corr = std::max(corr, c);
-    }
+    const double corr = max_correction(norms, nrhs);
     h.refine_steps = it;
     h.refine_corr = corr;
     if (corr <= h.opt.refine_tol) return ok_status();

@@ -178,12 +178,17 @@ struct Handle {
   // iterative refinement: residual, correction, per-column norms; what the
   // last refined solve did (lls_refinement_info)
   DevBuf rr, dd, nrm;
+  // the minimum-norm refinement of the TF32 modes: P^T products (m x nrhs)
+  // and A^T products (n x nrhs)
+  DevBuf rt, rs;
   int refine_steps = 0;
   double refine_corr = 0.0;
   DevBuf dstat;           // DevStatus
   // mixed precision sampling: bf16 copies of A_BR and A_BR^T, bf16 sketch /
   // product, fp32 product, tensor-core split-K partials, scalars
-  DevBuf G16, A16, A16t, Z16, F32, tc_ws, mixed_misc, oz_ws;
+  DevBuf G16, A16, A16t, Z16, F32, tc_ws, mixed_misc;
+  // workspace of the tensor-core update GEMMs (exact-slice or TF32 split)
+  DevBuf oz_ws;
   DevStatus* hstat = nullptr;  // pinned host mirror
   // lls_solve reuses one factor object between calls of the same shape
   std::unique_ptr<Factor> scratch_factor;
@@ -209,7 +214,7 @@ struct Handle {
   std::vector<DevBuf*> workspace() {
     return {&G,  &Wt, &P,  &P2,  &Q,   &Q2,  &S,   &gemm_ws, &panel_ws,   &bw,   &z,   &sp,   &sp2,
             &xc, &rr, &dd, &nrm, &dstat, &G16, &A16, &A16t,  &Z16,        &F32,  &tc_ws, &mixed_misc,
-            &oz_ws};
+            &oz_ws, &rt, &rs};
   }
   // Binds the workspace to `stream` (call once the stream is set).
   void bind_workspace() {

@@ -24,6 +24,7 @@ enum TraceKind {
   kTrBf16Gemm,     // tcgen05 BF16 sampling GEMM
   kTrConvert,      // FP64 -> BF16 conversions and slicing
   kTrOzGemm,       // FP64-accurate GEMM on tensor cores (exact BF16 slices)
+  kTrTf32Gemm,     // split-operand TF32 GEMM on tensor cores (3xTF32 / TF32)
   // phases of the method (each spans the kernels above that it launches)
   kTrPhaseSample,   // a1/a2 sketch and sample Y
   kTrPhaseQrY,      // a3 QR of Y and its T factor

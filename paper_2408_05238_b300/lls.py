@@ -31,6 +31,8 @@ LLS_ERR_NOT_FOUND = -7
 LLS_ERR_CAPACITY = -8
 LLS_FP64 = 0
 LLS_MIXED_BF16 = 1
+LLS_MIXED_BF16_3xTF32 = 2
+LLS_MIXED_BF16_TF32 = 3
 LLS_FACTOR_T = 0
 LLS_FACTOR_V = 1
 LLS_OOC_FARTHEST = 0
@@ -147,6 +149,9 @@ _sig("lls_k_gemm_bf16_tn", [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P])
 _sig("lls_k_gemm_oz", [C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _P, _I, _P, _I, _D,
                        _P, _I, _P, _P])
 _sig("lls_k_panel_qr_noalloc", [_I, _I, _P, _I, _P, _P, _P])
+_sig("lls_k_gemm_tf32", [C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _P, _I, _P, _I, _D,
+                         _P, _I, C.c_int, _P, _P])
+_sig("lls_k_trsm_upper_trans", [_I, _I, _P, _I, _P, _I, _P])
 
 EXPORTED = [n for n in dir(_lib) if n.startswith("lls_")]
 
@@ -551,6 +556,13 @@ def lls_k_trsm_upper(R: torch.Tensor, B: torch.Tensor):
     return B
 
 
+def lls_k_trsm_upper_trans(R: torch.Tensor, B: torch.Tensor):
+    r = R.shape[0]
+    _kcheck(_lib.lls_k_trsm_upper_trans(r, B.shape[1], _ptr(R), _ld(R), _ptr(B), _ld(B),
+                                        _stream()))
+    return B
+
+
 def lls_k_rank(T: torch.Tensor, tol: float):
     out = torch.zeros(3, dtype=torch.int64, device=T.device)
     length = min(T.shape)
@@ -581,6 +593,22 @@ def lls_k_gemm_oz(transa, transb, A, B, C_=None, alpha=1.0, beta=0.0, unit_lower
     _kcheck(_lib.lls_k_gemm_oz(int(transa), int(transb), int(unit_lower_a), int(unit_lower_b), m,
                                n, k, float(alpha), _ptr(A), _ld(A), _ptr(B), _ld(B), float(beta),
                                _ptr(C_), _ld(C_), _ptr(status), _stream()))
+    return C_, int(status.item())
+
+
+def lls_k_gemm_tf32(transa, transb, A, B, C_=None, alpha=1.0, beta=0.0, unit_lower_a=False,
+                    unit_lower_b=False, terms=3):
+    """FP64-operand GEMM on the TF32 tensor cores with split operands
+    (lls_k_gemm_tf32; terms = 3: 3xTF32, 1: plain TF32)."""
+    m = A.shape[1] if transa else A.shape[0]
+    k = A.shape[0] if transa else A.shape[1]
+    n = B.shape[0] if transb else B.shape[1]
+    if C_ is None:
+        C_ = torch.zeros((n, max(m, 1)), dtype=torch.float64, device=A.device).t()[:m]
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _kcheck(_lib.lls_k_gemm_tf32(int(transa), int(transb), int(unit_lower_a), int(unit_lower_b), m,
+                                 n, k, float(alpha), _ptr(A), _ld(A), _ptr(B), _ld(B), float(beta),
+                                 _ptr(C_), _ld(C_), int(terms), _ptr(status), _stream()))
     return C_, int(status.item())
 
 

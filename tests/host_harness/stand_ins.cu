@@ -325,5 +325,38 @@ Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double*
                   Scratch, cudaStream_t st) {
   return trsm_block(r, nrhs, R, ldr, B, ldb, st);
 }
+Status diag_gap(int64_t len, const double* d, int64_t r, double* out, cudaStream_t) {
+  double mn = INFINITY, mx = 0.0;
+  for (int64_t j = 0; j < len; ++j) {
+    if (j < r) mn = std::min(mn, std::fabs(d[j]));
+    else mx = std::max(mx, std::fabs(d[j]));
+  }
+  out[0] = r > 0 ? mn : 0.0;
+  out[1] = mx;
+  return ok_status();
+}
+size_t trsm_upper_trans_scratch_bytes(int64_t, int64_t) { return 0; }
+// R^T Y = B by forward substitution, one column at a time.
+Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
+                        int64_t ldb, Scratch, cudaStream_t) {
+  for (int64_t j = 0; j < nrhs; ++j) {
+    double* b = B + j * ldb;
+    for (int64_t i = 0; i < r; ++i) {
+      double s = b[i];
+      for (int64_t l = 0; l < i; ++l) s -= R[l + i * ldr] * b[l];
+      b[i] = s / R[i + i * ldr];
+    }
+  }
+  return ok_status();
+}
+// The split-TF32 products, exact here (their rounding is a kernel matter):
+// the TF32 modes' orchestration -- the minimum-norm refinement and the
+// transposed solve operator -- runs with exact products.
+size_t tf32_gemm_workspace_bytes(int64_t, int64_t, int64_t, int) { return 0; }
+Status tf32_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t n, int64_t k,
+                 double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                 double beta, double* C, int64_t ldc, int, Scratch s, int*, cudaStream_t st) {
+  return gemm(ta, tb, ma, mb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s, st);
+}
 }  // namespace lls
 

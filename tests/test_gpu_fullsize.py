@@ -74,11 +74,14 @@ def c3():
     return A, B, xref
 
 
-@pytest.mark.parametrize("precision", ["mixed"])
+@pytest.mark.parametrize("precision", ["mixed", "3xtf32"])
 def test_c3_full_size(lls, c3, precision):
+    """Exact-slice updates, and 3xTF32 updates with the minimum-norm
+    refinement (at most 10 steps)."""
     A, B, xref = c3
-    prec = {"mixed": lls.LLS_MIXED_BF16}[precision]
-    h = lls.lls_create(nb=128, q=1, seed=2003, precision=prec)
+    prec = {"mixed": lls.LLS_MIXED_BF16, "3xtf32": lls.LLS_MIXED_BF16_3xTF32}[precision]
+    h = lls.lls_create(nb=128, q=1, seed=2003, precision=prec,
+                       max_refine=10 if precision == "3xtf32" else 0, refine_tol=1e-12)
     try:
         X, rank, code = lls.lls_solve(h, A, B, 1e-6)
         torch.cuda.synchronize()

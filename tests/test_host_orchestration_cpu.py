@@ -8,7 +8,7 @@ modes, buffer reservations and copies of a solve -- and the worker pool, the
 serving queue, the tuning table, guard words and argument checks -- run here
 without a GPU ("device" memory is host memory).  The oracle gets the
 harness's deterministic sketch.  Over random shapes (tall, wide, narrow last
-steps, nb = 1 and nb > n, rank 0 to full), q = 0..4, both precision modes
+steps, nb = 1 and nb > n, rank 0 to full), q = 0..4, all four precision modes
 (the mixed mode's products are exact here: its orchestration is what is
 checked), with and without Nullify, explicit V and refinement, and for the
 out-of-core executor caches
@@ -136,7 +136,7 @@ def random_configs(seed, count, ooc):
         r = g.randint(0, min(m, n))
         P = -(-n // nb)
         nullify = g.randint(0, 1)
-        precision = 0 if ooc else g.randint(0, 1)
+        precision = 0 if ooc else g.randint(0, 3)
         yield dict(it=it, kind=kind, m=m, n=n, r=r, nb=nb, q=q, nullify=nullify,
                    precision=precision if nullify else 0,   # the fast option is FP64-only
                    explicit_v=0 if ooc else g.randint(0, 1),

@@ -361,6 +361,86 @@ def test_refine_leaves_nullspace_components():
     assert np.linalg.norm(x1 - (sol.x + V2 @ c)) < 1e-9 * np.linalg.norm(c)
 
 
+def _perturbed(sol, angle, rel, seed):
+    """A copy of sol's factors spoiled like a TF32 factorization: U and V
+    rotated by random orthogonal matrices exp(angle S) (S skew, so range(U_1)
+    and range(V_1) tilt by about `angle`) and T_11 perturbed by `rel`
+    relative."""
+    import copy
+
+    import scipy.linalg
+
+    g = np.random.default_rng(seed)
+    bad = copy.deepcopy(sol)
+    for name in ("U", "V"):
+        F = getattr(sol.utv, name)
+        S = g.standard_normal((F.shape[0], F.shape[0]))
+        setattr(bad.utv, name, F @ scipy.linalg.expm(angle * (S - S.T) / np.sqrt(F.shape[0])))
+    r = sol.rank
+    bad.utv.T[:r, :r] = np.triu(sol.utv.T[:r, :r] * (1 + rel * g.standard_normal((r, r))))
+    return bad
+
+
+def test_refine_min_norm_exact_factors_give_pinv_in_one_step():
+    """With exact factors P = A^+ and M = A^T P^T P P^T A^T = A^+: one step
+    from 0 is the truncated-SVD solution (b with a residual outside range(A))."""
+    A, X, Y = wl.lowrank_xy(90, 70, 25, seed=31, noise=0.0)
+    B = np.random.default_rng(8).standard_normal((90, 2))
+    sol = orc.solve(A, B, 1, 16, 1e-10 * wl.norm2_of_product(X, Y), seed=4, keep=True)
+    assert sol.rank == 25
+    x1 = orc.refine_min_norm(A, B, sol, steps=1)
+    x_ref = orc.pinv_solve(A, B, 25)
+    assert np.linalg.norm(x1 - x_ref) / np.linalg.norm(x_ref) < 1e-11
+
+
+def test_refine_min_norm_recovers_from_approximate_factors():
+    """Factors with a 1e-5 tilt of range(U_1) and range(V_1) and 1e-6
+    relative error in T_11 (a TF32-accurate factorization): refine converges
+    to a solution inside the tilted range(V_1), 1e-5 away from the
+    minimum-norm one, and so would M = A^T P^T P (fixed point U_1^T r = 0,
+    oblique to range(A)); refine_min_norm converges to the pseudoinverse
+    solution (its corrections stay in range(A^T), its fixed point has
+    A^T r = 0)."""
+    A, X, Y = wl.lowrank_xy(120, 80, 30, seed=13, noise=0.0)
+    B = np.random.default_rng(2).standard_normal((120, 2))
+    sol = orc.solve(A, B, 1, 16, 1e-10 * wl.norm2_of_product(X, Y), seed=6, keep=True)
+    bad = _perturbed(sol, 1e-5, 1e-6, seed=1)
+    x_ref = orc.pinv_solve(A, B, 30)
+    err = lambda x: np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)
+    x_plain = orc.refine(A, B, bad, x0=np.zeros_like(sol.x), steps=8)
+    assert err(x_plain) > 1e-7
+    U, T, V, r = bad.utv.U, bad.utv.T, bad.utv.V, bad.rank
+    x_obl = np.zeros_like(sol.x)
+    for _ in range(8):   # A^T P^T P (b - A x): the trailing P^T A^T left out
+        y = orc._back_substitution(T[:r, :r], U[:, :r].T @ (B - A @ x_obl))
+        x_obl = x_obl + A.T @ (U[:, :r] @ orc._forward_substitution_transposed(T[:r, :r], y))
+    assert err(x_obl) > 1e-7
+    errs = [err(orc.refine_min_norm(A, B, bad, steps=k)) for k in (1, 2, 6)]
+    assert errs[0] > 1e-9 and errs[1] < errs[0] and errs[2] < 1e-12
+    # the fixed point is a least-squares solution orthogonal to null(A)
+    x6 = orc.refine_min_norm(A, B, bad, steps=6)
+    assert np.linalg.norm(A.T @ (B - A @ x6)) < 1e-12 * np.linalg.norm(A) ** 2 * np.linalg.norm(x6)
+    N0 = np.linalg.svd(A)[2][30:].T
+    assert np.linalg.norm(N0.T @ x6) < 1e-12 * np.linalg.norm(x6)
+
+
+def test_refine_min_norm_needs_a_gap_at_the_rank():
+    """sigma_i = 0.8^i (no gap) with tol inside the spectrum: A is not of rank
+    r, M = A^T P^T P P^T A^T differs from P by about sigma_{r+1} / sigma_r and
+    its fixed point from the truncated solution P b.  The largest dropped
+    singular value of the diagonal blocks exceeds 1e-2 times the smallest
+    kept one, so refine_min_norm returns the solution unrefined."""
+    m, n = 60, 40
+    Q1 = np.linalg.qr(np.random.default_rng(1).standard_normal((m, m)))[0][:, :n]
+    Q2 = np.linalg.qr(np.random.default_rng(2).standard_normal((n, n)))[0]
+    A = (Q1 * 0.8 ** np.arange(n)) @ Q2.T
+    b = np.random.default_rng(3).standard_normal(m)
+    sol = orc.solve(A, b, 0, 8, 1e-3, seed=4, keep=True)
+    assert 0 < sol.rank < n
+    assert sol.diag[sol.rank:].max() > orc.MIN_NORM_GAP * sol.diag[:sol.rank].min()
+    assert np.array_equal(orc.refine_min_norm(A, b, sol, steps=3), sol.x)
+
+
 # -------------------------------------------------------------------- properties
 def test_normal_equation_residual_closed_forms():
     """The normalisation of the normal-equation residual (reading c15),
