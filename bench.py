@@ -64,6 +64,8 @@ def parse():
                    help="c2: one 16384^2 solve per step (default); batched: many small "
                         "problems per step; serving: Poisson arrivals through lls_submit")
     p.add_argument("--count", type=int, default=1024, help="batched: problems per step")
+    p.add_argument("--batched-mode", choices=["auto", "workers", "persistent"], default="auto",
+                   help="batched: one persistent launch (auto picks it for FP64) or the worker pool")
     p.add_argument("--workers", type=int, default=8)
     p.add_argument("--autotune", action="store_true",
                    help="batched/serving: tune (n_b, q) for every (m, n) bucket of the workload "
@@ -317,6 +319,8 @@ def run_batched(a):
     h = lls.lls_create(nb=0 if a.autotune else 64, q=1, seed=2004, precision=prec,
                        max_refine=default_refine(a.precision), refine_tol=1e-12)
     lls.lls_set_workers(h, a.workers)
+    lls.lls_set_batched_mode(h, {"auto": lls.LLS_BATCHED_AUTO, "workers": lls.LLS_BATCHED_WORKERS,
+                                 "persistent": lls.LLS_BATCHED_PERSISTENT}[a.batched_mode])
     tuning = autotune_buckets(lls, h, [(m, n) for (m, n, _, _) in sizes]) if a.autotune else None
     ranks = [C.c_int64(-1) for _ in probs]
     plist = [lls.make_problem(A, B, tol, X, rank_out=C.pointer(rk))
@@ -349,7 +353,8 @@ def run_batched(a):
            "config": {"workload": f"batched: {a.count} X Y problems, m in [256, 2048], n in "
                                   f"[128, m], rank in [n/4, n], nrhs in {{1, 8, 32}}, "
                                   + ("nb, q autotuned per (m, n) bucket" if a.autotune else "nb=64, q=1"),
-                      "workers": a.workers, "precision": a.precision, "tuning": tuning},
+                      "workers": a.workers, "precision": a.precision, "tuning": tuning,
+                      "batched_mode": a.batched_mode},
            "tflops": flops * a.steps / dt / 1e12, "rank_mismatches": wrong,
            "gpu_launches": launches, "device_allocations": allocs, "clocks": clk.summary()}
     print(json.dumps(out))

@@ -245,11 +245,36 @@ int lls_refinement_info(lls_handle h, int32_t* steps, double* correction);
 int lls_factor_diag(lls_handle h, int64_t factor_id, double* diag, int64_t len,
                     int64_t* rank_count);
 
-/* Solve count independent problems (device pointers in each entry) on the
- * handle's worker pool (lls_set_workers): largest first, several at a time
- * on separate streams.  Blocks until all are done.  Returns the first error;
- * each entry's status field holds its own result. */
+/* Solve count independent problems (device pointers in each entry).
+ * Blocks until all are done.  Returns the first error; each entry's status
+ * field holds its own result.  Two ways to run the batch (lls_set_batched_mode):
+ *  - persistent: the randUTV step loop and block SVDs (Fig. 2) of every
+ *    problem run in ONE kernel launch -- the paper's algorithm-by-blocks
+ *    idea (Sec. 3.4): each problem's factorization is cut into tasks on
+ *    64 x 64 blocks (sketch rows, sample and update tiles, the panel QRs with
+ *    their T factors, the block SVDs and their updates), a device task queue
+ *    holds one (phase, tasks claimed) word per problem, any CTA of the
+ *    persistent grid claims a ready task (largest problems first) and the
+ *    last task of a phase releases the next one (per-problem dependency
+ *    counters).  Then the worker pool decides each rank, runs Nullify and the
+ *    solve.  The factors are those of lls_solve up to the order of
+ *    floating-point sums.  FP64 only, explicit_v = 0, 1 <= m, n <= 16384,
+ *    n_b <= 64; the factors and workspace of all problems are held at once
+ *    (about 8 (m n + n^2 + 6 m n_b) bytes each).  A waiting CTA polls the
+ *    queue a bounded number of times (lls_debug_barrier_limit sets the same
+ *    limit) and then ends the launch with LLS_ERR_TIMEOUT for every problem.
+ *  - workers: each problem runs lls_solve's launch sequence on one of the
+ *    pool's worker streams (lls_set_workers), largest first, several at a
+ *    time. */
 int lls_solve_batched(lls_handle h, int64_t count, lls_problem* problems);
+
+/* How lls_solve_batched runs a batch: LLS_BATCHED_AUTO (persistent when
+ * every problem and the options allow it, else workers; the default),
+ * LLS_BATCHED_WORKERS, or LLS_BATCHED_PERSISTENT (lls_solve_batched then
+ * returns LLS_ERR_ARG, index 3, for a batch it cannot take).  LLS_ERR_ARG
+ * for another mode. */
+enum { LLS_BATCHED_AUTO = 0, LLS_BATCHED_WORKERS = 1, LLS_BATCHED_PERSISTENT = 2 };
+int lls_set_batched_mode(lls_handle h, int mode);
 
 /* Serving: enqueue one request (copied; buffers must stay alive until it
  * completes) and return at once; *ticket receives its id.  Requests start in
@@ -436,7 +461,8 @@ int64_t lls_alloc_count(void);
 int lls_debug_fail_allocation(int64_t after);
 
 /* Testing hook (failure detection without a GPU fault): a CTA of the
- * cooperative panel kernels waiting at their grid barrier gives up after
+ * cooperative panel kernels waiting at their grid barrier, or a CTA of the
+ * persistent batched factorization finding no ready task, gives up after
  * `polls` polls (default about 4 million, a few seconds) instead of
  * hanging; the kernel then exits and the call that launched it returns
  * LLS_ERR_TIMEOUT.  polls = 0 makes every wait that does not pass at once

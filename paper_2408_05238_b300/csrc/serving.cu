@@ -13,9 +13,12 @@
 // beside it.
 #include <algorithm>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
+#include <functional>
 #include <thread>
 
+#include "batched_factor.h"
 #include "lls.h"
 #include "solver.h"
 
@@ -23,6 +26,7 @@ namespace lls {
 
 struct Ticket {
   lls_problem req;
+  std::function<Status(Handle&)> job;  // set: run this on the worker instead of req
   int64_t bytes = 0;
   int status = LLS_PENDING;
   int err_arg = 0;
@@ -51,6 +55,7 @@ Handle::~Handle() {
   // Stream-ordered frees of the workspace before the stream goes away.
   for (DevBuf* b : workspace()) b->release();
   scratch_factor.reset();
+  batch_view.reset();
   if (stream) cudaStreamSynchronize(stream);
   if (hstat) cudaFreeHost(hstat);
   if (own_stream && stream) cudaStreamDestroy(stream);
@@ -133,7 +138,7 @@ void worker_loop(Handle::Pool* pool, int wi) {
     }
     w.opt = pool->parent->opt;
     w.tune = pool->parent->tune;
-    Status s = run_request(*pool->parent, w, t->req);
+    Status s = t->job ? t->job(w) : run_request(*pool->parent, w, t->req);
     {
       std::lock_guard<std::mutex> lock(pool->mu);
       pool->admitted_bytes -= t->bytes;
@@ -184,6 +189,228 @@ int64_t enqueue(Handle& h, const lls_problem& req) {
   return id;
 }
 
+int64_t enqueue_job(Handle& h, std::function<Status(Handle&)> job) {
+  Handle::Pool& pool = *h.pool;
+  auto t = std::make_shared<Ticket>();
+  std::memset(&t->req, 0, sizeof(t->req));
+  t->job = std::move(job);
+  int64_t id;
+  {
+    std::lock_guard<std::mutex> lock(pool.mu);
+    id = pool.next_ticket++;
+    pool.tickets[id] = t;
+    pool.queue.push_back(id);
+  }
+  pool.cv_work.notify_all();
+  return id;
+}
+
+// ---------------------------------------------------------------------------
+// lls_solve_batched in one persistent launch (batched_factor.cu): every
+// problem's factors and workspace live in one arena of the handle; the
+// kernel runs the step loop and block SVDs of all problems, then the worker
+// pool decides each rank, runs Nullify and the solve on views of the arena.
+// ---------------------------------------------------------------------------
+constexpr int64_t kPbMaxDim = 16384;
+
+// Offsets (bytes) of one problem's buffers in the arena.
+struct PBLayout {
+  int nb, q, steps;
+  size_t T, WV, TV, TU, US, VS, R, tauV, tauU, sigma, G, W, P, P2, Q, Q2, S;
+};
+
+bool persistent_eligible(Handle& h, int64_t count, const lls_problem* probs, std::string* why) {
+  if (!batched_factor_available()) return (*why = "persistent kernel not in this build"), false;
+  if (h.opt.precision != LLS_FP64) return (*why = "the persistent path is FP64"), false;
+  if (h.opt.explicit_v) return (*why = "the persistent path keeps V implicit"), false;
+  if (count > INT32_MAX / 2) return (*why = "too many problems"), false;
+  for (int64_t i = 0; i < count; ++i) {
+    const lls_problem& p = probs[i];
+    int nb = 0, q = 0;
+    effective_nb_q(h.opt, h.tune.get(), p.m, p.n, &nb, &q);
+    if (!p.A || p.m < 1 || p.n < 1 || p.m > kPbMaxDim || p.n > kPbMaxDim || nb > kPbMaxNb ||
+        p.lda < p.m || p.nrhs < 0)
+      return (*why = "problem " + std::to_string(i) + " is outside the persistent path's range " +
+                     "(1 <= m, n <= 16384, nb <= 64)"),
+             false;
+  }
+  return true;
+}
+
+Status solve_batched_persistent(Handle& h, int64_t count, lls_problem* probs,
+                                std::vector<int>& status) {
+  cudaStream_t st = h.stream;
+  // largest first: the scheduler prefers problems in this order
+  std::vector<int64_t> order(count);
+  for (int64_t i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    const lls_problem &pa = probs[a], &pb = probs[b];
+    return (double)pa.m * pa.n * std::min(pa.m, pa.n) > (double)pb.m * pb.n * std::min(pb.m, pb.n);
+  });
+  std::vector<PBLayout> lay(count);
+  size_t total = 0;
+  auto take = [&](size_t doubles) {
+    const size_t o = total;
+    total += (std::max<size_t>(doubles, 1) * sizeof(double) + 255) / 256 * 256;
+    return o;
+  };
+  for (int64_t k = 0; k < count; ++k) {
+    const lls_problem& p = probs[order[k]];
+    PBLayout& L = lay[k];
+    effective_nb_q(h.opt, h.tune.get(), p.m, p.n, &L.nb, &L.q);
+    L.steps = (int)ceil_div(std::min(p.m, p.n), L.nb);
+    const size_t blk = (size_t)L.nb * L.nb * L.steps, vec = (size_t)L.nb * L.steps;
+    L.T = take((size_t)p.m * p.n);
+    L.WV = take((size_t)p.n * p.n);
+    L.TV = take(blk);
+    L.TU = take(blk);
+    L.US = take(blk);
+    L.VS = take(blk);
+    L.R = take(blk);
+    L.tauV = take(vec);
+    L.tauU = take(vec);
+    L.sigma = take(vec);
+    L.G = take((size_t)p.m * L.nb);
+    L.W = take((size_t)p.m * L.nb);
+    L.P = take((size_t)p.m * L.nb);
+    L.P2 = take((size_t)p.m * L.nb);
+    L.Q = take((size_t)L.nb * p.n);
+    L.Q2 = take((size_t)L.nb * p.n);
+    L.S = take((size_t)L.nb * L.nb);
+  }
+  LLS_TRY(h.batch_arena.reserve(total));
+  // scheduler state and flags: problems, state, done, flags, finished, err
+  const size_t off_probs = 0, off_state = (sizeof(PBProblem) * count + 255) / 256 * 256;
+  const size_t off_done = off_state + 8 * (size_t)count;
+  const size_t off_flags = off_done + 4 * (size_t)count;
+  const size_t off_tail = off_flags + 8 * (size_t)count;
+  const size_t meta_bytes = off_tail + 16;
+  LLS_TRY(h.batch_meta.reserve(meta_bytes));
+  char* arena = h.batch_arena.as<char>();
+  char* meta = h.batch_meta.as<char>();
+  int* flags = reinterpret_cast<int*>(meta + off_flags);
+  std::vector<PBProblem> pp(count);
+  for (int64_t k = 0; k < count; ++k) {
+    const lls_problem& p = probs[order[k]];
+    const PBLayout& L = lay[k];
+    PBProblem& q = pp[k];
+    auto at = [&](size_t off) { return reinterpret_cast<double*>(arena + off); };
+    q.m = (int)p.m;
+    q.n = (int)p.n;
+    q.nb = L.nb;
+    q.q = L.q;
+    q.steps = L.steps;
+    q.nphases = pb_num_phases(q.m, q.n, q.nb, q.q);
+    q.seed = h.opt.seed;
+    q.A = p.A;
+    q.lda = p.lda;
+    q.T = at(L.T);
+    q.ldt = p.m;
+    q.WV = at(L.WV);
+    q.ldw = p.n;
+    q.TV = at(L.TV);
+    q.TU = at(L.TU);
+    q.US = at(L.US);
+    q.VS = at(L.VS);
+    q.Rblk = at(L.R);
+    q.tauV = at(L.tauV);
+    q.tauU = at(L.tauU);
+    q.sigma = at(L.sigma);
+    q.G = at(L.G);
+    q.W = at(L.W);
+    q.P = at(L.P);
+    q.P2 = at(L.P2);
+    q.Q = at(L.Q);
+    q.Q2 = at(L.Q2);
+    q.S = at(L.S);
+    q.flags = flags + 2 * k;
+  }
+  LLS_CUDA(cudaMemcpyAsync(meta + off_probs, pp.data(), sizeof(PBProblem) * count,
+                           cudaMemcpyHostToDevice, st));
+  LLS_CUDA(cudaMemsetAsync(meta + off_state, 0, meta_bytes - off_state, st));
+  PBArgs args;
+  args.count = (int)count;
+  args.probs = reinterpret_cast<const PBProblem*>(meta + off_probs);
+  args.state = reinterpret_cast<unsigned long long*>(meta + off_state);
+  args.done = reinterpret_cast<unsigned int*>(meta + off_done);
+  args.finished = reinterpret_cast<unsigned int*>(meta + off_tail);
+  args.err = reinterpret_cast<int*>(meta + off_tail + 8);
+  args.poll_limit = g_barrier_spin_limit.load(std::memory_order_relaxed);
+  {
+    TraceGuard tg(h);
+    LLS_TRY(batched_factor_launch(args, st));
+  }
+  std::vector<int> hflags(2 * (size_t)count + 4);
+  LLS_CUDA(cudaMemcpyAsync(hflags.data(), flags, (off_tail + 16 - off_flags), cudaMemcpyDeviceToHost,
+                           st));
+  LLS_CUDA(cudaStreamSynchronize(st));
+  const int sched_err = hflags[2 * count + 2];
+  // per problem: the rank, Nullify and the solve on the worker pool
+  std::vector<int64_t> ids(count, -1);
+  for (int64_t k = 0; k < count; ++k) {
+    const int64_t j = order[k];
+    if (sched_err) status[j] = LLS_ERR_TIMEOUT;
+    else if (hflags[2 * k]) status[j] = LLS_ERR_NONFINITE;
+    else if (hflags[2 * k + 1]) status[j] = LLS_ERR_SVD_NOCONV;
+    if (status[j] != LLS_PENDING) continue;
+    const lls_problem p = probs[j];
+    const PBLayout L = lay[k];
+    ids[k] = enqueue_job(h, [p, L, arena](Handle& w) -> Status {
+      Factor& f = w.view();
+      auto at = [&](size_t off) { return arena + off; };
+      const size_t blk = sizeof(double) * L.nb * L.nb * L.steps, vec = sizeof(double) * L.nb * L.steps;
+      f.m = p.m;
+      f.n = p.n;
+      f.ldt = p.m;
+      f.nb = L.nb;
+      f.q = L.q;
+      f.precision = LLS_FP64;
+      f.nullified = false;
+      f.has_v = f.has_a = false;
+      f.ks.clear();
+      f.bs.clear();
+      f.rz.clear();
+      f.rank = f.rank_count = 0;
+      for (int64_t k0 = 0; k0 < std::min(p.m, p.n); k0 += L.nb) {
+        f.ks.push_back(k0);
+        f.bs.push_back(std::min<int64_t>(L.nb, std::min(p.m - k0, p.n - k0)));
+      }
+      f.T.borrow(at(L.T), sizeof(double) * p.m * p.n);
+      f.WV.borrow(at(L.WV), sizeof(double) * p.n * p.n);
+      f.TV.borrow(at(L.TV), blk);
+      f.TU.borrow(at(L.TU), blk);
+      f.US.borrow(at(L.US), blk);
+      f.VS.borrow(at(L.VS), blk);
+      f.Rblk.borrow(at(L.R), blk);
+      f.tauV.borrow(at(L.tauV), vec);
+      f.tauU.borrow(at(L.tauU), vec);
+      f.sigma.borrow(at(L.sigma), vec);
+      LLS_TRY(w.dstat.reserve(sizeof(DevStatus)));
+      LLS_CUDA(cudaMemsetAsync(w.dstat.p, 0, sizeof(DevStatus), w.stream));
+      Status fs = finish_factorization(w, f, p.tol);
+      if (!fs.ok()) return fs;
+      if (p.rank_out) *p.rank_out = f.rank;
+      Status ss = solve_refined(w, f, p.A, p.lda, p.B, p.nrhs, p.ldb, p.X, p.ldx);
+      if (!ss.ok()) return ss;
+      return fs.code != LLS_OK ? fs : ss;
+    });
+  }
+  Handle::Pool& pool = *h.pool;
+  std::unique_lock<std::mutex> lock(pool.mu);
+  for (int64_t k = 0; k < count; ++k) {
+    if (ids[k] < 0) continue;
+    auto t = pool.tickets[ids[k]];
+    pool.cv_done.wait(lock, [&] { return t->done; });
+    status[order[k]] = t->status;
+    if (t->status < 0 && h.last_msg.empty()) {
+      h.last_arg = t->err_arg;
+      h.last_msg = "problem " + std::to_string(order[k]) + ": " + t->err_msg;
+    }
+    pool.tickets.erase(ids[k]);
+  }
+  return ok_status();
+}
+
 }  // namespace
 
 bool pool_busy(Handle& h) {
@@ -217,12 +444,45 @@ int lls_set_workers(lls_handle hh, int workers) {
   return LLS_OK;
 }
 
+int lls_set_batched_mode(lls_handle hh, int mode) {
+  Handle* h = reinterpret_cast<Handle*>(hh);
+  if (!h || mode < LLS_BATCHED_AUTO || mode > LLS_BATCHED_PERSISTENT) return LLS_ERR_ARG;
+  h->batched_mode = mode;
+  return LLS_OK;
+}
+
 int lls_solve_batched(lls_handle hh, int64_t count, lls_problem* problems) {
   Handle* h = reinterpret_cast<Handle*>(hh);
   if (!h || count < 0 || (count > 0 && !problems)) return LLS_ERR_ARG;
   if (count == 0) return LLS_OK;
   lls::Status ps = lls::ensure_pool(*h);
   if (!ps.ok()) return ps.code;
+  if (h->batched_mode != LLS_BATCHED_WORKERS) {
+    std::string why;
+    if (lls::persistent_eligible(*h, count, problems, &why)) {
+      std::vector<int> status(count, LLS_PENDING);
+      h->last_arg = 0;
+      h->last_msg.clear();
+      lls::Status s = lls::solve_batched_persistent(*h, count, problems, status);
+      if (!s.ok()) {
+        h->last_arg = s.arg;
+        h->last_msg = s.msg;
+        return s.code;
+      }
+      int first = LLS_OK;
+      for (int64_t i = 0; i < count; ++i) {
+        problems[i].status = status[i];
+        problems[i].factor_id = -1;
+        if (first == LLS_OK && status[i] < 0) first = status[i];
+      }
+      return first;
+    }
+    if (h->batched_mode == LLS_BATCHED_PERSISTENT) {
+      h->last_arg = 3;
+      h->last_msg = why;
+      return LLS_ERR_ARG;
+    }
+  }
   // Largest problems first, so the pool's tail is made of short requests.
   std::vector<int64_t> order(count);
   for (int64_t i = 0; i < count; ++i) order[i] = i;

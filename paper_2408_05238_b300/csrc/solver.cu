@@ -79,6 +79,59 @@ size_t factor_bytes(int64_t m, int64_t n, int nb, bool explicit_v, bool keep_a) 
   return b;
 }
 
+// The GEMMs of a factorization on the handle's stream: FP64 (fgemm), the
+// update products per the precision mode (xgemm: FP64, exact-slice or split
+// TF32 on the tensor cores) and the Gram products of the T factors (ggemm:
+// FP64-accurate in every mode -- the T factor decides whether I - W T W^T is
+// orthogonal, and a TF32 Gram's FP32 sums of squares would leave it off by
+// about 1e-6, so the TF32 modes take the exact-slice GEMM there).  Scratch
+// is grown to each shape's plan first: the plan depends on the shape alone,
+// so a result never depends on which handle (or worker) computed it or on
+// what that handle ran before.
+struct FactorGemms {
+  Handle& h;
+  cudaStream_t st;
+  int nb;
+  DevStatus* ds;
+  bool oz;
+  int tf_terms;
+  FactorGemms(Handle& h_, int nb_)
+      : h(h_), st(h_.stream), nb(nb_), ds(h_.dstat.as<DevStatus>()),
+        oz(h_.opt.precision == LLS_MIXED_BF16),
+        tf_terms(h_.opt.precision == LLS_MIXED_BF16_3xTF32 ? 3
+                 : h_.opt.precision == LLS_MIXED_BF16_TF32 ? 1 : 0) {}
+  bool tc() const { return oz || tf_terms > 0; }
+  size_t tc_ws_bytes(int64_t mm, int64_t nn, int64_t kk) const {
+    return oz ? oz_gemm_workspace_bytes(mm, nn, kk) : tf32_gemm_workspace_bytes(mm, nn, kk, tf_terms);
+  }
+  Status fgemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn, int64_t kk,
+               double alpha, const double* Aa, int64_t lda_, const double* Bb, int64_t ldb_,
+               double beta, double* Cc, int64_t ldc_) {
+    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
+    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
+                scratch_of(h.gemm_ws), st);
+  }
+  Status xgemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn, int64_t kk,
+               double alpha, const double* Aa, int64_t lda_, const double* Bb, int64_t ldb_,
+               double beta, double* Cc, int64_t ldc_) {
+    if (oz)
+      return oz_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_, false,
+                     scratch_of(h.oz_ws), &ds->barrier_err, st);
+    if (tf_terms)
+      return tf32_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
+                       tf_terms, scratch_of(h.oz_ws), &ds->barrier_err, st);
+    return fgemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_);
+  }
+  Status ggemm(int64_t kk, const double* W, int64_t ldw_, int64_t bb, double* S) {
+    if (tf_terms) {
+      LLS_TRY(h.oz_ws.reserve(oz_gemm_workspace_bytes(bb, bb, kk)));
+      return oz_gemm(true, false, kUnitLower, kUnitLower, bb, bb, kk, 1.0, W, ldw_, W, ldw_, 0.0, S,
+                     nb, false, scratch_of(h.oz_ws), &ds->barrier_err, st);
+    }
+    return xgemm(true, false, kUnitLower, kUnitLower, bb, bb, kk, 1.0, W, ldw_, W, ldw_, 0.0, S, nb);
+  }
+};
+
 // ---------------------------------------------------------------------------
 // randUTV + rank (+ Nullify when opt.nullify)
 // ---------------------------------------------------------------------------
@@ -143,53 +196,26 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
   // Mixed precision: the trailing updates and Nullify's products run on the
   // tensor cores, as FP64-accurate GEMMs (exact BF16 slices, oz_gemm.cu) or
   // with TF32 split operands (tf32_gemm.cu: 3xTF32 or plain TF32).
-  const bool oz = h.opt.precision == LLS_MIXED_BF16;
-  const int tf_terms = h.opt.precision == LLS_MIXED_BF16_3xTF32 ? 3
-                       : h.opt.precision == LLS_MIXED_BF16_TF32 ? 1 : 0;
-  const bool tc = oz || tf_terms > 0;
-  auto tc_ws_bytes = [&](int64_t mm, int64_t nn, int64_t kk) {
-    return oz ? oz_gemm_workspace_bytes(mm, nn, kk) : tf32_gemm_workspace_bytes(mm, nn, kk, tf_terms);
-  };
-  if (tc) {
+  FactorGemms g(h, nb);
+  if (g.tc()) {
     size_t need = 0;
     for (int64_t i = 0; i < steps; ++i) {
       const int64_t k = f.ks[i], b = f.bs[i], mp = m - k, np = n - k;
-      need = std::max(need, tc_ws_bytes(m, b, np));
-      need = std::max(need, tc_ws_bytes(m, np, b));
-      need = std::max(need, tc_ws_bytes(b, np - b, mp));
-      need = std::max(need, tc_ws_bytes(mp, np - b, b));
-      need = std::max(need, tc_ws_bytes(b, b, std::max(np, mp)));  // Gram W^T W
-      need = std::max(need, tc_ws_bytes(k, b, b));                 // A01 V_SVD
+      need = std::max(need, g.tc_ws_bytes(m, b, np));
+      need = std::max(need, g.tc_ws_bytes(m, np, b));
+      need = std::max(need, g.tc_ws_bytes(b, np - b, mp));
+      need = std::max(need, g.tc_ws_bytes(mp, np - b, b));
+      need = std::max(need, g.tc_ws_bytes(b, b, std::max(np, mp)));  // Gram W^T W
+      if (g.tf_terms) need = std::max(need, oz_gemm_workspace_bytes(b, b, std::max(np, mp)));
+      need = std::max(need, g.tc_ws_bytes(k, b, b));                 // A01 V_SVD
       if (f.has_v) {  // V's right update and V_SVD
-        need = std::max(need, tc_ws_bytes(n, b, np));
-        need = std::max(need, tc_ws_bytes(n, np, b));
-        need = std::max(need, tc_ws_bytes(n, b, b));
+        need = std::max(need, g.tc_ws_bytes(n, b, np));
+        need = std::max(need, g.tc_ws_bytes(n, np, b));
+        need = std::max(need, g.tc_ws_bytes(n, b, b));
       }
     }
     LLS_TRY(h.oz_ws.reserve(need));
   }
-  // FP64 GEMM with its split-K scratch grown to this shape's plan first: the
-  // plan depends on the shape alone, so a result never depends on which
-  // handle (or worker) computed it or on what that handle ran before.
-  auto fgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
-                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
-                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
-    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
-    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
-                scratch_of(h.gemm_ws), st);
-  };
-  auto xgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
-                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
-                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
-    if (oz)
-      return oz_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_, false,
-                     scratch_of(h.oz_ws), &ds->barrier_err, st);
-    if (tf_terms)
-      return tf32_gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
-                       tf_terms, scratch_of(h.oz_ws), &ds->barrier_err, st);
-    return fgemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_);
-  };
-
   // T <- A, with the finiteness check; V <- I; the refinement copy of A.
   LLS_TRY(copy_check(m, n, A, lda, f.T.d(), ldt, &ds->nonfinite, st));
   if (f.has_v) LLS_TRY(set_identity(n, f.Vx.d(), ldv, st));
@@ -214,12 +240,12 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       LLS_TRY(sample_bf16(h, ABR, ldt, mp, np, b, q, h.opt.seed, i, Y, ldw));
     } else {
       LLS_TRY(launch_sketch(h.opt.seed, i, mp, b, h.G.d(), std::max<int64_t>(m, 1), st));
-      LLS_TRY(fgemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.G.d(),
+      LLS_TRY(g.fgemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.G.d(),
                    std::max<int64_t>(m, 1), 0.0, Y, ldw));
       for (int it = 0; it < q; ++it) {
-        LLS_TRY(fgemm(false, false, kDense, kDense, mp, b, np, 1.0, ABR, ldt, Y, ldw, 0.0, h.Wt.d(),
+        LLS_TRY(g.fgemm(false, false, kDense, kDense, mp, b, np, 1.0, ABR, ldt, Y, ldw, 0.0, h.Wt.d(),
                      std::max<int64_t>(mp, 1)));
-        LLS_TRY(fgemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.Wt.d(),
+        LLS_TRY(g.fgemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, h.Wt.d(),
                      std::max<int64_t>(mp, 1), 0.0, Y, ldw));
       }
     }
@@ -227,26 +253,25 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     phase.reset();
     phase.emplace(kTrPhaseQrY, st);
     LLS_TRY(panel_qr(np, b, Y, ldw, tauVi, pws, &ds->barrier_err, st));
-    LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, b, b, np, 1.0, Y, ldw, Y, ldw, 0.0, h.S.d(),
-                  nb));
+    LLS_TRY(g.ggemm(np, Y, ldw, b, h.S.d()));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauVi, TVi, nb, st));
     // ---- a4: T(:, k:n) <- T(:, k:n) - (T(:, k:n) W_V) T_V W_V^T, all m rows
     phase.reset();
     phase.emplace(kTrPhaseRight, st);
     double* Tk = T + k * ldt;
-    LLS_TRY(xgemm(false, false, kDense, kUnitLower, m, b, np, 1.0, Tk, ldt, Y, ldw, 0.0, h.P.d(),
+    LLS_TRY(g.xgemm(false, false, kDense, kUnitLower, m, b, np, 1.0, Tk, ldt, Y, ldw, 0.0, h.P.d(),
                   m));
-    LLS_TRY(xgemm(false, false, kDense, kDense, m, b, b, 1.0, h.P.d(), m, TVi, nb, 0.0, h.P2.d(),
+    LLS_TRY(g.xgemm(false, false, kDense, kDense, m, b, b, 1.0, h.P.d(), m, TVi, nb, 0.0, h.P2.d(),
                   m));
-    LLS_TRY(xgemm(false, true, kDense, kUnitLower, m, np, b, -1.0, h.P2.d(), m, Y, ldw, 1.0, Tk,
+    LLS_TRY(g.xgemm(false, true, kDense, kUnitLower, m, np, b, -1.0, h.P2.d(), m, Y, ldw, 1.0, Tk,
                   ldt));
     if (f.has_v) {  // V(:, k:n) <- V(:, k:n) (I - W_V T_V W_V^T), all n rows
       double* Vk = f.Vx.d() + k * ldv;
-      LLS_TRY(xgemm(false, false, kDense, kUnitLower, n, b, np, 1.0, Vk, ldv, Y, ldw, 0.0, h.P.d(),
+      LLS_TRY(g.xgemm(false, false, kDense, kUnitLower, n, b, np, 1.0, Vk, ldv, Y, ldw, 0.0, h.P.d(),
                     ldv));
-      LLS_TRY(xgemm(false, false, kDense, kDense, n, b, b, 1.0, h.P.d(), ldv, TVi, nb, 0.0,
+      LLS_TRY(g.xgemm(false, false, kDense, kDense, n, b, b, 1.0, h.P.d(), ldv, TVi, nb, 0.0,
                     h.P2.d(), ldv));
-      LLS_TRY(xgemm(false, true, kDense, kUnitLower, n, np, b, -1.0, h.P2.d(), ldv, Y, ldw, 1.0, Vk,
+      LLS_TRY(g.xgemm(false, true, kDense, kUnitLower, n, np, b, -1.0, h.P2.d(), ldv, Y, ldw, 1.0, Vk,
                     ldv));
     }
     // ---- a5: [[A11; A21], T_U, W_U] = unpivoted_QR([A11; A21])
@@ -254,19 +279,18 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     phase.emplace(kTrPhasePanel, st);
     LLS_TRY(panel_qr(mp, b, ABR, ldt, tauUi, pws, &ds->barrier_err, st));
     LLS_TRY(copy_upper(b, ABR, ldt, f.Rblk.d() + i * blk, nb, st));
-    LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, b, b, mp, 1.0, ABR, ldt, ABR, ldt, 0.0,
-                  h.S.d(), nb));
+    LLS_TRY(g.ggemm(mp, ABR, ldt, b, h.S.d()));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauUi, TUi, nb, st));
     // ---- a6: [A12; A22] <- (I - W_U T_U W_U^T)^T [A12; A22]
     phase.reset();
     phase.emplace(kTrPhaseLeft, st);
     if (np > b) {
       double* A12 = ABR + b * ldt;
-      LLS_TRY(xgemm(true, false, kUnitLower, kDense, b, np - b, mp, 1.0, ABR, ldt, A12, ldt, 0.0,
+      LLS_TRY(g.xgemm(true, false, kUnitLower, kDense, b, np - b, mp, 1.0, ABR, ldt, A12, ldt, 0.0,
                     h.Q.d(), nb));
-      LLS_TRY(xgemm(true, false, kDense, kDense, b, np - b, b, 1.0, TUi, nb, h.Q.d(), nb, 0.0,
+      LLS_TRY(g.xgemm(true, false, kDense, kDense, b, np - b, b, 1.0, TUi, nb, h.Q.d(), nb, 0.0,
                     h.Q2.d(), nb));
-      LLS_TRY(xgemm(false, false, kUnitLower, kDense, mp, np - b, b, -1.0, ABR, ldt, h.Q2.d(), nb,
+      LLS_TRY(g.xgemm(false, false, kUnitLower, kDense, mp, np - b, b, -1.0, ABR, ldt, h.Q2.d(), nb,
                     1.0, A12, ldt));
     }
   }
@@ -283,12 +307,12 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     const int64_t k = f.ks[i], b = f.bs[i];
     LLS_TRY(set_diag_block(b, f.sigma.d() + i * nb, T + k + k * ldt, ldt, st));
     if (k > 0) {  // A01 <- A01 V_SVD
-      LLS_TRY(xgemm(false, false, kDense, kDense, k, b, b, 1.0, T + k * ldt, ldt,
+      LLS_TRY(g.xgemm(false, false, kDense, kDense, k, b, b, 1.0, T + k * ldt, ldt,
                     f.VS.d() + i * blk, nb, 0.0, h.P.d(), k));
       LLS_TRY(copy_matrix(k, b, h.P.d(), k, T + k * ldt, ldt, st));
     }
     if (f.has_v) {  // V(:, k:k+b) <- V(:, k:k+b) V_SVD (later steps never touch these columns)
-      LLS_TRY(xgemm(false, false, kDense, kDense, n, b, b, 1.0, f.Vx.d() + k * ldv, ldv,
+      LLS_TRY(g.xgemm(false, false, kDense, kDense, n, b, b, 1.0, f.Vx.d() + k * ldv, ldv,
                     f.VS.d() + i * blk, nb, 0.0, h.P.d(), ldv));
       LLS_TRY(copy_matrix(n, b, h.P.d(), ldv, f.Vx.d() + k * ldv, ldv, st));
     }
@@ -297,14 +321,32 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     const int64_t k = f.ks[i], b = f.bs[i], np = n - k;
     if (np > b) {  // A12 <- U_SVD^T A12
       double* A12 = T + k + (k + b) * ldt;
-      LLS_TRY(xgemm(true, false, kDense, kDense, b, np - b, b, 1.0, f.US.d() + i * blk, nb, A12,
+      LLS_TRY(g.xgemm(true, false, kDense, kDense, b, np - b, b, 1.0, f.US.d() + i * blk, nb, A12,
                     ldt, 0.0, h.Q.d(), nb));
       LLS_TRY(copy_matrix(b, np - b, h.Q.d(), nb, A12, ldt, st));
     }
   }
 
-  // ---- a8: Compute_rank
   phase.reset();
+  return finish_factorization(h, f, tol);
+}
+
+// ---------------------------------------------------------------------------
+// a8 Compute_rank and a9 Nullify on a factor whose step loop is done
+// ---------------------------------------------------------------------------
+Status finish_factorization(Handle& h, Factor& f, double tol) {
+  cudaStream_t st = h.stream;
+  const int64_t m = f.m, n = f.n, ldt = f.ldt, mn = std::min(m, n);
+  const int nb = f.nb;
+  const int64_t ldv = std::max<int64_t>(n, 1);
+  double* T = f.T.d();
+  LLS_TRY(h.dstat.reserve(sizeof(DevStatus)));
+  LLS_TRY(h.S.reserve(sizeof(double) * (size_t)nb * nb));
+  FactorGemms g(h, nb);
+  DevStatus* ds = g.ds;
+  Scratch pws = scratch_of(h.panel_ws);
+  std::optional<TraceScope> phase;
+  // ---- a8: Compute_rank
   phase.emplace(kTrPhaseRank, st);
   if (mn > 0) {
     LLS_TRY(resolve_tol(tol, std::max(m, n), T, &ds->tol, st));
@@ -373,13 +415,13 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       double* D0 = Xm + r * ldx;
       LLS_TRY(copy_cols_reversed(rows, bsz, Xm + j0 * ldx, ldx, Xc, rows, st));
       LLS_TRY(copy_matrix(rows, bsz, Xc, rows, h.P.d(), rows, st));
-      if (tc) LLS_TRY(h.oz_ws.reserve(std::max(tc_ws_bytes(rows, bsz, L), tc_ws_bytes(rows, L, bsz))));
-      if (tc) LLS_TRY(h.oz_ws.reserve(tc_ws_bytes(rows, bsz, bsz)));
-      LLS_TRY(xgemm(false, false, kDense, kDense, rows, bsz, L, 1.0, D0, ldx, Wbot, ldm, 1.0,
+      if (g.tc()) LLS_TRY(h.oz_ws.reserve(std::max(g.tc_ws_bytes(rows, bsz, L), g.tc_ws_bytes(rows, L, bsz))));
+      if (g.tc()) LLS_TRY(h.oz_ws.reserve(g.tc_ws_bytes(rows, bsz, bsz)));
+      LLS_TRY(g.xgemm(false, false, kDense, kDense, rows, bsz, L, 1.0, D0, ldx, Wbot, ldm, 1.0,
                     h.P.d(), rows));
-      LLS_TRY(xgemm(false, false, kDense, kDense, rows, bsz, bsz, 1.0, h.P.d(), rows, Tz, bsz, 0.0,
+      LLS_TRY(g.xgemm(false, false, kDense, kDense, rows, bsz, bsz, 1.0, h.P.d(), rows, Tz, bsz, 0.0,
                     h.P2.d(), rows));
-      LLS_TRY(xgemm(false, true, kDense, kDense, rows, L, bsz, -1.0, h.P2.d(), rows, Wbot, ldm, 1.0,
+      LLS_TRY(g.xgemm(false, true, kDense, kDense, rows, L, bsz, -1.0, h.P2.d(), rows, Wbot, ldm, 1.0,
                     D0, ldx));
       // X_rev -= P2 W_top^T with W_top = I, then reversed back into X
       LLS_TRY(axpy_matrix(rows, bsz, -1.0, h.P2.d(), rows, Xc, rows, st));
@@ -393,9 +435,8 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
       double* tz = f.RzTau.d() + bl.off_tau;
       LLS_TRY(rz_gather(bsz, L, T, ldt, j0, r, M, ldm, st));
       LLS_TRY(panel_qr(ldm, bsz, M, ldm, tz, pws, &ds->barrier_err, st));
-      if (tc) LLS_TRY(h.oz_ws.reserve(tc_ws_bytes(bsz, bsz, ldm)));
-      LLS_TRY(xgemm(true, false, kUnitLower, kUnitLower, bsz, bsz, ldm, 1.0, M, ldm, M, ldm, 0.0,
-                    h.S.d(), nb));
+      if (g.tc()) LLS_TRY(h.oz_ws.reserve(g.tc_ws_bytes(bsz, bsz, ldm)));
+      LLS_TRY(g.ggemm(ldm, M, ldm, bsz, h.S.d()));
       LLS_TRY(wy_tfactor(bsz, h.S.d(), nb, tz, Tz, bsz, st));
       LLS_TRY(rz_scatter(bsz, M, ldm, T, ldt, j0, r, L, st));
       // Update(C_01, D_0): the rows of T above the block
@@ -678,6 +719,12 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
                              cudaMemcpyDeviceToHost, st));
     LLS_CUDA(cudaStreamSynchronize(st));
     const double corr = max_correction(norms, nrhs);
+    if (it > 1 && corr > prev) {
+      // growing corrections: the factors are too inaccurate for this matrix
+      // (the iteration does not contract); keep the previous iterate
+      LLS_TRY(axpy_matrix(n, nrhs, -1.0, h.dd.d(), n, X, ldx, st));
+      break;
+    }
     h.refine_steps = it;
     h.refine_corr = corr;
     if (corr <= h.opt.refine_tol) return ok_status();
@@ -728,6 +775,12 @@ Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const d
                              cudaMemcpyDeviceToHost, st));
     LLS_CUDA(cudaStreamSynchronize(st));
     const double corr = max_correction(norms, nrhs);
+    if (it > 1 && corr > prev) {
+      // growing corrections: the factors are too inaccurate for this matrix
+      // (the iteration does not contract); keep the previous iterate
+      LLS_TRY(axpy_matrix(n, nrhs, -1.0, h.dd.d(), n, X, ldx, st));
+      break;
+    }
     h.refine_steps = it;
     h.refine_corr = corr;
     if (corr <= h.opt.refine_tol) return ok_status();

@@ -41,6 +41,7 @@ struct DevBuf {
   bool guarded = false;
   cudaStream_t stream = nullptr;
   bool ordered = false;
+  bool borrowed = false;  // a view into memory owned elsewhere (never freed here)
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
@@ -50,7 +51,20 @@ struct DevBuf {
     stream = s;
     ordered = true;
   }
+  // Points the buffer at `n` bytes owned by someone else (a batch arena).
+  void borrow(void* ptr, size_t n) {
+    release();
+    p = ptr;
+    bytes = n;
+    borrowed = true;
+  }
   void release() {
+    if (borrowed) {
+      p = nullptr;
+      bytes = 0;
+      borrowed = false;
+      return;
+    }
     if (p) {
       if (guarded) {
         cudaDeviceSynchronize();
@@ -69,6 +83,7 @@ struct DevBuf {
   // Grow to at least `need` bytes (contents are not kept).
   Status reserve(size_t need) {
     if (need <= bytes) return ok_status();
+    if (borrowed) return make_error(LLS_ERR_NOMEM, "borrowed buffer smaller than needed");
     release();
     if (need == 0) return ok_status();
     if (injected_alloc_failure())
@@ -192,6 +207,13 @@ struct Handle {
   DevStatus* hstat = nullptr;  // pinned host mirror
   // lls_solve reuses one factor object between calls of the same shape
   std::unique_ptr<Factor> scratch_factor;
+  // batched solves: a factor whose T, W_V and per-step blocks are views into
+  // the parent's batch arena (its own Nullify buffers grow on this stream)
+  std::unique_ptr<Factor> batch_view;
+  // lls_solve_batched: the persistent launch's arena (factors and workspace
+  // of every problem) and its scheduler state; how the batch runs
+  DevBuf batch_arena, batch_meta;
+  int batched_mode = 0;  // LLS_BATCHED_AUTO / _WORKERS / _PERSISTENT
   // resident factors, shared with the worker pool (guarded by factors_mu)
   std::map<int64_t, std::shared_ptr<Factor>> factors;
   int64_t next_factor = 0;
@@ -214,7 +236,7 @@ struct Handle {
   std::vector<DevBuf*> workspace() {
     return {&G,  &Wt, &P,  &P2,  &Q,   &Q2,  &S,   &gemm_ws, &panel_ws,   &bw,   &z,   &sp,   &sp2,
             &xc, &rr, &dd, &nrm, &dstat, &G16, &A16, &A16t,  &Z16,        &F32,  &tc_ws, &mixed_misc,
-            &oz_ws, &rt, &rs};
+            &oz_ws, &rt, &rs, &batch_arena, &batch_meta};
   }
   // Binds the workspace to `stream` (call once the stream is set).
   void bind_workspace() {
@@ -227,6 +249,13 @@ struct Handle {
       scratch_factor->bind(stream);
     }
     return *scratch_factor;
+  }
+  Factor& view() {
+    if (!batch_view) {
+      batch_view.reset(new Factor());
+      batch_view->bind(stream);
+    }
+    return *batch_view;
   }
 };
 
@@ -250,6 +279,11 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
 // max_refine = 0 or neither is there.  Records the steps in h.
 Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const double* B,
                      int64_t nrhs, int64_t ldb, double* X, int64_t ldx);
+// Compute_rank and Nullify (steps a8-a9) on a factor whose step loop and
+// block SVDs are done (f.T, WV, the per-step blocks, ks, bs filled): reads
+// the handle's device status (which must be cleared before the factor's
+// kernels ran), decides the rank against tol and annihilates T_12.
+Status finish_factorization(Handle& h, Factor& f, double tol);
 // Device bytes a factorization of m x n (and a solve with nrhs) will hold.
 size_t factor_bytes(int64_t m, int64_t n, int nb, bool explicit_v = false, bool keep_a = false);
 

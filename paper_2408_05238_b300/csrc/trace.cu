@@ -17,7 +17,7 @@ const char* trace_kind_name(int k) {
                                         "sketch_kernel",     "jacobi_svd_kernel",
                                         "small_kernels",     "bf16_gemm_kernel",
                                         "convert_kernels",   "oz_mma_kernel",
-                                        "tf32_mma_kernel",
+                                        "tf32_mma_kernel",   "batched_factor_kernel",
                                         "phase:sample",      "phase:qr_y",
                                         "phase:right_update", "phase:panel",
                                         "phase:left_update", "phase:block_svd",

@@ -25,6 +25,7 @@ enum TraceKind {
   kTrConvert,      // FP64 -> BF16 conversions and slicing
   kTrOzGemm,       // FP64-accurate GEMM on tensor cores (exact BF16 slices)
   kTrTf32Gemm,     // split-operand TF32 GEMM on tensor cores (3xTF32 / TF32)
+  kTrBatchedFactor,  // persistent batched factorization
   // phases of the method (each spans the kernels above that it launches)
   kTrPhaseSample,   // a1/a2 sketch and sample Y
   kTrPhaseQrY,      // a3 QR of Y and its T factor

@@ -35,6 +35,9 @@ LLS_MIXED_BF16_3xTF32 = 2
 LLS_MIXED_BF16_TF32 = 3
 LLS_FACTOR_T = 0
 LLS_FACTOR_V = 1
+LLS_BATCHED_AUTO = 0
+LLS_BATCHED_WORKERS = 1
+LLS_BATCHED_PERSISTENT = 2
 LLS_OOC_FARTHEST = 0
 LLS_OOC_LRU = 1
 
@@ -114,6 +117,7 @@ _sig("lls_poll", [_H, _I, C.POINTER(C.c_int)])
 _sig("lls_set_memory_cap", [_H, _I])
 _sig("lls_ticket_factor", [_H, _I, C.POINTER(_I)])
 _sig("lls_set_workers", [_H, C.c_int])
+_sig("lls_set_batched_mode", [_H, C.c_int])
 _sig("lls_cancel", [_H, _I])
 _sig("lls_debug_fail_allocation", [_I])
 _sig("lls_debug_barrier_limit", [_I])
@@ -361,6 +365,10 @@ def lls_ticket_factor(h, ticket: int):
 
 def lls_set_workers(h, workers: int):
     _check(h, _lib.lls_set_workers(h, int(workers)))
+
+
+def lls_set_batched_mode(h, mode: int):
+    _check(h, _lib.lls_set_batched_mode(h, int(mode)))
 
 
 def lls_cancel(h, ticket: int) -> int:

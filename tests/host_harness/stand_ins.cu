@@ -18,6 +18,7 @@
 #include <random>
 #include <vector>
 
+#include "batched_factor.h"
 #include "solver.h"
 #include "lls.h"
 
@@ -357,6 +358,73 @@ Status tf32_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, in
                  double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                  double beta, double* C, int64_t ldc, int, Scratch s, int*, cudaStream_t st) {
   return gemm(ta, tb, ma, mb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s, st);
+}
+// The persistent batched factorization, emulated: every problem's phases in
+// the kernel's order with the plain-loop launchers above, writing the
+// problem's buffers as the kernel does (so the driver's arena layout, the
+// factor views and the finishing path run here).
+bool batched_factor_available() { return true; }
+int pb_num_phases(int m, int n, int nb, int q) {
+  return 1 + (int)ceil_div(std::min(m, n), nb) * (8 + 2 * q) + 3;
+}
+size_t pb_workspace_doubles(int64_t m, int64_t n, int nb) {
+  return 4 * (size_t)m * nb + 2 * (size_t)nb * n + (size_t)nb * nb;
+}
+Status batched_factor_launch(const PBArgs& a, cudaStream_t st) {
+  for (int j = 0; j < a.count; ++j) {
+    const PBProblem& p = a.probs[j];
+    const int64_t m = p.m, n = p.n, nb = p.nb, ldt = p.ldt, ldw = p.ldw;
+    const size_t blk = (size_t)nb * nb;
+    LLS_TRY(copy_check(m, n, p.A, p.lda, p.T, ldt, p.flags, st));
+    for (int i = 0; i < p.steps; ++i) {
+      const int64_t k = i * nb, mp = m - k, np = n - k, b = std::min(nb, std::min(mp, np));
+      double* ABR = p.T + k + k * ldt;
+      double* Y = p.WV + k + k * ldw;
+      LLS_TRY(launch_sketch(p.seed, i, mp, b, p.G, m, st));
+      LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, p.G, m, 0.0, Y, ldw, {}, st));
+      for (int it = 0; it < p.q; ++it) {
+        LLS_TRY(gemm(false, false, kDense, kDense, mp, b, np, 1.0, ABR, ldt, Y, ldw, 0.0, p.W, m, {}, st));
+        LLS_TRY(gemm(true, false, kDense, kDense, np, b, mp, 1.0, ABR, ldt, p.W, m, 0.0, Y, ldw, {}, st));
+      }
+      LLS_TRY(panel_qr(np, b, Y, ldw, p.tauV + i * nb, {}, p.flags, st));
+      LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, b, b, np, 1.0, Y, ldw, Y, ldw, 0.0, p.S, nb, {}, st));
+      LLS_TRY(wy_tfactor(b, p.S, nb, p.tauV + i * nb, p.TV + i * blk, nb, st));
+      double* Tk = p.T + k * ldt;
+      LLS_TRY(gemm(false, false, kDense, kUnitLower, m, b, np, 1.0, Tk, ldt, Y, ldw, 0.0, p.P, m, {}, st));
+      LLS_TRY(gemm(false, false, kDense, kDense, m, b, b, 1.0, p.P, m, p.TV + i * blk, nb, 0.0, p.P2, m, {}, st));
+      LLS_TRY(gemm(false, true, kDense, kUnitLower, m, np, b, -1.0, p.P2, m, Y, ldw, 1.0, Tk, ldt, {}, st));
+      LLS_TRY(panel_qr(mp, b, ABR, ldt, p.tauU + i * nb, {}, p.flags, st));
+      LLS_TRY(copy_upper(b, ABR, ldt, p.Rblk + i * blk, nb, st));
+      LLS_TRY(gemm(true, false, kUnitLower, kUnitLower, b, b, mp, 1.0, ABR, ldt, ABR, ldt, 0.0, p.S, nb, {}, st));
+      LLS_TRY(wy_tfactor(b, p.S, nb, p.tauU + i * nb, p.TU + i * blk, nb, st));
+      if (np > b) {
+        double* A12 = ABR + b * ldt;
+        LLS_TRY(gemm(true, false, kUnitLower, kDense, b, np - b, mp, 1.0, ABR, ldt, A12, ldt, 0.0, p.Q, nb, {}, st));
+        LLS_TRY(gemm(true, false, kDense, kDense, b, np - b, b, 1.0, p.TU + i * blk, nb, p.Q, nb, 0.0, p.Q2, nb, {}, st));
+        LLS_TRY(gemm(false, false, kUnitLower, kDense, mp, np - b, b, -1.0, ABR, ldt, p.Q2, nb, 1.0, A12, ldt, {}, st));
+      }
+    }
+    const int64_t bl = std::min(nb, std::min(m, n) - (int64_t)(p.steps - 1) * nb);
+    LLS_TRY(jacobi_svd_batched(p.steps, (int)nb, (int)bl, p.Rblk, nb, blk, p.sigma, nb, p.US, nb, blk,
+                               p.VS, nb, blk, p.flags + 1, st));
+    for (int i = 0; i < p.steps; ++i) {
+      const int64_t k = i * nb, b = std::min(nb, std::min(m - k, n - k));
+      LLS_TRY(set_diag_block(b, p.sigma + i * nb, p.T + k + k * ldt, ldt, st));
+      if (k > 0) {
+        LLS_TRY(gemm(false, false, kDense, kDense, k, b, b, 1.0, p.T + k * ldt, ldt, p.VS + i * blk, nb, 0.0, p.P, k, {}, st));
+        LLS_TRY(copy_matrix(k, b, p.P, k, p.T + k * ldt, ldt, st));
+      }
+    }
+    for (int i = 0; i < p.steps; ++i) {
+      const int64_t k = i * nb, b = std::min(nb, std::min(m - k, n - k)), np = n - k;
+      if (np > b) {
+        double* A12 = p.T + k + (k + b) * ldt;
+        LLS_TRY(gemm(true, false, kDense, kDense, b, np - b, b, 1.0, p.US + i * blk, nb, A12, ldt, 0.0, p.Q, nb, {}, st));
+        LLS_TRY(copy_matrix(b, np - b, p.Q, nb, A12, ldt, st));
+      }
+    }
+  }
+  return ok_status();
 }
 }  // namespace lls
 

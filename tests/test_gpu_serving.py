@@ -292,3 +292,107 @@ def test_batched_on_the_full_size_distribution(lls):
         assert ref.rank == p.rank
         assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-9
         assert orc.normal_equation_residual(p.A, x, p.B, p.norm2) <= 1e-13
+
+
+# ------------------------------------------------------------------ one persistent launch
+def run_batch(lls, ps, mode, workers=6, nb=64, q=1, seed=2004):
+    h = lls.lls_create(nb=nb, q=q, seed=seed)
+    lls.lls_set_workers(h, workers)
+    lls.lls_set_batched_mode(h, mode)
+    keep, plist, ranks = [], [], []
+    try:
+        for p in ps:
+            A, B = dev(p.A), dev(p.B)
+            X = lls.empty_colmajor(p.A.shape[1], p.B.shape[1])
+            r = C.c_int64(-1)
+            ranks.append(r)
+            keep.append((A, B, X))
+            plist.append(lls.make_problem(A, B, p.tol, X, rank_out=C.pointer(r)))
+        code = lls._lib.lls_solve_batched(h, len(plist), (lls.lls_problem * len(plist))(*plist))
+        torch.cuda.synchronize()
+    finally:
+        lls.lls_destroy(h)
+    return code, [k[2].cpu().numpy() for k in keep], [r.value for r in ranks]
+
+
+def mixed_shapes():
+    """Uneven problems: tall, wide, a narrow last step, n < nb, full rank, a
+    zero matrix (rank 0), q's effect through the construction."""
+    ps = problems(14, 31)
+    g = np.random.default_rng(3)
+    for m, n, r in ((90, 300, 40), (333, 47, 47), (64, 64, 64), (700, 129, 100)):
+        A, X, Y = wl.lowrank_xy(m, n, r, seed=m * n + r, noise=1e-14)
+        ps.append(wl.Problem(A, g.standard_normal((m, 3)), 1e-10 * wl.norm2_of_product(X, Y),
+                             wl.norm2_of_product(X, Y), r, 64, 1))
+    Z = np.zeros((120, 80))
+    ps.append(wl.Problem(Z, g.standard_normal((120, 2)), 1e-10, 1.0, 0, 64, 1))
+    return ps
+
+
+@pytest.mark.parametrize("nb,q", [(64, 1), (32, 2), (48, 0)])
+def test_persistent_batched_matches_oracle(lls, nb, q):
+    """All problems factored in one persistent launch: ranks equal the
+    construction's, x matches the oracle's Fig. 4 solve."""
+    ps = mixed_shapes()
+    code, xs, ranks = run_batch(lls, ps, lls.LLS_BATCHED_PERSISTENT, nb=nb, q=q)
+    assert code == 0
+    for p, x, r in zip(ps, xs, ranks):
+        assert r == p.rank
+        ref = orc.solve(p.A, p.B, q, nb, p.tol, 2004)
+        if ref.rank == 0:
+            assert np.all(x == 0.0)
+            continue
+        assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-9
+        assert orc.normal_equation_residual(p.A, x, p.B, p.norm2) <= 1e-13
+
+
+def test_persistent_batched_alone_equals_in_batch_and_workers(lls):
+    """A problem's result does not depend on what else is in the persistent
+    launch (bit for bit: each task sums in a fixed order whatever CTA runs
+    it), and agrees with the worker-pool path to rounding."""
+    ps = mixed_shapes()
+    _, xs, _ = run_batch(lls, ps, lls.LLS_BATCHED_PERSISTENT)
+    _, xw, _ = run_batch(lls, ps, lls.LLS_BATCHED_WORKERS)
+    for i in (0, 5, len(ps) - 2):
+        _, x1, _ = run_batch(lls, [ps[i]], lls.LLS_BATCHED_PERSISTENT)
+        np.testing.assert_array_equal(x1[0], xs[i])
+    for p, a, b in zip(ps, xs, xw):
+        if p.rank:
+            assert np.linalg.norm(a - b) / np.linalg.norm(b) <= 1e-11
+
+
+def test_persistent_batched_reports_bad_problems_and_refusals(lls):
+    ps = problems(6, 41)
+    bad = wl.Problem(ps[2].A.copy(), ps[2].B, ps[2].tol, ps[2].norm2, ps[2].rank, 64, 1)
+    bad.A[3, 1] = np.nan
+    code, xs, ranks = run_batch(lls, ps[:2] + [bad] + ps[3:], lls.LLS_BATCHED_PERSISTENT)
+    assert code == lls.LLS_ERR_NONFINITE
+    for i in (0, 1, 3):
+        ref = orc.solve(ps[i].A, ps[i].B, 1, 64, ps[i].tol, 2004)
+        assert np.linalg.norm(xs[i] - ref.x) / np.linalg.norm(ref.x) <= 1e-9
+    # outside the persistent path (explicit V): refused in PERSISTENT mode
+    h = lls.lls_create(nb=64, q=1, seed=2004, explicit_v=1)
+    try:
+        lls.lls_set_batched_mode(h, lls.LLS_BATCHED_PERSISTENT)
+        p = ps[0]
+        A, B = dev(p.A), dev(p.B)
+        X = lls.empty_colmajor(p.A.shape[1], p.B.shape[1])
+        arr = (lls.lls_problem * 1)(lls.make_problem(A, B, p.tol, X))
+        assert lls._lib.lls_solve_batched(h, 1, arr) == lls.LLS_ERR_ARG
+    finally:
+        lls.lls_destroy(h)
+
+
+def test_persistent_batched_scheduler_wait_runs_out(lls):
+    """With the poll limit at zero, a CTA that finds no ready task gives up at
+    once: the launch ends with LLS_ERR_TIMEOUT (no hang, no fault) and the
+    next batch on a fresh handle solves."""
+    ps = problems(8, 51)
+    lls.lls_debug_barrier_limit(0)
+    try:
+        code, _, _ = run_batch(lls, ps, lls.LLS_BATCHED_PERSISTENT)
+    finally:
+        lls.lls_debug_barrier_limit(-1)
+    assert code == lls.LLS_ERR_TIMEOUT
+    code, xs, ranks = run_batch(lls, ps, lls.LLS_BATCHED_PERSISTENT)
+    assert code == 0 and ranks == [p.rank for p in ps]

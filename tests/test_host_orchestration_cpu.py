@@ -55,6 +55,7 @@ def harness():
         "lls_refinement_info": [H, C.POINTER(C.c_int32), C.POINTER(D)],
         "lls_solve_batched": [H, I, C.POINTER(binding.lls_problem)],
         "lls_set_workers": [H, C.c_int],
+        "lls_set_batched_mode": [H, C.c_int],
         "lls_set_memory_cap": [H, I],
         "lls_submit": [H, C.POINTER(binding.lls_problem), C.POINTER(I)],
         "lls_poll": [H, I, C.POINTER(C.c_int)],
@@ -217,12 +218,17 @@ def test_factor_reuse_export_and_refinement(harness, sketch):
     assert np.all(T[:r, r:] == 0.0) and np.all(np.tril(T, -1) == 0.0)
 
 
-def test_batched_pool_equals_alone(harness, sketch):
-    """Problems solved by the worker pool (three host threads) are
-    bit-identical to the same problems solved alone, and match the oracle."""
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batched_pool_equals_alone(harness, sketch, mode):
+    """Problems solved as a batch are bit-identical to the same problems
+    solved alone, and match the oracle: through the persistent launch's
+    driver (mode 0 picks it for these FP64 problems, mode 2 asks for it; the
+    kernel itself is emulated here by the plain-loop launchers in its phase
+    order) and through the worker pool (mode 1, three host threads)."""
     probs = [gap_problem(m, n, r, seed=s) for (m, n, r, s) in
              [(40, 30, 10, 1), (30, 45, 12, 2), (50, 50, 20, 3), (25, 12, 12, 4), (33, 33, 5, 5)]]
     h = create(harness, nb=8, q=1, seed=77)
+    assert harness.lls_set_batched_mode(h, mode) == 0
     try:
         alone = []
         for A, B, tol in probs:
@@ -387,3 +393,30 @@ def test_host_entry_point_and_phase_trace(harness, sketch):
     assert phases["phase:left_update"] == steps
     assert phases["phase:block_svd"] == phases["phase:rank"] == 1
     assert phases["phase:nullify"] == 1 and phases["phase:solve"] == 1
+
+
+def test_persistent_batched_mode_refuses_what_it_cannot_take(harness, sketch):
+    """LLS_BATCHED_PERSISTENT with an option the persistent path does not take
+    (explicit V) returns LLS_ERR_ARG naming argument 3; AUTO falls back to
+    the worker pool for the same batch; a mode outside 0..2 is refused."""
+    A, B, tol = gap_problem(30, 20, 8, seed=9)
+    h = create(harness, nb=8, q=1, seed=77, explicit_v=1)
+    try:
+        assert harness.lls_set_batched_mode(h, 3) == -1
+        Af, Bf, X = F(A), F(B), np.zeros((20, 2), order="F")
+        arr = (harness.binding.lls_problem * 1)()
+        p = arr[0]
+        p.A, p.m, p.n, p.lda = Af.ctypes.data, 30, 20, 30
+        p.B, p.nrhs, p.ldb = Bf.ctypes.data, 2, 30
+        p.tol, p.X, p.ldx, p.factor_id = tol, X.ctypes.data, 20, -1
+        assert harness.lls_set_batched_mode(h, 2) == 0
+        assert harness.lls_solve_batched(h, 1, arr) == -1
+        arg = C.c_int(0)
+        harness.lls_last_error(h, C.byref(arg), None, 0)
+        assert arg.value == 3
+        assert harness.lls_set_batched_mode(h, 0) == 0
+        assert harness.lls_solve_batched(h, 1, arr) == 0 and arr[0].status == 0
+        ref = orc.solve(A, B, 1, 8, tol, 77)
+        assert np.linalg.norm(X - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    finally:
+        harness.lls_destroy(h)
