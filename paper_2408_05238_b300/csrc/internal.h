@@ -108,6 +108,17 @@ Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, c
 // Rank scan with a device tolerance.
 Status rank_scan_dev(int64_t len, const double* T, int64_t ldt, const double* tol_dev,
                      int64_t* out, cudaStream_t st);
+// reflector_thin.cu: block reflectors applied to at most kThinMaxRhs vectors.
+constexpr int kThinMaxRhs = 16;
+size_t thin_scratch_bytes(int64_t M, int64_t b, int64_t nrhs);
+// x (M x nrhs) <- (I - W op(T) W^T) x, W M x b unit lower trapezoidal (ld
+// ldw), T b x b upper triangular, op(T) = T^T when transT; b <= 128.
+Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W, int64_t ldw,
+                             const double* T, int64_t ldt, bool transT, double* x, int64_t ldx,
+                             Scratch scratch, cudaStream_t st);
+// x(0:b, :) <- op(S) x(0:b, :) for a b x b block S (b <= 128).
+Status small_block_mul(int64_t b, int64_t nrhs, const double* S, int64_t lds, bool transS,
+                       double* x, int64_t ldx, cudaStream_t st);
 // Gap at the rank of a diagonal d (len entries, contiguous): out (device,
 // 2 doubles) = {min_{j < r} |d_j|, max_{j >= r} |d_j|}.
 Status diag_gap(int64_t len, const double* d, int64_t r, double* out, cudaStream_t st);

@@ -497,9 +497,17 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   LLS_TRY(copy_check(m, nrhs, B, ldb, Bw, m, &ds->nonfinite, st));
 
   // c = U^T b, one step at a time
+  const bool thin = nrhs <= kThinMaxRhs;
+  if (thin) LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(m, n), nb, nrhs)));
   for (size_t i = 0; i < f.ks.size(); ++i) {
     const int64_t k = f.ks[i], b = f.bs[i], mp = m - k;
     const double* WU = T + k + k * ldt;
+    if (thin) {  // b(k:m) <- (I - W_U T_U^T W_U^T) b(k:m); b(k:k+b) <- U_SVD^T b(k:k+b)
+      LLS_TRY(apply_reflectors_thin(mp, b, nrhs, WU, ldt, f.TU.d() + i * blk, nb, true, Bw + k, m,
+                                    scratch_of(h.gemm_ws), st));
+      LLS_TRY(small_block_mul(b, nrhs, f.US.d() + i * blk, nb, true, Bw + k, m, st));
+      continue;
+    }
     LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, mp, 1.0, WU, ldt, Bw + k, m, 0.0, p, nb));
     LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TU.d() + i * blk, nb, p, nb, 0.0,
                  p2, nb));
@@ -541,9 +549,16 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
     }
   }
   // x = V z, last step first
+  if (thin) LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(m, n), nb, nrhs)));
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii], np = n - k;
     const double* WVi = f.WV.d() + k + k * ldw;
+    if (thin) {  // z(k:k+b) <- V_SVD z(k:k+b); z(k:n) <- (I - W_V T_V W_V^T) z(k:n)
+      LLS_TRY(small_block_mul(b, nrhs, f.VS.d() + ii * blk, nb, false, Z + k, ldw, st));
+      LLS_TRY(apply_reflectors_thin(np, b, nrhs, WVi, ldw, f.TV.d() + ii * blk, nb, false, Z + k, ldw,
+                                    scratch_of(h.gemm_ws), st));
+      continue;
+    }
     LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.VS.d() + ii * blk, nb, Z + k, ldw,
                  0.0, p, nb));
     LLS_TRY(copy_matrix(b, nrhs, p, nb, Z + k, ldw, st));
@@ -591,6 +606,8 @@ Status apply_solve_transpose(Handle& h, Factor& f, const double* S, int64_t lds,
   double* p = h.sp.d();
   double* p2 = h.sp2.d();
   const double* T = f.T.d();
+  const bool thin = nrhs <= kThinMaxRhs;
+  if (thin) LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(m, n), nb, nrhs)));
   if (f.has_v) {  // z(0:r) = V(:, 0:r)^T S, V with Nullify's reflectors included
     LLS_TRY(fgemm(true, false, kDense, kDense, r, nrhs, n, 1.0, f.Vx.d(), ldw, S, lds, 0.0, Z, ldw));
   } else {
@@ -598,6 +615,12 @@ Status apply_solve_transpose(Handle& h, Factor& f, const double* S, int64_t lds,
     for (size_t i = 0; i < f.ks.size(); ++i) {
       const int64_t k = f.ks[i], b = f.bs[i], np = n - k;
       const double* WVi = f.WV.d() + k + k * ldw;
+      if (thin) {  // z(k:n) <- (I - W_V T_V^T W_V^T) z(k:n); z(k:k+b) <- V_SVD^T z(k:k+b)
+        LLS_TRY(apply_reflectors_thin(np, b, nrhs, WVi, ldw, f.TV.d() + i * blk, nb, true, Z + k, ldw,
+                                      scratch_of(h.gemm_ws), st));
+        LLS_TRY(small_block_mul(b, nrhs, f.VS.d() + i * blk, nb, true, Z + k, ldw, st));
+        continue;
+      }
       LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, np, 1.0, WVi, ldw, Z + k, ldw, 0.0, p,
                     nb));
       LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TV.d() + i * blk, nb, p, nb, 0.0,
@@ -637,6 +660,12 @@ Status apply_solve_transpose(Handle& h, Factor& f, const double* S, int64_t lds,
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii], mp = m - k;
     const double* WU = T + k + k * ldt;
+    if (thin) {  // w(k:k+b) <- U_SVD w(k:k+b); w(k:m) <- (I - W_U T_U W_U^T) w(k:m)
+      LLS_TRY(small_block_mul(b, nrhs, f.US.d() + ii * blk, nb, false, out + k, ldo, st));
+      LLS_TRY(apply_reflectors_thin(mp, b, nrhs, WU, ldt, f.TU.d() + ii * blk, nb, false, out + k, ldo,
+                                    scratch_of(h.gemm_ws), st));
+      continue;
+    }
     LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.US.d() + ii * blk, nb, out + k, ldo,
                   0.0, p, nb));
     LLS_TRY(copy_matrix(b, nrhs, p, nb, out + k, ldo, st));

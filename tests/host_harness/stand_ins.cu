@@ -336,6 +336,38 @@ Status diag_gap(int64_t len, const double* d, int64_t r, double* out, cudaStream
   out[1] = mx;
   return ok_status();
 }
+size_t thin_scratch_bytes(int64_t, int64_t, int64_t) { return 0; }
+// x <- (I - W op(T) W^T) x with unit lower W, plainly.
+Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W, int64_t ldw,
+                             const double* T, int64_t ldt, bool transT, double* x, int64_t ldx,
+                             Scratch, cudaStream_t) {
+  auto w = [&](int64_t r, int64_t j) { return r < j ? 0.0 : (r == j ? 1.0 : W[r + j * ldw]); };
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double* xc = x + c * ldx;
+    std::vector<double> p((size_t)b, 0.0), p2((size_t)b, 0.0);
+    for (int64_t j = 0; j < b; ++j)
+      for (int64_t r = 0; r < M; ++r) p[j] += w(r, j) * xc[r];
+    for (int64_t i = 0; i < b; ++i)
+      for (int64_t l = 0; l < b; ++l) {
+        const double t = transT ? (l <= i ? T[l + i * ldt] : 0.0) : (l >= i ? T[i + l * ldt] : 0.0);
+        p2[i] += t * p[l];
+      }
+    for (int64_t r = 0; r < M; ++r)
+      for (int64_t j = 0; j < b; ++j) xc[r] -= w(r, j) * p2[j];
+  }
+  return ok_status();
+}
+Status small_block_mul(int64_t b, int64_t nrhs, const double* S, int64_t lds, bool transS,
+                       double* x, int64_t ldx, cudaStream_t) {
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double* xc = x + c * ldx;
+    std::vector<double> y((size_t)b, 0.0);
+    for (int64_t i = 0; i < b; ++i)
+      for (int64_t l = 0; l < b; ++l) y[i] += (transS ? S[l + i * lds] : S[i + l * lds]) * xc[l];
+    for (int64_t i = 0; i < b; ++i) xc[i] = y[i];
+  }
+  return ok_status();
+}
 size_t trsm_upper_trans_scratch_bytes(int64_t, int64_t) { return 0; }
 // R^T Y = B by forward substitution, one column at a time.
 Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
