@@ -25,9 +25,11 @@ arXiv 2408.05238, Sec. 3):
 * ``refine``       -- iterative refinement of a solution with the solve
                       operator P = V_1 T_11^{-1} U_1^T of Fig. 4:
                       x <- x + P (b - A x), the residual in FP64.
-* ``refine_min_norm`` -- refinement from 0 with M = A^T P^T P P^T A^T, whose
-                      fixed point is the minimum-norm least-squares solution
-                      even when the factors are only approximate.
+* ``refine_min_norm`` -- two-stage refinement (least squares with the right
+                      preconditioner V_1 T_11^{-1}, then the projection onto
+                      range(A^T)) whose fixed point is the minimum-norm
+                      least-squares solution even when the factors are only
+                      approximate.
 * ``pinv_solve``   -- Sec. 2.2 truncated-SVD least squares, used as the
                       brute-force pin on small inputs.
 
@@ -451,48 +453,51 @@ MIN_NORM_GAP = 1e-2
 
 def refine_min_norm(A: np.ndarray, B: np.ndarray, sol: Solution, steps: int = 1) -> np.ndarray:
     """Refinement that also restores the minimum-norm property when the
-    factors are only approximate (the TF32 update modes): from x_0 = 0,
+    factors are only approximate (the TF32 update modes), in two stages of
+    ``steps`` iterations each, with the residuals and the products with A in
+    FP64 and the factors of ``sol`` (``solve(..., keep=True)``):
 
-        x_{k+1} = x_k + M (b - A x_k),   M = A^T P^T P P^T A^T,
+    1. least squares: with N = V_1 T_11^{-1}, from x = P b (P = N U_1^T),
+           x <- x + N N^T A^T (b - A x).
+       In z with x = N z this is z <- z + K^T (b - K z) for K = A N, which
+       equals U_1 up to the factors' error times the condition number of
+       T_11, so it contracts by about that much per step (not by its
+       square); its fixed point has V_1^T A^T r = 0, i.e. r orthogonal to
+       range(A V_1) = range(A): a least-squares solution x_ls.
+    2. minimum norm: with L = A^T U_1 T_11^{-T} (V_1 up to the same error),
+       from x = 0,
+           x <- x + L L^T (x_ls - x),
+       whose fixed point is the orthogonal projection of x_ls onto
+       range(L) = range(A^T): the minimum-norm least-squares solution.
+    For exact factors of a rank-r matrix one step of each stage gives the
+    pseudoinverse solution.
 
-    with P = V_1 T_11^{-1} U_1^T the solve operator of the factors of ``sol``
-    (``solve(..., keep=True)``) and the residual and the products with A in
-    FP64.  For exact factors of a rank-r matrix P = A^+ and M = A^+ (as
-    (A A^T)^+ = (A^+)^T A^+): one step from 0 gives the pseudoinverse
-    solution.  For approximate factors every correction lies in range(A^T)
-    (the leading A^T) and M annihilates every residual orthogonal to
-    range(A) (the trailing A^T), so the fixed point is the minimum-norm
-    least-squares solution itself -- not merely the solution within
-    range(V_1) that ``refine`` converges to -- and the iteration contracts
-    by about the relative error of P A on range(A^T).
-
-    The fixed point is the truncated solution only when A is of numerical
-    rank r: its singular values beyond the rank enter M through A (by about
-    sigma_{r+1} / sigma_r).  So, as the library does, the diagonal blocks'
-    singular values (``sol.diag``, before Nullify) are checked first: when
-    the largest dropped one exceeds MIN_NORM_GAP times the smallest kept one
-    there is no gap at the rank, and ``sol.x`` is returned unrefined."""
+    The fixed points are the truncated solution only when A is of numerical
+    rank r (its singular values beyond the rank enter through A).  So, as
+    the library does, the diagonal blocks' singular values (``sol.diag``,
+    before Nullify) are checked first: when the largest dropped one exceeds
+    MIN_NORM_GAP times the smallest kept one there is no gap at the rank, and
+    ``sol.x`` is returned unrefined."""
     if sol.utv is None:
         raise ValueError("refine_min_norm needs solve(..., keep=True)")
     A = np.asarray(A, dtype=np.float64)
     Bm = np.asarray(B, dtype=np.float64).reshape(A.shape[0], -1)
     r = sol.rank
     U, T, V = sol.utv.U, sol.utv.T, sol.utv.V
-    x = np.zeros((A.shape[1], Bm.shape[1]))
     if r == 0:
-        return x.reshape(np.shape(sol.x))
+        return np.zeros_like(np.asarray(sol.x, dtype=np.float64))
     if r < sol.diag.size and sol.diag[r:].max() > MIN_NORM_GAP * sol.diag[:r].min():
         return np.array(sol.x, dtype=np.float64)
-
-    def apply_p(R):   # V_1 T_11^{-1} U_1^T R
-        return V[:, :r] @ _back_substitution(T[:r, :r], U[:, :r].T @ R)
-
-    def apply_pt(S):  # U_1 T_11^{-T} V_1^T S
-        return U[:, :r] @ _forward_substitution_transposed(T[:r, :r], V[:, :r].T @ S)
-
-    for _ in range(steps):
-        res = Bm - A @ x
-        x = x + A.T @ apply_pt(apply_p(apply_pt(A.T @ res)))
+    T11, U1, V1 = T[:r, :r], U[:, :r], V[:, :r]
+    x = np.array(sol.x, dtype=np.float64).reshape(A.shape[1], -1)
+    for _ in range(steps):           # stage 1: least squares in range(V_1)
+        s = V1.T @ (A.T @ (Bm - A @ x))
+        x = x + V1 @ _back_substitution(T11, _forward_substitution_transposed(T11, s))
+    x_ls = x
+    x = np.zeros_like(x_ls)
+    for _ in range(steps):           # stage 2: projection onto range(A^T)
+        e = _back_substitution(T11, U1.T @ (A @ (x_ls - x)))
+        x = x + A.T @ (U1 @ _forward_substitution_transposed(T11, e))
     return x.reshape(np.shape(sol.x))
 
 

@@ -455,228 +455,176 @@ Status finish_factorization(Handle& h, Factor& f, double tol) {
 }
 
 // ---------------------------------------------------------------------------
-// a10: x = V (T_tl^{-1} (U^T b))
+// a10: x = V (T_tl^{-1} (U^T b)), from four replays of the stored factors
+// (U^T, U, V^T, V), which the refinement of the TF32 modes uses as well.
 // ---------------------------------------------------------------------------
+namespace {
+
+// FP64 GEMM on the handle's stream with its split-K scratch grown to the
+// shape's plan first.
+Status hgemm(Handle& h, bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
+             int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
+             int64_t ldb_, double beta, double* Cc, int64_t ldc_) {
+  LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
+  return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
+              scratch_of(h.gemm_ws), h.stream);
+}
+
+// Buffers of one replay: two nb x nrhs panels and the thin path's scratch.
+Status reserve_replay(Handle& h, Factor& f, int64_t nrhs) {
+  LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)f.nb * nrhs));
+  LLS_TRY(h.sp2.reserve(sizeof(double) * (size_t)f.nb * nrhs));
+  LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)f.nb * nrhs));
+  if (nrhs <= kThinMaxRhs)
+    LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(f.m, f.n), f.nb, nrhs)));
+  return ok_status();
+}
+
+// One step's reflector block applied to x (M x nrhs): x <- (I - W op(T) W^T) x.
+Status step_reflect(Handle& h, int64_t M, int64_t b, int64_t nrhs, const double* W, int64_t ldw_,
+                    const double* T, int nb, bool transT, double* x, int64_t ldx) {
+  if (nrhs <= kThinMaxRhs)
+    return apply_reflectors_thin(M, b, nrhs, W, ldw_, T, nb, transT, x, ldx, scratch_of(h.gemm_ws),
+                                 h.stream);
+  double* p = h.sp.d();
+  double* p2 = h.sp2.d();
+  LLS_TRY(hgemm(h, true, false, kUnitLower, kDense, b, nrhs, M, 1.0, W, ldw_, x, ldx, 0.0, p, nb));
+  LLS_TRY(hgemm(h, transT, false, kDense, kDense, b, nrhs, b, 1.0, T, nb, p, nb, 0.0, p2, nb));
+  return hgemm(h, false, false, kUnitLower, kDense, M, nrhs, b, -1.0, W, ldw_, p2, nb, 1.0, x, ldx);
+}
+
+// x(0:b) <- op(S) x(0:b) for one step's b x b singular-vector block.
+Status step_small(Handle& h, int64_t b, int64_t nrhs, const double* S, int nb, bool transS, double* x,
+                  int64_t ldx) {
+  if (nrhs <= kThinMaxRhs) return small_block_mul(b, nrhs, S, nb, transS, x, ldx, h.stream);
+  LLS_TRY(hgemm(h, transS, false, kDense, kDense, b, nrhs, b, 1.0, S, nb, x, ldx, 0.0, h.sp.d(), nb));
+  return copy_matrix(b, nrhs, h.sp.d(), nb, x, ldx, h.stream);
+}
+
+// One Nullify row block's reflectors applied to z (n x nrhs) in its
+// coordinates [rows j0..j0+bsz reversed; rows r..n]: z <- (I - W op(T_z) W^T) z
+// with W = [I; W_bot] (Fig. 3's Update, written as a QR of the reversed block).
+Status nullify_block(Handle& h, Factor& f, const Factor::RzBlock& bl, int64_t nrhs, bool transT,
+                     double* Z, int64_t ldz) {
+  cudaStream_t st = h.stream;
+  const int64_t r = f.rank, L = f.n - r, j0 = bl.j0, bsz = bl.bsz, ldm = bsz + L;
+  const double* M = f.RzM.d() + bl.off_m;
+  const double* Tz = f.RzT.d() + bl.off_t;
+  double* zc = h.xc.d();
+  double* p = h.sp.d();
+  double* p2 = h.sp2.d();
+  LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldz, zc, bsz, st));
+  LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
+  LLS_TRY(hgemm(h, true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldz, 1.0, p,
+                bsz));
+  LLS_TRY(hgemm(h, transT, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2, bsz));
+  LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p2, bsz, zc, bsz, st));  // W_top = I
+  LLS_TRY(hgemm(h, false, false, kDense, kDense, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0,
+                Z + r, ldz));
+  return copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldz, st);
+}
+
+}  // namespace
+
+// c (m x nrhs) <- U^T c = U_SVD,s^T H_s^T ... U_SVD,0^T H_0^T c (first step first).
+Status apply_ut(Handle& h, Factor& f, double* c, int64_t ldc, int64_t nrhs) {
+  const size_t blk = (size_t)f.nb * f.nb;
+  LLS_TRY(reserve_replay(h, f, nrhs));
+  for (size_t i = 0; i < f.ks.size(); ++i) {
+    const int64_t k = f.ks[i], b = f.bs[i];
+    LLS_TRY(step_reflect(h, f.m - k, b, nrhs, f.T.d() + k + k * f.ldt, f.ldt, f.TU.d() + i * blk, f.nb,
+                         true, c + k, ldc));
+    LLS_TRY(step_small(h, b, nrhs, f.US.d() + i * blk, f.nb, true, c + k, ldc));
+  }
+  return ok_status();
+}
+
+// w (m x nrhs) <- U w = H_0 U_SVD,0 ... H_s U_SVD,s w (last step first).
+Status apply_u(Handle& h, Factor& f, double* w, int64_t ldw_, int64_t nrhs) {
+  const size_t blk = (size_t)f.nb * f.nb;
+  LLS_TRY(reserve_replay(h, f, nrhs));
+  for (size_t ii = f.ks.size(); ii-- > 0;) {
+    const int64_t k = f.ks[ii], b = f.bs[ii];
+    LLS_TRY(step_small(h, b, nrhs, f.US.d() + ii * blk, f.nb, false, w + k, ldw_));
+    LLS_TRY(step_reflect(h, f.m - k, b, nrhs, f.T.d() + k + k * f.ldt, f.ldt, f.TU.d() + ii * blk, f.nb,
+                         false, w + k, ldw_));
+  }
+  return ok_status();
+}
+
+// z (n x nrhs) <- V z; rows kz..n of z are zero (kz = r for [y; 0]), which an
+// explicit V uses.  V = H_0 V_SVD,0 ... H_s V_SVD,s Z_0 ... Z_last with the
+// Nullify blocks Z in processing order: the last block first, then the steps
+// last first.
+Status apply_v(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs, int64_t kz) {
+  const int64_t n = f.n, ldv = std::max<int64_t>(n, 1);
+  const size_t blk = (size_t)f.nb * f.nb;
+  LLS_TRY(reserve_replay(h, f, nrhs));
+  if (f.has_v) {  // V with Nullify's reflectors included
+    LLS_TRY(h.z2.reserve(sizeof(double) * (size_t)n * nrhs));
+    LLS_TRY(hgemm(h, false, false, kDense, kDense, n, nrhs, kz, 1.0, f.Vx.d(), ldv, z, ldz, 0.0,
+                  h.z2.d(), ldv));
+    return copy_matrix(n, nrhs, h.z2.d(), ldv, z, ldz, h.stream);
+  }
+  if (f.nullified)
+    for (auto it = f.rz.rbegin(); it != f.rz.rend(); ++it)
+      LLS_TRY(nullify_block(h, f, *it, nrhs, false, z, ldz));
+  for (size_t ii = f.ks.size(); ii-- > 0;) {
+    const int64_t k = f.ks[ii], b = f.bs[ii];
+    LLS_TRY(step_small(h, b, nrhs, f.VS.d() + ii * blk, f.nb, false, z + k, ldz));
+    LLS_TRY(step_reflect(h, n - k, b, nrhs, f.WV.d() + k + k * ldv, ldv, f.TV.d() + ii * blk, f.nb,
+                         false, z + k, ldz));
+  }
+  return ok_status();
+}
+
+// z (n x nrhs) <- V^T z (the steps first step first, then the Nullify blocks
+// in processing order, each transposed).
+Status apply_vt(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs) {
+  const int64_t n = f.n, ldv = std::max<int64_t>(n, 1);
+  const size_t blk = (size_t)f.nb * f.nb;
+  LLS_TRY(reserve_replay(h, f, nrhs));
+  if (f.has_v) {
+    LLS_TRY(h.z2.reserve(sizeof(double) * (size_t)n * nrhs));
+    LLS_TRY(hgemm(h, true, false, kDense, kDense, n, nrhs, n, 1.0, f.Vx.d(), ldv, z, ldz, 0.0,
+                  h.z2.d(), ldv));
+    return copy_matrix(n, nrhs, h.z2.d(), ldv, z, ldz, h.stream);
+  }
+  for (size_t i = 0; i < f.ks.size(); ++i) {
+    const int64_t k = f.ks[i], b = f.bs[i];
+    LLS_TRY(step_reflect(h, n - k, b, nrhs, f.WV.d() + k + k * ldv, ldv, f.TV.d() + i * blk, f.nb, true,
+                         z + k, ldz));
+    LLS_TRY(step_small(h, b, nrhs, f.VS.d() + i * blk, f.nb, true, z + k, ldz));
+  }
+  if (f.nullified)
+    for (const auto& bl : f.rz) LLS_TRY(nullify_block(h, f, bl, nrhs, true, z, ldz));
+  return ok_status();
+}
+
 Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64_t ldb, double* X,
                       int64_t ldx) {
   cudaStream_t st = h.stream;
   const int64_t m = f.m, n = f.n, ldt = f.ldt, ldw = std::max<int64_t>(n, 1);
-  const int nb = f.nb;
-  const size_t blk = (size_t)nb * nb;
   const int64_t r = f.rank;
   if (n == 0 || nrhs == 0) return ok_status();
   if (r == 0 || m == 0) return fill_zero(n, nrhs, X, ldx, st);
   TraceScope solve_phase(kTrPhaseSolve, st);
   LLS_TRY(h.bw.reserve(sizeof(double) * (size_t)m * nrhs));
   LLS_TRY(h.z.reserve(sizeof(double) * (size_t)n * nrhs));
-  LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)nb * nrhs));
-  LLS_TRY(h.sp2.reserve(sizeof(double) * (size_t)nb * nrhs));
   LLS_TRY(h.dstat.reserve(sizeof(DevStatus)));
-  size_t gneed = 0;
-  for (size_t i = 0; i < f.ks.size(); ++i) {
-    gneed = std::max(gneed, gemm_scratch_bytes(f.bs[i], nrhs, m - f.ks[i]));
-    gneed = std::max(gneed, gemm_scratch_bytes(f.bs[i], nrhs, n - f.ks[i]));
-  }
-  gneed = std::max(gneed, gemm_scratch_bytes(nb, nrhs, n));
-  gneed = std::max(gneed, gemm_scratch_bytes(r, nrhs, nb));
-  LLS_TRY(h.gemm_ws.reserve(gneed));
-  auto fgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
-                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
-                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
-    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
-    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
-                scratch_of(h.gemm_ws), st);
-  };
   DevStatus* ds = h.dstat.as<DevStatus>();
   double* Bw = h.bw.d();
   double* Z = h.z.d();
-  double* p = h.sp.d();
-  double* p2 = h.sp2.d();
-  const double* T = f.T.d();
   LLS_CUDA(cudaMemsetAsync(&ds->nonfinite, 0, sizeof(int), st));
   LLS_TRY(copy_check(m, nrhs, B, ldb, Bw, m, &ds->nonfinite, st));
-
-  // c = U^T b, one step at a time
-  const bool thin = nrhs <= kThinMaxRhs;
-  if (thin) LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(m, n), nb, nrhs)));
-  for (size_t i = 0; i < f.ks.size(); ++i) {
-    const int64_t k = f.ks[i], b = f.bs[i], mp = m - k;
-    const double* WU = T + k + k * ldt;
-    if (thin) {  // b(k:m) <- (I - W_U T_U^T W_U^T) b(k:m); b(k:k+b) <- U_SVD^T b(k:k+b)
-      LLS_TRY(apply_reflectors_thin(mp, b, nrhs, WU, ldt, f.TU.d() + i * blk, nb, true, Bw + k, m,
-                                    scratch_of(h.gemm_ws), st));
-      LLS_TRY(small_block_mul(b, nrhs, f.US.d() + i * blk, nb, true, Bw + k, m, st));
-      continue;
-    }
-    LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, mp, 1.0, WU, ldt, Bw + k, m, 0.0, p, nb));
-    LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TU.d() + i * blk, nb, p, nb, 0.0,
-                 p2, nb));
-    LLS_TRY(fgemm(false, false, kUnitLower, kDense, mp, nrhs, b, -1.0, WU, ldt, p2, nb, 1.0, Bw + k,
-                 m));
-    LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.US.d() + i * blk, nb, Bw + k, m,
-                 0.0, p, nb));
-    LLS_TRY(copy_matrix(b, nrhs, p, nb, Bw + k, m, st));
-  }
-  // y = T_tl^{-1} c
+  LLS_TRY(apply_ut(h, f, Bw, m, nrhs));  // c = U^T b
   LLS_TRY(h.gemm_ws.reserve(trsm_upper_scratch_bytes(r, nrhs)));
-  LLS_TRY(trsm_upper(r, nrhs, T, ldt, Bw, m, scratch_of(h.gemm_ws), st));
-  if (f.has_v) {  // x = V(:, 0:r) y, V with Nullify's reflectors included
-    LLS_TRY(fgemm(false, false, kDense, kDense, n, nrhs, r, 1.0, f.Vx.d(), ldw, Bw, m, 0.0, X,
-                  ldx));
-    return read_nonfinite_flag(h, ds);
-  }
-  // z = [y; 0]
-  LLS_TRY(copy_matrix(r, nrhs, Bw, m, Z, ldw, st));
+  LLS_TRY(trsm_upper(r, nrhs, f.T.d(), ldt, Bw, m, scratch_of(h.gemm_ws), st));  // y = T_tl^{-1} c
+  LLS_TRY(copy_matrix(r, nrhs, Bw, m, Z, ldw, st));                              // z = [y; 0]
   if (r < n) LLS_TRY(fill_zero(n - r, nrhs, Z + r, ldw, st));
-  // Nullify reflectors, last processed block first
-  if (f.nullified) {
-    const int64_t L = n - r;
-    LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)nb * nrhs));
-    double* zc = h.xc.d();
-    for (auto it = f.rz.rbegin(); it != f.rz.rend(); ++it) {
-      const int64_t j0 = it->j0, bsz = it->bsz, ldm = bsz + L;
-      const double* M = f.RzM.d() + it->off_m;
-      const double* Tz = f.RzT.d() + it->off_t;
-      LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldw, zc, bsz, st));
-      LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
-      LLS_TRY(fgemm(true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldw, 1.0, p,
-                   bsz));
-      LLS_TRY(fgemm(false, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2, bsz));
-      LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p2, bsz, zc, bsz, st));  // W_top = I
-      LLS_TRY(fgemm(false, false, kDense, kDense, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0,
-                   Z + r, ldw));
-      LLS_TRY(copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldw, st));
-    }
-  }
-  // x = V z, last step first
-  if (thin) LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(m, n), nb, nrhs)));
-  for (size_t ii = f.ks.size(); ii-- > 0;) {
-    const int64_t k = f.ks[ii], b = f.bs[ii], np = n - k;
-    const double* WVi = f.WV.d() + k + k * ldw;
-    if (thin) {  // z(k:k+b) <- V_SVD z(k:k+b); z(k:n) <- (I - W_V T_V W_V^T) z(k:n)
-      LLS_TRY(small_block_mul(b, nrhs, f.VS.d() + ii * blk, nb, false, Z + k, ldw, st));
-      LLS_TRY(apply_reflectors_thin(np, b, nrhs, WVi, ldw, f.TV.d() + ii * blk, nb, false, Z + k, ldw,
-                                    scratch_of(h.gemm_ws), st));
-      continue;
-    }
-    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.VS.d() + ii * blk, nb, Z + k, ldw,
-                 0.0, p, nb));
-    LLS_TRY(copy_matrix(b, nrhs, p, nb, Z + k, ldw, st));
-    LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, np, 1.0, WVi, ldw, Z + k, ldw, 0.0, p,
-                 nb));
-    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.TV.d() + ii * blk, nb, p, nb, 0.0,
-                 p2, nb));
-    LLS_TRY(fgemm(false, false, kUnitLower, kDense, np, nrhs, b, -1.0, WVi, ldw, p2, nb, 1.0, Z + k,
-                 ldw));
-  }
+  LLS_TRY(apply_v(h, f, Z, ldw, nrhs, r));                                        // x = V z
   LLS_TRY(copy_matrix(n, nrhs, Z, ldw, X, ldx, st));
   return read_nonfinite_flag(h, ds);
-}
-
-// ---------------------------------------------------------------------------
-// out (m x nrhs) = P^T S = U_1 T_11^{-T} V_1^T S for S (n x nrhs): the
-// transpose of the solve operator of Fig. 4, replayed from the factors in the
-// opposite order to solve_factored -- V^T (each step's reflectors with T_V^T,
-// then V_SVD^T, first step first), Nullify's reflectors with their T factors
-// transposed (first block processed first), a forward substitution with
-// T_11^T, then U = H_0 U_SVD,0 H_1 U_SVD,1 ... applied to [y; 0] last step
-// first.  S must not be the handle's z buffer.
-// ---------------------------------------------------------------------------
-Status apply_solve_transpose(Handle& h, Factor& f, const double* S, int64_t lds, int64_t nrhs,
-                             double* out, int64_t ldo) {
-  cudaStream_t st = h.stream;
-  const int64_t m = f.m, n = f.n, ldt = f.ldt, ldw = std::max<int64_t>(n, 1);
-  const int nb = f.nb;
-  const size_t blk = (size_t)nb * nb;
-  const int64_t r = f.rank;
-  if (m == 0 || nrhs == 0) return ok_status();
-  if (r == 0 || n == 0) return fill_zero(m, nrhs, out, ldo, st);
-  LLS_TRY(h.z.reserve(sizeof(double) * (size_t)n * nrhs));
-  LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)nb * nrhs));
-  LLS_TRY(h.sp2.reserve(sizeof(double) * (size_t)nb * nrhs));
-  LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)nb * nrhs));
-  auto fgemm = [&](bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t mm, int64_t nn,
-                   int64_t kk, double alpha, const double* Aa, int64_t lda_, const double* Bb,
-                   int64_t ldb_, double beta, double* Cc, int64_t ldc_) -> Status {
-    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(mm, nn, kk)));
-    return gemm(ta, tb, ma, mb, mm, nn, kk, alpha, Aa, lda_, Bb, ldb_, beta, Cc, ldc_,
-                scratch_of(h.gemm_ws), st);
-  };
-  double* Z = h.z.d();
-  double* p = h.sp.d();
-  double* p2 = h.sp2.d();
-  const double* T = f.T.d();
-  const bool thin = nrhs <= kThinMaxRhs;
-  if (thin) LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(m, n), nb, nrhs)));
-  if (f.has_v) {  // z(0:r) = V(:, 0:r)^T S, V with Nullify's reflectors included
-    LLS_TRY(fgemm(true, false, kDense, kDense, r, nrhs, n, 1.0, f.Vx.d(), ldw, S, lds, 0.0, Z, ldw));
-  } else {
-    LLS_TRY(copy_matrix(n, nrhs, S, lds, Z, ldw, st));
-    for (size_t i = 0; i < f.ks.size(); ++i) {
-      const int64_t k = f.ks[i], b = f.bs[i], np = n - k;
-      const double* WVi = f.WV.d() + k + k * ldw;
-      if (thin) {  // z(k:n) <- (I - W_V T_V^T W_V^T) z(k:n); z(k:k+b) <- V_SVD^T z(k:k+b)
-        LLS_TRY(apply_reflectors_thin(np, b, nrhs, WVi, ldw, f.TV.d() + i * blk, nb, true, Z + k, ldw,
-                                      scratch_of(h.gemm_ws), st));
-        LLS_TRY(small_block_mul(b, nrhs, f.VS.d() + i * blk, nb, true, Z + k, ldw, st));
-        continue;
-      }
-      LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, np, 1.0, WVi, ldw, Z + k, ldw, 0.0, p,
-                    nb));
-      LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.TV.d() + i * blk, nb, p, nb, 0.0,
-                    p2, nb));
-      LLS_TRY(fgemm(false, false, kUnitLower, kDense, np, nrhs, b, -1.0, WVi, ldw, p2, nb, 1.0, Z + k,
-                    ldw));
-      LLS_TRY(fgemm(true, false, kDense, kDense, b, nrhs, b, 1.0, f.VS.d() + i * blk, nb, Z + k, ldw,
-                    0.0, p, nb));
-      LLS_TRY(copy_matrix(b, nrhs, p, nb, Z + k, ldw, st));
-    }
-    if (f.nullified) {
-      const int64_t L = n - r;
-      double* zc = h.xc.d();
-      for (const auto& bl : f.rz) {
-        const int64_t j0 = bl.j0, bsz = bl.bsz, ldm = bsz + L;
-        const double* M = f.RzM.d() + bl.off_m;
-        const double* Tz = f.RzT.d() + bl.off_t;
-        LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldw, zc, bsz, st));
-        LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
-        LLS_TRY(fgemm(true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldw, 1.0,
-                      p, bsz));
-        LLS_TRY(fgemm(true, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2,
-                      bsz));
-        LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p2, bsz, zc, bsz, st));  // W_top = I
-        LLS_TRY(fgemm(false, false, kDense, kDense, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0,
-                      Z + r, ldw));
-        LLS_TRY(copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldw, st));
-      }
-    }
-  }
-  // y = T_11^{-T} z(0:r)
-  LLS_TRY(h.gemm_ws.reserve(trsm_upper_trans_scratch_bytes(r, nrhs)));
-  LLS_TRY(trsm_upper_trans(r, nrhs, T, ldt, Z, ldw, scratch_of(h.gemm_ws), st));
-  // out = U [y; 0], last step first
-  LLS_TRY(copy_matrix(r, nrhs, Z, ldw, out, ldo, st));
-  if (r < m) LLS_TRY(fill_zero(m - r, nrhs, out + r, ldo, st));
-  for (size_t ii = f.ks.size(); ii-- > 0;) {
-    const int64_t k = f.ks[ii], b = f.bs[ii], mp = m - k;
-    const double* WU = T + k + k * ldt;
-    if (thin) {  // w(k:k+b) <- U_SVD w(k:k+b); w(k:m) <- (I - W_U T_U W_U^T) w(k:m)
-      LLS_TRY(small_block_mul(b, nrhs, f.US.d() + ii * blk, nb, false, out + k, ldo, st));
-      LLS_TRY(apply_reflectors_thin(mp, b, nrhs, WU, ldt, f.TU.d() + ii * blk, nb, false, out + k, ldo,
-                                    scratch_of(h.gemm_ws), st));
-      continue;
-    }
-    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.US.d() + ii * blk, nb, out + k, ldo,
-                  0.0, p, nb));
-    LLS_TRY(copy_matrix(b, nrhs, p, nb, out + k, ldo, st));
-    LLS_TRY(fgemm(true, false, kUnitLower, kDense, b, nrhs, mp, 1.0, WU, ldt, out + k, ldo, 0.0, p,
-                  nb));
-    LLS_TRY(fgemm(false, false, kDense, kDense, b, nrhs, b, 1.0, f.TU.d() + ii * blk, nb, p, nb, 0.0,
-                  p2, nb));
-    LLS_TRY(fgemm(false, false, kUnitLower, kDense, mp, nrhs, b, -1.0, WU, ldt, p2, nb, 1.0, out + k,
-                  ldo));
-  }
-  return ok_status();
 }
 
 namespace {
@@ -697,24 +645,49 @@ double max_correction(const std::vector<double>& norms, int64_t nrhs) {
 // diagonal blocks above which the minimum-norm refinement is not applied.
 constexpr double kMinNormGap = 1e-2;
 
-// The refinement of the TF32 modes, whose factors carry the TF32 split's
-// errors (range(V_1) is then off the row space by about that error times
-// the condition number of T_11, which x <- x + P r cannot repair): from
-// x_0 = 0, x <- x + A^T P^T P P^T A^T (b - A x).  Every correction is A^T
-// times something, so x stays in range(A^T); M = A^T P^T P P^T A^T equals
-// A^+ for exact factors and annihilates residuals orthogonal to range(A), so
-// for a matrix of numerical rank r the fixed point is the minimum-norm
-// least-squares solution.  Without a gap at the rank (singular values
-// beyond it comparable to the kept ones) A itself is not of rank r, M
-// differs from P by about sigma_{r+1} / sigma_r and the fixed point from the
-// truncated solution P b: the diagonal blocks' singular values are checked
-// first and, without a gap of kMinNormGap, x = P b is kept (warning).
+// x += D (n x nrhs), then the last correction's size: returns -1 when it
+// grew over `prev` (the correction is undone: the iteration does not
+// contract for these factors), else the correction.
+Status add_correction(Handle& h, int64_t n, int64_t nrhs, const double* D, double* X, int64_t ldx,
+                      double prev, bool first, double* corr) {
+  cudaStream_t st = h.stream;
+  std::vector<double> norms(2 * (size_t)nrhs);
+  LLS_TRY(refine_update(n, nrhs, D, n, X, ldx, h.nrm.d(), st));
+  LLS_CUDA(cudaMemcpyAsync(norms.data(), h.nrm.d(), sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost,
+                           st));
+  LLS_CUDA(cudaStreamSynchronize(st));
+  *corr = max_correction(norms, nrhs);
+  if (!first && *corr > prev) {
+    LLS_TRY(axpy_matrix(n, nrhs, -1.0, D, n, X, ldx, st));
+    *corr = -1.0;
+  }
+  return ok_status();
+}
+
+// The refinement of the TF32 modes.  Their factors carry the TF32 split's
+// errors, so range(V_1) is off the row space by about that error times the
+// condition number kappa of T_11: x <- x + P r then converges to a solution
+// in the tilted range(V_1), and a one-stage x <- x + A^T P^T P P^T A^T r
+// carries P P^T ~ (A^T A)^+ and contracts only when kappa^2 eps < 1.  Two
+// stages that need only kappa eps < 1:
+//  1. least squares: x <- x + N N^T A^T (b - A x), N = V_1 T_11^{-1}, from
+//     x = P b.  In z (x = N z) it is z <- z + K^T (b - K z) with K = A N
+//     = U_1 up to kappa eps; its fixed point has r orthogonal to
+//     range(A V_1) = range(A).
+//  2. minimum norm: x <- x + L L^T (x_ls - x), L = A^T U_1 T_11^{-T}, from
+//     x = 0: the fixed point is x_ls projected onto range(L) = range(A^T).
+// For a matrix of numerical rank r that is the minimum-norm least-squares
+// solution.  Without a gap at the rank (singular values beyond it
+// comparable to the kept ones) A itself is not of rank r and the fixed
+// points leave the truncated solution P b: the diagonal blocks' singular
+// values are checked first and, without a gap of kMinNormGap, x = P b is
+// kept (warning).
 Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const double* B,
                        int64_t nrhs, int64_t ldb, double* X, int64_t ldx) {
   cudaStream_t st = h.stream;
-  const int64_t m = f.m, n = f.n;
+  const int64_t m = f.m, n = f.n, r = f.rank, ldt = f.ldt;
   LLS_TRY(h.nrm.reserve(sizeof(double) * std::max<int64_t>(2 * nrhs, 2)));
-  LLS_TRY(diag_gap(std::min(m, n), f.sigma.d(), f.rank, h.nrm.d(), st));
+  LLS_TRY(diag_gap(std::min(m, n), f.sigma.d(), r, h.nrm.d(), st));
   double gap[2];
   LLS_CUDA(cudaMemcpyAsync(gap, h.nrm.d(), sizeof(gap), cudaMemcpyDeviceToHost, st));
   LLS_CUDA(cudaStreamSynchronize(st));
@@ -723,44 +696,71 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
                       "no gap at the rank (largest dropped / smallest kept singular value " +
                           std::to_string(gap[1] / gap[0]) + "): refinement not applied");
   LLS_TRY(h.rr.reserve(sizeof(double) * (size_t)m * nrhs));
-  LLS_TRY(h.rt.reserve(sizeof(double) * (size_t)m * nrhs));
   LLS_TRY(h.rs.reserve(sizeof(double) * (size_t)n * nrhs));
   LLS_TRY(h.dd.reserve(sizeof(double) * (size_t)n * nrhs));
-  LLS_TRY(h.nrm.reserve(sizeof(double) * 2 * (size_t)nrhs));
-  LLS_TRY(h.gemm_ws.reserve(std::max(gemm_scratch_bytes(m, nrhs, n), gemm_scratch_bytes(n, nrhs, m))));
-  std::vector<double> norms(2 * (size_t)nrhs);
-  LLS_TRY(fill_zero(n, nrhs, X, ldx, st));
-  double prev = 0.0;
-  for (int it = 1; it <= h.opt.max_refine; ++it) {
-    LLS_TRY(copy_matrix(m, nrhs, B, ldb, h.rr.d(), m, st));  // r = b - A x
-    LLS_TRY(gemm(false, false, kDense, kDense, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, h.rr.d(), m,
-                 scratch_of(h.gemm_ws), st));
-    LLS_TRY(gemm(true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, h.rr.d(), m, 0.0, h.rs.d(), n,
-                 scratch_of(h.gemm_ws), st));                   // A^T r
-    LLS_TRY(apply_solve_transpose(h, f, h.rs.d(), n, nrhs, h.rt.d(), m));   // P^T A^T r
-    LLS_TRY(solve_factored(h, f, h.rt.d(), nrhs, m, h.dd.d(), n));        // P P^T A^T r
-    LLS_TRY(apply_solve_transpose(h, f, h.dd.d(), n, nrhs, h.rt.d(), m));   // P^T P P^T A^T r
-    LLS_TRY(h.gemm_ws.reserve(gemm_scratch_bytes(n, nrhs, m)));
-    LLS_TRY(gemm(true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, h.rt.d(), m, 0.0, h.dd.d(), n,
-                 scratch_of(h.gemm_ws), st));                   // dx = A^T (...)
-    LLS_TRY(refine_update(n, nrhs, h.dd.d(), n, X, ldx, h.nrm.d(), st));
-    LLS_CUDA(cudaMemcpyAsync(norms.data(), h.nrm.d(), sizeof(double) * 2 * nrhs,
-                             cudaMemcpyDeviceToHost, st));
-    LLS_CUDA(cudaStreamSynchronize(st));
-    const double corr = max_correction(norms, nrhs);
-    if (it > 1 && corr > prev) {
-      // growing corrections: the factors are too inaccurate for this matrix
-      // (the iteration does not contract); keep the previous iterate
-      LLS_TRY(axpy_matrix(n, nrhs, -1.0, h.dd.d(), n, X, ldx, st));
-      break;
+  LLS_TRY(h.z2.reserve(sizeof(double) * (size_t)n * nrhs));
+  LLS_TRY(h.gemm_ws.reserve(std::max(trsm_upper_scratch_bytes(r, nrhs),
+                                     trsm_upper_trans_scratch_bytes(r, nrhs))));
+  double* rr = h.rr.d();
+  double* rs = h.rs.d();
+  double* dd = h.dd.d();
+  double* xls = h.z2.d();
+  auto trsm_both = [&](double* y, int64_t ldy, bool trans_first) -> Status {
+    LLS_TRY(h.gemm_ws.reserve(std::max(trsm_upper_scratch_bytes(r, nrhs),
+                                       trsm_upper_trans_scratch_bytes(r, nrhs))));
+    if (trans_first) LLS_TRY(trsm_upper_trans(r, nrhs, f.T.d(), ldt, y, ldy, scratch_of(h.gemm_ws), st));
+    LLS_TRY(trsm_upper(r, nrhs, f.T.d(), ldt, y, ldy, scratch_of(h.gemm_ws), st));
+    if (!trans_first) LLS_TRY(trsm_upper_trans(r, nrhs, f.T.d(), ldt, y, ldy, scratch_of(h.gemm_ws), st));
+    return ok_status();
+  };
+  int steps = 0;
+  double corr = 0.0;
+  bool converged[2] = {false, false};
+  for (int stage = 0; stage < 2; ++stage) {
+    if (stage == 1) {  // x_ls = x; x = 0
+      LLS_TRY(copy_matrix(n, nrhs, X, ldx, xls, n, st));
+      LLS_TRY(fill_zero(n, nrhs, X, ldx, st));
     }
-    h.refine_steps = it;
-    h.refine_corr = corr;
-    if (corr <= h.opt.refine_tol) return ok_status();
-    if (it > 1 && corr > 0.5 * prev) break;  // no longer contracting: rounding floor
-    prev = corr;
+    double prev = 0.0;
+    for (int it = 1; it <= h.opt.max_refine; ++it) {
+      double* D;
+      if (stage == 0) {  // dx = V [T_11^{-1} T_11^{-T} (V^T A^T (b - A x))(0:r); 0]
+        LLS_TRY(copy_matrix(m, nrhs, B, ldb, rr, m, st));
+        LLS_TRY(hgemm(h, false, false, kDense, kDense, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, rr, m));
+        LLS_TRY(hgemm(h, true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, rr, m, 0.0, rs, n));
+        LLS_TRY(apply_vt(h, f, rs, n, nrhs));
+        LLS_TRY(trsm_both(rs, n, true));
+        if (r < n) LLS_TRY(fill_zero(n - r, nrhs, rs + r, n, st));
+        LLS_TRY(apply_v(h, f, rs, n, nrhs, r));
+        D = rs;
+      } else {  // dx = A^T U [T_11^{-T} T_11^{-1} (U^T A (x_ls - x))(0:r); 0]
+        LLS_TRY(copy_matrix(n, nrhs, xls, n, rs, n, st));
+        LLS_TRY(axpy_matrix(n, nrhs, -1.0, X, ldx, rs, n, st));
+        LLS_TRY(hgemm(h, false, false, kDense, kDense, m, nrhs, n, 1.0, A, lda, rs, n, 0.0, rr, m));
+        LLS_TRY(apply_ut(h, f, rr, m, nrhs));
+        LLS_TRY(trsm_both(rr, m, false));
+        if (r < m) LLS_TRY(fill_zero(m - r, nrhs, rr + r, m, st));
+        LLS_TRY(apply_u(h, f, rr, m, nrhs));
+        LLS_TRY(hgemm(h, true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, rr, m, 0.0, dd, n));
+        D = dd;
+      }
+      double c = 0.0;
+      LLS_TRY(add_correction(h, n, nrhs, D, X, ldx, prev, it == 1, &c));
+      if (c < 0.0) break;  // grew: undone
+      ++steps;
+      corr = c;
+      if (c <= h.opt.refine_tol) {
+        converged[stage] = true;
+        break;
+      }
+      if (it > 1 && c > 0.5 * prev) break;  // no longer contracting: rounding floor
+      prev = c;
+    }
   }
-  return make_error(LLS_WARN_REFINE_NOCONV, "refinement correction " + std::to_string(h.refine_corr) +
+  h.refine_steps = steps;
+  h.refine_corr = corr;
+  if (converged[0] && converged[1]) return ok_status();
+  return make_error(LLS_WARN_REFINE_NOCONV, "refinement correction " + std::to_string(corr) +
                                                 " above refine_tol");
 }
 

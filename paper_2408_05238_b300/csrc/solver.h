@@ -193,9 +193,9 @@ struct Handle {
   // iterative refinement: residual, correction, per-column norms; what the
   // last refined solve did (lls_refinement_info)
   DevBuf rr, dd, nrm;
-  // the minimum-norm refinement of the TF32 modes: P^T products (m x nrhs)
-  // and A^T products (n x nrhs)
-  DevBuf rt, rs;
+  // the minimum-norm refinement of the TF32 modes: n x nrhs products and
+  // the least-squares solution of its first stage
+  DevBuf rs, z2;
   int refine_steps = 0;
   double refine_corr = 0.0;
   DevBuf dstat;           // DevStatus
@@ -236,7 +236,7 @@ struct Handle {
   std::vector<DevBuf*> workspace() {
     return {&G,  &Wt, &P,  &P2,  &Q,   &Q2,  &S,   &gemm_ws, &panel_ws,   &bw,   &z,   &sp,   &sp2,
             &xc, &rr, &dd, &nrm, &dstat, &G16, &A16, &A16t,  &Z16,        &F32,  &tc_ws, &mixed_misc,
-            &oz_ws, &rt, &rs, &batch_arena, &batch_meta};
+            &oz_ws, &rs, &z2, &batch_arena, &batch_meta};
   }
   // Binds the workspace to `stream` (call once the stream is set).
   void bind_workspace() {
@@ -284,6 +284,13 @@ Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const d
 // the handle's device status (which must be cleared before the factor's
 // kernels ran), decides the rank against tol and annihilates T_12.
 Status finish_factorization(Handle& h, Factor& f, double tol);
+// The solve's replays of the stored factors on nrhs columns, in place:
+// c (m rows) <- U^T c, w (m rows) <- U w, z (n rows) <- V^T z, and
+// z (n rows) <- V z where rows kz.. of z are zero.
+Status apply_ut(Handle& h, Factor& f, double* c, int64_t ldc, int64_t nrhs);
+Status apply_u(Handle& h, Factor& f, double* w, int64_t ldw, int64_t nrhs);
+Status apply_vt(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs);
+Status apply_v(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs, int64_t kz);
 // Device bytes a factorization of m x n (and a solve with nrhs) will hold.
 size_t factor_bytes(int64_t m, int64_t n, int nb, bool explicit_v = false, bool keep_a = false);
 
