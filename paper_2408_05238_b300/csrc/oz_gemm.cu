@@ -50,7 +50,9 @@ constexpr int OZ_BK = 64;         // K per smem tile (128-byte swizzle rows)
 constexpr int OZ_KC = 256;        // K per CTA: keeps every FP32 sum below 2^24
 constexpr int OZ_XST = 5;         // X-tile ring depth (one slice of one K tile each)
 constexpr int OZ_ZST = 2;         // Z ring depth (all 8 slices of one K tile each)
-constexpr int OZ_THREADS = 512;  // 16 warps: all run the epilogue
+constexpr int OZ_EPI_WARP0 = 2;  // warps 0 (TMA) and 1 (MMA issue), then the epilogue
+constexpr int OZ_EPI_WARPS = 16;
+constexpr int OZ_THREADS = (OZ_EPI_WARP0 + OZ_EPI_WARPS) * 32;
 constexpr uint32_t OZ_XBYTES = OZ_BM * OZ_BK * 2;         // 16 KB
 constexpr uint32_t OZ_ZTILE = OZ_BN * OZ_BK * 2;          // 8 KB
 constexpr uint32_t OZ_ZBYTES = OZ_ZTILE * OZ_S;           // 64 KB
@@ -266,6 +268,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -369,6 +374,7 @@ __device__ __noinline__ double slow_scaled(long long v, int p) {
 
 struct OzArgs {
   int M, N, K, kchunk;
+  int tiles_n, splits, items;  // work items: (row tile, column tile, K range)
   const int* expX;   // per output row (M)
   const int* expZ;   // per output column (N)
   double alpha, beta;
@@ -379,6 +385,12 @@ struct OzArgs {
   int* err;
 };
 
+// Persistent: one CTA per SM loops over (row tile, column tile, K range)
+// items.  The 8 diagonal accumulators fill all of tensor memory, so the
+// epilogue warps first drain them into exact int64 registers (H and L
+// folded into one v per output) and release tensor memory at once; the FP64
+// assembly, the loads of C and the stores then run while the MMAs of the
+// next item fill tensor memory again.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_mma_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapZ,
                   OzArgs a) {
@@ -388,16 +400,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   unsigned char* xring = smem;                       // OZ_XST x 16 KB
   unsigned char* zring = smem + OZ_XST * OZ_XBYTES;  // OZ_ZST x 64 KB
   __shared__ __align__(8) uint64_t xfull[OZ_XST], xempty[OZ_XST], zfull[OZ_ZST], zempty[OZ_ZST];
-  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ __align__(8) uint64_t tfull, tempty;
   __shared__ uint32_t s_tmem;
 
-  __shared__ int s_ex[OZ_BM], s_fz[OZ_BN];
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * OZ_BM, n0 = blockIdx.y * OZ_BN;
-  const int kbeg = blockIdx.z * a.kchunk;
-  const int kend = min(a.K, kbeg + a.kchunk);
-  const int nkb = (kend - kbeg + OZ_BK - 1) / OZ_BK;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < OZ_XST; ++i) {
@@ -408,7 +414,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(&zfull[i], 1);
       mbar_init(&zempty[i], 1);
     }
-    mbar_init(&done_bar, 1);
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, OZ_EPI_WARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -422,142 +429,154 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
+  auto item_coords = [&](int item, int& m0, int& n0, int& kbeg, int& nkb) {
+    const int ks = item % a.splits, t = item / a.splits;
+    m0 = (t / a.tiles_n) * OZ_BM;
+    n0 = (t % a.tiles_n) * OZ_BN;
+    kbeg = ks * a.kchunk;
+    nkb = (min(a.K, kbeg + a.kchunk) - kbeg + OZ_BK - 1) / OZ_BK;
+  };
+
   if (warp == 0 && lane == 0) {
     // ---- producer: per K tile, the 8 Z slices at once, then the 8 X slices
-    int it = 0;
+    uint32_t itx = 0, itz = 0;
     bool ok = true;
-    for (int kb = 0; kb < nkb && ok; ++kb) {
-      const int k = kbeg + kb * OZ_BK;
-      const int zs = kb % OZ_ZST;
-      if (kb >= OZ_ZST && !mbar_wait_spin(&zempty[zs], ((kb / OZ_ZST) - 1) & 1, a.err)) {
-        ok = false;
-        break;
-      }
-      mbar_expect_tx(&zfull[zs], OZ_ZBYTES);
-      tma_load_3d(zring + zs * OZ_ZBYTES, &mapZ, &zfull[zs], k, n0, 0);
-      for (int s = 0; s < OZ_S; ++s, ++it) {
-        const int xs = it % OZ_XST;
-        if (it >= OZ_XST && !mbar_wait_spin(&xempty[xs], ((it / OZ_XST) - 1) & 1, a.err)) {
+    for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
+      int m0, n0, kbeg, nkb;
+      item_coords(item, m0, n0, kbeg, nkb);
+      for (int kb = 0; kb < nkb && ok; ++kb, ++itz) {
+        const int k = kbeg + kb * OZ_BK;
+        const int zs = itz % OZ_ZST;
+        if (itz >= (uint32_t)OZ_ZST && !mbar_wait_spin(&zempty[zs], ((itz / OZ_ZST) - 1) & 1, a.err)) {
           ok = false;
           break;
         }
-        mbar_expect_tx(&xfull[xs], OZ_XBYTES);
-        tma_load_3d(xring + xs * OZ_XBYTES, &mapX, &xfull[xs], k, m0, s);
+        mbar_expect_tx(&zfull[zs], OZ_ZBYTES);
+        tma_load_3d(zring + zs * OZ_ZBYTES, &mapZ, &zfull[zs], k, n0, 0);
+        for (int s = 0; s < OZ_S; ++s, ++itx) {
+          const int xs = itx % OZ_XST;
+          if (itx >= (uint32_t)OZ_XST &&
+              !mbar_wait_spin(&xempty[xs], ((itx / OZ_XST) - 1) & 1, a.err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&xfull[xs], OZ_XBYTES);
+          tma_load_3d(xring + xs * OZ_XBYTES, &mapX, &xfull[xs], k, m0, s);
+        }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: diagonal d = s + t (0-based) accumulates X_s^T Z_t
-    int it = 0;
+    uint32_t itx = 0, itz = 0;
     bool ok = true;
-    for (int kb = 0; kb < nkb && ok; ++kb) {
-      const int zs = kb % OZ_ZST;
-      if (!mbar_wait_spin(&zfull[zs], (kb / OZ_ZST) & 1, a.err)) {
+    int li = 0;
+    for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x, ++li) {
+      int m0, n0, kbeg, nkb;
+      item_coords(item, m0, n0, kbeg, nkb);
+      // the epilogue of the previous item has drained tensor memory
+      if (li >= 1 && !mbar_wait_spin(&tempty, (li - 1) & 1, a.err)) {
         ok = false;
         break;
       }
-      // Fully unrolled issue: descriptors differ only in their start-address
-      // field, so each MMA is one add and the instruction (a rolled loop with
-      // per-MMA descriptor arithmetic left the tensor pipe ~40% idle).
-      const uint64_t zdesc = sdesc_sw128(smem_u32(zring + zs * OZ_ZBYTES));
-#pragma unroll
-      for (int s = 0; s < OZ_S; ++s) {
-        const int xs = it % OZ_XST;
-        if (!mbar_wait_spin(&xfull[xs], (it / OZ_XST) & 1, a.err)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int kb = 0; kb < nkb && ok; ++kb, ++itz) {
+        const int zs = itz % OZ_ZST;
+        if (!mbar_wait_spin(&zfull[zs], (itz / OZ_ZST) & 1, a.err)) {
           ok = false;
           break;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t xdesc = sdesc_sw128(smem_u32(xring + xs * OZ_XBYTES));
-        const uint32_t acc0 = (kb == 0 && s == 0) ? 0u : 1u;
+        // Fully unrolled issue: descriptors differ only in their start-address
+        // field, so each MMA is one add and the instruction (a rolled loop with
+        // per-MMA descriptor arithmetic left the tensor pipe ~40% idle).
+        const uint64_t zdesc = sdesc_sw128(smem_u32(zring + zs * OZ_ZBYTES));
 #pragma unroll
-        for (int t = 0; t < OZ_S - s; ++t) {
+        for (int s = 0; s < OZ_S; ++s, ++itx) {
+          const int xs = itx % OZ_XST;
+          if (!mbar_wait_spin(&xfull[xs], (itx / OZ_XST) & 1, a.err)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t xdesc = sdesc_sw128(smem_u32(xring + xs * OZ_XBYTES));
+          const uint32_t acc0 = (kb == 0 && s == 0) ? 0u : 1u;
 #pragma unroll
-          for (int kk = 0; kk < OZ_BK / 16; ++kk)
-            mma_bf16(tmem + (uint32_t)((s + t) * OZ_BN), xdesc + (uint64_t)((kk * 32) >> 4),
-                     zdesc + (uint64_t)((t * OZ_ZTILE + kk * 32) >> 4), kk == 0 ? acc0 : 1u);
+          for (int t = 0; t < OZ_S - s; ++t) {
+#pragma unroll
+            for (int kk = 0; kk < OZ_BK / 16; ++kk)
+              mma_bf16(tmem + (uint32_t)((s + t) * OZ_BN), xdesc + (uint64_t)((kk * 32) >> 4),
+                       zdesc + (uint64_t)((t * OZ_ZTILE + kk * 32) >> 4), kk == 0 ? acc0 : 1u);
+          }
+          mma_commit(&xempty[xs]);
         }
-        mma_commit(&xempty[xs]);
-        ++it;
+        if (ok) mma_commit(&zempty[zs]);
       }
-      if (ok) mma_commit(&zempty[zs]);
+      if (ok) mma_commit(&tfull);
     }
-    if (ok) mma_commit(&done_bar);
-  } else if (warp >= 2) {
-    // exponents of this tile's rows and columns, staged while the MMAs run
-    for (int t = threadIdx.x - 64; t < OZ_BM + OZ_BN; t += OZ_THREADS - 64) {
-      if (t < OZ_BM) s_ex[t] = (m0 + t < a.M) ? a.expX[m0 + t] : kZeroExp;
-      else s_fz[t - OZ_BM] = (n0 + t - OZ_BM < a.N) ? a.expZ[n0 + t - OZ_BM] : kZeroExp;
-    }
-  }
-
-  // ---- epilogue: exact integers -> FP64.  Warp w reads TMEM lanes
-  // 32 (w mod 4) .. +31 (its rows) and the 16 columns 16 (w / 4) .. +15, in
-  // two passes of 8.  The C values it updates are loaded first, while the
-  // tensor cores still work.
-  const int q = warp & 3;
-  const int il = q * 32 + lane;
-  const int i = m0 + il;
-  const bool row_ok = i < a.M;
-  const int cl0 = (warp >> 2) * 16;
-  const bool use_c = a.part == nullptr && a.beta != 0.0;
-  double cv[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int j = n0 + cl0 + c;
-    cv[c] = 0.0;
-    if (use_c && row_ok && j < a.N)
-      cv[c] = a.transC ? a.C[j + (int64_t)i * a.ldc] : a.C[i + (int64_t)j * a.ldc];
-  }
-  __syncwarp();
-  bool ready = nkb > 0 && mbar_wait(&done_bar, 0, a.err);
-  ready = __all_sync(0xffffffffu, ready);
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ready) {  // warp-uniform: the TMEM loads below are .sync.aligned
-    const int ei = s_ex[il];
+  } else if (warp >= OZ_EPI_WARP0) {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows)
+    // and the 16 columns 16 ((w - 2) / 4) .. +15, in two passes of 8
+    const int q = warp & 3;
+    const int cl0 = ((warp - OZ_EPI_WARP0) >> 2) * 16;
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
     const int bmode = a.part ? 3 : (a.beta == 0.0 ? 0 : (a.beta == 1.0 ? 1 : 2));
     const double alpha = a.alpha, beta = a.beta;
-    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    int li = 0;
+    for (int item = blockIdx.x; item < a.items; item += gridDim.x, ++li) {
+      int m0, n0, kbeg, nkb;
+      item_coords(item, m0, n0, kbeg, nkb);
+      bool ready = nkb > 0 && mbar_wait(&tfull, li & 1, a.err);
+      ready = __all_sync(0xffffffffu, ready);
+      if (!ready) break;  // warp-uniform: the TMEM loads below are .sync.aligned
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      long long V[16];
 #pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-      const int cl = cl0 + pass * 8;  // first column of this pass within the tile
-      const int jb = n0 + cl;
-      long long V[8];
-      __syncwarp();
+      for (int pass = 0; pass < 2; ++pass) {
+        const int cl = cl0 + pass * 8;
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        uint32_t r[4][8];
+        for (int half = 0; half < 2; ++half) {
+          uint32_t r[4][8];
 #pragma unroll
-        for (int d = 0; d < 4; ++d) tmem_ld8(trow + (uint32_t)((half * 4 + d) * OZ_BN + cl), r[d]);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int d = 0; d < 4; ++d) tmem_ld8(trow + (uint32_t)((half * 4 + d) * OZ_BN + cl), r[d]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          // |acc| <= 10.5e6 < 2^24: each pair x 128 + y fits in int32
-          const int x0 = __float2int_rn(__uint_as_float(r[0][c]));
-          const int x1 = __float2int_rn(__uint_as_float(r[1][c]));
-          const int x2 = __float2int_rn(__uint_as_float(r[2][c]));
-          const int x3 = __float2int_rn(__uint_as_float(r[3][c]));
-          const long long w = (long long)(x0 * 128 + x1) * 16384 + (x2 * 128 + x3);
-          if (half == 0) V[c] = w * (1LL << 19);
-          else V[c] += (w + (1LL << 8)) >> 9;
+          for (int c = 0; c < 8; ++c) {
+            // |acc| <= 10.5e6 < 2^24: each pair x 128 + y fits in int32
+            const int x0 = __float2int_rn(__uint_as_float(r[0][c]));
+            const int x1 = __float2int_rn(__uint_as_float(r[1][c]));
+            const int x2 = __float2int_rn(__uint_as_float(r[2][c]));
+            const int x3 = __float2int_rn(__uint_as_float(r[3][c]));
+            const long long w = (long long)(x0 * 128 + x1) * 16384 + (x2 * 128 + x3);
+            if (half == 0) V[pass * 8 + c] = w * (1LL << 19);
+            else V[pass * 8 + c] += (w + (1LL << 8)) >> 9;
+          }
         }
       }
-      if (row_ok) {
+      // tensor memory is drained: the next item's MMAs may start
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty);
+
+      const int i = m0 + q * 32 + lane;
+      if (i >= a.M) continue;
+      const int ei = a.expX[i];
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        const int jb = n0 + cl0 + pass * 8;
+        const int ncols = min(8, a.N - jb);
         double v[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const int fj = s_fz[cl + c];
           v[c] = 0.0;
+          const int fj = c < ncols ? a.expZ[jb + c] : kZeroExp;
           if (ei != kZeroExp && fj != kZeroExp) {
             const int p = ei + fj - 54;
-            if (!i64_scaled(V[c], p, v[c])) v[c] = slow_scaled(V[c], p);
+            if (!i64_scaled(V[pass * 8 + c], p, v[c])) v[c] = slow_scaled(V[pass * 8 + c], p);
           }
         }
         // one loop per output mode, so no FP64 instruction of another mode
         // is issued predicated off (FP64 issue slots are scarce on this part)
-        const int ncols = min(8, a.N - jb);
         if (bmode == 3) {
-          double* P = a.part + (int64_t)blockIdx.z * a.M * a.N + i + (int64_t)jb * a.M;
+          double* P = a.part + (int64_t)(item % a.splits) * a.M * a.N + i + (int64_t)jb * a.M;
 #pragma unroll
           for (int c = 0; c < 8; ++c)
             if (c < ncols) P[(int64_t)c * a.M] = v[c];
@@ -568,21 +587,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int c = 0; c < 8; ++c)
               if (c < ncols) cp[(int64_t)c * a.ldc] = alpha * v[c];
           } else if (bmode == 1) {
+            double cv[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cv[c] = c < ncols ? cp[(int64_t)c * a.ldc] : 0.0;
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-              if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], cv[pass * 8 + c]);
+              if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], cv[c]);
           } else {
+            double cv[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cv[c] = c < ncols ? cp[(int64_t)c * a.ldc] : 0.0;
 #pragma unroll
             for (int c = 0; c < 8; ++c)
-              if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], beta * cv[pass * 8 + c]);
+              if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], beta * cv[c]);
           }
         } else {
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             if (c >= ncols) break;
             double* cp = a.C + jb + c + (int64_t)i * a.ldc;
-            const double c0 = cv[pass * 8 + c];
-            *cp = bmode == 0 ? alpha * v[c] : fma(alpha, v[c], (bmode == 1 ? 1.0 : beta) * c0);
+            *cp = bmode == 0 ? alpha * v[c] : fma(alpha, v[c], (bmode == 1 ? 1.0 : beta) * *cp);
           }
         }
       }
@@ -742,6 +766,11 @@ Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int6
   a.N = (int)n;
   a.K = (int)k;
   a.kchunk = OZ_KC;
+  a.tiles_n = (int)ceil_div(n, OZ_BN);
+  a.splits = (int)splits;
+  const int64_t items = ceil_div(m, OZ_BM) * a.tiles_n * splits;
+  if (items > INT32_MAX) return make_error(LLS_ERR_ARG, "oz_gemm: too many tiles");
+  a.items = (int)items;
   a.expX = ex;
   a.expZ = fz;
   a.alpha = alpha;
@@ -753,8 +782,14 @@ Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int6
   a.err = err;
   const size_t smem = 1024 + (size_t)OZ_XST * OZ_XBYTES + (size_t)OZ_ZST * OZ_ZBYTES;
   LLS_TRY(allow_max_dyn_smem((const void*)oz_mma_kernel));
-  dim3 grid((unsigned)ceil_div(m, OZ_BM), (unsigned)ceil_div(n, OZ_BN), (unsigned)splits);
-  if (grid.y > 65535u || grid.z > 65535u) return make_error(LLS_ERR_ARG, "oz_gemm: grid too large");
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 148;
+  }
+  const unsigned grid = (unsigned)std::min<int64_t>(items, nsm);
   {
     TraceScope ts(kTrOzGemm, st, 2.0 * m * n * k, 16.0 * (double)(m + n) * k + 16.0 * m * n);
     oz_mma_kernel<<<grid, OZ_THREADS, smem, st>>>(mx, mz, a);
