@@ -150,11 +150,14 @@ typedef struct {
  * matrix X Y of rank min(m, n)/2 (X, Y Gaussian from the library's Philox
  * generator, X's columns scaled so the singular values spread over four
  * decades) with one Gaussian right-hand side and the default tol, it runs the
- * reference choice n_b = 32, q = 2, then times `trials` solves (host wall
- * clock, synchronous lls_solve on the handle's stream, current precision) for
- * each n_b in {32, 64, 128} (n_b <= min(m, n) beyond 32) and q in {0, 1, 2},
- * and keeps the fastest whose rank equals the reference's and whose x agrees
- * with the reference x to 1e-9 relative.  nb_out, q_out (host, may be NULL)
+ * reference choice n_b = 32, q = 2, then, for each n_b in {32, 64, 128}
+ * (n_b <= min(m, n) beyond 32; not above 64 when the handle's batches run in
+ * the persistent launch) and q in {0, 1, 2}, checks one solve against the
+ * reference and times `trials` copies of the problem solved together by
+ * lls_solve_batched (host wall clock, the handle's batched mode and
+ * precision) -- the concurrency batched and served work runs with -- and
+ * keeps the fastest candidate whose rank equals the reference's and whose x
+ * agrees with the reference x to 1e-9 relative.  nb_out, q_out (host, may be NULL)
  * receive the choice.  Errors: LLS_ERR_ARG (m, n outside 1..2^20, trials < 1,
  * or requests of this handle queued or running), LLS_ERR_NOMEM, and those of
  * lls_solve. */

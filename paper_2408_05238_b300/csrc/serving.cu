@@ -219,6 +219,8 @@ struct PBLayout {
   size_t T, WV, TV, TU, US, VS, R, tauV, tauU, sigma, G, W, P, P2, Q, Q2, S;
 };
 
+}  // namespace
+
 bool persistent_eligible(Handle& h, int64_t count, const lls_problem* probs, std::string* why) {
   if (!batched_factor_available()) return (*why = "persistent kernel not in this build"), false;
   if (h.opt.precision != LLS_FP64) return (*why = "the persistent path is FP64"), false;
@@ -236,6 +238,8 @@ bool persistent_eligible(Handle& h, int64_t count, const lls_problem* probs, std
   }
   return true;
 }
+
+namespace {
 
 Status solve_batched_persistent(Handle& h, int64_t count, lls_problem* probs,
                                 std::vector<int>& status) {

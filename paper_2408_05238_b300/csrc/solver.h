@@ -294,6 +294,9 @@ Status apply_v(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs, int64
 // Device bytes a factorization of m x n (and a solve with nrhs) will hold.
 size_t factor_bytes(int64_t m, int64_t n, int nb, bool explicit_v = false, bool keep_a = false);
 
+// Whether lls_solve_batched can run these problems in one persistent launch
+// with the handle's options (serving.cu); *why says why not.
+bool persistent_eligible(Handle& h, int64_t count, const lls_problem* probs, std::string* why);
 // Stops and joins the worker pool (serving.cu); queued requests are dropped.
 void stop_pool(Handle& h);
 // True while the handle's worker pool has requests queued or running.

@@ -3,17 +3,21 @@
 //
 // The randUTV loop (Fig. 2) leaves n_b and q to the user.  n_b trades the
 // number of sequential steps (panels, block SVDs) against the size of each
-// tensor-core product; q trades sampling work against how well the sample
-// captures the dominant subspace (the Remark after Fig. 2).  The tuner times
-// the candidates on a synthetic matrix of the bucket's shape and keeps the
-// fastest one that still reaches the reference answer.
+// product; q trades sampling work against how well the sample captures the
+// dominant subspace (the Remark after Fig. 2).  The tuner checks each
+// candidate's answer on one synthetic matrix of the bucket's shape and times
+// it on a batch of copies solved together (lls_solve_batched), the way
+// batched and served work runs, keeping the fastest candidate that still
+// reaches the reference answer.
 #include <cerrno>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
+#include "batched_factor.h"
 #include "lls.h"
 #include "solver.h"
 
@@ -81,12 +85,13 @@ int lls_autotune(lls_handle hh, int64_t m, int64_t n, int32_t trials, int32_t* n
   if (!h->tune) h->tune = std::make_shared<lls::TuneTable>();
   cudaStream_t st = h->stream;
   const int64_t r = std::max<int64_t>(1, std::min(m, n) / 2);
-  lls::DevMem X, Y, A, B, Xo, ws;
+  lls::DevMem X, Y, A, B, Xo, Xb, ws;
   if (cudaMalloc(&X.p, 8 * (size_t)m * r) != cudaSuccess ||
       cudaMalloc(&Y.p, 8 * (size_t)r * n) != cudaSuccess ||
       cudaMalloc(&A.p, 8 * (size_t)m * n) != cudaSuccess ||
       cudaMalloc(&B.p, 8 * (size_t)m) != cudaSuccess ||
-      cudaMalloc(&Xo.p, 8 * (size_t)n) != cudaSuccess) {
+      cudaMalloc(&Xo.p, 8 * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&Xb.p, 8 * (size_t)n * trials) != cudaSuccess) {
     cudaGetLastError();
     return LLS_ERR_NOMEM;
   }
@@ -123,6 +128,36 @@ int lls_autotune(lls_handle hh, int64_t m, int64_t n, int32_t trials, int32_t* n
     }
     return LLS_OK;
   };
+  // timing: `trials` copies solved together by lls_solve_batched, so each
+  // candidate is timed under the concurrency batched and served work runs
+  // with (the persistent launch, or the worker pool)
+  std::vector<lls_problem> batch((size_t)trials);
+  for (int t = 0; t < trials; ++t) {
+    lls_problem& p = batch[(size_t)t];
+    std::memset(&p, 0, sizeof(p));
+    p.A = (const double*)A.p;
+    p.m = m;
+    p.n = n;
+    p.lda = m;
+    p.B = (const double*)B.p;
+    p.nrhs = 1;
+    p.ldb = m;
+    p.tol = -1.0;
+    p.X = (double*)Xb.p + (size_t)t * n;
+    p.ldx = n;
+    p.factor_id = -1;
+  }
+  auto run_batch = [&](int nb, int q) -> int {
+    h->opt.nb = nb;
+    h->opt.q = q;
+    return lls_solve_batched(hh, trials, batch.data());
+  };
+  // n_b above the persistent launch's limit only where the batch runs on workers
+  std::string why;
+  h->opt.nb = lls::kPbMaxNb;
+  const bool persistent = h->batched_mode != LLS_BATCHED_WORKERS &&
+                          lls::persistent_eligible(*h, trials, batch.data(), &why);
+  h->opt = saved;
   // reference: the smallest block and the most power iterations
   int64_t rank_ref = -1;
   std::vector<double> x_ref, x;
@@ -136,15 +171,18 @@ int lls_autotune(lls_handle hh, int64_t m, int64_t n, int32_t trials, int32_t* n
   for (int a = 0; a < 3 && code >= 0; ++a) {
     const int nb = nbs[a];
     if (nb > 32 && nb > std::min(m, n)) continue;
+    if (persistent && nb > lls::kPbMaxNb) continue;
     for (int q = 0; q <= 2 && code >= 0; ++q) {
       int64_t rk = -1;
-      code = run(nb, q, &rk, &x);  // warm-up (workspace) and accuracy check
+      code = run(nb, q, &rk, &x);  // accuracy check
       if (code < 0) break;
       double d = 0.0;
       for (int64_t i = 0; i < n; ++i) d += (x[i] - x_ref[i]) * (x[i] - x_ref[i]);
       if (rk != rank_ref || !(std::sqrt(d) <= 1e-9 * ref_norm)) continue;
+      code = run_batch(nb, q);  // warm-up (workspace)
+      if (code < 0) break;
       const auto t0 = std::chrono::steady_clock::now();
-      for (int t = 0; t < trials && code >= 0; ++t) code = run(nb, q, &rk, nullptr);
+      code = run_batch(nb, q);
       const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (code >= 0 && dt < best_t) {
         best_t = dt;
