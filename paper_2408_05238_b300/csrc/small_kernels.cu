@@ -237,6 +237,35 @@ __global__ void trsm_block_kernel(int64_t k, const double* __restrict__ R, int64
   for (int64_t i = threadIdx.x; i < k; i += blockDim.x) b[i] = x[i];
 }
 
+// y (M x nrhs) -= op(A) x for op(A) M x K (A[i + k lda], or A^T: A[k + i lda]),
+// x K x nrhs: the off-diagonal block updates of a blocked triangular solve
+// with few right-hand sides (K <= kTrsmBlock, nrhs <= kThinMaxRhs), one thread
+// per row.  The general FP64 GEMM pads N to its 16-column tile, which costs
+// 16 times the FP64 work for one right-hand side on this part.
+__global__ void __launch_bounds__(256) gemv_thin_sub_kernel(int64_t M, int K, int nrhs,
+                                                            const double* __restrict__ A,
+                                                            int64_t lda, int trans,
+                                                            const double* __restrict__ x,
+                                                            int64_t ldx, double* y, int64_t ldy) {
+  __shared__ double xs[64 * 16];
+  for (int e = threadIdx.x; e < K * nrhs; e += blockDim.x) xs[e] = x[(e % K) + (int64_t)(e / K) * ldx];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double a = trans ? A[k + i * lda] : A[i + (int64_t)k * lda];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (c < nrhs) acc[c] = fma(a, xs[k + c * K], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    if (c < nrhs) y[i + (int64_t)c * ldy] -= acc[c];
+}
+
 // B <- R^{-T} B for one k x k diagonal block: forward substitution with the
 // transpose of the upper triangular R (R^T(l, i) = R(i, l)), one CTA per
 // right-hand side.
@@ -453,6 +482,18 @@ Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double*
 }
 
 constexpr int64_t kTrsmBlock = 64;
+static_assert(kTrsmBlock <= 64 && kThinMaxRhs <= 16, "gemv_thin_sub_kernel's shared x");
+
+// y (M x nrhs) -= op(A) x, thin: see gemv_thin_sub_kernel.
+Status gemv_thin_sub(int64_t M, int64_t K, int64_t nrhs, const double* A, int64_t lda, bool trans,
+                     const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
+  if (M <= 0 || K <= 0 || nrhs <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st, 2.0 * M * K * nrhs, 8.0 * M * K);
+  gemv_thin_sub_kernel<<<(unsigned)ceil_div(M, 256), 256, 0, st>>>(M, (int)K, (int)nrhs, A, lda,
+                                                                    trans ? 1 : 0, x, ldx, y, ldy);
+  LLS_LAUNCHED("gemv_thin_sub_kernel");
+  return ok_status();
+}
 
 size_t trsm_upper_scratch_bytes(int64_t r, int64_t nrhs) {
   size_t need = 0;
@@ -470,7 +511,9 @@ Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double*
   while (j1 > 0) {
     int64_t j0 = std::max<int64_t>(0, j1 - TB);
     LLS_TRY(trsm_block(j1 - j0, nrhs, R + j0 + j0 * ldr, ldr, B + j0, ldb, st));
-    if (j0 > 0)
+    if (j0 > 0 && nrhs <= kThinMaxRhs)
+      LLS_TRY(gemv_thin_sub(j0, j1 - j0, nrhs, R + j0 * ldr, ldr, false, B + j0, ldb, B, ldb, st));
+    else if (j0 > 0)
       LLS_TRY(gemm(false, false, kDense, kDense, j0, nrhs, j1 - j0, -1.0, R + j0 * ldr, ldr,
                    B + j0, ldb, 1.0, B, ldb, scratch, st));
     j1 = j0;
@@ -500,7 +543,10 @@ Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, d
       LLS_LAUNCHED("trsm_block_trans_kernel");
     }
     // B(j1:r) -= R(j0:j1, j1:r)^T B(j0:j1)
-    if (j1 < r)
+    if (j1 < r && nrhs <= kThinMaxRhs)
+      LLS_TRY(gemv_thin_sub(r - j1, j1 - j0, nrhs, R + j0 + j1 * ldr, ldr, true, B + j0, ldb, B + j1,
+                            ldb, st));
+    else if (j1 < r)
       LLS_TRY(gemm(true, false, kDense, kDense, r - j1, nrhs, j1 - j0, -1.0, R + j0 + j1 * ldr, ldr,
                    B + j0, ldb, 1.0, B + j1, ldb, scratch, st));
   }

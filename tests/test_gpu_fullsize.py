@@ -81,7 +81,7 @@ def test_c3_full_size(lls, c3, precision):
     A, B, xref = c3
     prec = {"mixed": lls.LLS_MIXED_BF16, "3xtf32": lls.LLS_MIXED_BF16_3xTF32}[precision]
     h = lls.lls_create(nb=128, q=1, seed=2003, precision=prec,
-                       max_refine=10 if precision == "3xtf32" else 0, refine_tol=1e-12)
+                       max_refine=10 if precision == "3xtf32" else 0, refine_tol=1e-11)
     try:
         X, rank, code = lls.lls_solve(h, A, B, 1e-6)
         torch.cuda.synchronize()

@@ -198,6 +198,7 @@ def test_tuned_batched_solves_use_the_table(lls, tmp_path):
     path.write_text("\n".join(rows) + "\n")
     h = lls.lls_create(nb=0, q=1, seed=2004)
     lls.lls_set_workers(h, 3)
+    lls.lls_set_batched_mode(h, lls.LLS_BATCHED_WORKERS)   # lls_solve's own launches
     lls.lls_tuning_load(h, str(path))
     try:
         held, plist = [], []

@@ -4,9 +4,10 @@ solve, and whole solves against the FP64 oracle.
 
 With 3xTF32 products (hi*hi + hi*lo + lo*hi, FP32 accumulation) the
 factorization carries errors of about 2^-21 ||A||, so the solve is at parity
-only after the minimum-norm refinement x <- x + A^T P^T P P^T A^T (b - A x)
-(from x = 0), and only where tol and the kept singular values sit well above
-that noise (tol = 1e-6 ||A|| here, as in the 32768 x 16384 workload).
+only after the minimum-norm refinement (least squares with the right
+preconditioner V_1 T_11^{-1}, then the projection onto range(A^T)), and only
+where tol and the kept singular values sit well above that noise
+(tol = 1e-6 ||A|| here, as in the 32768 x 16384 workload).
 Plain TF32 (hi*hi only, about 2^-11) reveals the rank of a matrix whose
 kept singular values stay above about 1e-2 ||A|| and fails on the
 geometric spectrum down to 1e-4: that failure is asserted, not hidden."""
@@ -80,13 +81,19 @@ def test_tf32_gemm_alpha_beta_unit_lower_gram(lls):
     got, st = lls.lls_k_gemm_tf32(0, 0, dev(A), dev(B), dev(C0), alpha=-0.5, beta=2.0)
     assert st == 0
     assert np.max(np.abs(host(got) - (2.0 * C0 - 0.5 * (A @ B)))) < 2e-6 * np.max(np.abs(A) @ np.abs(B))
+    # Gram W^T W of a unit lower W (its planes reused for both operands): the
+    # diagonal sums K squares of one sign, so the FP32 accumulation error grows
+    # with K instead of averaging out -- up to K 2^-24 relative.  That is why the
+    # solver forms its T factors' Gram matrices with the exact-slice GEMM.
     W = g.standard_normal((400, 64))
     Wl = np.tril(W, -1)
     Wl[np.arange(64), np.arange(64)] = 1.0
     Wd = dev(W)
-    got, st = lls.lls_k_gemm_tf32(1, 0, Wd, Wd, unit_lower_a=True, unit_lower_b=True)  # Gram W^T W
+    got, st = lls.lls_k_gemm_tf32(1, 0, Wd, Wd, unit_lower_a=True, unit_lower_b=True)
     assert st == 0
-    assert np.max(np.abs(host(got) - Wl.T @ Wl)) < 2e-6 * np.max(np.abs(Wl.T) @ np.abs(Wl))
+    err = np.abs(host(got) - Wl.T @ Wl) / (np.abs(Wl.T) @ np.abs(Wl))
+    assert err.max() < 400 * 2.0 ** -24
+    assert np.median(err) < 2e-6
 
 
 def test_trsm_upper_trans(lls):
@@ -101,7 +108,7 @@ def test_trsm_upper_trans(lls):
 # ------------------------------------------------------------------ solves
 def solve(lls, A, B, tol, nb, q, precision, max_refine=10, explicit_v=0, seed=2001):
     h = lls.lls_create(nb=nb, q=q, seed=seed, precision=precision, max_refine=max_refine,
-                       refine_tol=1e-13, explicit_v=explicit_v)
+                       refine_tol=1e-11, explicit_v=explicit_v)
     try:
         X, rank, code = lls.lls_solve(h, dev(A), dev(B), tol)
         steps, corr = lls.lls_refinement_info(h)
@@ -146,7 +153,7 @@ def test_3xtf32_factor_reuse_refines(lls):
     p = wl.c3_like(800, 400, 300, nrhs=1, nb=64, q=1)
     ref = orc.solve(p.A, p.B, 1, 64, p.tol, 2001)
     h = lls.lls_create(nb=64, q=1, seed=2001, precision=lls.LLS_MIXED_BF16_3xTF32, max_refine=10,
-                       refine_tol=1e-13)
+                       refine_tol=1e-11)
     try:
         fid, rank, _ = lls.lls_factor(h, dev(p.A), p.tol)
         assert rank == 300
