@@ -60,9 +60,12 @@ def parse():
                         "updates with the minimum-norm FP64 refinement")
     p.add_argument("--max-refine", type=int, default=None,
                    help="refinement steps (default 0 for fp64 and mixed, 10 for the TF32 modes)")
-    p.add_argument("--workload", choices=["c2", "c3", "batched", "serving"], default="c2",
+    p.add_argument("--workload", choices=["c2", "c3", "batched", "serving", "kernels"],
+                   default="c2",
                    help="c2: one 16384^2 solve per step (default); batched: many small "
-                        "problems per step; serving: Poisson arrivals through lls_submit")
+                        "problems per step; serving: Poisson arrivals through lls_submit; "
+                        "kernels: the tensor-core update GEMMs alone on one randUTV step's "
+                        "two shapes (n x n x nb and n x nb x n), through the step entry points")
     p.add_argument("--count", type=int, default=1024, help="batched: problems per step")
     p.add_argument("--batched-mode", choices=["auto", "workers", "persistent"], default="auto",
                    help="batched: one persistent launch (auto picks it for FP64) or the worker pool")
@@ -333,6 +336,9 @@ def run_batched(a):
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
+    # device time of the persistent factorization launch (the handle's own
+    # stream); the worker streams' rank, Nullify and solve are not traced
+    lls.lls_trace_enable(h, True)
     launches0, allocs0 = lls.lls_launch_count(), lls.lls_alloc_count()
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         t0 = time.perf_counter()
@@ -342,6 +348,9 @@ def run_batched(a):
         dt = time.perf_counter() - t0
     launches = lls.lls_launch_count() - launches0
     allocs = lls.lls_alloc_count() - allocs0
+    trace = lls.lls_trace_read(h)
+    lls.lls_trace_enable(h, False)
+    factor_s = trace.get("batched_factor_kernel", (0, 0.0))[1]
     flops = sum(pm.lls_flops(m, n, *nbq(lls, h, m, n, a.autotune), rk.value, k)
                 for (m, n, r, k), rk in zip(sizes, ranks))
     wrong = sum(rk.value != r for (_, _, _, _, r), rk in zip(probs, ranks))
@@ -356,6 +365,7 @@ def run_batched(a):
                       "workers": a.workers, "precision": a.precision, "tuning": tuning,
                       "batched_mode": a.batched_mode},
            "tflops": flops * a.steps / dt / 1e12, "rank_mismatches": wrong,
+           "persistent_factor_seconds_per_step": factor_s / a.steps if factor_s else None,
            "gpu_launches": launches, "device_allocations": allocs, "clocks": clk.summary()}
     print(json.dumps(out))
     return 0
@@ -449,6 +459,75 @@ def run_serving(a):
            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
            "solves_per_s": nreq / wall, "offered_per_s": a.rate, "tflops": flops / wall / 1e12,
            "clocks": clk.summary()}
+    print(json.dumps(out))
+    return 0
+
+
+def run_kernels(a):
+    """The trailing-update GEMMs of one randUTV step on an n x n matrix in the
+    tensor-core modes, through lls_k_gemm_oz / lls_k_gemm_tf32: the rank-nb
+    update C -= P W^T (n x n x nb) and the long product P = T W (n x nb x n),
+    each timed over K launches with CUDA events after W warm-ups (operands
+    larger than L2 at n >= 4096, no flush)."""
+    import torch
+
+    from paper_2408_05238_b300 import lls
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n, nb = a.n, a.nb
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    T = torch.randn(n, n, generator=g, dtype=torch.float64, device="cuda").t().contiguous().t()
+    W = torch.randn(n, nb, generator=g, dtype=torch.float64, device="cuda").t().contiguous().t()
+    P = torch.randn(n, nb, generator=g, dtype=torch.float64, device="cuda").t().contiguous().t()
+    out = {"metric": "tensor-core update GEMMs: TFLOP/s (FP64-equivalent) and GB/s per shape",
+           "config": {"workload": f"kernels: n={n}, nb={nb}", "n": n, "nb": nb}, "kernels": {}}
+    stream = torch.cuda.current_stream()
+    shapes = {"rank_nb_update": (0, 1, n, n, nb, P, W, T, -1.0, 1.0),
+              "long_product": (0, 0, n, nb, n, T, W, P, 1.0, 0.0)}
+    # tensor-core flops per FP64 multiply-add: 36 BF16 digit-plane products
+    # (exact slicing), 3 TF32 products (3xTF32)
+    for kname, planes, call in (
+            ("oz_mma_kernel", 36, lambda *x, **k: lls.lls_k_gemm_oz(*x, **k)),
+            ("tf32_mma_kernel", 3, lambda *x, **k: lls.lls_k_gemm_tf32(*x, terms=3, **k))):
+        for sname, (ta, tb, m, nn, k, A_, B_, C_, al, be) in shapes.items():
+            for _ in range(a.warmup):
+                call(ta, tb, A_, B_, C_, alpha=al, beta=be)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(a.steps):
+                call(ta, tb, A_, B_, C_, alpha=al, beta=be)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            dt = ev0.elapsed_time(ev1) / 1e3 / a.steps
+            flops = 2.0 * m * nn * k
+            byts = 8.0 * (m * k + k * nn + (2 if be else 1) * m * nn)
+            out["kernels"][f"{kname}:{sname}"] = {"m": m, "n": nn, "k": k, "ms": 1e3 * dt,
+                                                   "fp64_equiv_tflops": flops / dt / 1e12,
+                                                   "tensor_tflops": planes * flops / dt / 1e12,
+                                                   "fp64_operand_gbs": byts / dt / 1e9}
+    # the transposed triangular solve of the refinement (diagonal blocks of
+    # 64 and thin off-diagonal products), one right-hand side, on an n x n
+    # well-conditioned upper triangle
+    R = torch.triu(T) + n * torch.eye(n, dtype=torch.float64, device="cuda")
+    R = R.t().contiguous().t()
+    b = torch.randn(n, 1, generator=g, dtype=torch.float64, device="cuda")
+    for _ in range(a.warmup):
+        lls.lls_k_trsm_upper_trans(R, b.clone())
+    bs = [b.clone() for _ in range(a.steps)]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for bb in bs:
+        lls.lls_k_trsm_upper_trans(R, bb)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3 / a.steps
+    out["kernels"]["trsm_upper_trans:nrhs1"] = {"r": n, "ms": 1e3 * dt,
+                                                "blocks_of_64": -(-n // 64),
+                                                "us_per_block": 1e6 * dt / -(-n // 64),
+                                                "fp64_operand_gbs": 4.0 * n * n / dt / 1e9}
     print(json.dumps(out))
     return 0
 
@@ -631,6 +710,8 @@ def main():
         return run_batched(a)
     if a.workload == "serving":
         return run_serving(a)
+    if a.workload == "kernels":
+        return run_kernels(a)
 
     import numpy as np
     import torch

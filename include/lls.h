@@ -111,14 +111,20 @@ typedef struct {
                           x <- x + P (b - A x) with the FP64 residual and
                           P = V_1 T_11^{-1} U_1^T the factorization's solve
                           operator.  The TF32 modes (factors accurate to the
-                          TF32 split only): x_0 = 0,
-                          x <- x + A^T P^T P P^T A^T (b - A x), whose every
-                          correction lies in range(A^T) and whose fixed point
-                          is the minimum-norm least-squares solution itself;
-                          it contracts by about the factors' relative error
-                          times the condition number of T_11 per step (with
-                          max_refine = 0 these modes return x = P b at TF32
-                          accuracy) */
+                          TF32 split only) refine in two stages from
+                          x_0 = P b: (1) least squares,
+                          x <- x + N N^T A^T (b - A x) with N = V_1 T_11^{-1},
+                          then (2) the projection onto range(A^T):
+                          x <- x + L L^T (x_ls - x) from 0 with
+                          L = A^T U_1 T_11^{-T}; each stage contracts by
+                          about the factors' relative error times the
+                          condition number of T_11 (kappa eps < 1), and
+                          max_refine bounds each stage's steps.  When the
+                          largest dropped |T(i,i)| is above 1e-2 times the
+                          smallest kept one the split is not reliable and
+                          no refinement runs (LLS_WARN_REFINE_NOCONV).
+                          With max_refine = 0 these modes return x = P b at
+                          TF32 accuracy */
   double refine_tol;   /* refinement stops once every column has
                           ||dx_j|| <= refine_tol ||x_j||, >= 0 [1e-12] */
   int32_t reserved[2]; /* must be zero */
@@ -188,7 +194,10 @@ int lls_destroy(lls_handle h);
 /* Change the options (every field of lls_options) for later calls. */
 int lls_set_options(lls_handle h, const lls_options* opt);
 
-/* Solve min ||A X - B|| with minimum ||X|| (per column), tol absolute:
+/* Solve min ||A X - B|| with minimum ||X|| (per column) by the method of
+ * Sec. 3.2: A = U T V^T by randUTV (Fig. 2), the numerical rank r from
+ * diag(T) (Compute_rank), Nullify of T(0:r, r:n) (Fig. 3), then
+ * X = V(:, 0:r) T(0:r, 0:r)^{-1} U(:, 0:r)^T B (Fig. 4).  tol absolute:
  * diagonal entries of T with |T_jj| <= tol count as zero (tol < 0 selects
  * max(m,n) * eps * |T_00|).  Synchronous: returns when X is written.
  * rank (host pointer, may be NULL) receives r.  A is not modified. */
@@ -202,8 +211,9 @@ int lls_solve_host(lls_handle h, const double* A, int64_t m, int64_t n, int64_t 
                    const double* B, int64_t nrhs, int64_t ldb, double tol,
                    double* X, int64_t ldx, int64_t* rank);
 
-/* Factor A and keep the factorization resident (the paper's stored U
- * variant, Sec. 3.4).  *factor_id receives a handle-local id (>= 0). */
+/* Factor A and keep the factorization resident (the paper's variants that
+ * keep U and V for later right-hand sides, Sec. 3.5).
+ * *factor_id receives a handle-local id (>= 0). */
 int lls_factor(lls_handle h, const double* A, int64_t m, int64_t n, int64_t lda,
                double tol, int64_t* factor_id, int64_t* rank);
 
@@ -280,7 +290,9 @@ enum { LLS_BATCHED_AUTO = 0, LLS_BATCHED_WORKERS = 1, LLS_BATCHED_PERSISTENT = 2
 int lls_set_batched_mode(lls_handle h, int mode);
 
 /* Serving: enqueue one request (copied; buffers must stay alive until it
- * completes) and return at once; *ticket receives its id.  Requests start in
+ * completes) and return at once; *ticket receives its id.  Each request is
+ * one solve of lls_solve (Sec. 3.2, Figs. 2-4), or with a resident factor
+ * the solve of Fig. 4 alone.  Requests start in
  * arrival order as soon as a worker of the pool is free and the estimated
  * device memory of the running requests stays under the cap
  * (lls_set_memory_cap), and run concurrently on separate streams.
@@ -313,7 +325,7 @@ int lls_set_workers(lls_handle h, int workers);
 /* ---- out-of-core planning ---------------------------------------------
  * The host<->device traffic of a solve whose m x n matrix stays in host
  * memory and moves through a device cache of `cache_panels` whole column
- * panels (nb columns, all m rows; the paper's block cache, Sec. 3.4, with
+ * panels (nb columns, all m rows; the paper's block cache, Sec. 3.5, with
  * device memory as the cache and host memory as the disk).  The plan visits
  * the trailing panels in passes: per step of Fig. 2 the sampling passes
  * (the first product A^T G taken in the previous step's update pass; q + 1
@@ -438,8 +450,9 @@ typedef struct {
  * around each phase of the method: entries named "phase:sample",
  * "phase:qr_y", "phase:right_update", "phase:panel", "phase:left_update",
  * "phase:block_svd", "phase:rank", "phase:nullify" and "phase:solve" (steps
- * a1/a2 .. a10; a phase's time includes the kernels it launches, so phases
- * and kernel families are two views of the same time). */
+ * a1/a2 .. a10), and "phase:refine" (the iterative refinement after the
+ * solve); a phase's time includes the kernels it launches, so phases and
+ * kernel families are two views of the same time. */
 int lls_trace_enable(lls_handle h, int on);
 
 /* Copy up to max per-family and per-phase counters to out (host array);

@@ -108,8 +108,17 @@ Status resolve_tol(double tol, int64_t mn, const double* T00, double* tol_dev, c
 // Rank scan with a device tolerance.
 Status rank_scan_dev(int64_t len, const double* T, int64_t ldt, const double* tol_dev,
                      int64_t* out, cudaStream_t st);
-// reflector_thin.cu: block reflectors applied to at most kThinMaxRhs vectors.
+// reflector_thin.cu: products with at most kThinMaxRhs right-hand sides.
 constexpr int kThinMaxRhs = 16;
+// y (M x nrhs) = beta y + alpha op(A) x with op(A) M x K: A (M x K, ld lda)
+// or, trans, A^T for A K x M; unit_lower: the stored A reads as unit lower
+// trapezoidal (0 above the diagonal, 1 on it).  The K split, and so the
+// order of every sum, is a function of (trans, M, K, nrhs) only; split sums
+// need thin_gemv_scratch_bytes of scratch (0 when there is no split).
+size_t thin_gemv_scratch_bytes(bool trans, int64_t M, int64_t K, int64_t nrhs);
+Status thin_gemv(bool trans, bool unit_lower, int64_t M, int64_t K, int64_t nrhs, double alpha,
+                 const double* A, int64_t lda, const double* x, int64_t ldx, double beta, double* y,
+                 int64_t ldy, Scratch scratch, cudaStream_t st);
 size_t thin_scratch_bytes(int64_t M, int64_t b, int64_t nrhs);
 // x (M x nrhs) <- (I - W op(T) W^T) x, W M x b unit lower trapezoidal (ld
 // ldw), T b x b upper triangular, op(T) = T^T when transT; b <= 128.
@@ -148,5 +157,15 @@ Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, d
                         int64_t ldb, Scratch scratch, cudaStream_t st);
 Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
                   int64_t ldb, Scratch scratch, cudaStream_t st);
+// Inverses of the 64 x 64 diagonal blocks of an upper triangular r x r R
+// (blocks from the top, the last one partial), trsm_inverse_bytes(r) bytes;
+// then B <- R^{-1} B or, trans, R^{-T} B with them (nrhs <= kThinMaxRhs):
+// each diagonal block is a product with its inverse instead of a serial
+// substitution (the refinement's preconditioner applies T_11^{-1} and
+// T_11^{-T} many times with the same factor).
+size_t trsm_inverse_bytes(int64_t r);
+Status trsm_block_inverses(int64_t r, const double* R, int64_t ldr, double* Dinv, cudaStream_t st);
+Status trsm_upper_inv(int64_t r, int64_t nrhs, const double* R, int64_t ldr, const double* Dinv,
+                      double* B, int64_t ldb, bool trans, cudaStream_t st);
 
 }  // namespace lls

@@ -1,6 +1,6 @@
 // Out-of-core planning: the schedule and the host<->device panel traffic of
 // a randUTV solve whose matrix lives in host memory and passes through a
-// device cache of whole column panels (the paper's block cache, Sec. 3.4
+// device cache of whole column panels (the paper's block cache, Sec. 3.5
 // variants v23c-v23e, with the GPU's memory in the role of main memory and
 // host memory in the role of the disk).  Host code only: no CUDA call.
 //

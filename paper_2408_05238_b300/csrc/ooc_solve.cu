@@ -1,6 +1,6 @@
 // Out-of-core solve (lls_solve_ooc): the randUTV least-squares solve with
 // the matrix in pinned host memory and at most `cache_panels` column panels
-// of it on the device at a time (the paper's block cache of Sec. 3.4, with
+// of it on the device at a time (the paper's block cache of Sec. 3.5, with
 // device memory as the cache and host memory as the disk).
 //
 // The executor follows the schedule of ooc_plan.cu action by action: before

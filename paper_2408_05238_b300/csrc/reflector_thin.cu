@@ -1,142 +1,410 @@
-// Block reflectors applied to a few vectors: the replays of the solve of
-// Fig. 4 (c = U^T b by steps, x = V z in reverse step order) and of its
-// transpose (the refinement of the TF32 modes), for nrhs <= kThinMaxRhs.
+// Products with few right-hand sides (nrhs <= kThinMaxRhs): the replays of
+// the solve of Fig. 4 (c = U^T b by steps, x = V z in reverse step order),
+// their transposes (the refinement of the TF32 modes), the off-diagonal
+// block updates of the triangular solves, and the FP64 residual products
+// A x and A^T r of the refinement.
 //
-// x (M x nrhs) <- (I - W op(T) W^T) x with W the M x b unit lower
-// trapezoidal reflector block of one step and T its b x b upper triangular
-// compact-WY factor, op(T) = T or T^T, in three launches:
-//  1. thin_partials_kernel: each CTA sums W(r, j) x(r, c) over its chunk of
-//     rows (the x chunk staged in shared memory, one warp per column of W);
-//  2. thin_reduce_kernel: one CTA per right-hand side adds the chunks'
-//     partial sums in chunk order and forms p2 = op(T) (W^T x);
-//  3. thin_update_kernel: x(r, c) -= sum_j W(r, j) p2(j, c) on every row.
-// The general GEMM path launches several split-K products per step and
-// spends most of its time in launches for nrhs = 1; this reads W twice per
-// step at HBM speed.  Every sum runs in a fixed order, so results are
-// bit-identical run to run.
+// The general FP64 GEMM tiles N by 16, so one right-hand side costs it the
+// FP64 work of sixteen; on this part FP64 runs at 2 FMA per clock per SM,
+// and that padding made every such product ALU-bound at 16 times its work.
+// These kernels do nrhs columns of work and keep enough loads in flight to
+// stream the matrix at HBM speed when nrhs is small:
+//  * thin_n_kernel: y(i, c) = sum_k A(i, k) x(k, c).  A CTA owns 64 rows and
+//    a K chunk; thread (i, g) of 256 loads A(i, k) for 16 k of each 64-wide
+//    k tile (coalesced along i, 16 loads in flight), x staged in shared
+//    memory, the four k groups added in a fixed order at the end.
+//  * thin_t_kernel: y(j, c) = sum_i A(i, j) x(i, c).  A CTA owns 64 columns,
+//    a row chunk and up to 4 right-hand sides; each lane walks rows, 8
+//    columns per warp, the 32 lanes added by a fixed shuffle tree.
+//  * K or row chunks (a split fixed by the shape alone, so results are
+//    bit-identical run to run and handle to handle) write partial sums that
+//    thin_reduce_kernel adds in chunk order.
+// A unit lower trapezoidal operand (the reflector blocks W of a step) reads
+// 0 above and 1 on its diagonal, without touching the stored upper part.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
 namespace lls {
 namespace {
 
-constexpr int TH_THREADS = 256;
-constexpr int TH_ROWS = 256;  // rows per CTA chunk
+constexpr int TN_THREADS = 256;
+constexpr int TN_ROWS = 64;       // rows per CTA of thin_n_kernel
+constexpr int TN_KT = 64;         // k tile
+constexpr int TT_COLS = 64;       // columns per CTA of thin_t_kernel
+constexpr int TT_CG = 4;          // right-hand sides per CTA of thin_t_kernel (at most)
+constexpr int kSplitTarget = 296; // CTAs a split aims for: 2 per SM of a 148-SM part
+constexpr int kMinChunk = 256;    // the shortest K / row chunk a split makes
 
-__device__ __forceinline__ double w_unit_lower(const double* W, int64_t ldw, int64_t r, int j) {
-  if (r < j) return 0.0;
-  if (r == j) return 1.0;
-  return W[r + (int64_t)j * ldw];
+// FP64 instructions issue at a small fraction of the other pipes' rate on
+// this part, and an instruction predicated off still takes its issue slot,
+// so the kernels below are specialised on the number of right-hand sides
+// (NR, NC): every FP64 instruction issued does useful work.
+
+template <bool UL>
+__device__ __forceinline__ double load_a(const double* __restrict__ A, int64_t lda, int64_t i,
+                                         int64_t k) {
+  if (UL) {
+    if (i < k) return 0.0;
+    if (i == k) return 1.0;
+  }
+  return __ldg(A + i + k * lda);
 }
 
-__global__ void __launch_bounds__(TH_THREADS) thin_partials_kernel(int64_t M, int b, int nrhs,
-                                                                    const double* __restrict__ W,
-                                                                    int64_t ldw,
-                                                                    const double* __restrict__ x,
-                                                                    int64_t ldx,
-                                                                    double* __restrict__ part) {
-  __shared__ double xs[TH_ROWS * kThinMaxRhs];
-  const int64_t r0 = (int64_t)blockIdx.x * TH_ROWS;
-  const int rows = (int)(M - r0 < TH_ROWS ? M - r0 : TH_ROWS);
-  for (int e = threadIdx.x; e < rows * nrhs; e += TH_THREADS)
-    xs[(e % rows) + (e / rows) * TH_ROWS] = x[r0 + (e % rows) + (int64_t)(e / rows) * ldx];
+// y = beta y + alpha s without reading y when beta = 0.
+__device__ __forceinline__ void store_out(double* y, double alpha, double beta, double s) {
+  *y = beta == 0.0 ? alpha * s : fma(beta, *y, alpha * s);
+}
+
+template <bool UL, int NR>
+__global__ void __launch_bounds__(TN_THREADS) thin_n_kernel(int64_t M, int64_t K,
+                                                            const double* __restrict__ A,
+                                                            int64_t lda,
+                                                            const double* __restrict__ x,
+                                                            int64_t ldx, int64_t kchunk,
+                                                            double alpha, double beta, double* y,
+                                                            int64_t ldy, double* part) {
+  __shared__ double xs[TN_KT * NR];
+  __shared__ double red[4 * TN_ROWS * NR];
+  const int t = threadIdx.x, il = t & (TN_ROWS - 1), kg = t >> 6;
+  const int64_t i = (int64_t)blockIdx.x * TN_ROWS + il;
+  const int64_t kb = (int64_t)blockIdx.y * kchunk;
+  const int64_t ke = std::min<int64_t>(K, kb + kchunk);
+  double acc[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = 0.0;
+  for (int64_t kt = kb; kt < ke; kt += TN_KT) {
+    const int kn = (int)std::min<int64_t>(TN_KT, ke - kt);
+    __syncthreads();
+    // the k tile of x, zero beyond kn (so the FMAs below need no guard)
+    for (int e = t; e < TN_KT * NR; e += TN_THREADS) {
+      const int kk = e % TN_KT, c = e / TN_KT;
+      xs[e] = kk < kn ? x[kt + kk + (int64_t)c * ldx] : 0.0;
+    }
+    __syncthreads();
+    if (i < M) {
+      double a[16];
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        const int kk = kg * 16 + s;
+        a[s] = kk < kn ? load_a<UL>(A, lda, i, kt + kk) : 0.0;
+      }
+#pragma unroll
+      for (int s = 0; s < 16; ++s)
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] = fma(a[s], xs[kg * 16 + s + TN_KT * c], acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) red[kg * TN_ROWS * NR + il + TN_ROWS * c] = acc[c];
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* out = part + (int64_t)blockIdx.x * b * nrhs;
-  for (int j = warp; j < b; j += TH_THREADS / 32) {
-    double acc[kThinMaxRhs];
-#pragma unroll
-    for (int c = 0; c < kThinMaxRhs; ++c) acc[c] = 0.0;
-    for (int rr = lane; rr < rows; rr += 32) {
-      const double w = w_unit_lower(W, ldw, r0 + rr, j);
-#pragma unroll
-      for (int c = 0; c < kThinMaxRhs; ++c)
-        if (c < nrhs) acc[c] = fma(w, xs[rr + c * TH_ROWS], acc[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < kThinMaxRhs; ++c) {
-      if (c >= nrhs) break;
-      double s = acc[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) out[j + c * b] = s;
-    }
+  for (int e = t; e < TN_ROWS * NR; e += TN_THREADS) {
+    const int64_t row = (int64_t)blockIdx.x * TN_ROWS + (e % TN_ROWS);
+    if (row >= M) continue;
+    const int c = e / TN_ROWS;
+    const double s = ((red[e] + red[TN_ROWS * NR + e]) + red[2 * TN_ROWS * NR + e]) +
+                     red[3 * TN_ROWS * NR + e];
+    if (part)
+      part[(int64_t)blockIdx.y * M * NR + (int64_t)c * M + row] = s;
+    else
+      store_out(y + row + (int64_t)c * ldy, alpha, beta, s);
   }
 }
 
-// One CTA per right-hand side c: p = sum over chunks of the partials (chunk
-// order), p2 = op(T) p.
-__global__ void __launch_bounds__(TH_THREADS) thin_reduce_kernel(int b, int nrhs, int chunks,
-                                                                  const double* __restrict__ part,
-                                                                  const double* __restrict__ T,
-                                                                  int64_t ldt, int transT,
-                                                                  double* __restrict__ p2) {
-  __shared__ double p[128];
-  const int c = blockIdx.x;
-  for (int j = threadIdx.x; j < b; j += TH_THREADS) {
-    double s = 0.0;
-    for (int g = 0; g < chunks; ++g) s += part[(int64_t)g * b * nrhs + j + c * b];
-    p[j] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < b; i += TH_THREADS) {
-    double s = 0.0;
-    if (!transT) {
-      for (int l = i; l < b; ++l) s = fma(T[i + (int64_t)l * ldt], p[l], s);
+// Sum of V values per lane over the 32 lanes of a warp with FP64 adds on
+// halves: while V is even, each step keeps half of the values (the lane's
+// bit at the step's offset picks which) and adds the partner's copy of
+// them, so a lane does V/2 + V/4 + ... adds instead of 5 V; the remaining
+// offsets add whole sets.  Afterwards the lane holds the sums of the
+// original values base .. base + V / 2^halvings - 1.
+template <int V, int OFF>
+struct WarpSumHalves {
+  static __device__ __forceinline__ void run(double* v, int lane, int& base) {
+    if constexpr (OFF == 0) {
+      return;
+    } else if constexpr (V % 2 == 0) {
+      const bool up = (lane & OFF) != 0;
+#pragma unroll
+      for (int j = 0; j < V / 2; ++j) {
+        const double send = up ? v[j] : v[j + V / 2];
+        const double keep = up ? v[j + V / 2] : v[j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+      }
+      if (up) base += V / 2;
+      WarpSumHalves<V / 2, OFF / 2>::run(v, lane, base);
     } else {
-      for (int l = 0; l <= i; ++l) s = fma(T[l + (int64_t)i * ldt], p[l], s);
+#pragma unroll
+      for (int j = 0; j < V; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], OFF);
+      WarpSumHalves<V, OFF / 2>::run(v, lane, base);
     }
-    p2[i + c * b] = s;
+  }
+};
+// Halvings of a V-value sum over 32 lanes (at most 5) and what remains.
+constexpr int halvings(int V) { return (V % 2 == 0 && V > 1) ? 1 + (halvings(V / 2) < 4 ? halvings(V / 2) : 4) : 0; }
+
+template <bool UL, int NC>
+__global__ void __launch_bounds__(TN_THREADS) thin_t_kernel(int64_t M, int64_t K,
+                                                            const double* __restrict__ A,
+                                                            int64_t lda,
+                                                            const double* __restrict__ x,
+                                                            int64_t ldx, int cbase, int nrhs,
+                                                            int64_t ichunk, double alpha,
+                                                            double beta, double* y, int64_t ldy,
+                                                            double* part) {
+  constexpr int V = 8 * NC;
+  constexpr int H = halvings(V) < 5 ? halvings(V) : 5;
+  constexpr int R = V >> H;                       // values a lane holds at the end
+  constexpr int PLAIN = (1 << (5 - H)) - 1;       // lane bits of the whole-set steps
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t jb = (int64_t)blockIdx.x * TT_COLS + w * 8;
+  const int c0 = cbase + blockIdx.z * NC;
+  const int64_t ib = (int64_t)blockIdx.y * ichunk;
+  const int64_t ie = std::min<int64_t>(K, ib + ichunk);
+  double acc[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) acc[e] = 0.0;
+  const int64_t jn = M - jb;  // columns of this warp that exist: min(8, jn)
+#pragma unroll 4
+  for (int64_t i = ib + lane; i < ie; i += 32) {
+    double xv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) xv[c] = __ldg(x + i + (int64_t)(c0 + c) * ldx);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double a = u < jn ? load_a<UL>(A, lda, i, jb + u) : 0.0;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[u * NC + c] = fma(a, xv[c], acc[u * NC + c]);
+    }
+  }
+  int base = 0;
+  WarpSumHalves<V, 16>::run(acc, lane, base);
+  if ((lane & PLAIN) == 0) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int idx = base + j, u = idx / NC, c = idx % NC;
+      if (u >= jn) continue;
+      if (part)
+        part[(int64_t)blockIdx.y * M * nrhs + (int64_t)(c0 + c) * M + jb + u] = acc[j];
+      else
+        store_out(y + jb + u + (int64_t)(c0 + c) * ldy, alpha, beta, acc[j]);
+    }
   }
 }
 
-__global__ void __launch_bounds__(TH_THREADS) thin_update_kernel(int64_t M, int b, int nrhs,
-                                                                  const double* __restrict__ W,
-                                                                  int64_t ldw,
-                                                                  const double* __restrict__ p2,
-                                                                  double* __restrict__ x,
-                                                                  int64_t ldx) {
-  __shared__ double ps[128 * kThinMaxRhs];
-  for (int e = threadIdx.x; e < b * nrhs; e += TH_THREADS) ps[e] = p2[e];
+// y(e) = beta y + alpha sum_g part[g][e] over the M x nrhs entries e = i + c M
+// (y(i, c) at y[i + c ldy]): 32 entries per CTA, eight groups of chunks per
+// entry summed in a fixed order.
+__global__ void __launch_bounds__(256) thin_reduce_kernel(int64_t M, int nrhs, int splits,
+                                                          const double* __restrict__ part,
+                                                          double alpha, double beta, double* y,
+                                                          int64_t ldy) {
+  __shared__ double red[8][32];
+  const int o = threadIdx.x & 31, gg = threadIdx.x >> 5;
+  const int64_t tot = M * nrhs;
+  const int64_t e = (int64_t)blockIdx.x * 32 + o;
+  double s = 0.0;
+  if (e < tot) {
+#pragma unroll 4
+    for (int g = gg; g < splits; g += 8) s += part[(int64_t)g * tot + e];
+  }
+  red[gg][o] = s;
   __syncthreads();
-  const int64_t r = (int64_t)blockIdx.x * TH_THREADS + threadIdx.x;
-  if (r >= M) return;
-  double acc[kThinMaxRhs];
+  if (gg == 0 && e < tot) {
+    double t = red[0][o];
 #pragma unroll
-  for (int c = 0; c < kThinMaxRhs; ++c) acc[c] = 0.0;
-  const int jmax = (int)(r + 1 < b ? r + 1 : b);  // W(r, j) = 0 for j > r
-  for (int j = 0; j < jmax; ++j) {
-    const double w = w_unit_lower(W, ldw, r, j);
-#pragma unroll
-    for (int c = 0; c < kThinMaxRhs; ++c)
-      if (c < nrhs) acc[c] = fma(w, ps[j + c * b], acc[c]);
+    for (int q = 1; q < 8; ++q) t += red[q][o];
+    store_out(y + (e % M) + (e / M) * ldy, alpha, beta, t);
   }
-#pragma unroll
-  for (int c = 0; c < kThinMaxRhs; ++c)
-    if (c < nrhs) x[r + (int64_t)c * ldx] -= acc[c];
 }
 
-// x(0:b) <- op(S) x(0:b) for a b x b block S, one CTA per right-hand side.
-__global__ void __launch_bounds__(128) thin_small_mul_kernel(int b, const double* __restrict__ S,
+// Reflector replay, middle step: one CTA (512 threads) per right-hand side c
+// sums the row chunks' partials p = W^T x (four groups of chunks per entry,
+// fixed order) and forms p2 = op(T) p for the upper triangular T, four
+// threads per entry of p2 (every fourth l each, then two shuffle adds).
+__global__ void __launch_bounds__(512) thin_reduce_trmv_kernel(int b, int nrhs, int splits,
+                                                               const double* __restrict__ part,
+                                                               const double* __restrict__ T,
+                                                               int64_t ldt, int transT,
+                                                               double* __restrict__ p2) {
+  __shared__ double red[4][128];
+  __shared__ double p[128];
+  const int c = blockIdx.x, t = threadIdx.x;
+  {
+    const int j = t & 127, gg = t >> 7;
+    double s = 0.0;
+    if (j < b) {
+#pragma unroll 4
+      for (int g = gg; g < splits; g += 4) s += part[((int64_t)g * nrhs + c) * b + j];
+    }
+    red[gg][j] = s;
+  }
+  __syncthreads();
+  if (t < 128) p[t] = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
+  __syncthreads();
+  const int i = t >> 2, lg = t & 3;
+  double s = 0.0;
+  if (i < b) {
+    if (!transT) {
+      for (int l = i + ((lg - i) & 3); l < b; l += 4) s = fma(__ldg(T + i + (int64_t)l * ldt), p[l], s);
+    } else {
+      for (int l = lg; l <= i; l += 4) s = fma(__ldg(T + l + (int64_t)i * ldt), p[l], s);
+    }
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (i < b && lg == 0) p2[i + (int64_t)c * b] = s;
+}
+
+// x(0:b) <- op(S) x(0:b) for a full b x b block S, one CTA (512 threads) per
+// right-hand side, four threads per entry.
+__global__ void __launch_bounds__(512) thin_small_mul_kernel(int b, const double* __restrict__ S,
                                                              int64_t lds, int transS, double* x,
                                                              int64_t ldx) {
   __shared__ double xs[128];
   double* xc = x + (int64_t)blockIdx.x * ldx;
-  for (int i = threadIdx.x; i < b; i += 128) xs[i] = xc[i];
+  const int t = threadIdx.x, i = t >> 2, lg = t & 3;
+  if (t < b) xs[t] = xc[t];
   __syncthreads();
-  for (int i = threadIdx.x; i < b; i += 128) {
-    double s = 0.0;
-    for (int l = 0; l < b; ++l)
-      s = fma(transS ? S[l + (int64_t)i * lds] : S[i + (int64_t)l * lds], xs[l], s);
-    xc[i] = s;
+  double s = 0.0;
+  if (i < b) {
+    if (!transS) {
+      for (int l = lg; l < b; l += 4) s = fma(__ldg(S + i + (int64_t)l * lds), xs[l], s);
+    } else {
+      for (int l = lg; l < b; l += 4) s = fma(__ldg(S + l + (int64_t)i * lds), xs[l], s);
+    }
   }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  __syncthreads();  // every thread has read xs before x is overwritten
+  if (i < b && lg == 0) xc[i] = s;
+}
+
+struct Split {
+  int64_t splits, chunk;
+};
+
+// K chunks of thin_n_kernel: a multiple of the k tile, at least kMinChunk
+// long, enough of them for kSplitTarget CTAs.
+Split split_n(int64_t M, int64_t K) {
+  const int64_t tiles = ceil_div(M, TN_ROWS);
+  int64_t s = std::min(ceil_div(kSplitTarget, tiles), ceil_div(K, kMinChunk));
+  s = std::max<int64_t>(s, 1);
+  const int64_t chunk = ceil_div(ceil_div(K, s), TN_KT) * TN_KT;
+  return {ceil_div(K, chunk), chunk};
+}
+
+// Row chunks of thin_t_kernel: a multiple of 32 rows, at least kMinChunk.
+Split split_t(int64_t M, int64_t K, int64_t nrhs) {
+  const int64_t ctas = ceil_div(M, TT_COLS) * ceil_div(nrhs, TT_CG);
+  int64_t s = std::min(ceil_div(kSplitTarget, ctas), ceil_div(K, kMinChunk));
+  s = std::max<int64_t>(s, 1);
+  const int64_t chunk = ceil_div(ceil_div(K, s), 32) * 32;
+  return {ceil_div(K, chunk), chunk};
+}
+
+// Calls f(std::integral_constant<int, N>) for N = n in 1..MAX.
+template <int N, int MAX, class F>
+void dispatch_count(int n, F&& f) {
+  if constexpr (N <= MAX) {
+    if (n == N) f(std::integral_constant<int, N>{});
+    else dispatch_count<N + 1, MAX>(n, f);
+  }
+}
+
+template <bool UL>
+void launch_n(int64_t M, int64_t K, int nrhs, double alpha, const double* A, int64_t lda,
+              const double* x, int64_t ldx, double beta, double* y, int64_t ldy, double* part,
+              const Split& sp, cudaStream_t st) {
+  const dim3 grid((unsigned)ceil_div(M, TN_ROWS), (unsigned)sp.splits);
+  dispatch_count<1, kThinMaxRhs>(nrhs, [&](auto nr) {
+    thin_n_kernel<UL, decltype(nr)::value><<<grid, TN_THREADS, 0, st>>>(
+        M, K, A, lda, x, ldx, sp.chunk, alpha, beta, y, ldy, part);
+  });
+}
+
+// nrhs = 4 q + r right-hand sides: q groups of 4 in one launch, the r left
+// over in a second.
+template <bool UL>
+void launch_t(int64_t M, int64_t K, int nrhs, double alpha, const double* A, int64_t lda,
+              const double* x, int64_t ldx, double beta, double* y, int64_t ldy, double* part,
+              const Split& sp, cudaStream_t st) {
+  const int q = nrhs / TT_CG, r = nrhs % TT_CG;
+  const unsigned gx = (unsigned)ceil_div(M, TT_COLS), gy = (unsigned)sp.splits;
+  if (q > 0)
+    thin_t_kernel<UL, TT_CG><<<dim3(gx, gy, (unsigned)q), TN_THREADS, 0, st>>>(
+        M, K, A, lda, x, ldx, 0, nrhs, sp.chunk, alpha, beta, y, ldy, part);
+  if (r > 0)
+    dispatch_count<1, TT_CG - 1>(r, [&](auto nc) {
+      thin_t_kernel<UL, decltype(nc)::value><<<dim3(gx, gy, 1), TN_THREADS, 0, st>>>(
+          M, K, A, lda, x, ldx, q * TT_CG, nrhs, sp.chunk, alpha, beta, y, ldy, part);
+    });
+}
+
+// op(A) x into y (alpha, beta) or, with part != nullptr, into the chunks'
+// partial sums part[chunk][c][i].
+Status launch_thin(bool trans, bool unit_lower, int64_t M, int64_t K, int64_t nrhs, double alpha,
+                   const double* A, int64_t lda, const double* x, int64_t ldx, double beta,
+                   double* y, int64_t ldy, double* part, const Split& sp, cudaStream_t st) {
+  TraceScope ts(trans ? kTrThinT : kTrThinN, st, 2.0 * M * K * nrhs, 8.0 * M * K);
+  if (!trans) {
+    if (unit_lower)
+      launch_n<true>(M, K, (int)nrhs, alpha, A, lda, x, ldx, beta, y, ldy, part, sp, st);
+    else
+      launch_n<false>(M, K, (int)nrhs, alpha, A, lda, x, ldx, beta, y, ldy, part, sp, st);
+    LLS_LAUNCHED("thin_n_kernel");
+  } else {
+    if (unit_lower)
+      launch_t<true>(M, K, (int)nrhs, alpha, A, lda, x, ldx, beta, y, ldy, part, sp, st);
+    else
+      launch_t<false>(M, K, (int)nrhs, alpha, A, lda, x, ldx, beta, y, ldy, part, sp, st);
+    LLS_LAUNCHED("thin_t_kernel");
+  }
+  return ok_status();
+}
+
+Split split_of(bool trans, int64_t M, int64_t K, int64_t nrhs) {
+  return trans ? split_t(M, K, nrhs) : split_n(M, K);
 }
 
 }  // namespace
 
+size_t thin_gemv_scratch_bytes(bool trans, int64_t M, int64_t K, int64_t nrhs) {
+  if (M <= 0 || K <= 0 || nrhs <= 0) return 0;
+  const Split sp = split_of(trans, M, K, nrhs);
+  return sp.splits > 1 ? sizeof(double) * (size_t)sp.splits * M * nrhs : 0;
+}
+
+Status thin_gemv(bool trans, bool unit_lower, int64_t M, int64_t K, int64_t nrhs, double alpha,
+                 const double* A, int64_t lda, const double* x, int64_t ldx, double beta, double* y,
+                 int64_t ldy, Scratch scratch, cudaStream_t st) {
+  if (M <= 0 || nrhs <= 0) return ok_status();
+  if (nrhs > kThinMaxRhs) return make_error(LLS_ERR_ARG, "thin_gemv: nrhs <= 16");
+  if (K <= 0) {  // y = beta y
+    if (beta == 0.0) return fill_zero(M, nrhs, y, ldy, st);
+    return beta == 1.0 ? ok_status() : axpy_matrix(M, nrhs, beta - 1.0, y, ldy, y, ldy, st);
+  }
+  if (ceil_div(M, TN_ROWS) > INT32_MAX) return make_error(LLS_ERR_ARG, "thin_gemv: too many rows");
+  const Split sp = split_of(trans, M, K, nrhs);
+  if (sp.splits == 1)
+    return launch_thin(trans, unit_lower, M, K, nrhs, alpha, A, lda, x, ldx, beta, y, ldy, nullptr,
+                       sp, st);
+  if (scratch.bytes < thin_gemv_scratch_bytes(trans, M, K, nrhs))
+    return make_error(LLS_ERR_NOMEM, "thin_gemv: scratch too small");
+  double* part = static_cast<double*>(scratch.ptr);
+  LLS_TRY(launch_thin(trans, unit_lower, M, K, nrhs, 1.0, A, lda, x, ldx, 0.0, nullptr, 0, part, sp,
+                      st));
+  TraceScope ts(kTrThin, st);
+  thin_reduce_kernel<<<(unsigned)ceil_div(M * nrhs, 32), 256, 0, st>>>(M, (int)nrhs, (int)sp.splits,
+                                                                       part, alpha, beta, y, ldy);
+  LLS_LAUNCHED("thin_reduce_kernel");
+  return ok_status();
+}
+
 size_t thin_scratch_bytes(int64_t M, int64_t b, int64_t nrhs) {
-  return sizeof(double) * ((size_t)ceil_div(M, TH_ROWS) * b * nrhs + (size_t)b * nrhs);
+  if (M <= 0 || b <= 0 || nrhs <= 0) return 0;
+  const Split sp = split_t(b, M, nrhs);
+  return sizeof(double) * ((size_t)sp.splits * b * nrhs + (size_t)b * nrhs);
 }
 
 Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W, int64_t ldw,
@@ -147,29 +415,28 @@ Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W
     return make_error(LLS_ERR_ARG, "apply_reflectors_thin: b <= 128 and nrhs <= 16");
   if (scratch.bytes < thin_scratch_bytes(M, b, nrhs))
     return make_error(LLS_ERR_NOMEM, "apply_reflectors_thin: scratch too small");
-  const int64_t chunks = ceil_div(M, TH_ROWS);
-  if (chunks > INT32_MAX) return make_error(LLS_ERR_ARG, "apply_reflectors_thin: too many rows");
+  const Split sp = split_t(b, M, nrhs);
   double* part = static_cast<double*>(scratch.ptr);
-  double* p2 = part + (size_t)chunks * b * nrhs;
-  TraceScope ts(kTrSmall, st, 4.0 * M * b * nrhs, 16.0 * M * b);
-  thin_partials_kernel<<<(unsigned)chunks, TH_THREADS, 0, st>>>(M, (int)b, (int)nrhs, W, ldw, x,
-                                                                 ldx, part);
-  LLS_LAUNCHED("thin_partials_kernel");
-  thin_reduce_kernel<<<(unsigned)nrhs, TH_THREADS, 0, st>>>((int)b, (int)nrhs, (int)chunks, part, T,
-                                                            ldt, transT ? 1 : 0, p2);
-  LLS_LAUNCHED("thin_reduce_kernel");
-  thin_update_kernel<<<(unsigned)ceil_div(M, TH_THREADS), TH_THREADS, 0, st>>>(M, (int)b, (int)nrhs,
-                                                                               W, ldw, p2, x, ldx);
-  LLS_LAUNCHED("thin_update_kernel");
-  return ok_status();
+  double* p2 = part + (size_t)sp.splits * b * nrhs;
+  // p = W^T x by row chunks
+  LLS_TRY(launch_thin(true, true, b, M, nrhs, 1.0, W, ldw, x, ldx, 0.0, nullptr, 0, part, sp, st));
+  {  // p2 = op(T) p
+    TraceScope ts(kTrThin, st);
+    thin_reduce_trmv_kernel<<<(unsigned)nrhs, 512, 0, st>>>((int)b, (int)nrhs, (int)sp.splits, part,
+                                                            T, ldt, transT ? 1 : 0, p2);
+    LLS_LAUNCHED("thin_reduce_trmv_kernel");
+  }
+  // x -= W p2 (K = b <= 128: one K chunk)
+  const Split one{1, b};
+  return launch_thin(false, true, M, b, nrhs, -1.0, W, ldw, p2, b, 1.0, x, ldx, nullptr, one, st);
 }
 
 Status small_block_mul(int64_t b, int64_t nrhs, const double* S, int64_t lds, bool transS,
                        double* x, int64_t ldx, cudaStream_t st) {
   if (b <= 0 || nrhs <= 0) return ok_status();
   if (b > 128) return make_error(LLS_ERR_ARG, "small_block_mul: b <= 128");
-  TraceScope ts(kTrSmall, st);
-  thin_small_mul_kernel<<<(unsigned)nrhs, 128, 0, st>>>((int)b, S, lds, transS ? 1 : 0, x, ldx);
+  TraceScope ts(kTrThin, st);
+  thin_small_mul_kernel<<<(unsigned)nrhs, 512, 0, st>>>((int)b, S, lds, transS ? 1 : 0, x, ldx);
   LLS_LAUNCHED("thin_small_mul_kernel");
   return ok_status();
 }

@@ -219,70 +219,106 @@ refine_update_kernel(int64_t n, const double* __restrict__ D, int64_t ldd, doubl
   }
 }
 
-// Back substitution on one diagonal block, one CTA per right-hand side:
-// y_i = b_i / R(i,i), then b_l -= R(l,i) y_i for l < i, from the bottom.
-__global__ void trsm_block_kernel(int64_t k, const double* __restrict__ R, int64_t ldr, double* B,
-                                  int64_t ldb) {
-  extern __shared__ double x[];
+// One k x k diagonal block (k <= 128) of an upper triangular R, one CTA per
+// right-hand side: B <- R^{-1} B (back substitution) or, trans, B <- R^{-T} B
+// (forward substitution with R^T(l, i) = R(i, l)).  The block is staged in
+// shared memory with coalesced loads (k^2 / blockDim in flight per thread);
+// thread l owns x_l in a register and 1 / R(l, l); step i publishes
+// y_i = x_i / R(i, i) (as x_i times the reciprocal, computed off the serial
+// chain) and every thread still to be solved subtracts R(l, i) y_i.  One
+// barrier per step: each y_i has its own shared slot.
+__global__ void __launch_bounds__(128) trsm_diag_kernel(int k, const double* __restrict__ R,
+                                                        int64_t ldr, double* B, int64_t ldb,
+                                                        int trans) {
+  extern __shared__ double sm[];
+  double* Rs = sm;                      // k x k, ld k + 1
+  double* ys = sm + (size_t)k * (k + 1);  // k
+  const int ld = k + 1, l = threadIdx.x;
   double* b = B + (int64_t)blockIdx.x * ldb;
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) x[i] = b[i];
+#pragma unroll 16
+  for (int e = l; e < k * k; e += blockDim.x) Rs[(e % k) + ld * (e / k)] = __ldg(R + (e % k) + (int64_t)(e / k) * ldr);
+  double xl = l < k ? b[l] : 0.0;
   __syncthreads();
-  for (int64_t i = k - 1; i >= 0; --i) {
-    double yi = x[i] / R[i + i * ldr];
-    for (int64_t l = threadIdx.x; l < i; l += blockDim.x) x[l] = fma(-R[l + i * ldr], yi, x[l]);
-    __syncthreads();
-    if (threadIdx.x == 0) x[i] = yi;
-    __syncthreads();
+  const double rinv = l < k ? 1.0 / Rs[l + ld * l] : 0.0;
+  if (!trans) {
+    for (int i = k - 1; i >= 0; --i) {
+      if (l == i) ys[i] = xl * rinv;
+      __syncthreads();
+      if (l < i) xl = fma(-Rs[l + ld * i], ys[i], xl);
+    }
+  } else {
+    for (int i = 0; i < k; ++i) {
+      if (l == i) ys[i] = xl * rinv;
+      __syncthreads();
+      if (l > i && l < k) xl = fma(-Rs[i + ld * l], ys[i], xl);
+    }
   }
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) b[i] = x[i];
+  if (l < k) b[l] = ys[l];
 }
 
-// y (M x nrhs) -= op(A) x for op(A) M x K (A[i + k lda], or A^T: A[k + i lda]),
-// x K x nrhs: the off-diagonal block updates of a blocked triangular solve
-// with few right-hand sides (K <= kTrsmBlock, nrhs <= kThinMaxRhs), one thread
-// per row.  The general FP64 GEMM pads N to its 16-column tile, which costs
-// 16 times the FP64 work for one right-hand side on this part.
-__global__ void __launch_bounds__(256) gemv_thin_sub_kernel(int64_t M, int K, int nrhs,
-                                                            const double* __restrict__ A,
-                                                            int64_t lda, int trans,
-                                                            const double* __restrict__ x,
-                                                            int64_t ldx, double* y, int64_t ldy) {
-  __shared__ double xs[64 * 16];
-  for (int e = threadIdx.x; e < K * nrhs; e += blockDim.x) xs[e] = x[(e % K) + (int64_t)(e / K) * ldx];
+// Inverses of the 64 x 64 diagonal blocks of an upper triangular r x r
+// matrix R, blocks aligned from the top ([64 q, 64 q + 64), the last one
+// partial): one CTA of 64 threads per block, thread j forms column j of the
+// inverse by back substitution on e_j (X(j, j) = 1 / R(j, j), then
+// X(i, j) = -(sum_{l = i+1..j} R(i, l) X(l, j)) / R(i, i) for i < j).  Dinv
+// holds the blocks one after another, 64 x 64 column-major, zero below the
+// diagonal and outside a partial block.
+constexpr int kInvBlk = 64;
+__global__ void __launch_bounds__(kInvBlk) trsm_blockinv_kernel(int64_t r,
+                                                                const double* __restrict__ R,
+                                                                int64_t ldr, double* Dinv) {
+  extern __shared__ double sm[];
+  constexpr int LD = kInvBlk + 1;
+  double* Rs = sm;                        // kb x kb
+  double* Xs = sm + kInvBlk * LD;         // kb x kb
+  double* rinv = sm + 2 * kInvBlk * LD;   // kb
+  const int64_t j0 = (int64_t)blockIdx.x * kInvBlk;
+  const int kb = (int)(r - j0 < kInvBlk ? r - j0 : kInvBlk);
+  const int j = threadIdx.x;
+  const double* Rb = R + j0 + j0 * ldr;
+#pragma unroll 8
+  for (int e = j; e < kb * kb; e += kInvBlk) Rs[(e % kb) + LD * (e / kb)] = __ldg(Rb + (e % kb) + (int64_t)(e / kb) * ldr);
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  double acc[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) acc[c] = 0.0;
-  for (int k = 0; k < K; ++k) {
-    const double a = trans ? A[k + i * lda] : A[i + (int64_t)k * lda];
-#pragma unroll
-    for (int c = 0; c < 16; ++c)
-      if (c < nrhs) acc[c] = fma(a, xs[k + c * K], acc[c]);
+  if (j < kb) rinv[j] = 1.0 / Rs[j + LD * j];
+  __syncthreads();
+  if (j < kb) {
+    Xs[j + LD * j] = rinv[j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1; l <= j; ++l) s = fma(Rs[i + LD * l], Xs[l + LD * j], s);
+      Xs[i + LD * j] = -s * rinv[i];
+    }
   }
-#pragma unroll
-  for (int c = 0; c < 16; ++c)
-    if (c < nrhs) y[i + (int64_t)c * ldy] -= acc[c];
+  __syncthreads();
+  double* D = Dinv + (int64_t)blockIdx.x * kInvBlk * kInvBlk;
+  for (int e = j; e < kInvBlk * kInvBlk; e += kInvBlk) {
+    const int ii = e % kInvBlk, jj = e / kInvBlk;
+    D[e] = (ii <= jj && jj < kb) ? Xs[ii + LD * jj] : 0.0;
+  }
 }
 
-// B <- R^{-T} B for one k x k diagonal block: forward substitution with the
-// transpose of the upper triangular R (R^T(l, i) = R(i, l)), one CTA per
-// right-hand side.
-__global__ void trsm_block_trans_kernel(int64_t k, const double* __restrict__ R, int64_t ldr,
-                                        double* B, int64_t ldb) {
-  extern __shared__ double x[];
+// x(0:kb) <- op(D) x(0:kb) for one 64 x 64 upper triangular block inverse D
+// (op(D) = D^T when trans), one CTA per right-hand side, four threads per
+// entry (every fourth l each, then two shuffle adds).
+__global__ void __launch_bounds__(256) blk_inv_apply_kernel(int kb, const double* __restrict__ D,
+                                                            int trans, double* B, int64_t ldb) {
+  __shared__ double xs[kInvBlk];
   double* b = B + (int64_t)blockIdx.x * ldb;
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) x[i] = b[i];
+  const int t = threadIdx.x, i = t >> 2, lg = t & 3;
+  if (t < kb) xs[t] = b[t];
   __syncthreads();
-  for (int64_t i = 0; i < k; ++i) {
-    double yi = x[i] / R[i + i * ldr];
-    for (int64_t l = i + 1 + threadIdx.x; l < k; l += blockDim.x) x[l] = fma(-R[i + l * ldr], yi, x[l]);
-    __syncthreads();
-    if (threadIdx.x == 0) x[i] = yi;
-    __syncthreads();
+  double s = 0.0;
+  if (i < kb) {
+    if (!trans) {
+      for (int l = i + ((lg - i) & 3); l < kb; l += 4) s = fma(__ldg(D + i + kInvBlk * l), xs[l], s);
+    } else {
+      for (int l = lg; l <= i; l += 4) s = fma(__ldg(D + l + kInvBlk * i), xs[l], s);
+    }
   }
-  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) b[i] = x[i];
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  __syncthreads();
+  if (i < kb && lg == 0) b[i] = s;
 }
 
 // out[0] = min_{j < r} |d_j|, out[1] = max_{r <= j < len} |d_j| (0 when the
@@ -471,32 +507,35 @@ Status copy_cols_reversed(int64_t rows, int64_t cols, const double* src, int64_t
   return ok_status();
 }
 
+namespace {
+
+Status trsm_diag(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double* B, int64_t ldb,
+                 bool trans, cudaStream_t st) {
+  if (k <= 0 || nrhs <= 0) return ok_status();
+  if (k > 128) return make_error(LLS_ERR_ARG, "trsm: diagonal blocks of at most 128");
+  if (nrhs > 2147483647) return make_error(LLS_ERR_ARG, "trsm: too many right-hand sides");
+  const size_t smem = sizeof(double) * (size_t)(k * (k + 1) + k);
+  if (smem > 48 * 1024) LLS_TRY(allow_max_dyn_smem((const void*)trsm_diag_kernel));
+  TraceScope ts(kTrTrsmDiag, st);
+  trsm_diag_kernel<<<(unsigned)nrhs, 128, smem, st>>>((int)k, R, ldr, B, ldb, trans ? 1 : 0);
+  LLS_LAUNCHED("trsm_diag_kernel");
+  return ok_status();
+}
+
+}  // namespace
+
 Status trsm_block(int64_t k, int64_t nrhs, const double* R, int64_t ldr, double* B, int64_t ldb,
                   cudaStream_t st) {
-  if (k <= 0 || nrhs <= 0) return ok_status();
-  if (nrhs > 2147483647) return make_error(LLS_ERR_ARG, "trsm: too many right-hand sides");
-  TraceScope ts(kTrSmall, st);
-  trsm_block_kernel<<<(unsigned)nrhs, 128, sizeof(double) * k, st>>>(k, R, ldr, B, ldb);
-  LLS_LAUNCHED("trsm_block_kernel");
-  return ok_status();
+  return trsm_diag(k, nrhs, R, ldr, B, ldb, false, st);
 }
 
 constexpr int64_t kTrsmBlock = 64;
-static_assert(kTrsmBlock <= 64 && kThinMaxRhs <= 16, "gemv_thin_sub_kernel's shared x");
 
-// y (M x nrhs) -= op(A) x, thin: see gemv_thin_sub_kernel.
-Status gemv_thin_sub(int64_t M, int64_t K, int64_t nrhs, const double* A, int64_t lda, bool trans,
-                     const double* x, int64_t ldx, double* y, int64_t ldy, cudaStream_t st) {
-  if (M <= 0 || K <= 0 || nrhs <= 0) return ok_status();
-  TraceScope ts(kTrSmall, st, 2.0 * M * K * nrhs, 8.0 * M * K);
-  gemv_thin_sub_kernel<<<(unsigned)ceil_div(M, 256), 256, 0, st>>>(M, (int)K, (int)nrhs, A, lda,
-                                                                    trans ? 1 : 0, x, ldx, y, ldy);
-  LLS_LAUNCHED("gemv_thin_sub_kernel");
-  return ok_status();
-}
-
+// The off-diagonal updates use thin_gemv for nrhs <= kThinMaxRhs (K = 64: no
+// split, no scratch) and the FP64 GEMM otherwise.
 size_t trsm_upper_scratch_bytes(int64_t r, int64_t nrhs) {
   size_t need = 0;
+  if (nrhs <= kThinMaxRhs) return 0;
   for (int64_t j1 = r; j1 > 0; j1 -= kTrsmBlock) {
     const int64_t j0 = std::max<int64_t>(0, j1 - kTrsmBlock);
     if (j0 > 0) need = std::max(need, gemm_scratch_bytes(j0, nrhs, j1 - j0));
@@ -510,9 +549,11 @@ Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double*
   int64_t j1 = r;
   while (j1 > 0) {
     int64_t j0 = std::max<int64_t>(0, j1 - TB);
-    LLS_TRY(trsm_block(j1 - j0, nrhs, R + j0 + j0 * ldr, ldr, B + j0, ldb, st));
+    LLS_TRY(trsm_diag(j1 - j0, nrhs, R + j0 + j0 * ldr, ldr, B + j0, ldb, false, st));
+    // B(0:j0) -= R(0:j0, j0:j1) B(j0:j1)
     if (j0 > 0 && nrhs <= kThinMaxRhs)
-      LLS_TRY(gemv_thin_sub(j0, j1 - j0, nrhs, R + j0 * ldr, ldr, false, B + j0, ldb, B, ldb, st));
+      LLS_TRY(thin_gemv(false, false, j0, j1 - j0, nrhs, -1.0, R + j0 * ldr, ldr, B + j0, ldb, 1.0, B,
+                        ldb, Scratch{}, st));
     else if (j0 > 0)
       LLS_TRY(gemm(false, false, kDense, kDense, j0, nrhs, j1 - j0, -1.0, R + j0 * ldr, ldr,
                    B + j0, ldb, 1.0, B, ldb, scratch, st));
@@ -523,6 +564,7 @@ Status trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double*
 
 size_t trsm_upper_trans_scratch_bytes(int64_t r, int64_t nrhs) {
   size_t need = 0;
+  if (nrhs <= kThinMaxRhs) return 0;
   for (int64_t j0 = 0; j0 < r; j0 += kTrsmBlock) {
     const int64_t j1 = std::min(r, j0 + kTrsmBlock);
     if (j1 < r) need = std::max(need, gemm_scratch_bytes(r - j1, nrhs, j1 - j0));
@@ -533,22 +575,68 @@ size_t trsm_upper_trans_scratch_bytes(int64_t r, int64_t nrhs) {
 Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,
                         int64_t ldb, Scratch scratch, cudaStream_t st) {
   if (r <= 0 || nrhs <= 0) return ok_status();
-  if (nrhs > 2147483647) return make_error(LLS_ERR_ARG, "trsm: too many right-hand sides");
   for (int64_t j0 = 0; j0 < r; j0 += kTrsmBlock) {
     const int64_t j1 = std::min(r, j0 + kTrsmBlock);
-    {
-      TraceScope ts(kTrSmall, st);
-      trsm_block_trans_kernel<<<(unsigned)nrhs, 128, sizeof(double) * (j1 - j0), st>>>(
-          j1 - j0, R + j0 + j0 * ldr, ldr, B + j0, ldb);
-      LLS_LAUNCHED("trsm_block_trans_kernel");
-    }
+    LLS_TRY(trsm_diag(j1 - j0, nrhs, R + j0 + j0 * ldr, ldr, B + j0, ldb, true, st));
     // B(j1:r) -= R(j0:j1, j1:r)^T B(j0:j1)
     if (j1 < r && nrhs <= kThinMaxRhs)
-      LLS_TRY(gemv_thin_sub(r - j1, j1 - j0, nrhs, R + j0 + j1 * ldr, ldr, true, B + j0, ldb, B + j1,
-                            ldb, st));
+      LLS_TRY(thin_gemv(true, false, r - j1, j1 - j0, nrhs, -1.0, R + j0 + j1 * ldr, ldr, B + j0, ldb,
+                        1.0, B + j1, ldb, Scratch{}, st));
     else if (j1 < r)
       LLS_TRY(gemm(true, false, kDense, kDense, r - j1, nrhs, j1 - j0, -1.0, R + j0 + j1 * ldr, ldr,
                    B + j0, ldb, 1.0, B + j1, ldb, scratch, st));
+  }
+  return ok_status();
+}
+
+}  // namespace lls
+
+namespace lls {
+
+size_t trsm_inverse_bytes(int64_t r) {
+  return sizeof(double) * (size_t)ceil_div(std::max<int64_t>(r, 0), kInvBlk) * kInvBlk * kInvBlk;
+}
+
+Status trsm_block_inverses(int64_t r, const double* R, int64_t ldr, double* Dinv, cudaStream_t st) {
+  if (r <= 0) return ok_status();
+  const int64_t nblk = ceil_div(r, kInvBlk);
+  if (nblk > INT32_MAX) return make_error(LLS_ERR_ARG, "trsm_block_inverses: r too large");
+  const size_t smem = sizeof(double) * (2 * kInvBlk * (kInvBlk + 1) + kInvBlk);
+  LLS_TRY(allow_max_dyn_smem((const void*)trsm_blockinv_kernel));
+  TraceScope ts(kTrTrsmDiag, st);
+  trsm_blockinv_kernel<<<(unsigned)nblk, kInvBlk, smem, st>>>(r, R, ldr, Dinv);
+  LLS_LAUNCHED("trsm_blockinv_kernel");
+  return ok_status();
+}
+
+Status trsm_upper_inv(int64_t r, int64_t nrhs, const double* R, int64_t ldr, const double* Dinv,
+                      double* B, int64_t ldb, bool trans, cudaStream_t st) {
+  if (r <= 0 || nrhs <= 0) return ok_status();
+  if (nrhs > kThinMaxRhs) return make_error(LLS_ERR_ARG, "trsm_upper_inv: nrhs <= 16");
+  const int64_t nblk = ceil_div(r, kInvBlk);
+  auto apply = [&](int64_t q, int64_t kb, bool tr) -> Status {
+    TraceScope ts(kTrTrsmDiag, st);
+    blk_inv_apply_kernel<<<(unsigned)nrhs, 256, 0, st>>>((int)kb, Dinv + q * kInvBlk * kInvBlk,
+                                                         tr ? 1 : 0, B + q * kInvBlk, ldb);
+    LLS_LAUNCHED("blk_inv_apply_kernel");
+    return ok_status();
+  };
+  if (!trans) {  // R y = c, bottom block first
+    for (int64_t q = nblk - 1; q >= 0; --q) {
+      const int64_t j0 = q * kInvBlk, kb = std::min<int64_t>(kInvBlk, r - j0);
+      LLS_TRY(apply(q, kb, false));
+      if (j0 > 0)  // c(0:j0) -= R(0:j0, j0:j0+kb) y_q
+        LLS_TRY(thin_gemv(false, false, j0, kb, nrhs, -1.0, R + j0 * ldr, ldr, B + j0, ldb, 1.0, B,
+                          ldb, Scratch{}, st));
+    }
+  } else {  // R^T y = c, top block first
+    for (int64_t q = 0; q < nblk; ++q) {
+      const int64_t j0 = q * kInvBlk, j1 = std::min(r, j0 + kInvBlk);
+      LLS_TRY(apply(q, j1 - j0, true));
+      if (j1 < r)  // c(j1:r) -= R(j0:j1, j1:r)^T y_q
+        LLS_TRY(thin_gemv(true, false, r - j1, j1 - j0, nrhs, -1.0, R + j0 + j1 * ldr, ldr, B + j0,
+                          ldb, 1.0, B + j1, ldb, Scratch{}, st));
+    }
   }
   return ok_status();
 }

@@ -7,7 +7,7 @@
 //    reflectors (W_U below the diagonal of T, W_V in a side buffer), their
 //    compact-WY factors and the diagonal block's singular vectors; U^T b and,
 //    without an explicit V, V y are applied from them (the paper's v23t
-//    variant applies U to B on the fly, Sec. 3.4).
+//    variant applies U to B on the fly, Sec. 3.5).
 //  * The right update of step i runs over all m rows of columns k..n-1
 //    (Fig. 2 prints only the A_BR block; the rows above must change too for
 //    A V = U T to hold).
@@ -470,6 +470,19 @@ Status hgemm(Handle& h, bool ta, bool tb, OperandMode ma, OperandMode mb, int64_
               scratch_of(h.gemm_ws), h.stream);
 }
 
+// y = beta y + alpha op(A) x (op(A) mm x kk, x kk x nrhs): the thin products
+// for nrhs <= kThinMaxRhs, else the FP64 GEMM.
+Status hgemv(Handle& h, bool ta, int64_t mm, int64_t nrhs, int64_t kk, double alpha,
+             const double* Aa, int64_t lda_, const double* x, int64_t ldx, double beta, double* y,
+             int64_t ldy) {
+  if (nrhs <= kThinMaxRhs) {
+    LLS_TRY(h.gemm_ws.reserve(thin_gemv_scratch_bytes(ta, mm, kk, nrhs)));
+    return thin_gemv(ta, false, mm, kk, nrhs, alpha, Aa, lda_, x, ldx, beta, y, ldy,
+                     scratch_of(h.gemm_ws), h.stream);
+  }
+  return hgemm(h, ta, false, kDense, kDense, mm, nrhs, kk, alpha, Aa, lda_, x, ldx, beta, y, ldy);
+}
+
 // Buffers of one replay: two nb x nrhs panels and the thin path's scratch.
 Status reserve_replay(Handle& h, Factor& f, int64_t nrhs) {
   LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)f.nb * nrhs));
@@ -515,6 +528,13 @@ Status nullify_block(Handle& h, Factor& f, const Factor::RzBlock& bl, int64_t nr
   double* p2 = h.sp2.d();
   LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldz, zc, bsz, st));
   LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
+  if (nrhs <= kThinMaxRhs) {  // p = op(T_z) (p + W_bot^T Z_tail) in place
+    LLS_TRY(hgemv(h, true, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldz, 1.0, p, bsz));
+    LLS_TRY(small_block_mul(bsz, nrhs, Tz, bsz, transT, p, bsz, st));
+    LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p, bsz, zc, bsz, st));
+    LLS_TRY(hgemv(h, false, L, nrhs, bsz, -1.0, M + bsz, ldm, p, bsz, 1.0, Z + r, ldz));
+    return copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldz, st);
+  }
   LLS_TRY(hgemm(h, true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldz, 1.0, p,
                 bsz));
   LLS_TRY(hgemm(h, transT, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2, bsz));
@@ -608,7 +628,8 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   const int64_t r = f.rank;
   if (n == 0 || nrhs == 0) return ok_status();
   if (r == 0 || m == 0) return fill_zero(n, nrhs, X, ldx, st);
-  TraceScope solve_phase(kTrPhaseSolve, st);
+  std::optional<TraceScope> solve_phase;
+  if (!h.in_refine) solve_phase.emplace(kTrPhaseSolve, st);
   LLS_TRY(h.bw.reserve(sizeof(double) * (size_t)m * nrhs));
   LLS_TRY(h.z.reserve(sizeof(double) * (size_t)n * nrhs));
   LLS_TRY(h.dstat.reserve(sizeof(DevStatus)));
@@ -705,7 +726,18 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
   double* rs = h.rs.d();
   double* dd = h.dd.d();
   double* xls = h.z2.d();
+  // With few right-hand sides the 64 x 64 diagonal blocks of T_11 are
+  // inverted once and each triangular solve multiplies by them.
+  const bool thin = nrhs <= kThinMaxRhs;
+  if (thin) {
+    LLS_TRY(h.dinv.reserve(trsm_inverse_bytes(r)));
+    LLS_TRY(trsm_block_inverses(r, f.T.d(), ldt, h.dinv.d(), st));
+  }
   auto trsm_both = [&](double* y, int64_t ldy, bool trans_first) -> Status {
+    if (thin) {
+      LLS_TRY(trsm_upper_inv(r, nrhs, f.T.d(), ldt, h.dinv.d(), y, ldy, trans_first, st));
+      return trsm_upper_inv(r, nrhs, f.T.d(), ldt, h.dinv.d(), y, ldy, !trans_first, st);
+    }
     LLS_TRY(h.gemm_ws.reserve(std::max(trsm_upper_scratch_bytes(r, nrhs),
                                        trsm_upper_trans_scratch_bytes(r, nrhs))));
     if (trans_first) LLS_TRY(trsm_upper_trans(r, nrhs, f.T.d(), ldt, y, ldy, scratch_of(h.gemm_ws), st));
@@ -726,8 +758,8 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
       double* D;
       if (stage == 0) {  // dx = V [T_11^{-1} T_11^{-T} (V^T A^T (b - A x))(0:r); 0]
         LLS_TRY(copy_matrix(m, nrhs, B, ldb, rr, m, st));
-        LLS_TRY(hgemm(h, false, false, kDense, kDense, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, rr, m));
-        LLS_TRY(hgemm(h, true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, rr, m, 0.0, rs, n));
+        LLS_TRY(hgemv(h, false, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, rr, m));
+        LLS_TRY(hgemv(h, true, n, nrhs, m, 1.0, A, lda, rr, m, 0.0, rs, n));
         LLS_TRY(apply_vt(h, f, rs, n, nrhs));
         LLS_TRY(trsm_both(rs, n, true));
         if (r < n) LLS_TRY(fill_zero(n - r, nrhs, rs + r, n, st));
@@ -736,12 +768,12 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
       } else {  // dx = A^T U [T_11^{-T} T_11^{-1} (U^T A (x_ls - x))(0:r); 0]
         LLS_TRY(copy_matrix(n, nrhs, xls, n, rs, n, st));
         LLS_TRY(axpy_matrix(n, nrhs, -1.0, X, ldx, rs, n, st));
-        LLS_TRY(hgemm(h, false, false, kDense, kDense, m, nrhs, n, 1.0, A, lda, rs, n, 0.0, rr, m));
+        LLS_TRY(hgemv(h, false, m, nrhs, n, 1.0, A, lda, rs, n, 0.0, rr, m));
         LLS_TRY(apply_ut(h, f, rr, m, nrhs));
         LLS_TRY(trsm_both(rr, m, false));
         if (r < m) LLS_TRY(fill_zero(m - r, nrhs, rr + r, m, st));
         LLS_TRY(apply_u(h, f, rr, m, nrhs));
-        LLS_TRY(hgemm(h, true, false, kDense, kDense, n, nrhs, m, 1.0, A, lda, rr, m, 0.0, dd, n));
+        LLS_TRY(hgemv(h, true, n, nrhs, m, 1.0, A, lda, rr, m, 0.0, dd, n));
         D = dd;
       }
       double c = 0.0;
@@ -783,6 +815,12 @@ Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const d
   }
   if (h.opt.max_refine <= 0 || !A || m == 0 || n == 0 || nrhs == 0 || f.rank == 0)
     return ok_status();
+  TraceScope refine_phase(kTrPhaseRefine, h.stream);
+  struct InRefine {
+    Handle& h;
+    explicit InRefine(Handle& hh) : h(hh) { h.in_refine = true; }
+    ~InRefine() { h.in_refine = false; }
+  } in_refine(h);
   if (f.precision == LLS_MIXED_BF16_3xTF32 || f.precision == LLS_MIXED_BF16_TF32)
     return refine_min_norm(h, f, A, lda, B, nrhs, ldb, X, ldx);
   cudaStream_t st = h.stream;
@@ -795,8 +833,7 @@ Status solve_refined(Handle& h, Factor& f, const double* A, int64_t lda, const d
   for (int it = 1; it <= h.opt.max_refine; ++it) {
     // r = b - A x
     LLS_TRY(copy_matrix(m, nrhs, B, ldb, h.rr.d(), m, st));
-    LLS_TRY(gemm(false, false, kDense, kDense, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, h.rr.d(), m,
-                 scratch_of(h.gemm_ws), st));
+    LLS_TRY(hgemv(h, false, m, nrhs, n, -1.0, A, lda, X, ldx, 1.0, h.rr.d(), m));
     // d = P r; x += d
     LLS_TRY(solve_factored(h, f, h.rr.d(), nrhs, m, h.dd.d(), n));
     LLS_TRY(refine_update(n, nrhs, h.dd.d(), n, X, ldx, h.nrm.d(), st));

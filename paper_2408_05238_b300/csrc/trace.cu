@@ -18,11 +18,14 @@ const char* trace_kind_name(int k) {
                                         "small_kernels",     "bf16_gemm_kernel",
                                         "convert_kernels",   "oz_mma_kernel",
                                         "tf32_mma_kernel",   "batched_factor_kernel",
-                                        "phase:sample",      "phase:qr_y",
+                                        "thin_small_kernels", "thin_n_kernel",
+                                        "thin_t_kernel",     "trsm_diag_kernel",
+                                        "phase:sample",
+                                        "phase:qr_y",
                                         "phase:right_update", "phase:panel",
                                         "phase:left_update", "phase:block_svd",
                                         "phase:rank",        "phase:nullify",
-                                        "phase:solve"};
+                                        "phase:solve",       "phase:refine"};
   return (k >= 0 && k < kTrCount) ? names[k] : "unknown";
 }
 

@@ -26,6 +26,10 @@ enum TraceKind {
   kTrOzGemm,       // FP64-accurate GEMM on tensor cores (exact BF16 slices)
   kTrTf32Gemm,     // split-operand TF32 GEMM on tensor cores (3xTF32 / TF32)
   kTrBatchedFactor,  // persistent batched factorization
+  kTrThin,         // small kernels of the <= 16 right-hand-side path (T, S blocks, chunk sums)
+  kTrThinN,        // thin_n_kernel: op(A) x, rows of A per thread
+  kTrThinT,        // thin_t_kernel: A^T x, lanes along the rows of A
+  kTrTrsmDiag,     // trsm_diag_kernel: diagonal blocks of the triangular solves
   // phases of the method (each spans the kernels above that it launches)
   kTrPhaseSample,   // a1/a2 sketch and sample Y
   kTrPhaseQrY,      // a3 QR of Y and its T factor
@@ -36,6 +40,7 @@ enum TraceKind {
   kTrPhaseRank,     // a8 rank decision
   kTrPhaseNullify,  // a9 Nullify
   kTrPhaseSolve,    // a10 solve
+  kTrPhaseRefine,   // iterative refinement after the solve
   kTrCount
 };
 constexpr int kTrFirstPhase = kTrPhaseSample;

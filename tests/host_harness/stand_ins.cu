@@ -337,6 +337,24 @@ Status diag_gap(int64_t len, const double* d, int64_t r, double* out, cudaStream
   return ok_status();
 }
 size_t thin_scratch_bytes(int64_t, int64_t, int64_t) { return 0; }
+size_t thin_gemv_scratch_bytes(bool, int64_t, int64_t, int64_t) { return 0; }
+// y = beta y + alpha op(A) x, plainly (unit_lower: 0 above, 1 on the diagonal).
+Status thin_gemv(bool trans, bool unit_lower, int64_t M, int64_t K, int64_t nrhs, double alpha,
+                 const double* A, int64_t lda, const double* x, int64_t ldx, double beta, double* y,
+                 int64_t ldy, Scratch, cudaStream_t) {
+  auto a = [&](int64_t i, int64_t k) {  // stored A(i, k)
+    if (unit_lower && i <= k) return i == k ? 1.0 : 0.0;
+    return A[i + k * lda];
+  };
+  for (int64_t c = 0; c < nrhs; ++c)
+    for (int64_t i = 0; i < M; ++i) {
+      double s = 0.0;
+      for (int64_t k = 0; k < K; ++k) s += (trans ? a(k, i) : a(i, k)) * x[k + c * ldx];
+      double& out = y[i + c * ldy];
+      out = beta == 0.0 ? alpha * s : beta * out + alpha * s;
+    }
+  return ok_status();
+}
 // x <- (I - W op(T) W^T) x with unit lower W, plainly.
 Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W, int64_t ldw,
                              const double* T, int64_t ldt, bool transT, double* x, int64_t ldx,
@@ -367,6 +385,17 @@ Status small_block_mul(int64_t b, int64_t nrhs, const double* S, int64_t lds, bo
     for (int64_t i = 0; i < b; ++i) xc[i] = y[i];
   }
   return ok_status();
+}
+// The block-inverse solves: the inverses are not formed here, the solves
+// substitute (the inverses are a kernel matter).
+size_t trsm_inverse_bytes(int64_t r) { return sizeof(double) * (size_t)std::max<int64_t>(r, 1); }
+Status trsm_block_inverses(int64_t, const double*, int64_t, double*, cudaStream_t) {
+  return ok_status();
+}
+Status trsm_upper_inv(int64_t r, int64_t nrhs, const double* R, int64_t ldr, const double*,
+                      double* B, int64_t ldb, bool trans, cudaStream_t st) {
+  if (trans) return trsm_upper_trans(r, nrhs, R, ldr, B, ldb, Scratch{}, st);
+  return trsm_upper(r, nrhs, R, ldr, B, ldb, Scratch{}, st);
 }
 size_t trsm_upper_trans_scratch_bytes(int64_t, int64_t) { return 0; }
 // R^T Y = B by forward substitution, one column at a time.
