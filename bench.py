@@ -558,14 +558,18 @@ TF32_OF_BF16 = 1.1 / 2.25    # nominal dense TF32 / BF16 tensor rate of the part
 
 def default_refine(precision):
     return 10 if precision in ("3xtf32", "tf32") else 0
-# DRAM bytes per algorithmic byte of a kernel family, from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum over the family's launches
-# in one solve of a 4096-order case of the same construction, divided by the
-# algorithmic bytes the library's trace assigns to those launches; None
-# until captured for the kernel as it stands).  Full-size captures are
-# limited to one-pass metrics, so the bench line scales this ratio by the
-# algorithmic bytes of its own launches.
-TRAFFIC_PER_ALG_BYTE = {"dgemm_kernel": None, "oz_mma_kernel": None}
+
+
+# DRAM bytes per algorithmic byte of a kernel family, from small-case ncu
+# captures of the kernel as it stands (dram__bytes_read.sum +
+# dram__bytes_write.sum over the captured launches divided by the
+# algorithmic bytes the library's trace assigns to them): dgemm_kernel over
+# the seven launches of step 0 of a 4096^2 FP64 solve, oz_mma_kernel and
+# tf32_mma_kernel over the two shapes of a 6144^2 step (the rank-128 update
+# and the long product).  Full-size captures are limited to one-pass
+# metrics, so the bench line scales this ratio by the algorithmic bytes of
+# its own launches.
+TRAFFIC_PER_ALG_BYTE = {"dgemm_kernel": 0.965, "oz_mma_kernel": 1.12, "tf32_mma_kernel": 0.954}
 
 
 def time_dense(a, lls, pm, precision, A, B, Q1, Q2, sigma, steps, warmup, dist, local,

@@ -13,9 +13,10 @@
 //  2. C_ij = 2^(e_i + f_j) sum_{s,t} 2^-7(s+t) sum_k d_s(i,k) d'_t(k,j).  The
 //     36 products with s + t <= 9 run on tcgen05.mma kind::f16 (BF16 in,
 //     FP32 accumulate in tensor memory), one FP32 accumulator per diagonal
-//     D = s + t (8 of them, 64 columns each = all 512 TMEM columns).  Per K
-//     entry a diagonal gains at most 2^15 in magnitude, so with at most 256
-//     K entries per CTA every accumulator stays below 2^24: the FP32 sums
+//     D = s + t (8 of them for a 128 x 128 tile, in two passes of 4 x 128
+//     TMEM columns).  Per K entry a diagonal gains at most 2^15 in
+//     magnitude, so with at most 256 K entries per work item every
+//     accumulator stays below 2^24: the FP32 sums
 //     are exact integers.  Terms with s + t >= 10 are below 2^-55 relative
 //     to the row/column scales and are dropped.
 //  3. The epilogue combines the 8 exact integers into two 64-bit integers,
@@ -44,18 +45,19 @@ namespace lls {
 namespace {
 
 constexpr int OZ_S = 8;           // slices per operand
-constexpr int OZ_BM = 128;        // output rows per CTA (MMA M)
-constexpr int OZ_BN = 64;         // output columns per CTA (MMA N)
+constexpr int OZ_BM = 128;        // output rows per tile (MMA M)
+constexpr int OZ_BN = 128;        // output columns per tile (MMA N)
 constexpr int OZ_BK = 64;         // K per smem tile (128-byte swizzle rows)
-constexpr int OZ_KC = 256;        // K per CTA: keeps every FP32 sum below 2^24
-constexpr int OZ_XST = 5;         // X-tile ring depth (one slice of one K tile each)
-constexpr int OZ_ZST = 2;         // Z ring depth (all 8 slices of one K tile each)
+constexpr int OZ_KC = 256;        // K per work item: keeps every FP32 sum below 2^24
+constexpr int OZ_XST = 6;         // X ring depth (one 128 x 64 slice tile per stage)
+constexpr int OZ_ZST = 7;         // Z ring depth (one 128 x 64 slice tile per stage)
 constexpr int OZ_EPI_WARP0 = 2;  // warps 0 (TMA) and 1 (MMA issue), then the epilogue
-constexpr int OZ_EPI_WARPS = 16;
+constexpr int OZ_EPI_WARPS = 16;  // 4 lane quadrants x 4 groups of 32 columns
+constexpr int OZ_EPI_COLS = OZ_BN / (OZ_EPI_WARPS / 4);  // columns per epilogue thread
 constexpr int OZ_THREADS = (OZ_EPI_WARP0 + OZ_EPI_WARPS) * 32;
-constexpr uint32_t OZ_XBYTES = OZ_BM * OZ_BK * 2;         // 16 KB
-constexpr uint32_t OZ_ZTILE = OZ_BN * OZ_BK * 2;          // 8 KB
-constexpr uint32_t OZ_ZBYTES = OZ_ZTILE * OZ_S;           // 64 KB
+constexpr uint32_t OZ_TILE = OZ_BM * OZ_BK * 2;           // 16 KB, either operand
+constexpr int OZ_ACC = 4;         // diagonal accumulators per pass: 4 x 128 TMEM columns
+static_assert(OZ_BM == OZ_BN, "one tile shape and tensor-map box for both operands");
 constexpr int kZeroExp = -4000;   // exponent of an all-zero row / column
 constexpr long long kOzWaitLimit = 1LL << 24;
 
@@ -164,8 +166,16 @@ __global__ void __launch_bounds__(256) oz_rowmax_kcontig_kernel(int64_t R, int64
   const int64_t r = blockIdx.y;
   const int64_t k0 = (int64_t)blockIdx.x * OZ_KCH;
   unsigned long long m = 0;
-  for (int64_t k = k0 + threadIdx.x; k < min(K, k0 + OZ_KCH); k += 256) {
-    const unsigned long long b = abs_bits(op_load(src, ld, true, ul != 0, r, k));
+  static_assert(OZ_KCH == 4 * 256, "four loads per thread and chunk");
+  double v[4];  // in flight together
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t k = k0 + threadIdx.x + 256 * q;
+    v[q] = k < K ? op_load(src, ld, true, ul != 0, r, k) : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const unsigned long long b = abs_bits(v[q]);
     m = b > m ? b : m;
   }
 #pragma unroll
@@ -190,11 +200,22 @@ __global__ void __launch_bounds__(256) oz_slice_kcontig_chunk_kernel(
   const int64_t k0 = (int64_t)blockIdx.x * OZ_KCH;
   const int e = exps[r];
   const int64_t plane = R * ldk;
-  // two consecutive k per thread: one 4-byte store per plane (ldk and k0 are even)
-  for (int64_t k = k0 + 2 * threadIdx.x; k < min(ldk, k0 + OZ_KCH); k += 512) {
+  // two consecutive k per thread: one 4-byte store per plane (ldk and k0 are even);
+  // the chunk's four loads of this thread are issued first
+  double v[4];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int64_t k = k0 + 2 * threadIdx.x + 512 * q;
+    v[2 * q] = k < K ? op_load(src, ld, true, ul != 0, r, k) : 0.0;
+    v[2 * q + 1] = k + 1 < K ? op_load(src, ld, true, ul != 0, r, k + 1) : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int64_t k = k0 + 2 * threadIdx.x + 512 * q;
+    if (k >= ldk) continue;
     int d0[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0}, d1[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (k < K) make_digits(op_load(src, ld, true, ul != 0, r, k), e, d0);
-    if (k + 1 < K) make_digits(op_load(src, ld, true, ul != 0, r, k + 1), e, d1);
+    if (k < K) make_digits(v[2 * q], e, d0);
+    if (k + 1 < K) make_digits(v[2 * q + 1], e, d1);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s)
       *reinterpret_cast<__nv_bfloat162*>(out + s * plane + r * ldk + k) =
@@ -209,8 +230,15 @@ __global__ void oz_rowmax_rcontig_kernel(int64_t R, int64_t K, const double* __r
   const int64_t k0 = (int64_t)blockIdx.y * 64;
   unsigned long long m = 0;
   if (r < R) {
-    for (int64_t k = k0 + (threadIdx.x >> 5); k < min(K, k0 + 64); k += blockDim.x >> 5) {
-      unsigned long long b = abs_bits(op_load(src, ld, false, ul != 0, r, k));
+    double v[8];  // 256 threads: eight k per thread, loads in flight together
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = k0 + (threadIdx.x >> 5) + 8 * q;
+      v[q] = k < K ? op_load(src, ld, false, ul != 0, r, k) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const unsigned long long b = abs_bits(v[q]);
       m = b > m ? b : m;
     }
     if (m) atomicMax(mx + r, m);
@@ -234,10 +262,17 @@ __global__ void __launch_bounds__(256) oz_slice_rcontig_kernel(
   {
     const int64_t r = r0 + lane;
     const int e = r < R ? exps[r] : kZeroExp;
-    for (int kk = w; kk < 64; kk += 8) {  // coalesced: 32 consecutive rows per load
-      const int64_t k = k0 + kk;
+    double v[8];  // coalesced: 32 consecutive rows per load, eight loads in flight
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = k0 + w + 8 * q;
+      v[q] = (r < R && k < K) ? op_load(src, ld, false, ul != 0, r, k) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int kk = w + 8 * q;
       int d[OZ_S] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (r < R && k < K) make_digits(op_load(src, ld, false, ul != 0, r, k), e, d);
+      if (r < R && k0 + kk < K) make_digits(v[q], e, d);
 #pragma unroll
       for (int s = 0; s < OZ_S; ++s) tile[s][lane][kk] = (short)d[s];
     }
@@ -332,10 +367,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7])
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 }
 // v * 2^p as an FP64, assembled from bits with integer operations only (FP64
@@ -386,19 +420,84 @@ struct OzArgs {
 };
 
 // Persistent: one CTA per SM loops over (row tile, column tile, K range)
-// items.  The 8 diagonal accumulators fill all of tensor memory, so the
-// epilogue warps first drain them into exact int64 registers (H and L
-// folded into one v per output) and release tensor memory at once; the FP64
-// assembly, the loads of C and the stores then run while the MMAs of the
-// next item fill tensor memory again.
+// items of 128 x 128 outputs.  At N = 128 an MMA reads 8 KB of operands from
+// shared memory for 128 x 128 x 16 multiply-adds (N = 64 reads 6 KB for half
+// of them, and shared-memory bandwidth is what bounds these MMAs), but the 8
+// diagonal accumulators would need 1024 TMEM columns: each item therefore
+// runs in two passes over its K range, first the diagonals D = s + t = 4..7
+// (26 slice products per K tile, "pass 1" below) and then 0..3 (10
+// products, "pass 0"), each into the 4 x 128 columns of tensor memory.  The
+// epilogue drains the first pass into exact int64 registers (L), lets the
+// second start, adds it (H), and assembles, loads and stores the FP64
+// results while the next item's long first pass runs; the item's lines of C
+// are prefetched into L2 before its first pass is drained.
+//
+// Per K tile a pass consumes its X slices s = 0, 1, ... in order and its Z
+// slices from the highest t down, each Z slice last used at step s = (last
+// t) - t, so both operands stream through FIFO rings of single-slice tiles:
+// pass 0 loads Z3 Z2 Z1 Z0 then X0..X3; pass 1 loads Z7 Z6 Z5 Z4 X0 Z3 X1 Z2
+// X2 Z1 X3 Z0 X4..X7 -- the order in which the MMA thread needs them, so the
+// producer only ever waits for slots that MMAs already issued will free.
+struct OzLoad {
+  unsigned char z, slice;
+};
+__constant__ OzLoad kOzSeq0[8] = {{1, 3}, {1, 2}, {1, 1}, {1, 0}, {0, 0}, {0, 1}, {0, 2}, {0, 3}};
+__constant__ OzLoad kOzSeq1[16] = {{1, 7}, {1, 6}, {1, 5}, {1, 4}, {0, 0}, {1, 3}, {0, 1}, {1, 2},
+                                   {0, 2}, {1, 1}, {0, 3}, {1, 0}, {0, 4}, {0, 5}, {0, 6}, {0, 7}};
+
+// The MMAs of one K tile of pass P.  zb: ring position of the tile's first Z
+// slice (Z_t sits at zb + NZ - 1 - t); cx: next X position.
+template <int P>
+__device__ __forceinline__ bool oz_issue_ktile(uint32_t tmem, unsigned char* xring,
+                                               unsigned char* zring, uint64_t* xfull,
+                                               uint64_t* xempty, uint64_t* zfull,
+                                               uint64_t* zempty, uint32_t zb, uint32_t& cx,
+                                               bool first_ktile, int* err) {
+  constexpr int NS = P ? 8 : 4;  // X slices and Z slices of the pass
+  const uint32_t zs0 = zb % OZ_ZST;  // slot of position zb; position zb + j sits in zslot(j)
+  auto zslot = [&](int j) { return zs0 + j >= OZ_ZST ? zs0 + j - OZ_ZST : zs0 + j; };
+  constexpr int kNeed1[8] = {4, 5, 6, 7, 8, 8, 8, 8};
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    // Z slices first needed at step s: positions zb + have .. zb + need - 1
+    const int need = P ? kNeed1[s] : 4;
+    const int have = s == 0 ? 0 : (P ? kNeed1[s > 0 ? s - 1 : 0] : 4);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+      if (j >= have && j < need &&
+          !mbar_wait_spin(&zfull[zslot(j)], ((zb + j) / OZ_ZST) & 1, err))
+        return false;
+    const uint32_t xs = cx % OZ_XST;
+    if (!mbar_wait_spin(&xfull[xs], (cx / OZ_XST) & 1, err)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint64_t xdesc = sdesc_sw128(smem_u32(xring + xs * OZ_TILE));
+    constexpr int kTlo1[8] = {4, 3, 2, 1, 0, 0, 0, 0};
+    const int tlo = P ? kTlo1[s] : 0, thi = (P ? 7 : 3) - s;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < tlo || t > thi) continue;
+      const uint64_t zdesc = sdesc_sw128(smem_u32(zring + zslot(NS - 1 - t) * OZ_TILE));
+      const uint32_t acc = (uint32_t)(s + t - OZ_ACC * P);
+#pragma unroll
+      for (int kk = 0; kk < OZ_BK / 16; ++kk)
+        mma_bf16(tmem + acc * OZ_BN, xdesc + (uint64_t)((kk * 32) >> 4),
+                 zdesc + (uint64_t)((kk * 32) >> 4), (first_ktile && s == 0 && kk == 0) ? 0u : 1u);
+    }
+    mma_commit(&xempty[xs]);
+    ++cx;
+    mma_commit(&zempty[zslot(s)]);  // position zb + s: the slice whose last step this was
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_mma_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapZ,
                   OzArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* xring = smem;                       // OZ_XST x 16 KB
-  unsigned char* zring = smem + OZ_XST * OZ_XBYTES;  // OZ_ZST x 64 KB
+  unsigned char* xring = smem;                     // OZ_XST x 16 KB
+  unsigned char* zring = smem + OZ_XST * OZ_TILE;  // OZ_ZST x 16 KB
   __shared__ __align__(8) uint64_t xfull[OZ_XST], xempty[OZ_XST], zfull[OZ_ZST], zempty[OZ_ZST];
   __shared__ __align__(8) uint64_t tfull, tempty;
   __shared__ uint32_t s_tmem;
@@ -438,139 +537,137 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   };
 
   if (warp == 0 && lane == 0) {
-    // ---- producer: per K tile, the 8 Z slices at once, then the 8 X slices
-    uint32_t itx = 0, itz = 0;
+    // ---- producer: both passes' slice tiles in the MMA thread's order
+    uint32_t px = 0, pz = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
       int m0, n0, kbeg, nkb;
       item_coords(item, m0, n0, kbeg, nkb);
-      for (int kb = 0; kb < nkb && ok; ++kb, ++itz) {
-        const int k = kbeg + kb * OZ_BK;
-        const int zs = itz % OZ_ZST;
-        if (itz >= (uint32_t)OZ_ZST && !mbar_wait_spin(&zempty[zs], ((itz / OZ_ZST) - 1) & 1, a.err)) {
-          ok = false;
-          break;
-        }
-        mbar_expect_tx(&zfull[zs], OZ_ZBYTES);
-        tma_load_3d(zring + zs * OZ_ZBYTES, &mapZ, &zfull[zs], k, n0, 0);
-        for (int s = 0; s < OZ_S; ++s, ++itx) {
-          const int xs = itx % OZ_XST;
-          if (itx >= (uint32_t)OZ_XST &&
-              !mbar_wait_spin(&xempty[xs], ((itx / OZ_XST) - 1) & 1, a.err)) {
-            ok = false;
-            break;
+      for (int pass = 0; pass < 2 && ok; ++pass) {  // diagonals 4..7, then 0..3
+        const OzLoad* seq = pass ? kOzSeq0 : kOzSeq1;
+        const int nseq = pass ? 8 : 16;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+          const int k = kbeg + kb * OZ_BK;
+          for (int e = 0; e < nseq; ++e) {
+            const OzLoad ld = seq[e];
+            uint32_t& pos = ld.z ? pz : px;
+            const uint32_t st = ld.z ? OZ_ZST : OZ_XST;
+            const uint32_t slot = pos % st;
+            uint64_t* emp = ld.z ? &zempty[slot] : &xempty[slot];
+            uint64_t* ful = ld.z ? &zfull[slot] : &xfull[slot];
+            if (pos >= st && !mbar_wait_spin(emp, ((pos / st) - 1) & 1, a.err)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(ful, OZ_TILE);
+            tma_load_3d((ld.z ? zring : xring) + slot * OZ_TILE, ld.z ? &mapZ : &mapX, ful, k,
+                        ld.z ? n0 : m0, ld.slice);
+            ++pos;
           }
-          mbar_expect_tx(&xfull[xs], OZ_XBYTES);
-          tma_load_3d(xring + xs * OZ_XBYTES, &mapX, &xfull[xs], k, m0, s);
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: diagonal d = s + t (0-based) accumulates X_s^T Z_t
-    uint32_t itx = 0, itz = 0;
+    // ---- MMA issuer: pass 0 then pass 1 of every item, each into all of TMEM
+    uint32_t cx = 0, cz = 0, hs = 0;
     bool ok = true;
-    int li = 0;
-    for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x, ++li) {
+    for (int item = blockIdx.x; item < a.items && ok; item += gridDim.x) {
       int m0, n0, kbeg, nkb;
       item_coords(item, m0, n0, kbeg, nkb);
-      // the epilogue of the previous item has drained tensor memory
-      if (li >= 1 && !mbar_wait_spin(&tempty, (li - 1) & 1, a.err)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int kb = 0; kb < nkb && ok; ++kb, ++itz) {
-        const int zs = itz % OZ_ZST;
-        if (!mbar_wait_spin(&zfull[zs], (itz / OZ_ZST) & 1, a.err)) {
+      for (int pass = 0; pass < 2 && ok; ++pass, ++hs) {
+        // the epilogue has drained the previous pass
+        if (hs >= 1 && !mbar_wait_spin(&tempty, (hs - 1) & 1, a.err)) {
           ok = false;
           break;
         }
-        // Fully unrolled issue: descriptors differ only in their start-address
-        // field, so each MMA is one add and the instruction (a rolled loop with
-        // per-MMA descriptor arithmetic left the tensor pipe ~40% idle).
-        const uint64_t zdesc = sdesc_sw128(smem_u32(zring + zs * OZ_ZBYTES));
-#pragma unroll
-        for (int s = 0; s < OZ_S; ++s, ++itx) {
-          const int xs = itx % OZ_XST;
-          if (!mbar_wait_spin(&xfull[xs], (itx / OZ_XST) & 1, a.err)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t xdesc = sdesc_sw128(smem_u32(xring + xs * OZ_XBYTES));
-          const uint32_t acc0 = (kb == 0 && s == 0) ? 0u : 1u;
-#pragma unroll
-          for (int t = 0; t < OZ_S - s; ++t) {
-#pragma unroll
-            for (int kk = 0; kk < OZ_BK / 16; ++kk)
-              mma_bf16(tmem + (uint32_t)((s + t) * OZ_BN), xdesc + (uint64_t)((kk * 32) >> 4),
-                       zdesc + (uint64_t)((t * OZ_ZTILE + kk * 32) >> 4), kk == 0 ? acc0 : 1u);
-          }
-          mma_commit(&xempty[xs]);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kb = 0; kb < nkb && ok; ++kb) {  // diagonals 4..7, then 0..3
+          ok = pass ? oz_issue_ktile<0>(tmem, xring, zring, xfull, xempty, zfull, zempty, cz, cx,
+                                        kb == 0, a.err)
+                    : oz_issue_ktile<1>(tmem, xring, zring, xfull, xempty, zfull, zempty, cz, cx,
+                                        kb == 0, a.err);
+          cz += pass ? 4 : 8;
         }
-        if (ok) mma_commit(&zempty[zs]);
+        if (ok) mma_commit(&tfull);
       }
-      if (ok) mma_commit(&tfull);
     }
   } else if (warp >= OZ_EPI_WARP0) {
     // ---- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +31 (its rows)
-    // and the 16 columns 16 ((w - 2) / 4) .. +15, in two passes of 8
+    // and the 32 columns 32 ((w - 2) / 4) .. +31, in chunks of 4 (18 warps
+    // put five on two SM sub-partitions, whose register files then hold 96
+    // registers a thread: the 32 exact sums take 64 of them).
     const int q = warp & 3;
-    const int cl0 = ((warp - OZ_EPI_WARP0) >> 2) * 16;
+    const int cg0 = ((warp - OZ_EPI_WARP0) >> 2) * OZ_EPI_COLS;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
     const int bmode = a.part ? 3 : (a.beta == 0.0 ? 0 : (a.beta == 1.0 ? 1 : 2));
     const double alpha = a.alpha, beta = a.beta;
-    int li = 0;
-    for (int item = blockIdx.x; item < a.items; item += gridDim.x, ++li) {
+    uint32_t hs = 0;
+    bool alive = true;
+    for (int item = blockIdx.x; item < a.items && alive; item += gridDim.x) {
       int m0, n0, kbeg, nkb;
       item_coords(item, m0, n0, kbeg, nkb);
-      bool ready = nkb > 0 && mbar_wait(&tfull, li & 1, a.err);
-      ready = __all_sync(0xffffffffu, ready);
-      if (!ready) break;  // warp-uniform: the TMEM loads below are .sync.aligned
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      long long V[16];
+      if ((bmode == 1 || bmode == 2) && !a.transC) {
+        // the C lines this thread will read, into L2 while the item's MMAs run
+        const int ip = m0 + q * 32 + lane;
+        if (ip < a.M) {
+          const double* cp = a.C + ip + (int64_t)(n0 + cg0) * a.ldc;
+          const int nc = min(OZ_EPI_COLS, a.N - n0 - cg0);
+          for (int c = 0; c < nc; ++c)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(cp + (int64_t)c * a.ldc));
+        }
+      }
+      long long V[OZ_EPI_COLS];
 #pragma unroll
-      for (int pass = 0; pass < 2; ++pass) {
-        const int cl = cl0 + pass * 8;
+      for (int pass = 0; pass < 2; ++pass, ++hs) {
+        bool ready = nkb > 0 && mbar_wait(&tfull, hs & 1, a.err);
+        ready = __all_sync(0xffffffffu, ready);
+        if (!ready) {  // warp-uniform: the TMEM loads below are .sync.aligned
+          alive = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint32_t r[4][8];
+        for (int ch = 0; ch < OZ_EPI_COLS / 4; ++ch) {  // 4 columns at a time
+          uint32_t r[OZ_ACC][4];
 #pragma unroll
-          for (int d = 0; d < 4; ++d) tmem_ld8(trow + (uint32_t)((half * 4 + d) * OZ_BN + cl), r[d]);
+          for (int d = 0; d < OZ_ACC; ++d)
+            tmem_ld4(trow + (uint32_t)(d * OZ_BN + cg0 + ch * 4), r[d]);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int c = 0; c < 4; ++c) {
             // |acc| <= 10.5e6 < 2^24: each pair x 128 + y fits in int32
             const int x0 = __float2int_rn(__uint_as_float(r[0][c]));
             const int x1 = __float2int_rn(__uint_as_float(r[1][c]));
             const int x2 = __float2int_rn(__uint_as_float(r[2][c]));
             const int x3 = __float2int_rn(__uint_as_float(r[3][c]));
             const long long w = (long long)(x0 * 128 + x1) * 16384 + (x2 * 128 + x3);
-            if (half == 0) V[pass * 8 + c] = w * (1LL << 19);
-            else V[pass * 8 + c] += (w + (1LL << 8)) >> 9;
+            if (pass == 0) V[ch * 4 + c] = (w + (1LL << 8)) >> 9;  // diagonals 4..7: L
+            else V[ch * 4 + c] += w * (1LL << 19);                 // diagonals 0..3: H
           }
         }
+        // this pass's accumulators are drained: the next pass may start
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty);
       }
-      // tensor memory is drained: the next item's MMAs may start
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty);
+      if (!alive) break;
 
       const int i = m0 + q * 32 + lane;
       if (i >= a.M) continue;
       const int ei = a.expX[i];
 #pragma unroll
-      for (int pass = 0; pass < 2; ++pass) {
-        const int jb = n0 + cl0 + pass * 8;
-        const int ncols = min(8, a.N - jb);
-        double v[8];
+      for (int ch = 0; ch < OZ_EPI_COLS / 4; ++ch) {  // chunks of 4 columns
+        const int jb = n0 + cg0 + ch * 4;
+        const int ncols = min(4, a.N - jb);
+        if (ncols <= 0) break;
+        double v[4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < 4; ++c) {
           v[c] = 0.0;
           const int fj = c < ncols ? a.expZ[jb + c] : kZeroExp;
           if (ei != kZeroExp && fj != kZeroExp) {
             const int p = ei + fj - 54;
-            if (!i64_scaled(V[pass * 8 + c], p, v[c])) v[c] = slow_scaled(V[pass * 8 + c], p);
+            if (!i64_scaled(V[ch * 4 + c], p, v[c])) v[c] = slow_scaled(V[ch * 4 + c], p);
           }
         }
         // one loop per output mode, so no FP64 instruction of another mode
@@ -578,32 +675,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (bmode == 3) {
           double* P = a.part + (int64_t)(item % a.splits) * a.M * a.N + i + (int64_t)jb * a.M;
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
+          for (int c = 0; c < 4; ++c)
             if (c < ncols) P[(int64_t)c * a.M] = v[c];
         } else if (!a.transC) {
           double* cp = a.C + i + (int64_t)jb * a.ldc;
           if (bmode == 0) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < 4; ++c)
               if (c < ncols) cp[(int64_t)c * a.ldc] = alpha * v[c];
           } else if (bmode == 1) {
-            double cv[8];
+            double cv[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) cv[c] = c < ncols ? cp[(int64_t)c * a.ldc] : 0.0;
+            for (int c = 0; c < 4; ++c) cv[c] = c < ncols ? cp[(int64_t)c * a.ldc] : 0.0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < 4; ++c)
               if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], cv[c]);
           } else {
-            double cv[8];
+            double cv[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) cv[c] = c < ncols ? cp[(int64_t)c * a.ldc] : 0.0;
+            for (int c = 0; c < 4; ++c) cv[c] = c < ncols ? cp[(int64_t)c * a.ldc] : 0.0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+            for (int c = 0; c < 4; ++c)
               if (c < ncols) cp[(int64_t)c * a.ldc] = fma(alpha, v[c], beta * cv[c]);
           }
         } else {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
+          for (int c = 0; c < 4; ++c) {
             if (c >= ncols) break;
             double* cp = a.C + jb + c + (int64_t)i * a.ldc;
             *cp = bmode == 0 ? alpha * v[c] : fma(alpha, v[c], (bmode == 1 ? 1.0 : beta) * *cp);
@@ -760,7 +857,7 @@ Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int6
 
   CUtensorMap mx, mz;
   LLS_TRY(make_slice_map(&mx, Xs, k, m, pad8(k), OZ_BM, 1));
-  LLS_TRY(make_slice_map(&mz, Zs, k, n, pad8(k), OZ_BN, OZ_S));
+  LLS_TRY(make_slice_map(&mz, Zs, k, n, pad8(k), OZ_BN, 1));
   OzArgs a;
   a.M = (int)m;
   a.N = (int)n;
@@ -780,7 +877,7 @@ Status oz_gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int6
   a.transC = transC ? 1 : 0;
   a.part = part;
   a.err = err;
-  const size_t smem = 1024 + (size_t)OZ_XST * OZ_XBYTES + (size_t)OZ_ZST * OZ_ZBYTES;
+  const size_t smem = 1024 + (size_t)(OZ_XST + OZ_ZST) * OZ_TILE;
   LLS_TRY(allow_max_dyn_smem((const void*)oz_mma_kernel));
   static int nsm = 0;
   if (!nsm) {

@@ -21,16 +21,44 @@
 namespace lls {
 namespace {
 
-__global__ void maxabs_f64_kernel(int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
-                                  unsigned long long* out) {
-  double mx = 0.0;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * n;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    double v = fabs(A[(idx % m) + (idx / m) * lda]);
-    mx = v > mx ? v : mx;  // NaN-free input (checked on entry)
+// FP64 arithmetic issues at a small fraction of the integer rate on this
+// part, so the conversions below work on the bits: |x| compares as its
+// 63-bit pattern, the power-of-two scaling is a shift of the exponent field
+// and the rounding to BF16 is done on the mantissa bits.
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// max |A(i, j)| as its bit pattern (a NaN-free input, checked on entry):
+// block (row group of 1024, column group), four rows per thread, two
+// columns per pass, so eight loads are in flight per thread.
+__global__ void __launch_bounds__(256) maxabs_f64_kernel(int64_t m, int64_t n,
+                                                         const double* __restrict__ A,
+                                                         int64_t lda, unsigned long long* out) {
+  unsigned long long mx = 0;
+  const int64_t i0 = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  for (int64_t j = blockIdx.y; j < n; j += 2 * (int64_t)gridDim.y) {
+    const int64_t j2 = j + gridDim.y;
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + 256 * u;
+      v[u] = i < m ? __ldg(A + i + j * lda) : 0.0;
+      v[4 + u] = (i < m && j2 < n) ? __ldg(A + i + j2 * lda) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const unsigned long long b = abs_bits(v[u]);
+      mx = b > mx ? b : mx;
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = t > mx ? t : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
 }
 
 __global__ void maxabs_f32_kernel(int64_t m, int64_t n, const float* __restrict__ A, int64_t lda,
@@ -53,29 +81,67 @@ __device__ __forceinline__ double pow2_scale(double maxabs) {
   return ldexp(1.0, -e);
 }
 
-// A16 (m x n, ld16) and A16t (n x m, ld16t) = bf16(s A), through a 32 x 32
-// shared-memory tile so both writes are coalesced.
-__global__ void convert_transpose_kernel(int64_t m, int64_t n, const double* __restrict__ A,
-                                         int64_t lda, const unsigned long long* maxbits,
-                                         __nv_bfloat16* __restrict__ A16, int64_t ld16,
-                                         __nv_bfloat16* __restrict__ A16t, int64_t ld16t) {
-  __shared__ __nv_bfloat16 tile[32][33];
-  const double s = pow2_scale(__longlong_as_double((long long)*maxbits));
+// The e of pow2_scale from the maximum's bits: 2^e > max (frexp convention).
+__device__ __forceinline__ int scale_exp(unsigned long long maxbits) {
+  const int E = (int)(maxbits >> 52);
+  return maxbits == 0 ? 0 : (E == 0 ? -1021 : E - 1022);
+}
+
+// bf16(v 2^-e) from the bits of v, rounded to nearest with ties to even on
+// the 45 dropped mantissa bits; values that fall below BF16's normal range
+// (below 2^-126, i.e. 2^-126 relative to the scaled maximum 1) become +-0.
+__device__ __forceinline__ unsigned short bf16_scaled_bits(double v, int e) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned short sgn = (unsigned short)((u >> 63) << 15);
+  const int E = (int)((u >> 52) & 0x7FF);
+  int eb = E - e - 1023 + 127;
+  if (E == 0 || eb <= 0) return sgn;
+  const unsigned long long mant = u & ((1ull << 52) - 1);
+  unsigned int m7 = (unsigned int)(mant >> 45);
+  const unsigned long long rem = mant & ((1ull << 45) - 1), half = 1ull << 44;
+  if (rem > half || (rem == half && (m7 & 1u))) {
+    if (++m7 == 128u) {
+      m7 = 0;
+      ++eb;
+    }
+  }
+  return (unsigned short)(sgn | (unsigned short)(eb << 7) | (unsigned short)m7);
+}
+
+// A16 (m x n, ld16) and A16t (n x m, ld16t) = bf16(2^-e A), through a 32 x 32
+// shared-memory tile so both writes are coalesced; the four loads of a
+// thread are issued before any conversion.
+__global__ void __launch_bounds__(256) convert_transpose_kernel(
+    int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
+    const unsigned long long* maxbits, __nv_bfloat16* __restrict__ A16, int64_t ld16,
+    __nv_bfloat16* __restrict__ A16t, int64_t ld16t) {
+  __shared__ unsigned short tile[32][33];
+  const int e = scale_exp(*maxbits);
   const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    int64_t i = i0 + tx, j = j0 + r;
-    __nv_bfloat16 v = __float2bfloat16(0.f);
-    if (i < m && j < n) {
-      v = __double2bfloat16(A[i + j * lda] * s);
-      A16[i + j * ld16] = v;
-    }
-    tile[r][tx] = v;
+  const int64_t i = i0 + tx;
+  double v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t j = j0 + ty + 8 * q;
+    v[q] = (i < m && j < n) ? __ldg(A + i + j * lda) : 0.0;
+  }
+  unsigned short* a16 = reinterpret_cast<unsigned short*>(A16);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q;
+    const int64_t j = j0 + r;
+    const unsigned short bits = bf16_scaled_bits(v[q], e);
+    if (i < m && j < n) a16[i + j * ld16] = bits;
+    tile[r][tx] = bits;
   }
   __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    int64_t j = j0 + tx, i = i0 + r;
-    if (i < m && j < n) A16t[j + i * ld16t] = tile[tx][r];
+  unsigned short* a16t = reinterpret_cast<unsigned short*>(A16t);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = ty + 8 * q;
+    const int64_t j = j0 + tx, ii = i0 + r;
+    if (ii < m && j < n) a16t[j + ii * ld16t] = tile[tx][r];
   }
 }
 
@@ -133,9 +199,12 @@ Status sample_bf16(Handle& h, const double* A, int64_t lda, int64_t mp, int64_t 
   float* F = h.F32.as<float>();
 
   {
-    TraceScope ts(kTrConvert, st, 0.0, (8.0 + 4.0) * mp * np);
+    TraceScope ts(kTrConvertBf16, st, 0.0, (8.0 + 8.0 + 4.0) * mp * np);
     LLS_CUDA(cudaMemsetAsync(amax, 0, 16, st));
-    maxabs_f64_kernel<<<grid_of(mp * np), 256, 0, st>>>(mp, np, A, lda, amax);
+    const unsigned gx = (unsigned)ceil_div(mp, 1024);
+    const unsigned gy = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>({np, 65535, ceil_div(148 * 8, gx)}));
+    maxabs_f64_kernel<<<dim3(gx, gy), 256, 0, st>>>(mp, np, A, lda, amax);
     LLS_LAUNCHED("maxabs_f64_kernel");
     dim3 grid((unsigned)ceil_div(mp, 32), (unsigned)ceil_div(np, 32));
     convert_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(mp, np, A, lda, amax, A16, ld16, A16t,

@@ -134,11 +134,22 @@ __global__ void __launch_bounds__(256) tf_split_kcontig_kernel(int64_t R, int64_
                                                                 int64_t ldk) {
   const int64_t k0 = (int64_t)blockIdx.x * kTfSplitChunk;
   const int64_t plane = R * ldk;
+  static_assert(kTfSplitChunk == 2 * 512, "two passes of 512 entries per chunk");
   for (int64_t r = blockIdx.y; r < R; r += gridDim.y) {
-    for (int64_t k = k0 + 2 * threadIdx.x; k < min(ldk, k0 + kTfSplitChunk); k += 512) {
+    double v[4];  // the chunk's four loads of this thread in flight together
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int64_t k = k0 + 2 * threadIdx.x + 512 * q;
+      v[2 * q] = k < K ? op_load(src, ld, true, ul != 0, r, k) : 0.0;
+      v[2 * q + 1] = k + 1 < K ? op_load(src, ld, true, ul != 0, r, k + 1) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int64_t k = k0 + 2 * threadIdx.x + 512 * q;
+      if (k >= ldk) continue;
       uint32_t t0[P], t1[P];
-      tf32_split<P>(k < K ? op_load(src, ld, true, ul != 0, r, k) : 0.0, t0);
-      tf32_split<P>(k + 1 < K ? op_load(src, ld, true, ul != 0, r, k + 1) : 0.0, t1);
+      tf32_split<P>(v[2 * q], t0);
+      tf32_split<P>(v[2 * q + 1], t1);
 #pragma unroll
       for (int p = 0; p < P; ++p)
         *reinterpret_cast<uint2*>(out + p * plane + r * ldk + k) = make_uint2(t0[p], t1[p]);
@@ -159,12 +170,18 @@ __global__ void __launch_bounds__(256) tf_split_rcontig_kernel(int64_t R, int64_
   const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
   {
     const int64_t r = r0 + lane;
-    for (int kk = w; kk < 64; kk += 8) {
-      const int64_t k = k0 + kk;
-      uint32_t t[P];
-      tf32_split<P>((r < R && k < K) ? op_load(src, ld, false, ul != 0, r, k) : 0.0, t);
+    double v[8];  // all eight loads in flight before any split
 #pragma unroll
-      for (int p = 0; p < P; ++p) tile[p][lane][kk] = t[p];
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = k0 + w + 8 * q;
+      v[q] = (r < R && k < K) ? op_load(src, ld, false, ul != 0, r, k) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      uint32_t t[P];
+      tf32_split<P>(v[q], t);
+#pragma unroll
+      for (int p = 0; p < P; ++p) tile[p][lane][w + 8 * q] = t[p];
     }
   }
   __syncthreads();

@@ -22,7 +22,7 @@ enum TraceKind {
   kTrSvd,          // batched Jacobi SVD
   kTrSmall,        // copies, rank scan, gathers, TRSM blocks
   kTrBf16Gemm,     // tcgen05 BF16 sampling GEMM
-  kTrConvert,      // FP64 -> BF16 conversions and slicing
+  kTrConvert,      // FP64 -> exact BF16 digit slices and TF32 split planes
   kTrOzGemm,       // FP64-accurate GEMM on tensor cores (exact BF16 slices)
   kTrTf32Gemm,     // split-operand TF32 GEMM on tensor cores (3xTF32 / TF32)
   kTrBatchedFactor,  // persistent batched factorization
@@ -30,6 +30,7 @@ enum TraceKind {
   kTrThinN,        // thin_n_kernel: op(A) x, rows of A per thread
   kTrThinT,        // thin_t_kernel: A^T x, lanes along the rows of A
   kTrTrsmDiag,     // trsm_diag_kernel: diagonal blocks of the triangular solves
+  kTrConvertBf16,  // max |A| and the BF16 copies of the trailing block for the sample
   // phases of the method (each spans the kernels above that it launches)
   kTrPhaseSample,   // a1/a2 sketch and sample Y
   kTrPhaseQrY,      // a3 QR of Y and its T factor

@@ -28,7 +28,7 @@ def scaled_err(got, ref, A, B):
 
 @pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (130, 70, 200), (300, 129, 1000), (128, 64, 256),
-                                   (257, 65, 4097)])
+                                   (257, 65, 4097), (1030, 515, 777)])
 def test_oz_gemm_matches_fp64(lls, ta, tb, m, n, k):
     g = np.random.default_rng(m + 3 * n + 7 * k + ta + 2 * tb)
     A = g.standard_normal((m, k)) * 10.0 ** g.uniform(-8, 8, (m, 1))
@@ -37,6 +37,17 @@ def test_oz_gemm_matches_fp64(lls, ta, tb, m, n, k):
     assert st == 0
     err = scaled_err(host(got), A @ B, A, B)
     assert err < 2e-16, err
+
+
+def test_oz_gemm_rank_update_many_items(lls):
+    """The randUTV update shape C -= P W^T with more 128 x 128 items than
+    SMs, so every CTA of the persistent grid runs several items through
+    both passes and the operand rings wrap many times."""
+    g = np.random.default_rng(12)
+    P, W, C0 = g.standard_normal((2304, 128)), g.standard_normal((2200, 128)), g.standard_normal((2304, 2200))
+    got, st = lls.lls_k_gemm_oz(0, 1, dev(P), dev(W), dev(C0), alpha=-1.0, beta=1.0)
+    assert st == 0
+    assert np.max(np.abs(host(got) - (C0 - P @ W.T))) < 1e-12
 
 
 def test_oz_gemm_alpha_beta(lls):
