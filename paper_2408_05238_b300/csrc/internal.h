@@ -125,6 +125,12 @@ size_t thin_scratch_bytes(int64_t M, int64_t b, int64_t nrhs);
 Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W, int64_t ldw,
                              const double* T, int64_t ldt, bool transT, double* x, int64_t ldx,
                              Scratch scratch, cudaStream_t st);
+// xo(k_i + r) = sum_l op(S_i)(r, l) x(k_i + l) for every block i of a replay
+// at once (k_i = i nb, b_i = min(nb, kmax - k_i), S_i = S + i nb^2, ld nb;
+// nb <= 128, nrhs <= 65535), out of place.
+Status small_blocks_batched(int64_t nblk, int64_t nb, int64_t kmax, int64_t nrhs, const double* S,
+                            bool transS, const double* x, int64_t ldx, double* xo, int64_t ldxo,
+                            cudaStream_t st);
 // x(0:b, :) <- op(S) x(0:b, :) for a b x b block S (b <= 128).
 Status small_block_mul(int64_t b, int64_t nrhs, const double* S, int64_t lds, bool transS,
                        double* x, int64_t ldx, cudaStream_t st);
@@ -141,6 +147,9 @@ Status axpy_matrix(int64_t m, int64_t n, double alpha, const double* X, int64_t 
                    int64_t ldy, cudaStream_t st);
 // dst(i, :) = src(rows - 1 - i, :) for a rows x cols block.
 Status copy_rows_reversed(int64_t rows, int64_t cols, const double* src, int64_t lds,
+                          double* dst, int64_t ldd, cudaStream_t st);
+// dst(rows - 1 - i, :) += alpha src(i, :).
+Status axpy_rows_reversed(int64_t rows, int64_t cols, double alpha, const double* src, int64_t lds,
                           double* dst, int64_t ldd, cudaStream_t st);
 // dst(:, j) = src(:, cols - 1 - j).
 Status copy_cols_reversed(int64_t rows, int64_t cols, const double* src, int64_t lds,

@@ -18,7 +18,10 @@
 //    columns per warp, the 32 lanes added by a fixed shuffle tree.
 //  * K or row chunks (a split fixed by the shape alone, so results are
 //    bit-identical run to run and handle to handle) write partial sums that
-//    thin_reduce_kernel adds in chunk order.
+//    thin_reduce_kernel adds in a fixed order.
+//  * A replay's b x b singular-vector blocks touch rows that no other step
+//    of the replay reads afterwards (or before), so small_blocks_kernel
+//    applies all of them in one launch.
 // A unit lower trapezoidal operand (the reflector blocks W of a step) reads
 // 0 above and 1 on its diagonal, without touching the stored upper part.
 #include <algorithm>
@@ -35,7 +38,11 @@ constexpr int TN_KT = 64;         // k tile
 constexpr int TT_COLS = 64;       // columns per CTA of thin_t_kernel
 constexpr int TT_CG = 4;          // right-hand sides per CTA of thin_t_kernel (at most)
 constexpr int kSplitTarget = 296; // CTAs a split aims for: 2 per SM of a 148-SM part
-constexpr int kMinChunk = 256;    // the shortest K / row chunk a split makes
+constexpr int kMinChunkT = 64;    // the shortest row chunk of thin_t_kernel (K <= 64: no split)
+// FP64 multiply-adds issue at 2 per clock per SM here, so a product of a few
+// hundred thousand of them takes microseconds even when spread over every SM:
+// the splits below keep every SM busy down to chunks of one k tile / one row
+// per lane rather than amortising per-CTA overheads over long chunks.
 
 // FP64 instructions issue at a small fraction of the other pipes' rate on
 // this part, and an instruction predicated off still takes its issue slot,
@@ -218,42 +225,60 @@ __global__ void __launch_bounds__(256) thin_reduce_kernel(int64_t M, int nrhs, i
   }
 }
 
-// Reflector replay, middle step: one CTA (512 threads) per right-hand side c
-// sums the row chunks' partials p = W^T x (four groups of chunks per entry,
-// fixed order) and forms p2 = op(T) p for the upper triangular T, four
-// threads per entry of p2 (every fourth l each, then two shuffle adds).
-__global__ void __launch_bounds__(512) thin_reduce_trmv_kernel(int b, int nrhs, int splits,
-                                                               const double* __restrict__ part,
-                                                               const double* __restrict__ T,
-                                                               int64_t ldt, int transT,
-                                                               double* __restrict__ p2) {
-  __shared__ double red[4][128];
-  __shared__ double p[128];
-  const int c = blockIdx.x, t = threadIdx.x;
-  {
-    const int j = t & 127, gg = t >> 7;
-    double s = 0.0;
-    if (j < b) {
-#pragma unroll 4
-      for (int g = gg; g < splits; g += 4) s += part[((int64_t)g * nrhs + c) * b + j];
-    }
-    red[gg][j] = s;
-  }
+// Reflector replay, middle step: p2 = op(T) p for the upper triangular b x b T,
+// 16 entries of p2 per CTA (grid: ceil(b / 16) x nrhs), eight threads per entry
+// (every eighth l each, then three shuffle adds).
+__global__ void __launch_bounds__(128) thin_trmv_kernel(int b, const double* __restrict__ p,
+                                                        const double* __restrict__ T, int64_t ldt,
+                                                        int transT, double* __restrict__ p2) {
+  __shared__ double ps[128];
+  const int c = blockIdx.y, t = threadIdx.x;
+  for (int l = t; l < b; l += 128) ps[l] = p[l + (int64_t)c * b];
   __syncthreads();
-  if (t < 128) p[t] = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
-  __syncthreads();
-  const int i = t >> 2, lg = t & 3;
+  const int i = blockIdx.x * 16 + (t >> 3), lg = t & 7;
   double s = 0.0;
   if (i < b) {
     if (!transT) {
-      for (int l = i + ((lg - i) & 3); l < b; l += 4) s = fma(__ldg(T + i + (int64_t)l * ldt), p[l], s);
+      for (int l = i + ((lg - i) & 7); l < b; l += 8) s = fma(__ldg(T + i + (int64_t)l * ldt), ps[l], s);
     } else {
-      for (int l = lg; l <= i; l += 4) s = fma(__ldg(T + l + (int64_t)i * ldt), p[l], s);
+      for (int l = lg; l <= i; l += 8) s = fma(__ldg(T + l + (int64_t)i * ldt), ps[l], s);
     }
   }
   s += __shfl_xor_sync(0xffffffffu, s, 1);
   s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
   if (i < b && lg == 0) p2[i + (int64_t)c * b] = s;
+}
+
+// The b x b singular-vector blocks of all steps of a replay in one launch,
+// out of place: xo(k + r) = sum_l op(S_i)(r, l) x(k + l) for block i (rows
+// k = i nb .. k + b_i, b_i = min(nb, kmax - k), S_i = S + i nb^2 with ld nb).
+// Grid: (blocks, ceil(nb / 16), nrhs); 16 rows per CTA, eight threads per row.
+__global__ void __launch_bounds__(128) small_blocks_kernel(int nb, int64_t kmax,
+                                                           const double* __restrict__ S, int transS,
+                                                           const double* __restrict__ x, int64_t ldx,
+                                                           double* __restrict__ xo, int64_t ldxo) {
+  __shared__ double xs[128];
+  const int64_t k = (int64_t)blockIdx.x * nb;
+  const int b = (int)(kmax - k < nb ? kmax - k : nb);
+  const int c = blockIdx.z, t = threadIdx.x;
+  const double* xc = x + k + (int64_t)c * ldx;
+  for (int l = t; l < b; l += 128) xs[l] = xc[l];
+  __syncthreads();
+  const double* Si = S + (int64_t)blockIdx.x * nb * nb;
+  const int r = blockIdx.y * 16 + (t >> 3), lg = t & 7;
+  double s = 0.0;
+  if (r < b) {
+    if (!transS) {
+      for (int l = lg; l < b; l += 8) s = fma(__ldg(Si + r + (int64_t)l * nb), xs[l], s);
+    } else {
+      for (int l = lg; l < b; l += 8) s = fma(__ldg(Si + l + (int64_t)r * nb), xs[l], s);
+    }
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  if (r < b && lg == 0) xo[k + r + (int64_t)c * ldxo] = s;
 }
 
 // x(0:b) <- op(S) x(0:b) for a full b x b block S, one CTA (512 threads) per
@@ -284,20 +309,21 @@ struct Split {
   int64_t splits, chunk;
 };
 
-// K chunks of thin_n_kernel: a multiple of the k tile, at least kMinChunk
-// long, enough of them for kSplitTarget CTAs.
+// K chunks of thin_n_kernel: a multiple of the k tile, enough of them for
+// kSplitTarget CTAs.
 Split split_n(int64_t M, int64_t K) {
   const int64_t tiles = ceil_div(M, TN_ROWS);
-  int64_t s = std::min(ceil_div(kSplitTarget, tiles), ceil_div(K, kMinChunk));
+  int64_t s = std::min(ceil_div(kSplitTarget, tiles), ceil_div(K, TN_KT));
   s = std::max<int64_t>(s, 1);
   const int64_t chunk = ceil_div(ceil_div(K, s), TN_KT) * TN_KT;
   return {ceil_div(K, chunk), chunk};
 }
 
-// Row chunks of thin_t_kernel: a multiple of 32 rows, at least kMinChunk.
+// Row chunks of thin_t_kernel: a multiple of 32 rows, enough of them for
+// kSplitTarget CTAs.
 Split split_t(int64_t M, int64_t K, int64_t nrhs) {
   const int64_t ctas = ceil_div(M, TT_COLS) * ceil_div(nrhs, TT_CG);
-  int64_t s = std::min(ceil_div(kSplitTarget, ctas), ceil_div(K, kMinChunk));
+  int64_t s = std::min(ceil_div(kSplitTarget, ctas), ceil_div(K, kMinChunkT));
   s = std::max<int64_t>(s, 1);
   const int64_t chunk = ceil_div(ceil_div(K, s), 32) * 32;
   return {ceil_div(K, chunk), chunk};
@@ -404,7 +430,7 @@ Status thin_gemv(bool trans, bool unit_lower, int64_t M, int64_t K, int64_t nrhs
 size_t thin_scratch_bytes(int64_t M, int64_t b, int64_t nrhs) {
   if (M <= 0 || b <= 0 || nrhs <= 0) return 0;
   const Split sp = split_t(b, M, nrhs);
-  return sizeof(double) * ((size_t)sp.splits * b * nrhs + (size_t)b * nrhs);
+  return sizeof(double) * ((size_t)sp.splits * b * nrhs + 2 * (size_t)b * nrhs);
 }
 
 Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W, int64_t ldw,
@@ -417,18 +443,36 @@ Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W
     return make_error(LLS_ERR_NOMEM, "apply_reflectors_thin: scratch too small");
   const Split sp = split_t(b, M, nrhs);
   double* part = static_cast<double*>(scratch.ptr);
-  double* p2 = part + (size_t)sp.splits * b * nrhs;
-  // p = W^T x by row chunks
+  double* p = part + (size_t)sp.splits * b * nrhs;
+  double* p2 = p + (size_t)b * nrhs;
+  // p = W^T x by row chunks, the chunks summed in order
   LLS_TRY(launch_thin(true, true, b, M, nrhs, 1.0, W, ldw, x, ldx, 0.0, nullptr, 0, part, sp, st));
-  {  // p2 = op(T) p
+  {
     TraceScope ts(kTrThin, st);
-    thin_reduce_trmv_kernel<<<(unsigned)nrhs, 512, 0, st>>>((int)b, (int)nrhs, (int)sp.splits, part,
-                                                            T, ldt, transT ? 1 : 0, p2);
-    LLS_LAUNCHED("thin_reduce_trmv_kernel");
+    thin_reduce_kernel<<<(unsigned)ceil_div(b * nrhs, 32), 256, 0, st>>>(b, (int)nrhs, (int)sp.splits,
+                                                                        part, 1.0, 0.0, p, b);
+    LLS_LAUNCHED("thin_reduce_kernel");
+    // p2 = op(T) p
+    thin_trmv_kernel<<<dim3((unsigned)ceil_div(b, 16), (unsigned)nrhs), 128, 0, st>>>(
+        (int)b, p, T, ldt, transT ? 1 : 0, p2);
+    LLS_LAUNCHED("thin_trmv_kernel");
   }
   // x -= W p2 (K = b <= 128: one K chunk)
   const Split one{1, b};
   return launch_thin(false, true, M, b, nrhs, -1.0, W, ldw, p2, b, 1.0, x, ldx, nullptr, one, st);
+}
+
+Status small_blocks_batched(int64_t nblk, int64_t nb, int64_t kmax, int64_t nrhs, const double* S,
+                            bool transS, const double* x, int64_t ldx, double* xo, int64_t ldxo,
+                            cudaStream_t st) {
+  if (nblk <= 0 || nrhs <= 0) return ok_status();
+  if (nb > 128) return make_error(LLS_ERR_ARG, "small_blocks_batched: nb <= 128");
+  if (nblk > INT32_MAX || nrhs > 65535) return make_error(LLS_ERR_ARG, "small_blocks_batched: size");
+  TraceScope ts(kTrThin, st, 2.0 * kmax * nb * nrhs, 8.0 * (double)nblk * nb * nb);
+  small_blocks_kernel<<<dim3((unsigned)nblk, (unsigned)ceil_div(nb, 16), (unsigned)nrhs), 128, 0,
+                        st>>>((int)nb, kmax, S, transS ? 1 : 0, x, ldx, xo, ldxo);
+  LLS_LAUNCHED("small_blocks_kernel");
+  return ok_status();
 }
 
 Status small_block_mul(int64_t b, int64_t nrhs, const double* S, int64_t lds, bool transS,

@@ -149,6 +149,18 @@ __global__ void rows_reversed_kernel(int64_t rows, int64_t cols, const double* _
   }
 }
 
+// dst(rows - 1 - i, j) += alpha src(i, j).
+__global__ void axpy_rows_reversed_kernel(int64_t rows, int64_t cols, double alpha,
+                                          const double* __restrict__ src, int64_t lds, double* dst,
+                                          int64_t ldd) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < rows * cols;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % rows, j = idx / rows;
+    double* d = dst + (rows - 1 - i) + j * ldd;
+    *d = fma(alpha, src[i + j * lds], *d);
+  }
+}
+
 __global__ void cols_reversed_kernel(int64_t rows, int64_t cols, const double* __restrict__ src,
                                      int64_t lds, double* __restrict__ dst, int64_t ldd) {
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < rows * cols;
@@ -495,6 +507,16 @@ Status copy_rows_reversed(int64_t rows, int64_t cols, const double* src, int64_t
   TraceScope ts(kTrSmall, st);
   rows_reversed_kernel<<<grid_for(rows * cols), EW, 0, st>>>(rows, cols, src, lds, dst, ldd);
   LLS_LAUNCHED("rows_reversed_kernel");
+  return ok_status();
+}
+
+Status axpy_rows_reversed(int64_t rows, int64_t cols, double alpha, const double* src, int64_t lds,
+                          double* dst, int64_t ldd, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return ok_status();
+  TraceScope ts(kTrSmall, st);
+  axpy_rows_reversed_kernel<<<grid_for(rows * cols), EW, 0, st>>>(rows, cols, alpha, src, lds, dst,
+                                                                  ldd);
+  LLS_LAUNCHED("axpy_rows_reversed_kernel");
   return ok_status();
 }
 

@@ -526,15 +526,17 @@ Status nullify_block(Handle& h, Factor& f, const Factor::RzBlock& bl, int64_t nr
   double* zc = h.xc.d();
   double* p = h.sp.d();
   double* p2 = h.sp2.d();
+  if (nrhs <= kThinMaxRhs) {
+    // p = reversed rows of the block + W_bot^T Z_tail; p2 = op(T_z) p; the
+    // block's rows (W_top = I, reversed) and the tail take -p2 and -W_bot p2
+    LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldz, p, bsz, st));
+    LLS_TRY(hgemv(h, true, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldz, 1.0, p, bsz));
+    LLS_TRY(small_blocks_batched(1, bsz, bsz, nrhs, Tz, transT, p, bsz, p2, bsz, st));
+    LLS_TRY(axpy_rows_reversed(bsz, nrhs, -1.0, p2, bsz, Z + j0, ldz, st));
+    return hgemv(h, false, L, nrhs, bsz, -1.0, M + bsz, ldm, p2, bsz, 1.0, Z + r, ldz);
+  }
   LLS_TRY(copy_rows_reversed(bsz, nrhs, Z + j0, ldz, zc, bsz, st));
   LLS_TRY(copy_matrix(bsz, nrhs, zc, bsz, p, bsz, st));
-  if (nrhs <= kThinMaxRhs) {  // p = op(T_z) (p + W_bot^T Z_tail) in place
-    LLS_TRY(hgemv(h, true, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldz, 1.0, p, bsz));
-    LLS_TRY(small_block_mul(bsz, nrhs, Tz, bsz, transT, p, bsz, st));
-    LLS_TRY(axpy_matrix(bsz, nrhs, -1.0, p, bsz, zc, bsz, st));
-    LLS_TRY(hgemv(h, false, L, nrhs, bsz, -1.0, M + bsz, ldm, p, bsz, 1.0, Z + r, ldz));
-    return copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldz, st);
-  }
   LLS_TRY(hgemm(h, true, false, kDense, kDense, bsz, nrhs, L, 1.0, M + bsz, ldm, Z + r, ldz, 1.0, p,
                 bsz));
   LLS_TRY(hgemm(h, transT, false, kDense, kDense, bsz, nrhs, bsz, 1.0, Tz, bsz, p, bsz, 0.0, p2, bsz));
@@ -544,18 +546,37 @@ Status nullify_block(Handle& h, Factor& f, const Factor::RzBlock& bl, int64_t nr
   return copy_rows_reversed(bsz, nrhs, zc, bsz, Z + j0, ldz, st);
 }
 
+// With few right-hand sides every step's b x b block of a replay in one
+// launch: x(0:kmax) <- blockdiag(op(S_i)) x(0:kmax).  In U^T / V^T order each
+// block multiplies rows k_i..k_i+b_i after that step's reflector, and no later
+// step touches those rows; in U / V order each multiplies them before its
+// reflector, and no earlier step has touched them: either way all of them can
+// run together, after (or before) the reflector loop.
+Status batched_small(Handle& h, Factor& f, const double* S, bool transS, double* x, int64_t ldx,
+                     int64_t nrhs) {
+  const int64_t nblk = (int64_t)f.ks.size();
+  if (nblk == 0) return ok_status();
+  const int64_t kmax = f.ks.back() + f.bs.back();
+  LLS_TRY(h.sbat.reserve(sizeof(double) * (size_t)kmax * nrhs));
+  LLS_TRY(small_blocks_batched(nblk, f.nb, kmax, nrhs, S, transS, x, ldx, h.sbat.d(), kmax,
+                               h.stream));
+  return copy_matrix(kmax, nrhs, h.sbat.d(), kmax, x, ldx, h.stream);
+}
+
 }  // namespace
 
 // c (m x nrhs) <- U^T c = U_SVD,s^T H_s^T ... U_SVD,0^T H_0^T c (first step first).
 Status apply_ut(Handle& h, Factor& f, double* c, int64_t ldc, int64_t nrhs) {
   const size_t blk = (size_t)f.nb * f.nb;
   LLS_TRY(reserve_replay(h, f, nrhs));
+  const bool thin = nrhs <= kThinMaxRhs;
   for (size_t i = 0; i < f.ks.size(); ++i) {
     const int64_t k = f.ks[i], b = f.bs[i];
     LLS_TRY(step_reflect(h, f.m - k, b, nrhs, f.T.d() + k + k * f.ldt, f.ldt, f.TU.d() + i * blk, f.nb,
                          true, c + k, ldc));
-    LLS_TRY(step_small(h, b, nrhs, f.US.d() + i * blk, f.nb, true, c + k, ldc));
+    if (!thin) LLS_TRY(step_small(h, b, nrhs, f.US.d() + i * blk, f.nb, true, c + k, ldc));
   }
+  if (thin) LLS_TRY(batched_small(h, f, f.US.d(), true, c, ldc, nrhs));
   return ok_status();
 }
 
@@ -563,9 +584,11 @@ Status apply_ut(Handle& h, Factor& f, double* c, int64_t ldc, int64_t nrhs) {
 Status apply_u(Handle& h, Factor& f, double* w, int64_t ldw_, int64_t nrhs) {
   const size_t blk = (size_t)f.nb * f.nb;
   LLS_TRY(reserve_replay(h, f, nrhs));
+  const bool thin = nrhs <= kThinMaxRhs;
+  if (thin) LLS_TRY(batched_small(h, f, f.US.d(), false, w, ldw_, nrhs));
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii];
-    LLS_TRY(step_small(h, b, nrhs, f.US.d() + ii * blk, f.nb, false, w + k, ldw_));
+    if (!thin) LLS_TRY(step_small(h, b, nrhs, f.US.d() + ii * blk, f.nb, false, w + k, ldw_));
     LLS_TRY(step_reflect(h, f.m - k, b, nrhs, f.T.d() + k + k * f.ldt, f.ldt, f.TU.d() + ii * blk, f.nb,
                          false, w + k, ldw_));
   }
@@ -589,9 +612,11 @@ Status apply_v(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs, int64
   if (f.nullified)
     for (auto it = f.rz.rbegin(); it != f.rz.rend(); ++it)
       LLS_TRY(nullify_block(h, f, *it, nrhs, false, z, ldz));
+  const bool thin = nrhs <= kThinMaxRhs;
+  if (thin) LLS_TRY(batched_small(h, f, f.VS.d(), false, z, ldz, nrhs));
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii];
-    LLS_TRY(step_small(h, b, nrhs, f.VS.d() + ii * blk, f.nb, false, z + k, ldz));
+    if (!thin) LLS_TRY(step_small(h, b, nrhs, f.VS.d() + ii * blk, f.nb, false, z + k, ldz));
     LLS_TRY(step_reflect(h, n - k, b, nrhs, f.WV.d() + k + k * ldv, ldv, f.TV.d() + ii * blk, f.nb,
                          false, z + k, ldz));
   }
@@ -610,12 +635,14 @@ Status apply_vt(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs) {
                   h.z2.d(), ldv));
     return copy_matrix(n, nrhs, h.z2.d(), ldv, z, ldz, h.stream);
   }
+  const bool thin = nrhs <= kThinMaxRhs;
   for (size_t i = 0; i < f.ks.size(); ++i) {
     const int64_t k = f.ks[i], b = f.bs[i];
     LLS_TRY(step_reflect(h, n - k, b, nrhs, f.WV.d() + k + k * ldv, ldv, f.TV.d() + i * blk, f.nb, true,
                          z + k, ldz));
-    LLS_TRY(step_small(h, b, nrhs, f.VS.d() + i * blk, f.nb, true, z + k, ldz));
+    if (!thin) LLS_TRY(step_small(h, b, nrhs, f.VS.d() + i * blk, f.nb, true, z + k, ldz));
   }
+  if (thin) LLS_TRY(batched_small(h, f, f.VS.d(), true, z, ldz, nrhs));
   if (f.nullified)
     for (const auto& bl : f.rz) LLS_TRY(nullify_block(h, f, bl, nrhs, true, z, ldz));
   return ok_status();

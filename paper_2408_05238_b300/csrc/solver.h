@@ -196,6 +196,7 @@ struct Handle {
   // the minimum-norm refinement of the TF32 modes: n x nrhs products and
   // the least-squares solution of its first stage
   DevBuf rs, z2, dinv;  // dinv: inverses of T_11's 64 x 64 diagonal blocks
+  DevBuf sbat;          // a replay's batched singular-vector block products
   int refine_steps = 0;
   double refine_corr = 0.0;
   bool in_refine = false;  // solves inside the refinement trace as phase:refine only
@@ -237,7 +238,7 @@ struct Handle {
   std::vector<DevBuf*> workspace() {
     return {&G,  &Wt, &P,  &P2,  &Q,   &Q2,  &S,   &gemm_ws, &panel_ws,   &bw,   &z,   &sp,   &sp2,
             &xc, &rr, &dd, &nrm, &dstat, &G16, &A16, &A16t,  &Z16,        &F32,  &tc_ws, &mixed_misc,
-            &oz_ws, &rs, &z2, &dinv, &batch_arena, &batch_meta};
+            &oz_ws, &rs, &z2, &dinv, &sbat, &batch_arena, &batch_meta};
   }
   // Binds the workspace to `stream` (call once the stream is set).
   void bind_workspace() {

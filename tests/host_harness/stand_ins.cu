@@ -375,6 +375,28 @@ Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W
   }
   return ok_status();
 }
+Status axpy_rows_reversed(int64_t rows, int64_t cols, double alpha, const double* src, int64_t lds,
+                          double* dst, int64_t ldd, cudaStream_t) {
+  for (int64_t j = 0; j < cols; ++j)
+    for (int64_t i = 0; i < rows; ++i) dst[(rows - 1 - i) + j * ldd] += alpha * src[i + j * lds];
+  return ok_status();
+}
+Status small_blocks_batched(int64_t nblk, int64_t nb, int64_t kmax, int64_t nrhs, const double* S,
+                            bool transS, const double* x, int64_t ldx, double* xo, int64_t ldxo,
+                            cudaStream_t) {
+  for (int64_t i = 0; i < nblk; ++i) {
+    const int64_t k = i * nb, b = std::min(nb, kmax - k);
+    const double* Si = S + i * nb * nb;
+    for (int64_t c = 0; c < nrhs; ++c)
+      for (int64_t r = 0; r < b; ++r) {
+        double s = 0.0;
+        for (int64_t l = 0; l < b; ++l)
+          s += (transS ? Si[l + r * nb] : Si[r + l * nb]) * x[k + l + c * ldx];
+        xo[k + r + c * ldxo] = s;
+      }
+  }
+  return ok_status();
+}
 Status small_block_mul(int64_t b, int64_t nrhs, const double* S, int64_t lds, bool transS,
                        double* x, int64_t ldx, cudaStream_t) {
   for (int64_t c = 0; c < nrhs; ++c) {
