@@ -524,6 +524,26 @@ def run_kernels(a):
     ev1.record(stream)
     torch.cuda.synchronize()
     dt = ev0.elapsed_time(ev1) / 1e3 / a.steps
+    # the Householder panel (steps a3/a5) on a full-height block column of the
+    # C2 and C3 matrices, through the allocation-free entry point
+    for pm_ in (16384, 32768):
+        Pn = torch.randn(nb, pm_, generator=g, dtype=torch.float64, device="cuda").t()
+        tau = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        stat = torch.zeros(1, dtype=torch.int32, device="cuda")
+        panels = [Pn.clone() for _ in range(a.warmup + a.steps)]
+        for q_ in range(a.warmup):
+            lls.lls_k_panel_qr_noalloc(panels[q_], tau, stat)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for q_ in range(a.steps):
+            lls.lls_k_panel_qr_noalloc(panels[a.warmup + q_], tau, stat)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        dtp = ev0.elapsed_time(ev1) / 1e3 / a.steps
+        fl = 2.0 * pm_ * nb * nb - 2.0 * nb ** 3 / 3.0
+        out["kernels"][f"panel_qr:{pm_}x{nb}"] = {"ms": 1e3 * dtp, "status": int(stat.item()),
+                                                    "fp64_tflops": fl / dtp / 1e12}
+        del panels
     out["kernels"]["trsm_upper_trans:nrhs1"] = {"r": n, "ms": 1e3 * dt,
                                                 "blocks_of_64": -(-n // 64),
                                                 "us_per_block": 1e6 * dt / -(-n // 64),

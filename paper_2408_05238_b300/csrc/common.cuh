@@ -98,7 +98,8 @@ __device__ inline bool grid_sync(const GridBarrier& bar, unsigned int& epoch) {
     s_fail = 0;
     const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
     const unsigned int target = (epoch + 1) * nb;
-    __threadfence();
+    // release: this CTA's writes, ordered before it by the __syncthreads above,
+    // are visible to whoever acquires the count (no separate fence needed)
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar.count) : "memory");
     long long it = 0;
     for (;;) {
@@ -112,7 +113,6 @@ __device__ inline bool grid_sync(const GridBarrier& bar, unsigned int& epoch) {
       }
       if (it > 4096) __nanosleep(64);
     }
-    __threadfence();
   }
   ++epoch;
   __syncthreads();

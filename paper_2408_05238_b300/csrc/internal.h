@@ -61,9 +61,16 @@ constexpr size_t panel_qr_scratch_layout_bytes(int64_t G, int64_t n) {
 }
 size_t panel_qr_scratch_bytes(int64_t m, int64_t n);
 // Householder QR of the m x n panel in place; tau[min(m,n)]; err (device
-// int) is raised if a grid barrier timed out.
+// int) is raised if a grid barrier timed out.  shared_device: panels of other
+// streams of this process may run at the same time (batched and served work):
+// a panel that fits one thread-block cluster then always takes the cluster
+// kernel, which needs no cooperative launch and so no library-wide gate;
+// otherwise the cluster kernel is kept for panels of at most kClusterPanelRows
+// rows, beyond which its FP64 work on <= 16 SMs outlasts the grid-wide slab
+// kernel's barriers.
+constexpr int64_t kClusterPanelRows = 1024;
 Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
-                int* err, cudaStream_t st);
+                int* err, cudaStream_t st, bool shared_device = false);
 // T factor (k x k, ldt) of H_0 ... H_{k-1} = I - W T W^T from the Gram
 // matrix S = W^T W (k x k, lds) and tau.
 Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, double* T,

@@ -673,9 +673,9 @@ size_t panel_qr_scratch_bytes(int64_t m, int64_t n) {
 }
 
 Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
-                int* err, cudaStream_t st) {
+                int* err, cudaStream_t st, bool shared_device) {
   if (m <= 0 || n <= 0) return ok_status();
-  {
+  if (shared_device || m <= kClusterPanelRows || !slab_plan(m, n).fits) {
     const ClusterPlan cp = cluster_plan(m, n);
     if (cp.fits) {
       const int64_t k = std::min(m, n);

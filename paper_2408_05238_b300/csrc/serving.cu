@@ -164,6 +164,7 @@ Status ensure_pool(Handle& h) {
     if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
       return make_error(LLS_ERR_CUDA, "cannot create a worker stream");
     w->own_stream = true;
+    w->shares_device = true;
     w->bind_workspace();
     pool->workers.push_back(std::move(w));
   }

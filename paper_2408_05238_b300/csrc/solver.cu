@@ -252,7 +252,7 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     // ---- a3: [Y, T_V, W_V] = unpivoted_QR(Y)
     phase.reset();
     phase.emplace(kTrPhaseQrY, st);
-    LLS_TRY(panel_qr(np, b, Y, ldw, tauVi, pws, &ds->barrier_err, st));
+    LLS_TRY(panel_qr(np, b, Y, ldw, tauVi, pws, &ds->barrier_err, st, h.shares_device));
     LLS_TRY(g.ggemm(np, Y, ldw, b, h.S.d()));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauVi, TVi, nb, st));
     // ---- a4: T(:, k:n) <- T(:, k:n) - (T(:, k:n) W_V) T_V W_V^T, all m rows
@@ -277,7 +277,7 @@ Status factorize(Handle& h, Factor& f, const double* A, int64_t m, int64_t n, in
     // ---- a5: [[A11; A21], T_U, W_U] = unpivoted_QR([A11; A21])
     phase.reset();
     phase.emplace(kTrPhasePanel, st);
-    LLS_TRY(panel_qr(mp, b, ABR, ldt, tauUi, pws, &ds->barrier_err, st));
+    LLS_TRY(panel_qr(mp, b, ABR, ldt, tauUi, pws, &ds->barrier_err, st, h.shares_device));
     LLS_TRY(copy_upper(b, ABR, ldt, f.Rblk.d() + i * blk, nb, st));
     LLS_TRY(g.ggemm(mp, ABR, ldt, b, h.S.d()));
     LLS_TRY(wy_tfactor(b, h.S.d(), nb, tauUi, TUi, nb, st));
@@ -434,7 +434,7 @@ Status finish_factorization(Handle& h, Factor& f, double tol) {
       double* Tz = f.RzT.d() + bl.off_t;
       double* tz = f.RzTau.d() + bl.off_tau;
       LLS_TRY(rz_gather(bsz, L, T, ldt, j0, r, M, ldm, st));
-      LLS_TRY(panel_qr(ldm, bsz, M, ldm, tz, pws, &ds->barrier_err, st));
+      LLS_TRY(panel_qr(ldm, bsz, M, ldm, tz, pws, &ds->barrier_err, st, h.shares_device));
       if (g.tc()) LLS_TRY(h.oz_ws.reserve(g.tc_ws_bytes(bsz, bsz, ldm)));
       LLS_TRY(g.ggemm(ldm, M, ldm, bsz, h.S.d()));
       LLS_TRY(wy_tfactor(bsz, h.S.d(), nb, tz, Tz, bsz, st));

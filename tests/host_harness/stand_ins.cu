@@ -50,7 +50,7 @@ Status gemm(bool ta, bool tb, OperandMode ma, OperandMode mb, int64_t m, int64_t
   return ok_status();
 }
 Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch, int*,
-                cudaStream_t) {
+                cudaStream_t, bool) {
   const int64_t k = std::min(m, n);
   for (int64_t j = 0; j < k; ++j) {
     double alpha = A[j + j * lda], sig = 0.0;
