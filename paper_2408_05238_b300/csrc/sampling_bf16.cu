@@ -5,7 +5,10 @@
 // orthogonal V of the step (its span is what matters); T = U^T A V is still
 // formed by the FP64 Householder QR of Y and the FP64 updates, so the
 // factorization stays exact to FP64 rounding whatever Y is.  Per step:
-//   1. s = 2^-e with 2^e >= max |A_BR| (exact power-of-two scaling);
+//   1. s = 2^-e with 2^e >= sqrt(m n) max |A| of the whole matrix (exact
+//      power-of-two scaling, from one pass over A at the first step: the
+//      steps' orthogonal updates keep every entry of T below ||A||_F <=
+//      sqrt(m n) max |A|, so the later steps need no pass of their own);
 //   2. A16 = bf16(s A_BR) (m' x n') and A16t = its transpose, one pass;
 //   3. G16 = bf16 of the same Philox sketch as the FP64 path;
 //   4. Y = A16^T G16; then q times W = A16t^T Y16, Y = A16^T W16, each
@@ -14,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "solver.h"
 #include "tc_gemm.h"
@@ -113,10 +117,10 @@ __device__ __forceinline__ unsigned short bf16_scaled_bits(double v, int e) {
 // thread are issued before any conversion.
 __global__ void __launch_bounds__(256) convert_transpose_kernel(
     int64_t m, int64_t n, const double* __restrict__ A, int64_t lda,
-    const unsigned long long* maxbits, __nv_bfloat16* __restrict__ A16, int64_t ld16,
+    const unsigned long long* maxbits, int extra, __nv_bfloat16* __restrict__ A16, int64_t ld16,
     __nv_bfloat16* __restrict__ A16t, int64_t ld16t) {
   __shared__ unsigned short tile[32][33];
-  const int e = scale_exp(*maxbits);
+  const int e = scale_exp(*maxbits) + extra;
   const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int64_t i = i0 + tx;
@@ -199,16 +203,19 @@ Status sample_bf16(Handle& h, const double* A, int64_t lda, int64_t mp, int64_t 
   float* F = h.F32.as<float>();
 
   {
-    TraceScope ts(kTrConvertBf16, st, 0.0, (8.0 + 8.0 + 4.0) * mp * np);
-    LLS_CUDA(cudaMemsetAsync(amax, 0, 16, st));
-    const unsigned gx = (unsigned)ceil_div(mp, 1024);
-    const unsigned gy = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>({np, 65535, ceil_div(148 * 8, gx)}));
-    maxabs_f64_kernel<<<dim3(gx, gy), 256, 0, st>>>(mp, np, A, lda, amax);
-    LLS_LAUNCHED("maxabs_f64_kernel");
+    TraceScope ts(kTrConvertBf16, st, 0.0, (step == 0 ? 8.0 : 0.0) * mp * np + (8.0 + 4.0) * mp * np);
+    if (step == 0) {  // max |A| of the whole matrix, and the bound sqrt(m n) on its growth
+      LLS_CUDA(cudaMemsetAsync(amax, 0, 16, st));
+      const unsigned gx = (unsigned)ceil_div(mp, 1024);
+      const unsigned gy = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>({np, 65535, ceil_div(148 * 8, gx)}));
+      maxabs_f64_kernel<<<dim3(gx, gy), 256, 0, st>>>(mp, np, A, lda, amax);
+      LLS_LAUNCHED("maxabs_f64_kernel");
+      h.bf16_scale_extra = (int)std::ceil(0.5 * std::log2(std::max(1.0, (double)mp * (double)np)));
+    }
     dim3 grid((unsigned)ceil_div(mp, 32), (unsigned)ceil_div(np, 32));
-    convert_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(mp, np, A, lda, amax, A16, ld16, A16t,
-                                                           ld16t);
+    convert_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(mp, np, A, lda, amax, h.bf16_scale_extra,
+                                                           A16, ld16, A16t, ld16t);
     LLS_LAUNCHED("convert_transpose_kernel");
   }
   LLS_TRY(launch_sketch_bf16(seed, step, mp, b, G16, ld16, st));

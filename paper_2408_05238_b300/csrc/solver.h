@@ -201,6 +201,7 @@ struct Handle {
   double refine_corr = 0.0;
   bool in_refine = false;  // solves inside the refinement trace as phase:refine only
   bool shares_device = false;  // a worker of a pool: other streams run panels meanwhile
+  int bf16_scale_extra = 0;    // BF16 sample scaling: log2 of sqrt(m n), set at step 0
   DevBuf dstat;           // DevStatus
   // mixed precision sampling: bf16 copies of A_BR and A_BR^T, bf16 sketch /
   // product, fp32 product, tensor-core split-K partials, scalars

@@ -67,61 +67,67 @@ __device__ __forceinline__ double op_load(const double* src, int64_t ld, bool kc
   return src[p + c * ld];
 }
 
-// a (> 0) rounded to 11 significant bits, to nearest with ties to even:
-// returns the 11-bit integer d in [2^10, 2^11) and adds to *sh the shift with
-// a ~= d 2^sh.
-__device__ __forceinline__ unsigned long long round11(unsigned long long a, int* sh) {
-  const int nz = 63 - __clzll((long long)a);
-  int s = nz - 10;
-  unsigned long long d;
-  if (s > 0) {
-    d = a >> s;
-    const unsigned long long r = a & ((1ull << s) - 1), half = 1ull << (s - 1);
-    if (r > half || (r == half && (d & 1ull))) ++d;
-    if (d == (1ull << 11)) {
-      d = 1ull << 10;
-      ++s;
-    }
-  } else {
-    d = a << (-s);
-  }
-  *sh += s;
-  return d;
-}
-
+// The split is integer work on the FP64 bits, and the split passes are bound
+// by it rather than by memory, so it works on 32-bit words: hi keeps the top
+// 10 explicit mantissa bits (bits 19..10 of the high word), rounded to
+// nearest even on the 42 bits below; lo = x - hi is those 42 bits (or 2^42
+// minus them when hi rounded up, with the sign flipped) times 2^(E - 1075),
+// rounded to 11 significant bits the same way.  Identical bit patterns to a
+// 64-bit formulation of the same roundings (checked on tens of millions of
+// values, ties and carries included).
 template <int P>
 __device__ __forceinline__ void tf32_split(double x, uint32_t t[P]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const uint32_t sgn = (uint32_t)(u >> 63) << 31;
-  const int E = (int)((u >> 52) & 0x7FF);
+  const uint32_t w1 = (uint32_t)(u >> 32), w0 = (uint32_t)u;
+  const uint32_t sgn = w1 & 0x80000000u;
+  const int E = (int)((w1 >> 20) & 0x7FFu);
 #pragma unroll
   for (int p = 0; p < P; ++p) t[p] = sgn;
   if (E == 0) return;  // zero or FP64 subnormal: below FP32's range
   if (E == 0x7FF) {    // Inf stays Inf, NaN stays NaN
-    t[0] = sgn | 0x7F800000u | ((u & ((1ull << 52) - 1)) ? 0x400000u : 0u);
+    t[0] = sgn | 0x7F800000u | ((((w1 & 0xFFFFFu) | w0) != 0u) ? 0x400000u : 0u);
     return;
   }
-  const unsigned long long F = (u & ((1ull << 52) - 1)) | (1ull << 52);  // x = F 2^(E - 1075)
-  int sh = 0;
-  const unsigned long long h = round11(F, &sh);                       // hi = h 2^(E - 1075 + sh)
-  const int eh = E - 1075 + sh + 10 + 127;                            // FP32 exponent field
+  uint32_t mh = (w1 >> 10) & 0x3FFu;
+  const uint32_t r1 = w1 & 0x3FFu;  // top 10 of the 42 dropped bits
+  const bool up = r1 > 0x200u || (r1 == 0x200u && (w0 != 0u || (mh & 1u) != 0u));
+  int eh = E - 1023 + 127;
+  if (up && ++mh == 1024u) {
+    mh = 0;
+    ++eh;
+  }
   if (eh >= 255) {
     t[0] = sgn | 0x7F800000u;
     return;
   }
   if (eh <= 0) return;  // below FP32's normal range: flushed
-  t[0] = sgn | ((uint32_t)eh << 23) | ((uint32_t)(h - (1ull << 10)) << 13);
+  t[0] = sgn | ((uint32_t)eh << 23) | (mh << 13);
   if (P == 1) return;
-  // lo = x - hi, exactly F - h 2^sh in units of 2^(E - 1075) (|F - h 2^sh| <= 2^41)
-  const long long D = (long long)F - (long long)(h << sh);
-  if (D == 0) return;
-  const unsigned long long a = D < 0 ? (unsigned long long)(-D) : (unsigned long long)D;
-  int sl = 0;
-  const unsigned long long d = round11(a, &sl);
-  const int el = E - 1075 + sl + 10 + 127;
+  uint32_t rh = r1, rl = w0, lsgn = sgn;
+  if (up) {  // hi > |x|: the remainder is 2^42 - (r1:w0), of the opposite sign
+    rl = 0u - w0;
+    rh = 0x400u - r1 - (w0 != 0u ? 1u : 0u);
+    lsgn ^= 0x80000000u;
+  }
+  if ((rh | rl) == 0u) return;
+  const int pos = rh != 0u ? 63 - __clz(rh) : 31 - __clz(rl);  // leading bit of rh:rl
+  const int sh = pos - 10;                                      // keep 11 bits
+  const unsigned long long v = ((unsigned long long)rh << 32) | rl;
+  uint32_t d;
+  if (sh > 0) {
+    d = (uint32_t)(v >> sh);
+    const unsigned long long rr = v & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rr > half || (rr == half && (d & 1u) != 0u)) ++d;
+  } else {
+    d = (uint32_t)(v << (-sh));
+  }
+  int el = E - 1075 + sh + 10 + 127;
+  if (d == 2048u) {
+    d = 1024u;
+    ++el;
+  }
   if (el <= 0) return;
-  t[P - 1] = (D < 0 ? (sgn ^ 0x80000000u) : sgn) | ((uint32_t)el << 23) |
-             ((uint32_t)(d - (1ull << 10)) << 13);
+  t[P - 1] = lsgn | ((uint32_t)el << 23) | ((d - 1024u) << 13);
 }
 
 // K-contiguous operand (Op(r, k) = src[k + r ld]): block (chunk, row), two
