@@ -338,6 +338,18 @@ __global__ void __launch_bounds__(TF_THREADS, 1)
       int m0, n0, kbeg, nkb;
       item_coords(item, m0, n0, kbeg, nkb);
       const int ab = li & 1;
+      if (use_c) {
+        // the C lines this thread will read, into L2 while the item's MMAs run
+        // (read from DRAM in dependent chunks, they made the epilogue the
+        // bound of the rank-b updates)
+        const int ip = m0 + q * 32 + lane, jp = n0 + ch * 64;
+        if (ip < a.M) {
+          const double* cp = a.C + ip + (int64_t)jp * a.ldc;
+          const int nc = min(64, a.N - jp);
+          for (int c = 0; c < nc; ++c)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(cp + (int64_t)c * a.ldc));
+        }
+      }
       bool ready = tc::mbar_wait(&tfull[ab], (li >> 1) & 1, a.err);
       ready = __all_sync(0xffffffffu, ready);
       if (!ready) break;  // warp-uniform: the TMEM loads below are .sync.aligned
