@@ -3,6 +3,7 @@
 // only enqueues work on `st`.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +24,14 @@ enum OperandMode { kDense = 0, kUnitLower = 1 };
 // sizes: one thread's smaller value could land between another's set and
 // launch.  Raising it once, to the maximum, is safe for every launch.
 Status allow_max_dyn_smem(const void* fn);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time libcuda dependency); nullptr when the driver lacks it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
 
 // Reusable device scratch owned by the caller of a launcher.
 struct Scratch {
@@ -71,6 +80,28 @@ size_t panel_qr_scratch_bytes(int64_t m, int64_t n);
 constexpr int64_t kClusterPanelRows = 1024;
 Status panel_qr(int64_t m, int64_t n, double* A, int64_t lda, double* tau, Scratch scratch,
                 int* err, cudaStream_t st, bool shared_device = false);
+// Cooperative launch (all G CTAs resident at once, as the grid barrier
+// needs) behind a library-wide gate that orders cooperative kernels of
+// different streams, so two of them never wait on each other's CTAs.
+Status coop_launch(const void* fn, int G, int threads, void** args, size_t smem,
+                   cudaStream_t st);
+
+// replay_persistent.cu -------------------------------------------------------
+// The steps of one replay of stored block reflectors as one cooperative
+// launch (nrhs <= 4, nb <= 128): step i (k = i nb, b = min(nb, kmax - k))
+// applies I - W_i op(T_i) W_i^T to rows k..M-1 of x (ldx, nrhs columns),
+// W_i the unit lower reflectors at W + k + k ldw, T_i the b x b upper factor
+// at T + i nb^2 (ld nb); forward: steps 0..nsteps-1 with op(T) = T^T,
+// otherwise nsteps-1..0 with op(T) = T.  err (device int) is raised if a
+// grid barrier timed out.  The reflector chunks are TMA tensor loads, so W
+// must be 16-byte aligned with an even ldw (replay_persistent_fits).
+size_t replay_persistent_scratch_bytes(int64_t nb, int64_t nrhs);
+bool replay_persistent_fits(int64_t nb, int64_t nrhs, const double* W, int64_t ldw, int64_t M,
+                            int64_t kmax);
+Status replay_persistent(bool forward, int64_t M, int64_t nb, int64_t nsteps, int64_t kmax,
+                         const double* W, int64_t ldw, const double* T, double* x, int64_t ldx,
+                         int64_t nrhs, Scratch scratch, int* err, cudaStream_t st);
+
 // T factor (k x k, ldt) of H_0 ... H_{k-1} = I - W T W^T from the Gram
 // matrix S = W^T W (k x k, lds) and tau.
 Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, double* T,

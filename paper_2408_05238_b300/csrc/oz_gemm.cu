@@ -729,30 +729,11 @@ __global__ void oz_reduce_kernel(int M, int N, int splits, const double* __restr
 }
 
 // ---------------------------------------------------------------------------
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn oz_encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  });
-  return fn;
-}
 
 // Slices [8][R][ldk] bf16 as a 3-D tensor (K, R, 8) with box (64, rows, planes).
 Status make_slice_map(CUtensorMap* map, const void* base, int64_t K, int64_t R, int64_t ldk,
                       int box_rows, int box_planes) {
-  EncodeTiledFn fn = oz_encode_fn();
+  EncodeTiledFn fn = tensor_map_encoder();
   if (!fn) return make_error(LLS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)R, (cuuint64_t)OZ_S};
   cuuint64_t strides[2] = {(cuuint64_t)(ldk * 2), (cuuint64_t)(R * ldk * 2)};

@@ -576,6 +576,8 @@ SlabPlan slab_plan(int64_t m, int64_t n) {
   return p;
 }
 
+}  // namespace
+
 Status coop_launch_gated(const void* fn, int G, int threads, void** args, size_t smem,
                          cudaStream_t st);
 
@@ -607,6 +609,8 @@ Status coop_launch_gated(const void* fn, int G, int threads, void** args, size_t
   LLS_CUDA(cudaEventRecord(gate.last, st));
   return ok_status();
 }
+
+namespace {
 
 // Largest cluster the panel kernel may use on this device: 16 CTAs (a
 // non-portable size) when the device can hold one such cluster at the

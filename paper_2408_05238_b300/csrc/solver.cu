@@ -58,10 +58,11 @@ size_t loop_gemm_scratch(int64_t m, int64_t n, int nb, int64_t max_nrhs) {
 // would go through the driver's shared staging buffer).
 Status read_nonfinite_flag(Handle& h, const DevStatus* ds) {
   if (!h.hstat) LLS_CUDA(cudaMallocHost((void**)&h.hstat, sizeof(DevStatus)));
-  LLS_CUDA(cudaMemcpyAsync(&h.hstat->nonfinite, &ds->nonfinite, sizeof(int),
-                           cudaMemcpyDeviceToHost, h.stream));
+  LLS_CUDA(cudaMemcpyAsync(&h.hstat->nonfinite, &ds->nonfinite, 2 * sizeof(int),
+                           cudaMemcpyDeviceToHost, h.stream));  // nonfinite, barrier_err
   LLS_CUDA(cudaStreamSynchronize(h.stream));
   if (h.hstat->nonfinite) return make_error(LLS_ERR_NONFINITE, "B has a NaN or Inf entry", 6);
+  if (h.hstat->barrier_err) return make_error(LLS_ERR_TIMEOUT, "a replay's grid barrier timed out");
   return ok_status();
 }
 
@@ -483,14 +484,39 @@ Status hgemv(Handle& h, bool ta, int64_t mm, int64_t nrhs, int64_t kk, double al
   return hgemm(h, ta, false, kDense, kDense, mm, nrhs, kk, alpha, Aa, lda_, x, ldx, beta, y, ldy);
 }
 
+// A replay with at most four right-hand sides runs as one cooperative
+// launch (replay_persistent) unless other streams of the process share the
+// device (worker handles), where the per-step kernels keep it free of the
+// cooperative-launch gate.
+bool persistent_replay(const Handle& h, const Factor& f, int64_t nrhs) {
+  return nrhs <= 4 && f.nb <= 128 && !h.shares_device && !f.ks.empty();
+}
+bool persistent_replay(const Handle& h, const Factor& f, int64_t nrhs, const double* W,
+                       int64_t ldw_, int64_t M) {
+  return persistent_replay(h, f, nrhs) &&
+         replay_persistent_fits(f.nb, nrhs, W, ldw_, M, f.ks.back() + f.bs.back());
+}
+
 // Buffers of one replay: two nb x nrhs panels and the thin path's scratch.
 Status reserve_replay(Handle& h, Factor& f, int64_t nrhs) {
   LLS_TRY(h.sp.reserve(sizeof(double) * (size_t)f.nb * nrhs));
   LLS_TRY(h.sp2.reserve(sizeof(double) * (size_t)f.nb * nrhs));
   LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)f.nb * nrhs));
-  if (nrhs <= kThinMaxRhs)
-    LLS_TRY(h.gemm_ws.reserve(thin_scratch_bytes(std::max(f.m, f.n), f.nb, nrhs)));
+  if (nrhs <= kThinMaxRhs) {
+    size_t need = thin_scratch_bytes(std::max(f.m, f.n), f.nb, nrhs);
+    if (persistent_replay(h, f, nrhs)) need = std::max(need, replay_persistent_scratch_bytes(f.nb, nrhs));
+    LLS_TRY(h.gemm_ws.reserve(need));
+  }
   return ok_status();
+}
+
+// Every reflector step of one replay (forward: U^T / V^T order) in a single
+// cooperative launch; W, ldw and Tf are the factor's reflectors and T factors.
+Status replay_steps(Handle& h, Factor& f, bool forward, int64_t M, const double* W, int64_t ldw_,
+                    const double* Tf, double* x, int64_t ldx, int64_t nrhs) {
+  const int64_t kmax = f.ks.back() + f.bs.back();
+  return replay_persistent(forward, M, f.nb, (int64_t)f.ks.size(), kmax, W, ldw_, Tf, x, ldx, nrhs,
+                           scratch_of(h.gemm_ws), &h.dstat.as<DevStatus>()->barrier_err, h.stream);
 }
 
 // One step's reflector block applied to x (M x nrhs): x <- (I - W op(T) W^T) x.
@@ -570,12 +596,15 @@ Status apply_ut(Handle& h, Factor& f, double* c, int64_t ldc, int64_t nrhs) {
   const size_t blk = (size_t)f.nb * f.nb;
   LLS_TRY(reserve_replay(h, f, nrhs));
   const bool thin = nrhs <= kThinMaxRhs;
-  for (size_t i = 0; i < f.ks.size(); ++i) {
-    const int64_t k = f.ks[i], b = f.bs[i];
-    LLS_TRY(step_reflect(h, f.m - k, b, nrhs, f.T.d() + k + k * f.ldt, f.ldt, f.TU.d() + i * blk, f.nb,
-                         true, c + k, ldc));
-    if (!thin) LLS_TRY(step_small(h, b, nrhs, f.US.d() + i * blk, f.nb, true, c + k, ldc));
-  }
+  if (persistent_replay(h, f, nrhs, f.T.d(), f.ldt, f.m))
+    LLS_TRY(replay_steps(h, f, true, f.m, f.T.d(), f.ldt, f.TU.d(), c, ldc, nrhs));
+  else
+    for (size_t i = 0; i < f.ks.size(); ++i) {
+      const int64_t k = f.ks[i], b = f.bs[i];
+      LLS_TRY(step_reflect(h, f.m - k, b, nrhs, f.T.d() + k + k * f.ldt, f.ldt, f.TU.d() + i * blk,
+                           f.nb, true, c + k, ldc));
+      if (!thin) LLS_TRY(step_small(h, b, nrhs, f.US.d() + i * blk, f.nb, true, c + k, ldc));
+    }
   if (thin) LLS_TRY(batched_small(h, f, f.US.d(), true, c, ldc, nrhs));
   return ok_status();
 }
@@ -586,6 +615,8 @@ Status apply_u(Handle& h, Factor& f, double* w, int64_t ldw_, int64_t nrhs) {
   LLS_TRY(reserve_replay(h, f, nrhs));
   const bool thin = nrhs <= kThinMaxRhs;
   if (thin) LLS_TRY(batched_small(h, f, f.US.d(), false, w, ldw_, nrhs));
+  if (persistent_replay(h, f, nrhs, f.T.d(), f.ldt, f.m))
+    return replay_steps(h, f, false, f.m, f.T.d(), f.ldt, f.TU.d(), w, ldw_, nrhs);
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii];
     if (!thin) LLS_TRY(step_small(h, b, nrhs, f.US.d() + ii * blk, f.nb, false, w + k, ldw_));
@@ -614,6 +645,8 @@ Status apply_v(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs, int64
       LLS_TRY(nullify_block(h, f, *it, nrhs, false, z, ldz));
   const bool thin = nrhs <= kThinMaxRhs;
   if (thin) LLS_TRY(batched_small(h, f, f.VS.d(), false, z, ldz, nrhs));
+  if (persistent_replay(h, f, nrhs, f.WV.d(), ldv, n))
+    return replay_steps(h, f, false, n, f.WV.d(), ldv, f.TV.d(), z, ldz, nrhs);
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii];
     if (!thin) LLS_TRY(step_small(h, b, nrhs, f.VS.d() + ii * blk, f.nb, false, z + k, ldz));
@@ -636,12 +669,15 @@ Status apply_vt(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs) {
     return copy_matrix(n, nrhs, h.z2.d(), ldv, z, ldz, h.stream);
   }
   const bool thin = nrhs <= kThinMaxRhs;
-  for (size_t i = 0; i < f.ks.size(); ++i) {
-    const int64_t k = f.ks[i], b = f.bs[i];
-    LLS_TRY(step_reflect(h, n - k, b, nrhs, f.WV.d() + k + k * ldv, ldv, f.TV.d() + i * blk, f.nb, true,
-                         z + k, ldz));
-    if (!thin) LLS_TRY(step_small(h, b, nrhs, f.VS.d() + i * blk, f.nb, true, z + k, ldz));
-  }
+  if (persistent_replay(h, f, nrhs, f.WV.d(), ldv, n))
+    LLS_TRY(replay_steps(h, f, true, n, f.WV.d(), ldv, f.TV.d(), z, ldz, nrhs));
+  else
+    for (size_t i = 0; i < f.ks.size(); ++i) {
+      const int64_t k = f.ks[i], b = f.bs[i];
+      LLS_TRY(step_reflect(h, n - k, b, nrhs, f.WV.d() + k + k * ldv, ldv, f.TV.d() + i * blk, f.nb,
+                           true, z + k, ldz));
+      if (!thin) LLS_TRY(step_small(h, b, nrhs, f.VS.d() + i * blk, f.nb, true, z + k, ldz));
+    }
   if (thin) LLS_TRY(batched_small(h, f, f.VS.d(), true, z, ldz, nrhs));
   if (f.nullified)
     for (const auto& bl : f.rz) LLS_TRY(nullify_block(h, f, bl, nrhs, true, z, ldz));
@@ -663,7 +699,7 @@ Status solve_factored(Handle& h, Factor& f, const double* B, int64_t nrhs, int64
   DevStatus* ds = h.dstat.as<DevStatus>();
   double* Bw = h.bw.d();
   double* Z = h.z.d();
-  LLS_CUDA(cudaMemsetAsync(&ds->nonfinite, 0, sizeof(int), st));
+  LLS_CUDA(cudaMemsetAsync(&ds->nonfinite, 0, 2 * sizeof(int), st));  // nonfinite, barrier_err
   LLS_TRY(copy_check(m, nrhs, B, ldb, Bw, m, &ds->nonfinite, st));
   LLS_TRY(apply_ut(h, f, Bw, m, nrhs));  // c = U^T b
   LLS_TRY(h.gemm_ws.reserve(trsm_upper_scratch_bytes(r, nrhs)));
@@ -818,6 +854,7 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
   }
   h.refine_steps = steps;
   h.refine_corr = corr;
+  LLS_TRY(read_nonfinite_flag(h, h.dstat.as<DevStatus>()));  // the replays' barrier flag
   if (converged[0] && converged[1]) return ok_status();
   return make_error(LLS_WARN_REFINE_NOCONV, "refinement correction " + std::to_string(corr) +
                                                 " above refine_tol");

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstddef>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -125,6 +126,8 @@ struct DevStatus {
   int64_t rank[3];  // prefix, count, nan
   double tol;
 };
+static_assert(offsetof(DevStatus, barrier_err) == offsetof(DevStatus, nonfinite) + sizeof(int),
+              "nonfinite and barrier_err are read back as one pair");
 
 // A randUTV factorization A V = U T kept on the device.
 //  T       m x n (ld = m): T's upper trapezoid; below the diagonal of each

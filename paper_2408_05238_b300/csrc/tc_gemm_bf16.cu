@@ -262,30 +262,11 @@ __global__ void splitk_sum_f32_kernel(int M, int N, int splits, const float* __r
 // ---------------------------------------------------------------------------
 // Tensor maps via the driver entry point (no link-time libcuda dependency).
 // ---------------------------------------------------------------------------
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  });
-  return fn;
-}
 
 // rows x cols column-major bf16 matrix (rows contiguous = K), box 64 x box_cols.
 Status make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld,
                 int box_cols) {
-  EncodeTiledFn fn = encode_fn();
+  EncodeTiledFn fn = tensor_map_encoder();
   if (!fn) return make_error(LLS_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16)
     return make_error(LLS_ERR_ARG, "bf16 operand must be 16-byte aligned with ld % 8 == 0");

@@ -20,7 +20,7 @@ const char* trace_kind_name(int k) {
                                         "tf32_mma_kernel",   "batched_factor_kernel",
                                         "thin_small_kernels", "thin_n_kernel",
                                         "thin_t_kernel",     "trsm_diag_kernel",
-                                        "bf16_convert_kernels",
+                                        "bf16_convert_kernels", "replay_kernel",
                                         "phase:sample",
                                         "phase:qr_y",
                                         "phase:right_update", "phase:panel",

@@ -31,6 +31,7 @@ enum TraceKind {
   kTrThinT,        // thin_t_kernel: A^T x, lanes along the rows of A
   kTrTrsmDiag,     // trsm_diag_kernel: diagonal blocks of the triangular solves
   kTrConvertBf16,  // max |A| and the BF16 copies of the trailing block for the sample
+  kTrReplay,       // replay_kernel: a replay's reflector steps in one cooperative launch
   // phases of the method (each spans the kernels above that it launches)
   kTrPhaseSample,   // a1/a2 sketch and sample Y
   kTrPhaseQrY,      // a3 QR of Y and its T factor

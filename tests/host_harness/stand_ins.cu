@@ -375,6 +375,23 @@ Status apply_reflectors_thin(int64_t M, int64_t b, int64_t nrhs, const double* W
   }
   return ok_status();
 }
+size_t replay_persistent_scratch_bytes(int64_t, int64_t) { return 0; }
+bool replay_persistent_fits(int64_t nb, int64_t nrhs, const double* W, int64_t ldw, int64_t,
+                            int64_t) {
+  return nrhs >= 1 && nrhs <= 4 && nb >= 1 && nb <= 128 && ldw % 2 == 0 &&
+         reinterpret_cast<uintptr_t>(W) % 16 == 0;
+}
+// The replay's steps one after another, each as the plain thin step above.
+Status replay_persistent(bool forward, int64_t M, int64_t nb, int64_t nsteps, int64_t kmax,
+                         const double* W, int64_t ldw, const double* T, double* x, int64_t ldx,
+                         int64_t nrhs, Scratch, int*, cudaStream_t st) {
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int64_t i = forward ? s : nsteps - 1 - s, k = i * nb, b = std::min(nb, kmax - k);
+    LLS_TRY(apply_reflectors_thin(M - k, b, nrhs, W + k + k * ldw, ldw, T + i * nb * nb, nb, forward,
+                                  x + k, ldx, {}, st));
+  }
+  return ok_status();
+}
 Status axpy_rows_reversed(int64_t rows, int64_t cols, double alpha, const double* src, int64_t lds,
                           double* dst, int64_t ldd, cudaStream_t) {
   for (int64_t j = 0; j < cols; ++j)
