@@ -72,6 +72,18 @@ int lls_k_trsm_upper(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
 int lls_k_trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
                            double* B, int64_t ldb, void* stream);
 
+/* B <- R^{-1} B (trans = 0) or R^{-T} B (trans = 1) for the upper
+ * triangular r x r matrix R through the inverses of its 64 x 64 diagonal
+ * blocks, the triangular solves of the refinement of the TF32 modes
+ * (T_11^{-1} and T_11^{-T} of Fig. 4's solve operator): with nrhs <= 4 one
+ * cooperative launch with a grid barrier per block (LLS_ERR_TIMEOUT if a
+ * barrier wait ran out; R and B stay valid device memory), with nrhs <= 16
+ * two launches a block; LLS_ERR_ARG for nrhs > 16.  Scratch is allocated
+ * stream-ordered on `stream` and freed before returning; the call waits for
+ * the stream. */
+int lls_k_trsm_upper_blockinv(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
+                              double* B, int64_t ldb, int trans, void* stream);
+
 /* Compute_rank (Fig. 4) of diag(T) (len entries, T with leading dimension
  * ldt): out[0] = length of the leading run of |T_jj| > tol, out[1] = number
  * of |T_jj| > tol, out[2] = 1 if a diagonal entry is NaN (device int64[3]). */

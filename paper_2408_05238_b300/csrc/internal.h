@@ -102,6 +102,14 @@ Status replay_persistent(bool forward, int64_t M, int64_t nb, int64_t nsteps, in
                          const double* W, int64_t ldw, const double* T, double* x, int64_t ldx,
                          int64_t nrhs, Scratch scratch, int* err, cudaStream_t st);
 
+// trsm_persistent.cu ----------------------------------------------------------
+// trsm_upper_inv (below) for nrhs <= 4 as one cooperative launch, a grid
+// barrier per 64-row block; scratch: 8 bytes (the barrier's counter); err
+// (device int) is raised if a barrier timed out.
+Status trsm_upper_inv_persistent(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
+                                 const double* Dinv, double* B, int64_t ldb, bool trans,
+                                 Scratch scratch, int* err, cudaStream_t st);
+
 // T factor (k x k, ldt) of H_0 ... H_{k-1} = I - W T W^T from the Gram
 // matrix S = W^T W (k x k, lds) and tau.
 Status wy_tfactor(int64_t k, const double* S, int64_t lds, const double* tau, double* T,

@@ -796,7 +796,19 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
     LLS_TRY(h.dinv.reserve(trsm_inverse_bytes(r)));
     LLS_TRY(trsm_block_inverses(r, f.T.d(), ldt, h.dinv.d(), st));
   }
+  // With at most four, each solve is one cooperative launch (a grid barrier
+  // per block) unless worker streams share the device.
+  const bool coop_trsm = nrhs <= 4 && !h.shares_device;
+  if (coop_trsm) LLS_TRY(h.sp2.reserve(64));
   auto trsm_both = [&](double* y, int64_t ldy, bool trans_first) -> Status {
+    if (coop_trsm) {
+      int* err = &h.dstat.as<DevStatus>()->barrier_err;
+      const Scratch sc = scratch_of(h.sp2);
+      LLS_TRY(trsm_upper_inv_persistent(r, nrhs, f.T.d(), ldt, h.dinv.d(), y, ldy, trans_first, sc,
+                                        err, st));
+      return trsm_upper_inv_persistent(r, nrhs, f.T.d(), ldt, h.dinv.d(), y, ldy, !trans_first, sc,
+                                       err, st);
+    }
     if (thin) {
       LLS_TRY(trsm_upper_inv(r, nrhs, f.T.d(), ldt, h.dinv.d(), y, ldy, trans_first, st));
       return trsm_upper_inv(r, nrhs, f.T.d(), ldt, h.dinv.d(), y, ldy, !trans_first, st);

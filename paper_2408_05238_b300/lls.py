@@ -156,6 +156,7 @@ _sig("lls_k_panel_qr_noalloc", [_I, _I, _P, _I, _P, _P, _P])
 _sig("lls_k_gemm_tf32", [C.c_int, C.c_int, C.c_int, C.c_int, _I, _I, _I, _D, _P, _I, _P, _I, _D,
                          _P, _I, C.c_int, _P, _P])
 _sig("lls_k_trsm_upper_trans", [_I, _I, _P, _I, _P, _I, _P])
+_sig("lls_k_trsm_upper_blockinv", [_I, _I, _P, _I, _P, _I, _I, _P])
 
 EXPORTED = [n for n in dir(_lib) if n.startswith("lls_")]
 
@@ -568,6 +569,13 @@ def lls_k_trsm_upper_trans(R: torch.Tensor, B: torch.Tensor):
     r = R.shape[0]
     _kcheck(_lib.lls_k_trsm_upper_trans(r, B.shape[1], _ptr(R), _ld(R), _ptr(B), _ld(B),
                                         _stream()))
+    return B
+
+
+def lls_k_trsm_upper_blockinv(R: torch.Tensor, B: torch.Tensor, trans: bool = False):
+    r = R.shape[0]
+    _kcheck(_lib.lls_k_trsm_upper_blockinv(r, B.shape[1], _ptr(R), _ld(R), _ptr(B), _ld(B),
+                                           int(trans), _stream()))
     return B
 
 

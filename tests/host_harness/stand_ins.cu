@@ -436,6 +436,11 @@ Status trsm_upper_inv(int64_t r, int64_t nrhs, const double* R, int64_t ldr, con
   if (trans) return trsm_upper_trans(r, nrhs, R, ldr, B, ldb, Scratch{}, st);
   return trsm_upper(r, nrhs, R, ldr, B, ldb, Scratch{}, st);
 }
+Status trsm_upper_inv_persistent(int64_t r, int64_t nrhs, const double* R, int64_t ldr,
+                                 const double* Dinv, double* B, int64_t ldb, bool trans, Scratch,
+                                 int*, cudaStream_t st) {
+  return trsm_upper_inv(r, nrhs, R, ldr, Dinv, B, ldb, trans, st);
+}
 size_t trsm_upper_trans_scratch_bytes(int64_t, int64_t) { return 0; }
 // R^T Y = B by forward substitution, one column at a time.
 Status trsm_upper_trans(int64_t r, int64_t nrhs, const double* R, int64_t ldr, double* B,

@@ -109,6 +109,8 @@ def test_kernel_entry_points_reject_bad_sizes(lib):
     assert L.lls_k_sketch(1, 0, 10, 2, None, 5, None) == lib.LLS_ERR_ARG
     assert L.lls_k_philox(1, -1, 2, 2, None, None) == lib.LLS_ERR_ARG
     assert L.lls_k_geqrf(10, 3, None, 5, None, None, 3, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_trsm_upper_blockinv(10, 17, None, 10, None, 10, 0, None) == lib.LLS_ERR_ARG
+    assert L.lls_k_trsm_upper_blockinv(10, 2, None, 10, None, 10, 1, None) == lib.LLS_ERR_ARG
     assert L.lls_k_jacobi_svd(129, None, 129, None, None, 129, None, 129, None, None) == lib.LLS_ERR_ARG
     assert L.lls_k_trsm_upper(5, 1, None, 4, None, 5, None) == lib.LLS_ERR_ARG
     assert L.lls_k_rank(-1, None, 1, 0.0, None, None) == lib.LLS_ERR_ARG
