@@ -83,11 +83,12 @@ def test_gemm_unit_lower_operands(lls, ta):
 
 
 # -------------------------------------------------------------- a3/a5 panel QR
-# (2000, 64), (300, 128), (129, 7): one thread-block cluster; (16384, 128): the
-# cooperative shared-memory (slab) kernel; (40000, 128): slabs too tall for
-# shared memory, the cooperative global-memory kernel
+# (300, 128), (129, 7), (8, 12): one thread-block cluster; (2000, 64) to
+# (30000, 128): the cooperative shared-memory (slab) kernel, odd and ragged
+# slabs included; (40000, 128): slabs too tall for shared memory, the
+# cooperative global-memory kernel
 @pytest.mark.parametrize("m,n", [(2000, 64), (129, 7), (300, 128), (16384, 128), (40000, 128),
-                                 (8, 12), (5000, 1)])
+                                 (8, 12), (5000, 1), (7001, 128), (2049, 37), (30000, 128)])
 def test_panel_qr_matches_oracle(lls, m, n):
     Y = np.random.default_rng(m + n).standard_normal((m, n))
     A, tau, T = lls.lls_k_geqrf(dev(Y))
@@ -103,13 +104,14 @@ def test_panel_qr_matches_oracle(lls, m, n):
     assert np.allclose(T, orc.wy_factor(W_ref, tau_ref), rtol=0, atol=1e-12 * max(1, np.abs(T).max()))
 
 
-def test_panel_qr_zero_and_rank_deficient_columns(lls):
+@pytest.mark.parametrize("m", [500, 9000])
+def test_panel_qr_zero_and_rank_deficient_columns(lls, m):
     """A zero column gives tau = 0 on both sides; after a dependent column the
     trailing rows of R are not unique (the reflector is built from rounding
     noise), so rows before it are compared and the rest is checked for
     validity: Q R = Y with Q = I - W T W^T orthogonal."""
     g = np.random.default_rng(3)
-    Y = g.standard_normal((500, 10))
+    Y = g.standard_normal((m, 10))
     Y[:, 3] = 0.0
     Y[:, 6] = Y[:, 1] * 2.0
     A, tau, T = lls.lls_k_geqrf(dev(Y))
@@ -121,8 +123,8 @@ def test_panel_qr_zero_and_rank_deficient_columns(lls):
     assert abs(R[6, 6]) < 1e-12
     W = np.tril(A, -1)[:, :10]
     W[np.arange(10), np.arange(10)] = 1.0
-    Q = np.eye(500) - W @ T @ W.T
-    assert np.allclose(Q.T @ Q, np.eye(500), atol=1e-13)
+    Q = np.eye(m) - W @ T @ W.T
+    assert np.allclose(Q.T @ Q, np.eye(m), atol=1e-13)
     assert np.allclose(Q[:, :10] @ R, Y, atol=1e-12)
 
 

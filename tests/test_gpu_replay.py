@@ -2,8 +2,9 @@
 the refinement's operators) with at most four right-hand sides run as one
 cooperative launch per replay (replay_kernel) when the factor's leading
 dimension is even (its reflector chunks are TMA tensor loads); five or more
-right-hand sides, or an odd leading dimension, take the per-step kernels.  Checked here: x against the FP64 oracle for 1..4 right-hand sides
-and several block sizes (ragged last step included), agreement with the
+right-hand sides, or an odd leading dimension, take the per-step kernels.
+Checked here: x against the FP64 oracle for 1..4 right-hand sides and
+several block sizes (ragged last step included), agreement with the
 per-step path on the same factor, one launch per replay in the trace,
 bit-identical repeats, and a grid-barrier timeout reported as
 LLS_ERR_TIMEOUT with the handle still usable afterwards (the wait runs out
