@@ -163,36 +163,42 @@ __global__ void __launch_bounds__(256) tf_split_kcontig_kernel(int64_t R, int64_
   }
 }
 
-// R-contiguous operand (Op(r, k) = src[r + k ld]): a 32 (r) x 64 (k) tile read
-// along r, transposed through shared memory and written along k.
+// R-contiguous operand (Op(r, k) = src[r + k ld]): a 64 (r) x 64 (k) tile read
+// along r (512 contiguous bytes a column, 16 loads in flight a thread),
+// transposed through shared memory and written along k.
 template <int P>
 __global__ void __launch_bounds__(256) tf_split_rcontig_kernel(int64_t R, int64_t K,
                                                                 const double* __restrict__ src,
                                                                 int64_t ld, int ul,
                                                                 uint32_t* __restrict__ out,
                                                                 int64_t ldk) {
-  __shared__ uint32_t tile[P][32][65];
+  __shared__ uint32_t tile[P][64][65];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 8 warps
-  const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 64;
+  const int64_t r0 = (int64_t)blockIdx.x * 64, k0 = (int64_t)blockIdx.y * 64;
   {
-    const int64_t r = r0 + lane;
-    double v[8];  // all eight loads in flight before any split
+    double v[16];  // all sixteen loads in flight before any split
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int64_t k = k0 + w + 8 * q;
-      v[q] = (r < R && k < K) ? op_load(src, ld, false, ul != 0, r, k) : 0.0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t r = r0 + lane + 32 * h;
+        v[2 * q + h] = (r < R && k < K) ? op_load(src, ld, false, ul != 0, r, k) : 0.0;
+      }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      uint32_t t[P];
-      tf32_split<P>(v[q], t);
+    for (int q = 0; q < 8; ++q)
 #pragma unroll
-      for (int p = 0; p < P; ++p) tile[p][lane][w + 8 * q] = t[p];
-    }
+      for (int h = 0; h < 2; ++h) {
+        uint32_t t[P];
+        tf32_split<P>(v[2 * q + h], t);
+#pragma unroll
+        for (int p = 0; p < P; ++p) tile[p][lane + 32 * h][w + 8 * q] = t[p];
+      }
   }
   __syncthreads();
   const int64_t plane = R * ldk;
-  for (int rr = w; rr < 32; rr += 8) {
+  for (int rr = w; rr < 64; rr += 8) {
     const int64_t r = r0 + rr, k = k0 + 2 * lane;
     if (r >= R || k >= ldk) continue;
 #pragma unroll
@@ -456,7 +462,7 @@ Status split_operand(int64_t R, int64_t K, const double* src, int64_t ld, bool k
     tf_split_kcontig_kernel<P><<<g, 256, 0, st>>>(R, K, src, ld, ul ? 1 : 0, out, ldk);
     LLS_LAUNCHED("tf_split_kcontig_kernel");
   } else {
-    dim3 g((unsigned)ceil_div(R, 32), (unsigned)ceil_div(ldk, 64));
+    dim3 g((unsigned)ceil_div(R, 64), (unsigned)ceil_div(ldk, 64));
     if (g.y > 65535u) return make_error(LLS_ERR_ARG, "tf32_gemm: K too large");
     tf_split_rcontig_kernel<P><<<g, 256, 0, st>>>(R, K, src, ld, ul ? 1 : 0, out, ldk);
     LLS_LAUNCHED("tf_split_rcontig_kernel");
