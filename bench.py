@@ -548,6 +548,53 @@ def run_kernels(a):
                                                 "blocks_of_64": -(-n // 64),
                                                 "us_per_block": 1e6 * dt / -(-n // 64),
                                                 "fp64_operand_gbs": 4.0 * n * n / dt / 1e9}
+    # the same solve through the block inverses (the refinement's form): one
+    # cooperative launch with a grid barrier per block of 64
+    for _ in range(a.warmup):
+        lls.lls_k_trsm_upper_blockinv(R, b.clone(), trans=True)
+    bs = [b.clone() for _ in range(a.steps)]
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for bb in bs:
+        lls.lls_k_trsm_upper_blockinv(R, bb, trans=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3 / a.steps
+    out["kernels"]["trsm_upper_blockinv_trans:nrhs1"] = {
+        "r": n, "ms": 1e3 * dt, "us_per_block": 1e6 * dt / -(-n // 64),
+        "note": "includes the 64 x 64 block inverses and the entry point's scratch allocation"}
+    del R, bs
+    # the replays of the solve (Fig. 4: c = U^T b, x = V z) on an FP64 factor
+    # of an n x n/2 rank-n/4 X Y matrix, one right-hand side: each replay one
+    # cooperative launch (replay_kernel), times from the library's trace
+    mr, nr_, rr = n, n // 2, n // 4
+    X = torch.randn(mr, rr, generator=g, dtype=torch.float64, device="cuda")
+    Yf = torch.randn(rr, nr_, generator=g, dtype=torch.float64, device="cuda")
+    Af = (X @ Yf).t().contiguous().t()
+    del X, Yf
+    nrm = float(torch.linalg.matrix_norm(Af, ord=2))
+    h = lls.lls_create(nb=nb, q=1, seed=2001)
+    try:
+        fid, rank, _ = lls.lls_factor(h, Af, 1e-10 * nrm)
+        bf = torch.randn(mr, 1, generator=g, dtype=torch.float64, device="cuda")
+        for _ in range(a.warmup):
+            lls.lls_solve_factored(h, fid, bf, nr_)
+        torch.cuda.synchronize()
+        lls.lls_trace_enable(h, True)
+        for _ in range(a.steps):
+            lls.lls_solve_factored(h, fid, bf, nr_)
+        torch.cuda.synchronize()
+        tr = lls.lls_trace_read(h)
+        lls.lls_trace_enable(h, False)
+        launches, secs = tr.get("replay_kernel", (0, 0.0))[:2]
+        steps_ = -(-nr_ // nb)
+        out["kernels"][f"replay_kernel:{mr}x{nr_}"] = {
+            "rank": rank, "launches_per_solve": launches / a.steps,
+            "ms_per_launch": 1e3 * secs / max(launches, 1),
+            "us_per_step": 1e6 * secs / max(launches, 1) / steps_,
+            "solve_ms": 1e3 * tr["phase:solve"][1] / a.steps}
+    finally:
+        lls.lls_destroy(h)
     print(json.dumps(out))
     return 0
 
