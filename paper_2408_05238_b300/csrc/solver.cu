@@ -484,16 +484,23 @@ Status hgemv(Handle& h, bool ta, int64_t mm, int64_t nrhs, int64_t kk, double al
   return hgemm(h, ta, false, kDense, kDense, mm, nrhs, kk, alpha, Aa, lda_, x, ldx, beta, y, ldy);
 }
 
-// A replay with at most four right-hand sides runs as one cooperative
-// launch (replay_persistent) unless other streams of the process share the
-// device (worker handles), where the per-step kernels keep it free of the
-// cooperative-launch gate.
-bool persistent_replay(const Handle& h, const Factor& f, int64_t nrhs) {
-  return nrhs <= 4 && f.nb <= 128 && !h.shares_device && !f.ks.empty();
+// With at most four right-hand sides, a factor whose larger side has at
+// least kPersistentMinRows rows replays its reflectors as one cooperative
+// launch each (replay_persistent) and the refinement's triangular solves
+// likewise (trsm_upper_inv_persistent).  The choice depends on the shape
+// alone, never on the handle, so a solve gives the same bits on any handle or
+// worker; smaller factors -- the batched and most served problems -- keep the
+// per-step kernels, which need no cooperative launch and let worker streams
+// overlap.
+constexpr int64_t kPersistentMinRows = 4096;
+bool persistent_solve(const Factor& f, int64_t nrhs) {
+  return nrhs <= 4 && f.nb <= 128 && !f.ks.empty() && std::max(f.m, f.n) >= kPersistentMinRows;
 }
-bool persistent_replay(const Handle& h, const Factor& f, int64_t nrhs, const double* W,
-                       int64_t ldw_, int64_t M) {
-  return persistent_replay(h, f, nrhs) &&
+// The reflectors also need a TMA map: an even leading dimension and a 16-byte
+// aligned base, which every factor buffer of the library has (its arenas
+// align each buffer to 256 bytes).
+bool persistent_replay(const Factor& f, int64_t nrhs, const double* W, int64_t ldw_, int64_t M) {
+  return persistent_solve(f, nrhs) &&
          replay_persistent_fits(f.nb, nrhs, W, ldw_, M, f.ks.back() + f.bs.back());
 }
 
@@ -504,7 +511,7 @@ Status reserve_replay(Handle& h, Factor& f, int64_t nrhs) {
   LLS_TRY(h.xc.reserve(sizeof(double) * (size_t)f.nb * nrhs));
   if (nrhs <= kThinMaxRhs) {
     size_t need = thin_scratch_bytes(std::max(f.m, f.n), f.nb, nrhs);
-    if (persistent_replay(h, f, nrhs)) need = std::max(need, replay_persistent_scratch_bytes(f.nb, nrhs));
+    if (persistent_solve(f, nrhs)) need = std::max(need, replay_persistent_scratch_bytes(f.nb, nrhs));
     LLS_TRY(h.gemm_ws.reserve(need));
   }
   return ok_status();
@@ -596,7 +603,7 @@ Status apply_ut(Handle& h, Factor& f, double* c, int64_t ldc, int64_t nrhs) {
   const size_t blk = (size_t)f.nb * f.nb;
   LLS_TRY(reserve_replay(h, f, nrhs));
   const bool thin = nrhs <= kThinMaxRhs;
-  if (persistent_replay(h, f, nrhs, f.T.d(), f.ldt, f.m))
+  if (persistent_replay(f, nrhs, f.T.d(), f.ldt, f.m))
     LLS_TRY(replay_steps(h, f, true, f.m, f.T.d(), f.ldt, f.TU.d(), c, ldc, nrhs));
   else
     for (size_t i = 0; i < f.ks.size(); ++i) {
@@ -615,7 +622,7 @@ Status apply_u(Handle& h, Factor& f, double* w, int64_t ldw_, int64_t nrhs) {
   LLS_TRY(reserve_replay(h, f, nrhs));
   const bool thin = nrhs <= kThinMaxRhs;
   if (thin) LLS_TRY(batched_small(h, f, f.US.d(), false, w, ldw_, nrhs));
-  if (persistent_replay(h, f, nrhs, f.T.d(), f.ldt, f.m))
+  if (persistent_replay(f, nrhs, f.T.d(), f.ldt, f.m))
     return replay_steps(h, f, false, f.m, f.T.d(), f.ldt, f.TU.d(), w, ldw_, nrhs);
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii];
@@ -645,7 +652,7 @@ Status apply_v(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs, int64
       LLS_TRY(nullify_block(h, f, *it, nrhs, false, z, ldz));
   const bool thin = nrhs <= kThinMaxRhs;
   if (thin) LLS_TRY(batched_small(h, f, f.VS.d(), false, z, ldz, nrhs));
-  if (persistent_replay(h, f, nrhs, f.WV.d(), ldv, n))
+  if (persistent_replay(f, nrhs, f.WV.d(), ldv, n))
     return replay_steps(h, f, false, n, f.WV.d(), ldv, f.TV.d(), z, ldz, nrhs);
   for (size_t ii = f.ks.size(); ii-- > 0;) {
     const int64_t k = f.ks[ii], b = f.bs[ii];
@@ -669,7 +676,7 @@ Status apply_vt(Handle& h, Factor& f, double* z, int64_t ldz, int64_t nrhs) {
     return copy_matrix(n, nrhs, h.z2.d(), ldv, z, ldz, h.stream);
   }
   const bool thin = nrhs <= kThinMaxRhs;
-  if (persistent_replay(h, f, nrhs, f.WV.d(), ldv, n))
+  if (persistent_replay(f, nrhs, f.WV.d(), ldv, n))
     LLS_TRY(replay_steps(h, f, true, n, f.WV.d(), ldv, f.TV.d(), z, ldz, nrhs));
   else
     for (size_t i = 0; i < f.ks.size(); ++i) {
@@ -796,9 +803,9 @@ Status refine_min_norm(Handle& h, Factor& f, const double* A, int64_t lda, const
     LLS_TRY(h.dinv.reserve(trsm_inverse_bytes(r)));
     LLS_TRY(trsm_block_inverses(r, f.T.d(), ldt, h.dinv.d(), st));
   }
-  // With at most four, each solve is one cooperative launch (a grid barrier
-  // per block) unless worker streams share the device.
-  const bool coop_trsm = nrhs <= 4 && !h.shares_device;
+  // With at most four on a large factor (persistent_solve), each solve is one
+  // cooperative launch with a grid barrier per block.
+  const bool coop_trsm = persistent_solve(f, nrhs);
   if (coop_trsm) LLS_TRY(h.sp2.reserve(64));
   auto trsm_both = [&](double* y, int64_t ldy, bool trans_first) -> Status {
     if (coop_trsm) {

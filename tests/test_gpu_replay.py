@@ -1,8 +1,11 @@
 """Replays of the stored reflectors (c = U^T b and x = V z of Fig. 4, and
 the refinement's operators) with at most four right-hand sides run as one
-cooperative launch per replay (replay_kernel) when the factor's leading
-dimension is even (its reflector chunks are TMA tensor loads); five or more
-right-hand sides, or an odd leading dimension, take the per-step kernels.
+cooperative launch per replay (replay_kernel) on factors whose larger side
+has at least 4096 rows and whose leading dimension is even (the reflector
+chunks are TMA tensor loads); five or more right-hand sides, smaller factors
+or an odd leading dimension take the per-step kernels.  The choice depends on
+the shape alone, so batched and served solves keep giving the same bits as
+solves alone.
 Checked here: x against the FP64 oracle for 1..4 right-hand sides and
 several block sizes (ragged last step included), agreement with the
 per-step path on the same factor, one launch per replay in the trace,
@@ -37,9 +40,9 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("m,n,r,nb", [(2000, 1000, 400, 64), (1500, 1100, 900, 128),
-                                      (700, 1300, 500, 96), (3000, 200, 200, 48),
-                                      (1001, 500, 300, 64)])
+@pytest.mark.parametrize("m,n,r,nb", [(4096, 1000, 400, 64), (4200, 1500, 1100, 128),
+                                      (900, 4100, 500, 96), (6000, 200, 200, 48),
+                                      (4097, 500, 300, 64), (2000, 1000, 400, 64)])
 def test_replay_against_oracle_and_per_step_path(lls, m, n, r, nb):
     A, X, Y = wl.lowrank_xy(m, n, r, seed=m + n + r, noise=1e-14)
     nrm = wl.norm2_of_product(X, Y)
@@ -58,9 +61,11 @@ def test_replay_against_oracle_and_per_step_path(lls, m, n, r, nb):
             x = host(lls.lls_solve_factored(h, fid, dev(B[:, :nrhs]), n))
             tr = lls.lls_trace_read(h)
             lls.lls_trace_enable(h, False)
-            # U^T and V one launch each; a factor with an odd leading dimension
-            # (no TMA map: 16-byte rows) keeps the per-step kernels for that side
-            assert tr.get("replay_kernel", (0,))[0] == (m % 2 == 0) + (n % 2 == 0)
+            # U^T and V one launch each on a factor with 4096 rows or columns; an
+            # odd leading dimension (no TMA map: 16-byte rows) keeps the
+            # per-step kernels for that side, and so does a smaller factor
+            want = (m % 2 == 0) + (n % 2 == 0) if max(m, n) >= 4096 else 0
+            assert tr.get("replay_kernel", (0,))[0] == want
             assert rel(x, ref.x[:, :nrhs]) <= 1e-9
             assert np.max(np.abs(x - x5[:, :nrhs])) <= 1e-12 * np.max(np.abs(x5))
         assert orc.normal_equation_residual(A, x, B[:, :4], nrm) <= 1e-13
@@ -69,19 +74,23 @@ def test_replay_against_oracle_and_per_step_path(lls, m, n, r, nb):
 
 
 def test_replay_repeats_are_bit_identical(lls):
-    p = wl.c2_like(1024, nrhs=3, nb=128)
+    A, X, Y = wl.lowrank_xy(4096, 1024, 700, seed=41, noise=1e-14)
+    B = np.random.default_rng(42).standard_normal((4096, 3))
+    tol = 1e-10 * wl.norm2_of_product(X, Y)
     h = lls.lls_create(nb=128, q=1, seed=2001)
     try:
-        fid, _, _ = lls.lls_factor(h, dev(p.A), p.tol)
-        a = host(lls.lls_solve_factored(h, fid, dev(p.B), 1024))
-        b = host(lls.lls_solve_factored(h, fid, dev(p.B), 1024))
+        fid, _, _ = lls.lls_factor(h, dev(A), tol)
+        lls.lls_trace_enable(h, True)
+        a = host(lls.lls_solve_factored(h, fid, dev(B), 1024))
+        assert lls.lls_trace_read(h)["replay_kernel"][0] == 2
+        b = host(lls.lls_solve_factored(h, fid, dev(B), 1024))
         assert np.array_equal(a, b)
     finally:
         lls.lls_destroy(h)
 
 
 def test_3xtf32_refinement_replays_in_one_launch_each(lls):
-    p = wl.c3_like(1024, 512, 384, nrhs=2, nb=64, q=1)
+    p = wl.c3_like(4096, 1024, 768, nrhs=2, nb=64, q=1)
     ref = orc.solve(p.A, p.B, 1, 64, p.tol, 2001)
     h = lls.lls_create(nb=64, q=1, seed=2001, precision=lls.LLS_MIXED_BF16_3xTF32, max_refine=10,
                        refine_tol=1e-11)
@@ -92,7 +101,7 @@ def test_3xtf32_refinement_replays_in_one_launch_each(lls):
         steps, _ = lls.lls_refinement_info(h)
     finally:
         lls.lls_destroy(h)
-    assert code == lls.LLS_OK and rank == 384
+    assert code == lls.LLS_OK and rank == 768
     assert rel(host(X), ref.x) <= 1e-9
     # the solve's two replays, then two per refinement iteration (V^T, V or
     # U^T, U); an iteration whose correction grew is undone and not counted
