@@ -218,6 +218,34 @@ def test_factor_reuse_export_and_refinement(harness, sketch):
     assert np.all(T[:r, r:] == 0.0) and np.all(np.tril(T, -1) == 0.0)
 
 
+@pytest.mark.parametrize("m,precision", [(4096, 0), (4097, 0), (4096, 2)])
+def test_large_factor_replays_and_solves(harness, sketch, m, precision):
+    """A factor with 4096 rows takes the solve kernels chosen for large factors
+    (one cooperative launch per replay and per triangular solve, with at most
+    four right-hand sides; an odd leading dimension keeps the per-step kernels
+    for U); five right-hand sides take the per-step kernels.  Both match the
+    oracle and each other, in FP64 and in the 3xTF32 mode with refinement."""
+    n, r = 24, 10
+    A, B, tol = gap_problem(m, n, r, seed=m + precision, nrhs=5)
+    ref = orc.solve(A, B, 1, 8, tol, 77)
+    xs = []
+    for nrhs in (2, 5):
+        h = create(harness, nb=8, q=1, seed=77, precision=precision,
+                   max_refine=8 if precision else 0)
+        try:
+            Bn = F(B[:, :nrhs])
+            X = np.zeros((n, nrhs), order="F")
+            rk = I(0)
+            code = harness.lls_solve(h, F(A).ctypes.data, m, n, m, Bn.ctypes.data, nrhs, m, tol,
+                                     X.ctypes.data, n, C.byref(rk))
+        finally:
+            harness.lls_destroy(h)
+        assert code == 0 and rk.value == r
+        assert np.linalg.norm(X - ref.x[:, :nrhs]) <= 1e-9 * np.linalg.norm(ref.x[:, :nrhs])
+        xs.append(X)
+    assert np.max(np.abs(xs[0] - xs[1][:, :2])) <= 1e-12 * np.max(np.abs(xs[1]))
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batched_pool_equals_alone(harness, sketch, mode):
     """Problems solved as a batch are bit-identical to the same problems
