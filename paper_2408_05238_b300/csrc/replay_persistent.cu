@@ -138,6 +138,7 @@ struct Ring {
   uint64_t* full;      // an mbarrier a slot
   const CUtensorMap* map;
   uint32_t bytes;      // RP_CH x nb doubles a chunk
+  int* fail;           // shared: a thread's chunk wait ran out
 };
 
 __device__ __forceinline__ void issue(const Ring& rg, const Chunk& c, unsigned gq) {
@@ -232,11 +233,9 @@ __device__ __forceinline__ bool stream_run(const ReplayArgs& a, const Ring& rg, 
   const int n = s.nD + s.nA;
   for (int q = 0; q < n; ++q, ++gq) {
     const int slot = gq % RP_STAGES;
-    if (!tc::mbar_wait(&rg.full[slot], (gq / RP_STAGES) & 1, a.bar.err)) {
-      const int left = n - q - 1 < RP_STAGES - 1 ? n - q - 1 : RP_STAGES - 1;
-      drain(rg, gq + 1, left);
-      return false;
-    }
+    // a wait that runs out is acted on by the whole CTA after this chunk's
+    // barrier (the threads of a CTA need not see the same outcome)
+    if (!tc::mbar_wait(&rg.full[slot], (gq / RP_STAGES) & 1, a.bar.err)) *rg.fail = 1;
     const double* Wq = rg.W + slot * RP_CH * RP_NB;
     const Chunk c = chunk_at(s, q);
     const int64_t r = c.r0 + lane, rk = r - c.k;
@@ -285,6 +284,11 @@ __device__ __forceinline__ bool stream_run(const ReplayArgs& a, const Ring& rg, 
       }
     }
     __syncthreads();  // the slot and the group sums are free again
+    if (*rg.fail) {  // the same in every thread now: let the issued chunks land, then leave
+      const int left = n - q < RP_STAGES ? n - q : RP_STAGES;
+      drain(rg, gq, left);
+      return false;
+    }
     if (t == 0 && q + RP_STAGES < n) issue(rg, chunk_at(s, q + RP_STAGES), gq + RP_STAGES);
   }
   return true;
@@ -318,7 +322,8 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
   __shared__ double p2s[RP_NB * NR];
   __shared__ double ps[RP_NB * NR];
   __shared__ __align__(8) uint64_t full[RP_STAGES];
-  const Ring rg{sm, full, &wmap, (uint32_t)(sizeof(double) * RP_CH * a.nb)};
+  __shared__ int s_fail;
+  const Ring rg{sm, full, &wmap, (uint32_t)(sizeof(double) * RP_CH * a.nb), &s_fail};
   double* Ts = sm + RP_STAGES * RP_CH * RP_NB;
   double* red = Ts + RP_TRI;
   unsigned int epoch = 0;
@@ -330,6 +335,7 @@ __global__ void __launch_bounds__(RP_THREADS, 1)
   if (t == 0) {
     for (int q = 0; q < RP_STAGES; ++q) tc::mbar_init(&full[q], 1);
     tc::mbar_init_fence();
+    s_fail = 0;
   }
   __syncthreads();
 
